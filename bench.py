@@ -1,0 +1,367 @@
+#!/usr/bin/env python3
+"""Benchmark of the ZipPIR online server Response on GB300.
+
+One step = one online Response for the workload's batch: the LWE answer
+ans = D.q mod 2^32 over the whole database and the Paillier-side compression
+t = (b' + H'.cko) mod m, both through the C ABI. Default workload: a 1 GiB
+database (32768 x 32768 bytes uniform mod 256), one query, n = 1024, a 2048-bit
+modulus. value = database bytes scanned per second (GB/s, 1 GB = 1e9 B) with
+inputs resident in HBM; e2e = the same metric through zp_respond_host with host
+buffers (query and offsets copied in, compressed answer copied out, each step).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload 1gib|tiny|batch64]
+
+--impl reference times the oracle (the plain CPU implementation) on a bounded
+sample of the same workload on the host cores.
+Under torchrun (N > 1) every rank runs its own replica of the workload on its own
+GPU (the Response does not need any exchange between GPUs), value = all ranks'
+bytes / the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "online GB/s of DB scanned (1 query and batched) vs HBM/int8 roofline; p99 ms"
+
+WORKLOADS = {
+    # name: (R, C, n, B, description)
+    "1gib": (32768, 32768, 1024, 1,
+             "1 GiB database 32768x32768 u8 uniform mod 256, 1 query, n=1024, 2048-bit Paillier "
+             "modulus: GEMV answer + compression"),
+    "tiny": (1024, 1024, 1024, 1,
+             "1 MiB database 1024x1024, 1 query, n=1024, 2048-bit modulus"),
+    "batch64": (32768, 32768, 1024, 64,
+                "1 GiB database 32768x32768, 64 queries of 64 clients, n=1024, 2048-bit moduli"),
+}
+KEY_BITS = 2048
+L = KEY_BITS // 32
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs"), "measured"
+    return 6800.0, "fallback"
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons in the background."""
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self.proc = None
+        self.mark = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append((time.time(), line.strip()))
+
+    def window(self, t0, t1):
+        self.mark = (t0, t1)
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        t0, t1 = self.mark if self.mark else (0, 1e18)
+        rows = [s for (t, s) in self.samples if t0 - 0.15 <= t <= t1 + 0.15] or \
+            [s for (_, s) in self.samples]
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            parts = [x.strip() for x in r.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- distributed
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    return world, rank, local
+
+
+def dist_max(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def dist_barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ----------------------------------------------------------------------------- CPU oracle baseline
+def cpu_baseline(R, C, n, B, target_s=12.0):
+    """Times the oracle's online Response (matvec mod 2^32 + compression with Python
+    ints) on a bounded sample of rows of the same workload; returns GB/s of database
+    bytes scanned, threads used and a description of the sample."""
+    import synth
+    from oracle import lwe, zippir
+    from oracle.params import Params
+
+    P = Params(n=n, key_bits=KEY_BITS)
+    ell = P.ell
+    rows = min(R, ell * 8)          # whole packed rows
+    D = synth.database(rows, C, 101)
+    q = synth.uniform_queries(1, C, 102)[0]
+    # hint rows: uniform u32, statistically equal to -D.A for a uniform A (the hint
+    # itself is offline work and not part of the timed online Response)
+    Hn = synth.rng(103).integers(0, 2**32, size=(rows, n), dtype=np.uint64).astype(np.uint32)
+    m = synth.random_odd_modulus(KEY_BITS, 104)
+    cko = synth.uniform_below(m, n, 105)
+    done_bytes, t_used, reps = 0, 0.0, 0
+    t0 = time.perf_counter()
+    while True:
+        ans = lwe.matvec_mod_q(D, q)
+        zippir.compress_rows(ans, Hn, cko, m, P)
+        reps += 1
+        done_bytes += rows * C
+        t_used = time.perf_counter() - t0
+        if t_used >= target_s or reps >= 50:
+            break
+    per_q = t_used / reps
+    gbs = done_bytes / t_used / 1e9
+    return {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": "%d of %d rows (%d packed rows) x %d columns, 1 query, %d repetition(s), "
+                      "%.2f s per repetition; numpy uint64 matvec + Python-int compression, "
+                      "single thread" % (rows, R, rows // ell, C, reps, per_q),
+            "seconds": t_used}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    R, C, n, B, desc = WORKLOADS[args.workload]
+    vals = []
+    cb = None
+    for i in range(args.warmup + args.steps):
+        r = cpu_baseline(R, C, n, B, target_s=3.0)
+        if i >= args.warmup:
+            vals.append(r["value"])
+            cb = r
+    v = statistics.mean(vals)
+    ms = R * C * B / (v * 1e9) * 1e3
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "GB/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic",
+            "config": {"workload": desc, "R": R, "C": C, "n": n, "B": B, "key_bits": KEY_BITS},
+            "cpu_baseline": {"kind": "oracle", "cores": cb["cores"], "sample": cb["sample"],
+                             "value": v, "unit": "GB/s"},
+            "e2e": {"value": v, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def run_ours(args, world, rank, local):
+    import torch
+    import paper_2603_09190_gb300 as zp
+    from paper_2603_09190_gb300 import build as zb
+    import synth
+
+    if rank == 0:
+        zb.build()
+    dist_barrier(world)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    R, C, n, B, desc = WORKLOADS[args.workload]
+    ld = zp.db_pitch(C)
+
+    ctx = zp.Context(local, n=n, key_bits=KEY_BITS)
+    D = synth.device_database(R, C, 1 + rank, dev, ld=ld)
+    A = synth.device_uniform_u32((C, n), 2 + rank, dev)
+    db = zp.Database(ctx, D, R, C, ld)
+    db.gen_hint(A)
+    del A
+    moduli = [synth.random_odd_modulus(KEY_BITS, 1000 + b) for b in range(B)]
+    clients = [ctx.register_client(m) for m in moduli]
+    Q = synth.device_uniform_u32((B, C), 3 + rank, dev)
+    # cko uniform below each client's m (limbs drawn on the host once)
+    cko_h = np.stack([synth.ints_to_limbs(synth.uniform_below(moduli[b], n, 2000 + b), L)
+                      for b in range(B)])
+    CKO = torch.from_numpy(cko_h.view(np.int32)).to(dev)
+    ans = torch.empty((B, R), dtype=torch.int32, device=dev)
+    T = torch.empty((B, db.d1p, L), dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    sp = stream.cuda_stream
+    handles = [c.handle for c in clients]
+
+    def step(ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        zp.zp_answer(db.handle, Q.data_ptr(), B, ans.data_ptr(), sp)
+        if ev is not None:
+            ev[1].record(stream)
+        zp.zp_compress(db.handle, handles, ans.data_ptr(), CKO.data_ptr(), B, T.data_ptr(), sp)
+        if ev is not None:
+            ev[2].record(stream)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    if ctx.device_status() != 0:
+        raise RuntimeError("device status nonzero after warm-up")
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches0 = ctx.kernel_launches()
+    dist_barrier(world)
+    torch.cuda.synchronize()
+    tw0 = time.time()
+    start.record(stream)
+    for k in range(args.steps):
+        step(evs[k])
+    end.record(stream)
+    torch.cuda.synchronize()
+    tw1 = time.time()
+    dist_barrier(world)
+    launches = ctx.kernel_launches() - launches0
+    sampler.window(tw0, tw1)
+    ms_total = start.elapsed_time(end)
+    ms_total = dist_max(ms_total, world)
+    ms_step = ms_total / args.steps
+    ans_ms = [e[0].elapsed_time(e[1]) for e in evs]
+    cmp_ms = [e[1].elapsed_time(e[2]) for e in evs]
+    step_ms = [e[0].elapsed_time(e[2]) for e in evs]
+    db_bytes = R * C * B
+    value = db_bytes * world / (ms_step * 1e-3) / 1e9
+
+    # ---- e2e through the host-buffer entry point
+    hQ = torch.empty((B, C), dtype=torch.int32, pin_memory=True)
+    hQ.copy_(Q.cpu())
+    hC = torch.from_numpy(cko_h.view(np.int32)).pin_memory()
+    hT = torch.empty((B, db.d1p, L), dtype=torch.int32, pin_memory=True)
+    hQn, hCn, hTn = hQ.numpy().view(np.uint32), hC.numpy().view(np.uint32), hT.numpy().view(np.uint32)
+    for _ in range(3):
+        zp.zp_respond_host(db.handle, handles, hQn, hCn, B, hTn, None, sp)
+    e2e_steps = max(3, min(args.steps, 200))
+    dist_barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        zp.zp_respond_host(db.handle, handles, hQn, hCn, B, hTn, None, sp)
+    torch.cuda.synchronize()
+    e2e_s = dist_max((time.perf_counter() - t0) / e2e_steps, world)
+    dist_barrier(world)
+    sampler.stop()
+    clocks = sampler.summary()
+    status = ctx.device_status()
+    if status != 0:
+        raise RuntimeError("device status 0x%x after timing" % status)
+
+    if rank != 0:
+        return 0
+    hbm_peak, peak_kind = load_peaks()
+    ans_avg = statistics.mean(ans_ms)
+    # algorithmic bytes of one zp_answer (B = 1: query-plane prep + GEMV): D, q, ans
+    alg_bytes = R * C + 4 * C * B + 4 * R * B
+    achieved = alg_bytes / (ans_avg * 1e-3) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+            "frac": achieved / hbm_peak, "traffic": None,
+            "kernel": "zp_answer (k_qplanes + k_gemv)" if B == 1 else "zp_answer (batched)",
+            "peak_kind": peak_kind}
+    cb = cpu_baseline(R, C, n, B) if world == 1 and not args.no_cpu else None
+    line = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic",
+            "config": {"workload": desc, "R": R, "C": C, "n": n, "B": B, "key_bits": KEY_BITS,
+                       "l2": "inputs larger than L2 (database %d MiB > 129 MB L2); no flush"
+                             % (R * C >> 20),
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "stages_ms": {"answer_avg": ans_avg, "compress_avg": statistics.mean(cmp_ms),
+                          "step_p50": float(np.percentile(step_ms, 50)),
+                          "step_p99": float(np.percentile(step_ms, 99))},
+            "gib_s": value * 1e9 / 2**30,
+            "roofline": roof,
+            "e2e": {"value": db_bytes * world / e2e_s / 1e9, "unit": "GB/s",
+                    "h2d_bytes_per_step": 4 * B * C + 4 * B * n * L,
+                    "d2h_bytes_per_step": 4 * B * db.d1p * L, "ms_per_step": e2e_s * 1e3},
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "cpu_baseline": cb}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="1gib", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+    return run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,176 @@
+/*
+ * zippir.h -- C ABI of the GB300 (sm_103a) library for the online server phase of
+ * ZipPIR (arXiv 2603.09190): the LWE answer ans = D.q mod 2^32 and the per-query
+ * LWE-to-Paillier answer compression t = (b' + H'.cko) mod m.
+ *
+ * Orientation. The database D is R x C, row-major, entries in Z_p (p = 256, one
+ * byte each). The paper writes Response as b = db^T qu_0 with db of shape
+ * d0 x d1; here D = db^T, so R = d1 (answer length) and C = d0 (query length).
+ * A record is column i0 of D.
+ *
+ * Conventions for every entry point:
+ *  - Return value: ZP_OK (0) or a negative ZP_E* code; zp_last_error() gives a
+ *    message for the calling thread. No C++ exception crosses this boundary.
+ *  - Pointers named d* are DEVICE pointers on the context's device, h* are HOST
+ *    pointers. The caller owns every buffer it passes; the library never frees
+ *    them and keeps only the database pointer (non-owning) between calls, so the
+ *    database must stay alive and unchanged (except through zp_update_rows) until
+ *    zp_db_destroy. The library owns its internal state (the negated hint in its
+ *    compression layout, row sums, per-client constants, scratch) and frees it in
+ *    the matching *_destroy.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream). Stream-taking calls
+ *    are asynchronous: they validate arguments on the host, return an error before
+ *    launching anything if validation fails, and otherwise enqueue work on
+ *    `stream`. Device buffers must not be reused by the caller before that work
+ *    completes. The *_host entry points synchronise `stream` before returning.
+ *  - All arithmetic is exact integer arithmetic; results are bit-identical to the
+ *    definitions cited at each call.
+ */
+#ifndef ZIPPIR_H
+#define ZIPPIR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum zp_status {
+  ZP_OK = 0,
+  ZP_EINVAL = -1,      /* bad argument: null pointer, size, alignment, value range */
+  ZP_ENOMEM = -2,      /* device or host allocation failed */
+  ZP_ECUDA = -3,       /* a CUDA runtime/driver call failed */
+  ZP_ETIMEOUT = -4,    /* a bounded device-side wait gave up (kernel returned early) */
+  ZP_ESTATE = -5,      /* call out of order, e.g. zp_compress before zp_gen_hint */
+  ZP_EUNSUPPORTED = -6 /* parameters this build does not implement */
+};
+
+enum zp_secret {
+  ZP_SECRET_UNIFORM = 0, /* LWE secret uniform in Z_q: packing scale gamma = q + n q^2 (Sec. 3.3) */
+  ZP_SECRET_BINARY = 1   /* LWE secret in {0,1}:     packing scale gamma = q + n q   (Sec. 3.3.3) */
+};
+
+typedef struct zp_params {
+  uint32_t n;        /* LWE dimension (1 <= n <= 4096) */
+  uint32_t key_bits; /* bits of every client's Paillier modulus m; 2048 in this build */
+  uint32_t secret;   /* enum zp_secret */
+  uint32_t p_bits;   /* log2 of the plaintext modulus p; must be 8 (one byte per entry) */
+} zp_params;
+
+typedef struct zp_ctx zp_ctx;       /* one device, one parameter set */
+typedef struct zp_db zp_db;         /* one resident database and its hint */
+typedef struct zp_client zp_client; /* one client's public Paillier modulus and constants */
+
+/* Library ABI version (major*10000 + minor*100 + patch). */
+int zp_version(void);
+
+/* Copies the calling thread's last error message (NUL-terminated, truncated to len).
+ * Returns the message length. */
+int zp_last_error(char* buf, size_t len);
+
+/* Creates a context on CUDA device `device` for parameters *P.
+ * Derived slot count (batched compression theorem, Sec. 3.3): ell is the largest
+ * integer with gamma^ell < 2^(key_bits-1), so m > gamma^ell for every key of
+ * key_bits bits and the packed hint is the same for all clients.
+ * Errors: ZP_EINVAL (P null, n out of range, p_bits != 8), ZP_EUNSUPPORTED
+ * (key_bits != 2048), ZP_ECUDA (device unusable). */
+int zp_init(int device, const zp_params* P, zp_ctx** out);
+int zp_ctx_destroy(zp_ctx* ctx);
+
+/* Registers the database D (Algorithm "ZipPIR", db in Z_p^{d0 x d1}; here R x C).
+ * dD: device pointer to R rows of ld_bytes bytes; row r holds D[r, 0..C-1], bytes
+ * C..ld_bytes-1 are ignored. dD must be 16-byte aligned and ld_bytes a multiple of
+ * 16 with ld_bytes >= C. 1 <= R <= 2^20, 1 <= C <= 2^20.
+ * The library computes per-row sums of D (R x 4 bytes, library-owned) and keeps dD.
+ * Errors: ZP_EINVAL, ZP_ENOMEM, ZP_ECUDA. Synchronous. */
+int zp_setup_db(zp_ctx* ctx, const uint8_t* dD, uint32_t R, uint32_t C, uint64_t ld_bytes,
+                zp_db** out);
+
+/* Reports the packing of this database: slots per Paillier plaintext (ell), packed
+ * rows d1' = ceil(R / ell), and 32-bit limbs per element of Z_m (L = key_bits/32). */
+int zp_db_info(const zp_db* db, uint32_t* ell, uint32_t* d1p, uint32_t* L);
+int zp_db_destroy(zp_db* db);
+
+/* Global hint (Algorithm "ZipPIR" caption; reused by all clients, Sec. 4.3
+ * "Reusability of the offline phase"): H+ = D.A mod 2^32, written to dH.
+ * dA: C x n u32, row-major (the public LWE matrix). dH: R x n u32, row-major,
+ * output; may be NULL if the caller does not want H+.
+ * The library also stores the paper's H = -H+ mod 2^32 in its compression layout;
+ * zp_compress needs it. hRows: NULL to compute every row, else a HOST array of
+ * nrows distinct row indices < R whose hint rows are recomputed (the idle-time
+ * regeneration after zp_update_rows, Sec. 6 "Database updates"); other rows of dH
+ * are left untouched. hRows is read before the call returns. The same dA must be
+ * passed on every call for one database. Asynchronous on `stream`.
+ * Errors: ZP_EINVAL (null dA, bad row index), ZP_ENOMEM, ZP_ECUDA. */
+int zp_gen_hint(zp_db* db, const uint32_t* dA, uint32_t* dH, const uint32_t* hRows,
+                uint32_t nrows, void* stream);
+
+/* LWE answer (Algorithm "ZipPIR", Response, first line): for each of B queries,
+ * ans[b][r] = sum_c D[r][c] * Q[b][c] mod 2^32.
+ * dQ: B x C u32 row-major (query b at dQ + b*C). dAns: B x R u32 row-major output.
+ * 1 <= B <= 4096. Asynchronous on `stream`. Errors: ZP_EINVAL, ZP_ENOMEM, ZP_ECUDA. */
+int zp_answer(zp_db* db, const uint32_t* dQ, uint32_t B, uint32_t* dAns, void* stream);
+
+/* Registers a client's public Paillier modulus m (Algorithm "ZipPIR", Setup: the
+ * client sends m). hM: HOST array of L = key_bits/32 little-endian u32 limbs; m
+ * must be odd with exactly key_bits bits. The library derives the Barrett constant
+ * floor(2^(64 L) / m) and copies both to the device. Synchronous.
+ * Errors: ZP_EINVAL (null, wrong L, m even or of the wrong size), ZP_ENOMEM, ZP_ECUDA. */
+int zp_register_client(zp_ctx* ctx, const uint32_t* hM, uint32_t L, zp_client** out);
+int zp_client_destroy(zp_client* cl);
+
+/* Answer compression (Algorithm "ZipPIR", Response, second line, with batched
+ * compression, Sec. 4.3): for each query b of client clients[b] with modulus m_b,
+ *   t[b][r'] = ( sum_{j<ell} gamma^j * ( ans[b][r' ell + j]
+ *                                       + sum_{i<n} H[r' ell + j][i] * cko[b][i] ) ) mod m_b
+ * for r' < d1', where H = -D.A mod 2^32 (from zp_gen_hint) and answer rows
+ * >= R count as zero. This equals (b' + H'.cko) mod m with the packed answer b'
+ * and packed hint H'.
+ * dAns: B x R u32 (from zp_answer). dCKO: B x n x L u32 limbs, little-endian, each
+ * value < m_b (precondition; a value >= m_b gives the same result as its residue
+ * only if it is < 2^(32 L)). dT: B x d1' x L u32 output, little-endian limbs.
+ * Asynchronous on `stream`. Errors: ZP_EINVAL, ZP_ESTATE (no hint yet, or rows
+ * updated since the last zp_gen_hint), ZP_ENOMEM, ZP_ECUDA. */
+int zp_compress(zp_db* db, zp_client* const* clients, const uint32_t* dAns,
+                const uint32_t* dCKO, uint32_t B, uint32_t* dT, void* stream);
+
+/* The whole online Response for B queries on DEVICE buffers: zp_answer into dAns,
+ * then zp_compress into dT. Asynchronous on `stream`. */
+int zp_respond(zp_db* db, zp_client* const* clients, const uint32_t* dQ, const uint32_t* dCKO,
+               uint32_t B, uint32_t* dAns, uint32_t* dT, void* stream);
+
+/* The whole online Response on HOST buffers: copies hQ (B x C u32) and hCKO
+ * (B x n x L u32) to library-owned device buffers, runs zp_respond, copies the
+ * compressed answers to hT (B x d1' x L u32) and, if hAns is not NULL, the plain
+ * answers to hAns (B x R u32), then synchronises `stream`. Host buffers may be
+ * pageable or pinned (pinned is faster). Errors as zp_respond. */
+int zp_respond_host(zp_db* db, zp_client* const* clients, const uint32_t* hQ,
+                    const uint32_t* hCKO, uint32_t B, uint32_t* hT, uint32_t* hAns,
+                    void* stream);
+
+/* Database update (Sec. 6, "Database updates"): overwrites rows hRows[0..k-1]
+ * (HOST array of distinct indices < R, read before the call returns) of the
+ * caller's database buffer with dNewRows (k x C bytes, row-major, pitch C),
+ * updates the row sums and marks those hint rows stale. zp_compress returns
+ * ZP_ESTATE until zp_gen_hint has recomputed every stale row (for example with
+ * the same row list). Asynchronous on `stream`.
+ * Errors: ZP_EINVAL, ZP_ENOMEM, ZP_ECUDA. */
+int zp_update_rows(zp_db* db, const uint32_t* hRows, uint32_t k, const uint8_t* dNewRows,
+                   void* stream);
+
+/* Number of hint rows marked stale by zp_update_rows and not yet regenerated. */
+int zp_stale_rows(const zp_db* db, uint32_t* count);
+
+/* Number of kernels this context has launched so far (all entry points). */
+int zp_kernel_launches(const zp_ctx* ctx, uint64_t* count);
+
+/* Device-side error word of the context: nonzero after a kernel gave up a bounded
+ * wait (its code says which). Reading it synchronises the device. The word is
+ * cleared by the read. */
+int zp_device_status(zp_ctx* ctx, uint32_t* code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ZIPPIR_H */

@@ -1,0 +1,371 @@
+"""Python binding of libzippir (the GB300 library for the ZipPIR online server phase).
+
+Argument marshalling only: every step of the computation runs in the CUDA kernels
+behind the C ABI in ``include/zippir.h``. The binding loads the in-tree
+``_lib/libzippir.so`` and raises ``ImportError`` if it has not been built -- there is
+no CPU fallback. PyTorch provides device memory and streams; tensors are passed by
+their data pointers after dtype/device/shape checks.
+
+Low-level functions carry the C names (``zp_init``, ``zp_setup_db``, ``zp_gen_hint``,
+``zp_answer``, ``zp_register_client``, ``zp_compress``, ``zp_respond``,
+``zp_respond_host``, ``zp_update_rows`` ...); ``Context``, ``Database`` and
+``Client`` wrap them with ownership.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libzippir.so")
+
+ZP_OK, ZP_EINVAL, ZP_ENOMEM, ZP_ECUDA, ZP_ETIMEOUT, ZP_ESTATE, ZP_EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
+SECRETS = {"uniform": 0, "binary": 1}
+
+# every symbol declared in include/zippir.h
+EXPORTS = [
+    "zp_version", "zp_last_error", "zp_init", "zp_ctx_destroy", "zp_setup_db", "zp_db_info",
+    "zp_db_destroy", "zp_gen_hint", "zp_answer", "zp_register_client", "zp_client_destroy",
+    "zp_compress", "zp_respond", "zp_respond_host", "zp_update_rows", "zp_stale_rows",
+    "zp_device_status", "zp_kernel_launches",
+]
+
+
+class ZipPIRError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("zippir error %d: %s" % (code, msg))
+        self.code = code
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_uint32), ("key_bits", ctypes.c_uint32),
+                ("secret", ctypes.c_uint32), ("p_bits", ctypes.c_uint32)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Loads libzippir.so (raises ImportError when it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError("libzippir.so is not built (%s); run __graft_entry__.build()" % path)
+    L = ctypes.CDLL(path)
+    vp, u32, u64, i32 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
+    pp = ctypes.POINTER(ctypes.c_void_p)
+    sig = {
+        "zp_version": (i32, []),
+        "zp_last_error": (i32, [ctypes.c_char_p, ctypes.c_size_t]),
+        "zp_init": (i32, [i32, ctypes.POINTER(_Params), pp]),
+        "zp_ctx_destroy": (i32, [vp]),
+        "zp_setup_db": (i32, [vp, vp, u32, u32, u64, pp]),
+        "zp_db_info": (i32, [vp, ctypes.POINTER(u32), ctypes.POINTER(u32), ctypes.POINTER(u32)]),
+        "zp_db_destroy": (i32, [vp]),
+        "zp_gen_hint": (i32, [vp, vp, vp, vp, u32, vp]),
+        "zp_answer": (i32, [vp, vp, u32, vp, vp]),
+        "zp_register_client": (i32, [vp, vp, u32, pp]),
+        "zp_client_destroy": (i32, [vp]),
+        "zp_compress": (i32, [vp, vp, vp, vp, u32, vp, vp]),
+        "zp_respond": (i32, [vp, vp, vp, vp, u32, vp, vp, vp]),
+        "zp_respond_host": (i32, [vp, vp, vp, vp, u32, vp, vp, vp]),
+        "zp_update_rows": (i32, [vp, vp, u32, vp, vp]),
+        "zp_stale_rows": (i32, [vp, ctypes.POINTER(u32)]),
+        "zp_device_status": (i32, [vp, ctypes.POINTER(u32)]),
+        "zp_kernel_launches": (i32, [vp, ctypes.POINTER(u64)]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def last_error() -> str:
+    buf = ctypes.create_string_buffer(1024)
+    load_library().zp_last_error(buf, 1024)
+    return buf.value.decode(errors="replace")
+
+
+def _check(rc: int):
+    if rc != ZP_OK:
+        raise ZipPIRError(rc, last_error())
+
+
+def _ptr(t) -> int | None:
+    """Device pointer of a torch tensor / int / None."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _need(t, dtype_name: str, numel: int | None = None, what: str = "tensor"):
+    import torch
+    dt = {"u8": torch.uint8, "i32": torch.int32}[dtype_name]
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("%s must be a torch tensor" % what)
+    if t.dtype != dt:
+        raise TypeError("%s must have dtype %s (u32 data is passed as int32)" % (what, dt))
+    if not t.is_cuda:
+        raise TypeError("%s must be on a CUDA device" % what)
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % what)
+    if numel is not None and t.numel() < numel:
+        raise ValueError("%s has %d elements, needs %d" % (what, t.numel(), numel))
+
+
+# ----------------------------------------------------------------------------- thin C-named calls
+def zp_version() -> int:
+    return load_library().zp_version()
+
+
+def zp_init(device: int, n: int, key_bits: int = 2048, secret: str = "uniform", p_bits: int = 8) -> int:
+    P = _Params(n, key_bits, SECRETS[secret], p_bits)
+    out = ctypes.c_void_p()
+    _check(load_library().zp_init(device, ctypes.byref(P), ctypes.byref(out)))
+    return out.value
+
+
+def zp_ctx_destroy(ctx: int):
+    _check(load_library().zp_ctx_destroy(ctx))
+
+
+def zp_setup_db(ctx: int, dD: int, R: int, C: int, ld: int) -> int:
+    out = ctypes.c_void_p()
+    _check(load_library().zp_setup_db(ctx, dD, R, C, ld, ctypes.byref(out)))
+    return out.value
+
+
+def zp_db_info(db: int) -> tuple[int, int, int]:
+    a, b, c = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32()
+    _check(load_library().zp_db_info(db, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return a.value, b.value, c.value
+
+
+def zp_db_destroy(db: int):
+    _check(load_library().zp_db_destroy(db))
+
+
+def zp_gen_hint(db: int, dA: int, dH: int | None, hRows: np.ndarray | None, stream: int | None):
+    if hRows is None:
+        _check(load_library().zp_gen_hint(db, dA, dH, None, 0, stream))
+    else:
+        r = np.ascontiguousarray(hRows, dtype=np.uint32)
+        _check(load_library().zp_gen_hint(db, dA, dH, r.ctypes.data, len(r), stream))
+
+
+def zp_answer(db: int, dQ: int, B: int, dAns: int, stream: int | None):
+    _check(load_library().zp_answer(db, dQ, B, dAns, stream))
+
+
+def zp_register_client(ctx: int, m: int, L: int) -> int:
+    limbs = np.frombuffer(int(m).to_bytes(4 * L, "little"), dtype="<u4").copy()
+    out = ctypes.c_void_p()
+    _check(load_library().zp_register_client(ctx, limbs.ctypes.data, L, ctypes.byref(out)))
+    return out.value
+
+
+def zp_client_destroy(cl: int):
+    _check(load_library().zp_client_destroy(cl))
+
+
+def _client_array(clients) -> ctypes.Array:
+    arr = (ctypes.c_void_p * len(clients))()
+    for i, c in enumerate(clients):
+        arr[i] = c.handle if isinstance(c, Client) else c
+    return arr
+
+
+def zp_compress(db: int, clients, dAns: int, dCKO: int, B: int, dT: int, stream: int | None):
+    _check(load_library().zp_compress(db, ctypes.cast(_client_array(clients), ctypes.c_void_p),
+                                      dAns, dCKO, B, dT, stream))
+
+
+def zp_respond(db: int, clients, dQ: int, dCKO: int, B: int, dAns: int, dT: int, stream: int | None):
+    _check(load_library().zp_respond(db, ctypes.cast(_client_array(clients), ctypes.c_void_p),
+                                     dQ, dCKO, B, dAns, dT, stream))
+
+
+def zp_respond_host(db: int, clients, hQ: np.ndarray, hCKO: np.ndarray, B: int, hT: np.ndarray,
+                    hAns: np.ndarray | None, stream: int | None):
+    for a in (hQ, hCKO, hT) + ((hAns,) if hAns is not None else ()):
+        if not a.flags["C_CONTIGUOUS"] or a.dtype.itemsize != 4:
+            raise ValueError("host buffers must be C-contiguous 32-bit arrays")
+    _check(load_library().zp_respond_host(
+        db, ctypes.cast(_client_array(clients), ctypes.c_void_p), hQ.ctypes.data, hCKO.ctypes.data,
+        B, hT.ctypes.data, None if hAns is None else hAns.ctypes.data, stream))
+
+
+def zp_update_rows(db: int, hRows: np.ndarray, dNew: int, stream: int | None):
+    r = np.ascontiguousarray(hRows, dtype=np.uint32)
+    _check(load_library().zp_update_rows(db, r.ctypes.data, len(r), dNew, stream))
+
+
+def zp_stale_rows(db: int) -> int:
+    c = ctypes.c_uint32()
+    _check(load_library().zp_stale_rows(db, ctypes.byref(c)))
+    return c.value
+
+
+def zp_device_status(ctx: int) -> int:
+    c = ctypes.c_uint32()
+    _check(load_library().zp_device_status(ctx, ctypes.byref(c)))
+    return c.value
+
+
+def zp_kernel_launches(ctx: int) -> int:
+    c = ctypes.c_uint64()
+    _check(load_library().zp_kernel_launches(ctx, ctypes.byref(c)))
+    return c.value
+
+
+# ----------------------------------------------------------------------------- owning wrappers
+class Context:
+    """One device and one parameter set (n, key size, secret distribution)."""
+
+    def __init__(self, device: int = 0, n: int = 1024, key_bits: int = 2048, secret: str = "uniform"):
+        self.device, self.n, self.key_bits, self.secret = device, n, key_bits, secret
+        self.handle = zp_init(device, n, key_bits, secret)
+        self.L = key_bits // 32
+
+    def register_client(self, m: int) -> "Client":
+        return Client(self, m)
+
+    def device_status(self) -> int:
+        return zp_device_status(self.handle)
+
+    def kernel_launches(self) -> int:
+        return zp_kernel_launches(self.handle)
+
+    def close(self):
+        if self.handle:
+            zp_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Client:
+    """A client's public Paillier modulus m, registered on the device."""
+
+    def __init__(self, ctx: Context, m: int):
+        self.ctx, self.m = ctx, int(m)
+        self.handle = zp_register_client(ctx.handle, self.m, ctx.L)
+
+    def close(self):
+        if self.handle:
+            zp_client_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def db_pitch(C: int) -> int:
+    """Row pitch (bytes) the library accepts for C columns: C rounded up to 16."""
+    return (C + 15) // 16 * 16
+
+
+class Database:
+    """A resident database (R x C bytes, row pitch ``ld``) and its hint.
+
+    ``D`` is a CUDA uint8 tensor of shape (R, ld) (or (R*ld,)); it must outlive the
+    Database and must be changed only through ``update_rows``.
+    """
+
+    def __init__(self, ctx: Context, D, R: int, C: int, ld: int | None = None):
+        ld = db_pitch(C) if ld is None else ld
+        _need(D, "u8", R * ld, "D")
+        self.ctx, self.D, self.R, self.C, self.ld = ctx, D, R, C, ld
+        self.handle = zp_setup_db(ctx.handle, _ptr(D), R, C, ld)
+        self.ell, self.d1p, self.L = zp_db_info(self.handle)
+
+    def gen_hint(self, A, H=None, rows=None, stream=None):
+        import torch
+        _need(A, "i32", self.C * self.ctx.n, "A")
+        if H is not None:
+            _need(H, "i32", self.R * self.ctx.n, "H")
+        zp_gen_hint(self.handle, _ptr(A), _ptr(H), None if rows is None else np.asarray(rows),
+                    _stream(stream))
+        return H
+
+    def answer(self, Q, out=None, stream=None):
+        import torch
+        B = Q.shape[0] if Q.dim() == 2 else 1
+        _need(Q, "i32", B * self.C, "Q")
+        if out is None:
+            out = torch.empty((B, self.R), dtype=torch.int32, device=Q.device)
+        _need(out, "i32", B * self.R, "ans")
+        zp_answer(self.handle, _ptr(Q), B, _ptr(out), _stream(stream))
+        return out
+
+    def compress(self, clients, ans, CKO, out=None, stream=None):
+        import torch
+        B = len(clients)
+        _need(ans, "i32", B * self.R, "ans")
+        _need(CKO, "i32", B * self.ctx.n * self.L, "cko")
+        if out is None:
+            out = torch.empty((B, self.d1p, self.L), dtype=torch.int32, device=ans.device)
+        _need(out, "i32", B * self.d1p * self.L, "T")
+        zp_compress(self.handle, clients, _ptr(ans), _ptr(CKO), B, _ptr(out), _stream(stream))
+        return out
+
+    def respond(self, clients, Q, CKO, ans=None, out=None, stream=None):
+        import torch
+        B = len(clients)
+        _need(Q, "i32", B * self.C, "Q")
+        _need(CKO, "i32", B * self.ctx.n * self.L, "cko")
+        if ans is None:
+            ans = torch.empty((B, self.R), dtype=torch.int32, device=Q.device)
+        if out is None:
+            out = torch.empty((B, self.d1p, self.L), dtype=torch.int32, device=Q.device)
+        zp_respond(self.handle, clients, _ptr(Q), _ptr(CKO), B, _ptr(ans), _ptr(out), _stream(stream))
+        return ans, out
+
+    def respond_host(self, clients, hQ: np.ndarray, hCKO: np.ndarray, hT: np.ndarray | None = None,
+                     hAns: np.ndarray | None = None, stream=None):
+        B = len(clients)
+        if hT is None:
+            hT = np.empty((B, self.d1p, self.L), dtype=np.uint32)
+        zp_respond_host(self.handle, clients, hQ, hCKO, B, hT, hAns, _stream(stream))
+        return hT
+
+    def update_rows(self, rows, new_rows, stream=None):
+        _need(new_rows, "u8", len(rows) * self.C, "new_rows")
+        zp_update_rows(self.handle, np.asarray(rows), _ptr(new_rows), _stream(stream))
+
+    def stale_rows(self) -> int:
+        return zp_stale_rows(self.handle)
+
+    def close(self):
+        if self.handle:
+            zp_db_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

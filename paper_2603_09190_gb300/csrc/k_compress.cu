@@ -1,0 +1,340 @@
+// k_compress.cu -- answer compression (Algorithm "ZipPIR", Response, second line, with
+// the batched packing of Sec. 3.3 / Sec. 4.3):
+//   t[b][r'] = ( sum_{j<ell} gamma^j ( ans[b][r' ell + j] + V[b][r' ell + j] ) ) mod m_b,
+//   V[b][row] = sum_{i<n} H[row][i] * cko[b][i]           (exact, < 2^(32 L + 42)),
+// with H = -D.A mod 2^32. Since H'[r', i] = sum_j gamma^j H[r' ell + j][i], this equals
+// (b'[r'] + sum_i H'[r', i] cko[i]) mod m without ever forming the ~2000-bit packed
+// hint: the wide products are taken per answer row and packed afterwards.
+//
+// Two kernels:
+//  * k_vmul_simt: V on CUDA cores, one thread per (row, limb of cko), 96-bit
+//    column accumulators, then one carry-propagation pass per row;
+//  * k_pack_reduce: one warp per (query, packed row): Horner evaluation
+//    X = (..((W_{ell-1}) gamma + W_{ell-2}) gamma + ..) gamma + W_0 with
+//    W_j = ans + V of row r' ell + j (X < 2^4064), then Barrett reduction mod m
+//    (Barrett, CRYPTO '86; the quotient-estimate form of the Handbook of Applied
+//    Cryptography, Alg. 14.42) with the per-client constant mu = floor(2^(64 L) / m).
+//    Big integers live in shared memory; products are summed per output column in
+//    96-bit accumulators and carries are resolved across the warp with a
+//    generate/propagate ballot (one integer addition over the 32 lane flags).
+#include "zp_internal.cuh"
+
+namespace {
+
+constexpr int VW = ZP_VW;  // words of V per row
+
+// ------------------------------------------------------------------ 96-bit MAC
+__device__ __forceinline__ void mac96(uint32_t& c0, uint32_t& c1, uint32_t& c2, uint32_t a,
+                                      uint32_t b) {
+  asm("mad.lo.cc.u32 %0, %3, %4, %0;\n\t"
+      "madc.hi.cc.u32 %1, %3, %4, %1;\n\t"
+      "addc.u32 %2, %2, 0;"
+      : "+r"(c0), "+r"(c1), "+r"(c2)
+      : "r"(a), "r"(b));
+}
+
+// ------------------------------------------------------------------ V on CUDA cores
+// grid (ceil(R/4), B), block 256 = 4 rows x 64 limbs.
+__global__ void __launch_bounds__(256)
+    k_vmul_simt(const uint32_t* __restrict__ hneg, uint32_t R, uint32_t n,
+                const uint32_t* __restrict__ cko, uint32_t* __restrict__ V) {
+  __shared__ uint32_t S[4][ZP_MAX_L][3];
+  const uint32_t b = blockIdx.y;
+  const uint32_t rr = threadIdx.x >> 6, l = threadIdx.x & 63;
+  const uint32_t row = blockIdx.x * 4 + rr;
+  uint32_t c0 = 0, c1 = 0, c2 = 0;
+  if (row < R) {
+    const uint32_t* h = hneg + (uint64_t)row * n;
+    const uint32_t* ck = cko + (uint64_t)b * n * ZP_MAX_L + l;
+    for (uint32_t i = 0; i < n; ++i) mac96(c0, c1, c2, __ldg(h + i), __ldg(ck + (uint64_t)i * ZP_MAX_L));
+  }
+  S[rr][l][0] = c0;
+  S[rr][l][1] = c1;
+  S[rr][l][2] = c2;
+  __syncthreads();
+  if (l == 0 && row < R) {
+    // word w = S[w].lo + S[w-1].mid + S[w-2].hi + carry
+    uint32_t* out = V + ((uint64_t)b * R + row) * VW;
+    uint64_t carry = 0;
+    for (int w = 0; w < VW; ++w) {
+      uint64_t s = carry;
+      if (w < ZP_MAX_L) s += S[rr][w][0];
+      if (w >= 1 && w - 1 < ZP_MAX_L) s += S[rr][w - 1][1];
+      if (w >= 2 && w - 2 < ZP_MAX_L) s += S[rr][w - 2][2];
+      out[w] = (uint32_t)s;
+      carry = s >> 32;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ warp big integers
+// A big integer of WPL*32 words is held with words [WPL*lane, WPL*lane + WPL) in lane.
+
+// Adds per-word 64-bit column values v (each < 2^62) into normalized 32-bit words w.
+template <int WPL>
+__device__ __forceinline__ void warp_normalize(const uint64_t (&v)[WPL], uint32_t (&w)[WPL]) {
+  const uint32_t lane = lane_id();
+  uint64_t c = 0;
+#pragma unroll
+  for (int t = 0; t < WPL; ++t) {
+    const uint64_t s = v[t] + c;
+    w[t] = (uint32_t)s;
+    c = s >> 32;
+  }
+  uint64_t cin = __shfl_up_sync(0xffffffffu, c, 1);
+  if (lane == 0) cin = 0;
+  uint32_t cc;
+  {
+    const uint64_t s = (uint64_t)w[0] + cin;
+    w[0] = (uint32_t)s;
+    cc = (uint32_t)(s >> 32);
+  }
+#pragma unroll
+  for (int t = 1; t < WPL; ++t) {
+    const uint64_t s = (uint64_t)w[t] + cc;
+    w[t] = (uint32_t)s;
+    cc = (uint32_t)(s >> 32);
+  }
+  uint32_t all = 0xFFFFFFFFu;
+#pragma unroll
+  for (int t = 0; t < WPL; ++t) all &= w[t];
+  const uint32_t G = __ballot_sync(0xffffffffu, cc != 0);
+  const uint32_t P = __ballot_sync(0xffffffffu, all == 0xFFFFFFFFu);
+  const uint32_t K = (uint32_t)((uint64_t)G + (uint64_t)(G | P)) ^ P;  // carry into each lane
+  if ((K >> lane) & 1u) {
+    uint32_t c1 = 1;
+#pragma unroll
+    for (int t = 0; t < WPL; ++t) {
+      const uint64_t s = (uint64_t)w[t] + c1;
+      w[t] = (uint32_t)s;
+      c1 = (uint32_t)(s >> 32);
+    }
+  }
+}
+
+// a -= b over the warp (mod 2^(32*32*WPL)).
+template <int WPL>
+__device__ __forceinline__ void warp_sub(uint32_t (&a)[WPL], const uint32_t (&b)[WPL]) {
+  const uint32_t lane = lane_id();
+  uint32_t br = 0;
+#pragma unroll
+  for (int t = 0; t < WPL; ++t) {
+    const uint64_t s = (uint64_t)a[t] - b[t] - br;
+    a[t] = (uint32_t)s;
+    br = (uint32_t)(s >> 63);
+  }
+  uint32_t any = 0;
+#pragma unroll
+  for (int t = 0; t < WPL; ++t) any |= a[t];
+  const uint32_t G = __ballot_sync(0xffffffffu, br != 0);
+  const uint32_t P = __ballot_sync(0xffffffffu, any == 0);
+  const uint32_t K = (uint32_t)((uint64_t)G + (uint64_t)(G | P)) ^ P;  // borrow into each lane
+  if ((K >> lane) & 1u) {
+    uint32_t b1 = 1;
+#pragma unroll
+    for (int t = 0; t < WPL; ++t) {
+      const uint64_t s = (uint64_t)a[t] - b1;
+      a[t] = (uint32_t)s;
+      b1 = (uint32_t)(s >> 63);
+    }
+  }
+}
+
+// a >= b over the warp.
+template <int WPL>
+__device__ __forceinline__ bool warp_geq(const uint32_t (&a)[WPL], const uint32_t (&b)[WPL]) {
+  int cmp = 0;
+#pragma unroll
+  for (int t = WPL - 1; t >= 0; --t)
+    if (cmp == 0 && a[t] != b[t]) cmp = a[t] > b[t] ? 1 : -1;
+  const uint32_t GT = __ballot_sync(0xffffffffu, cmp > 0);
+  const uint32_t LT = __ballot_sync(0xffffffffu, cmp < 0);
+  if ((GT | LT) == 0) return true;
+  const int top = 31 - __clz(GT | LT);
+  return (GT >> top) & 1u;
+}
+
+// Column sums of the product a (na words) x b (nb words) for output words [0, nw):
+// col[w] = sum_{i+j=w} a[i] b[j] as three 32-bit words (exact: < 2^96). Lanes take
+// output words in a strided pattern, which balances the triangular column lengths.
+__device__ __forceinline__ void warp_mul_cols(const uint32_t* a, int na, const uint32_t* b, int nb,
+                                              uint32_t (*col)[3], int nw) {
+  for (int w = (int)lane_id(); w < nw; w += 32) {
+    uint32_t c0 = 0, c1 = 0, c2 = 0;
+    const int i0 = w - (nb - 1) > 0 ? w - (nb - 1) : 0;
+    const int i1 = w < na - 1 ? w : na - 1;
+    for (int i = i0; i <= i1; ++i) mac96(c0, c1, c2, a[i], b[w - i]);
+    col[w][0] = c0;
+    col[w][1] = c1;
+    col[w][2] = c2;
+  }
+}
+
+// Gathers normalized words [0, WPL*32) of a product whose columns [0, nw) are in col.
+template <int WPL>
+__device__ __forceinline__ void warp_cols_to_words(const uint32_t (*col)[3], int nw,
+                                                   uint32_t (&w)[WPL]) {
+  const uint32_t lane = lane_id();
+  uint64_t v[WPL];
+#pragma unroll
+  for (int t = 0; t < WPL; ++t) {
+    const int x = (int)lane * WPL + t;
+    uint64_t s = 0;
+    if (x < nw) s += col[x][0];
+    if (x >= 1 && x - 1 < nw) s += col[x - 1][1];
+    if (x >= 2 && x - 2 < nw) s += col[x - 2][2];
+    v[t] = s;
+  }
+  warp_normalize<WPL>(v, w);
+}
+
+struct PackWarpSmem {
+  uint32_t X[ZP_XW];        // Horner accumulator (< 2^4064)
+  uint32_t col[160][3];     // product columns
+  uint32_t q1[ZP_MAX_L + 1];
+  uint32_t q3[ZP_MAX_L + 1];
+  uint32_t m[ZP_MAX_L + 1];
+  uint32_t mu[ZP_MAX_L + 1];
+};
+
+constexpr int PACK_WARPS = 4;
+
+struct ClientPtrs {
+  const uint32_t* m;
+  const uint32_t* mu;
+};
+
+// grid (ceil(d1p / PACK_WARPS), B), block PACK_WARPS warps. Requires L == ZP_MAX_L.
+__global__ void __launch_bounds__(PACK_WARPS * 32)
+    k_pack_reduce(const uint32_t* __restrict__ ans, const uint32_t* __restrict__ V, uint32_t R,
+                  uint32_t ell, uint32_t d1p, uint32_t g0, uint32_t g1, uint32_t g2,
+                  const ClientPtrs* __restrict__ cl, uint32_t* __restrict__ T) {
+  __shared__ PackWarpSmem sm[PACK_WARPS];
+  const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t b = blockIdx.y;
+  const uint32_t rp = blockIdx.x * PACK_WARPS + warp;
+  if (rp >= d1p) return;
+  PackWarpSmem& S = sm[warp];
+  constexpr int L = ZP_MAX_L;
+
+  for (int x = lane; x < L + 1; x += 32) {
+    S.m[x] = x < L ? cl[b].m[x] : 0u;
+    S.mu[x] = cl[b].mu[x];
+  }
+  for (int x = lane; x < ZP_XW; x += 32) S.X[x] = 0u;
+  __syncwarp();
+
+  // ---- Horner: X <- X * gamma + W_j, j = ell-1 .. 0 (gamma = g0 + g1 2^32 + g2 2^64)
+  const uint32_t* ansb = ans + (uint64_t)b * R;
+  const uint32_t* Vb = V + (uint64_t)b * R * VW;
+  for (int j = (int)ell - 1; j >= 0; --j) {
+    const uint32_t row = rp * ell + (uint32_t)j;
+    const bool have = row < R;
+    uint64_t v[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int x = (int)lane * 4 + t;
+      const uint32_t x0 = S.X[x];
+      const uint32_t x1 = x >= 1 ? S.X[x - 1] : 0u;
+      const uint32_t x2 = x >= 2 ? S.X[x - 2] : 0u;
+      const uint32_t x3 = x >= 3 ? S.X[x - 3] : 0u;
+      uint64_t s = 0;
+      s += (uint32_t)((uint64_t)g0 * x0);
+      s += (uint32_t)(((uint64_t)g0 * x1) >> 32);
+      s += (uint32_t)((uint64_t)g1 * x1);
+      s += (uint32_t)(((uint64_t)g1 * x2) >> 32);
+      s += (uint32_t)((uint64_t)g2 * x2);
+      s += (uint32_t)(((uint64_t)g2 * x3) >> 32);
+      if (have) {
+        if (x < VW) s += Vb[(uint64_t)row * VW + x];
+        if (x == 0) s += ansb[row];
+      }
+      v[t] = s;
+    }
+    __syncwarp();
+    uint32_t w[4];
+    warp_normalize<4>(v, w);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) S.X[lane * 4 + t] = w[t];
+    __syncwarp();
+  }
+
+  // ---- Barrett: q1 = floor(X / b^(L-1)), q3 = floor(q1 mu / b^(L+1)),
+  //      r = (X mod b^(L+1)) - (q3 m mod b^(L+1)), then r -= m while r >= m.
+  for (int x = lane; x < L + 1; x += 32) S.q1[x] = S.X[L - 1 + x];
+  __syncwarp();
+  warp_mul_cols(S.q1, L + 1, S.mu, L + 1, S.col, 2 * L + 1);
+  __syncwarp();
+  {
+    uint32_t w[5];  // words 0..159 of q1 * mu; q3 = words L+1 .. 2L+1
+    warp_cols_to_words<5>(S.col, 2 * L + 1, w);
+    __syncwarp();
+#pragma unroll
+    for (int t = 0; t < 5; ++t) {
+      const int x = (int)lane * 5 + t;
+      if (x >= L + 1 && x < 2 * L + 2) S.q3[x - (L + 1)] = w[t];
+    }
+  }
+  __syncwarp();
+  warp_mul_cols(S.q3, L + 1, S.m, L, S.col, L + 1);
+  __syncwarp();
+  uint32_t r[3], r2[3], mm[3];
+  warp_cols_to_words<3>(S.col, L + 1, r2);
+#pragma unroll
+  for (int t = 0; t < 3; ++t) {
+    const int x = (int)lane * 3 + t;
+    r2[t] = x < L + 1 ? r2[t] : 0u;
+    r[t] = x < L + 1 ? S.X[x] : 0u;
+    mm[t] = x < L ? S.m[x] : 0u;
+  }
+  warp_sub<3>(r, r2);
+#pragma unroll
+  for (int t = 0; t < 3; ++t)
+    if ((int)lane * 3 + t >= L + 1) r[t] = 0u;  // mod b^(L+1)
+  for (int it = 0; it < 3; ++it) {
+    if (!warp_geq<3>(r, mm)) break;
+    warp_sub<3>(r, mm);
+  }
+  uint32_t* out = T + ((uint64_t)b * d1p + rp) * L;
+#pragma unroll
+  for (int t = 0; t < 3; ++t) {
+    const int x = (int)lane * 3 + t;
+    if (x < L) out[x] = r[t];
+  }
+}
+
+}  // namespace
+
+int zp_launch_compress(zp_db* db, zp_client* const* clients, const uint32_t* dAns,
+                       const uint32_t* dCKO, uint32_t B, uint32_t* dT, cudaStream_t st) {
+  zp_ctx* ctx = db->ctx;
+  const uint32_t R = db->R, n = ctx->P.n;
+  int rc = zp_scratch_reserve(&db->s_v, (size_t)B * R * VW * sizeof(uint32_t));
+  if (rc) return rc;
+  rc = zp_scratch_reserve(&db->s_clients, (size_t)B * sizeof(ClientPtrs));
+  if (rc) return rc;
+  uint32_t* V = static_cast<uint32_t*>(db->s_v.p);
+  ClientPtrs* dcl = static_cast<ClientPtrs*>(db->s_clients.p);
+  {
+    ClientPtrs* h = new ClientPtrs[B];
+    for (uint32_t b = 0; b < B; ++b) h[b] = ClientPtrs{clients[b]->d_m, clients[b]->d_mu};
+    // pageable source: the copy is staged before cudaMemcpyAsync returns
+    cudaError_t e = cudaMemcpyAsync(dcl, h, B * sizeof(ClientPtrs), cudaMemcpyHostToDevice, st);
+    delete[] h;
+    if (e != cudaSuccess) return zp_cuda_check(e, "cudaMemcpyAsync(clients)");
+  }
+  {
+    dim3 grid((R + 3) / 4, B);
+    ctx->launches++;
+    k_vmul_simt<<<grid, 256, 0, st>>>(db->d_hneg, R, n, dCKO, V);
+    ZP_CUDA(cudaGetLastError());
+  }
+  {
+    dim3 grid((db->d1p + PACK_WARPS - 1) / PACK_WARPS, B);
+    ctx->launches++;
+    k_pack_reduce<<<grid, PACK_WARPS * 32, 0, st>>>(dAns, V, R, ctx->ell, db->d1p, ctx->gamma_w[0],
+                                                    ctx->gamma_w[1], ctx->gamma_w[2], dcl, dT);
+    ZP_CUDA(cudaGetLastError());
+  }
+  return ZP_OK;
+}

@@ -1,0 +1,190 @@
+// k_gemv.cu -- the single-query LWE answer (Algorithm "ZipPIR", Response, first line):
+//   ans[r] = sum_c D[r][c] * q[c]  mod 2^32.
+//
+// Design (GB300, HBM-bound): D is streamed once through a TMA ring of 64 x 256-byte
+// tiles (cp.async.bulk.tensor, L2 evict-first), the query is pre-split into its four
+// byte planes q = sum_k 2^(8k) q_k so that one dp4a multiplies four database bytes by
+// four plane bytes, and each thread keeps one 32-bit accumulator per (row, plane).
+// Accumulators wrap mod 2^32, which is exact because (x mod 2^32) 2^(8k) = x 2^(8k)
+// mod 2^32. Work is split "stream-K" style: the tile sequence (row block, column
+// tile) is cut into one contiguous range per CTA, so every CTA streams the same
+// number of bytes; a CTA adds its partial row sums to ans with atomicAdd, which is
+// order-independent under wrap-around, so the result is deterministic.
+#include <cstdio>
+
+#include "zp_internal.cuh"
+
+namespace {
+
+constexpr int TR = 64;                   // rows per tile
+constexpr int TCB = 256;                 // bytes (= columns) per tile row
+constexpr int NCW = 8;                   // consumer warps
+constexpr int TILE_BYTES = TR * TCB;     // 16 KiB
+constexpr int QT_BYTES = 4 * 16 * 16;    // q planes of one column tile: 4 planes x 16 chunks x 16 B
+constexpr int STAGE_BYTES = TILE_BYTES + QT_BYTES;
+constexpr int STAGES = 6;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 2 * STAGES * 8;
+constexpr int CTAS_PER_SM = 2;
+
+// Byte planes of the query for the GEMV tile layout. Word index
+//   ((ct * 4 + k) * 16 + j) * 4 + w
+// packs byte k of q[c] for c = ct*256 + j*16 + w*4 + i into bits 8i..8i+7 (i < 4);
+// columns >= C give 0. Also zeroes ans (the GEMV accumulates into it).
+__global__ void k_qplanes(const uint32_t* __restrict__ q, uint32_t C, uint32_t nct,
+                          uint32_t* __restrict__ qp, uint32_t* __restrict__ ans, uint32_t R) {
+  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t total = nct * 256u;
+  if (tid < total) {
+    const uint32_t w = tid & 3u, j = (tid >> 2) & 15u, k = (tid >> 6) & 3u, ct = tid >> 8;
+    const uint32_t c0 = ct * 256u + j * 16u + w * 4u;
+    uint32_t v = 0;
+#pragma unroll
+    for (uint32_t i = 0; i < 4; ++i) {
+      const uint32_t c = c0 + i;
+      const uint32_t x = c < C ? q[c] : 0u;
+      v |= ((x >> (8u * k)) & 0xFFu) << (8u * i);
+    }
+    qp[tid] = v;
+  }
+  for (uint32_t r = tid; r < R; r += gridDim.x * blockDim.x) ans[r] = 0u;
+}
+
+__global__ void __launch_bounds__((NCW + 1) * 32, 1)
+    k_gemv(const __grid_constant__ CUtensorMap tmap, const uint32_t* __restrict__ qp,
+           uint32_t* __restrict__ ans, uint32_t R, uint32_t nrb, uint32_t nct,
+           uint32_t* status) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+  uint64_t* empty = full + STAGES;
+  const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint64_t T = (uint64_t)nrb * nct;
+  const uint64_t t_begin = T * blockIdx.x / gridDim.x;
+  const uint64_t t_end = T * (blockIdx.x + 1) / gridDim.x;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], NCW);
+    }
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (t_begin >= t_end) return;
+
+  if (warp == NCW) {  // ---------------- producer warp: one elected lane issues copies
+    if (lane == 0) {
+      prefetch_tmap(&tmap);
+      const uint64_t pol = l2_policy_evict_first();
+      uint32_t issued = 0;
+      for (uint64_t t = t_begin; t < t_end; ++t, ++issued) {
+        const uint32_t s = issued % STAGES, round = issued / STAGES;
+        if (round > 0 &&
+            !mbar_wait_bounded(&empty[s], (round - 1) & 1u, status, ZP_DEV_TIMEOUT_GEMV))
+          break;
+        const uint32_t rb = (uint32_t)(t / nct), ct = (uint32_t)(t % nct);
+        uint8_t* st = smem + s * STAGE_BYTES;
+        mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
+        tma_load_2d_hint(st, &tmap, (int32_t)(ct * TCB), (int32_t)(rb * TR), &full[s], pol);
+        bulk_load(st + TILE_BYTES, qp + (size_t)ct * 256u, QT_BYTES, &full[s]);
+      }
+      // Stay alive until every copy this thread issued has landed (bounded).
+      const uint32_t first = issued > STAGES ? issued - STAGES : 0;
+      for (uint32_t i = first; i < issued; ++i)
+        mbar_wait_bounded(&full[i % STAGES], (i / STAGES) & 1u, status, ZP_DEV_TIMEOUT_GEMV);
+    }
+    return;
+  }
+
+  // ---------------- consumer warps
+  const uint32_t j = lane & 15u;                   // 16-byte chunk of the 256-byte tile row
+  const uint32_t rg = warp * 2u + (lane >> 4);     // row group: rows 4 rg .. 4 rg + 3
+  uint32_t acc[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) acc[r][k] = 0u;
+
+  auto flush = [&](uint32_t rb) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      uint32_t v = acc[r][0] + (acc[r][1] << 8) + (acc[r][2] << 16) + (acc[r][3] << 24);
+      v += __shfl_xor_sync(0xffffffffu, v, 8);
+      v += __shfl_xor_sync(0xffffffffu, v, 4);
+      v += __shfl_xor_sync(0xffffffffu, v, 2);
+      v += __shfl_xor_sync(0xffffffffu, v, 1);
+      const uint32_t row = rb * TR + rg * 4u + (uint32_t)r;
+      if (j == 0 && row < R) atomicAdd(&ans[row], v);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) acc[r][k] = 0u;
+    }
+  };
+
+  uint32_t cur_rb = (uint32_t)(t_begin / nct);
+  uint32_t consumed = 0;
+  bool ok = true;
+  for (uint64_t t = t_begin; t < t_end; ++t, ++consumed) {
+    const uint32_t rb = (uint32_t)(t / nct);
+    if (rb != cur_rb) {
+      flush(cur_rb);
+      cur_rb = rb;
+    }
+    const uint32_t s = consumed % STAGES, round = consumed / STAGES;
+    if (!mbar_wait_bounded(&full[s], round & 1u, status, ZP_DEV_TIMEOUT_GEMV)) {
+      ok = false;
+      break;
+    }
+    const uint8_t* st = smem + s * STAGE_BYTES;
+    const uint4* qv = reinterpret_cast<const uint4*>(st + TILE_BYTES);
+    uint4 qk[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) qk[k] = qv[k * 16 + j];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const uint4 d = *reinterpret_cast<const uint4*>(st + (rg * 4 + r) * TCB + j * 16);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        uint32_t a = acc[r][k];
+        a = __dp4a(d.x, qk[k].x, a);
+        a = __dp4a(d.y, qk[k].y, a);
+        a = __dp4a(d.z, qk[k].z, a);
+        a = __dp4a(d.w, qk[k].w, a);
+        acc[r][k] = a;
+      }
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[s]);
+  }
+  if (ok) flush(cur_rb);
+}
+
+bool g_attr_done[64] = {false};
+
+}  // namespace
+
+int zp_launch_gemv(zp_db* db, const uint32_t* dq, uint32_t* dans, cudaStream_t st) {
+  zp_ctx* ctx = db->ctx;
+  const uint32_t nct = (db->C + TCB - 1) / TCB;
+  const uint32_t nrb = (db->R + TR - 1) / TR;
+  const size_t qp_bytes = (size_t)nct * QT_BYTES;
+  int rc = zp_scratch_reserve(&db->s_qplanes, qp_bytes);
+  if (rc) return rc;
+  uint32_t* qp = static_cast<uint32_t*>(db->s_qplanes.p);
+  {
+    const uint32_t total = nct * 256u;
+    const uint32_t blocks = (total + 255) / 256;
+    ctx->launches++;
+    k_qplanes<<<blocks, 256, 0, st>>>(dq, db->C, nct, qp, dans, db->R);
+  }
+  if (!g_attr_done[ctx->device & 63]) {
+    ZP_CUDA(cudaFuncSetAttribute(k_gemv, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    g_attr_done[ctx->device & 63] = true;
+  }
+  const uint64_t T = (uint64_t)nrb * nct;
+  uint64_t grid = (uint64_t)ctx->num_sms * CTAS_PER_SM;
+  if (grid > T) grid = T;
+  ctx->launches++;
+  k_gemv<<<(unsigned)grid, (NCW + 1) * 32, SMEM_BYTES, st>>>(db->tmap_gemv, qp, dans, db->R, nrb,
+                                                             nct, ctx->d_status);
+  ZP_CUDA(cudaGetLastError());
+  return ZP_OK;
+}

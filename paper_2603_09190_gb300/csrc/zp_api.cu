@@ -1,0 +1,550 @@
+// zp_api.cu -- host side of the C ABI declared in include/zippir.h: argument
+// validation, handle lifetime, per-client constants, scratch management and the
+// dispatch to the kernels of the online Response (Algorithm "ZipPIR").
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <exception>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "zp_internal.cuh"
+
+#define ZP_VERSION_NUM 100  // 0.1.0
+
+static thread_local std::string g_err;
+
+int zp_set_error(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+int zp_cuda_check(cudaError_t e, const char* what) {
+  return zp_set_error(ZP_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+int zp_scratch_reserve(zp_scratch* s, size_t bytes) {
+  if (bytes <= s->bytes) return ZP_OK;
+  if (s->p) {
+    cudaError_t e = cudaFree(s->p);
+    s->p = nullptr;
+    s->bytes = 0;
+    if (e != cudaSuccess) return zp_cuda_check(e, "cudaFree(scratch)");
+  }
+  const size_t want = bytes + bytes / 4 + 256;
+  cudaError_t e = cudaMalloc(&s->p, want);
+  if (e != cudaSuccess) {
+    s->p = nullptr;
+    return zp_set_error(ZP_ENOMEM, "cudaMalloc(%zu bytes): %s", want, cudaGetErrorString(e));
+  }
+  s->bytes = want;
+  return ZP_OK;
+}
+
+static void scratch_free(zp_scratch* s) {
+  if (s->p) cudaFree(s->p);
+  s->p = nullptr;
+  s->bytes = 0;
+}
+
+// ------------------------------------------------------------------ tensor maps
+typedef CUresult (*PFN_encodeTiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                    const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                    const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                    CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static PFN_encodeTiled get_encode_fn() {
+  static PFN_encodeTiled fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_encodeTiled>(p);
+  }
+  return fn;
+}
+
+int zp_encode_tmap_2d(CUtensorMap* map, CUtensorMapDataType dt, const void* base, uint64_t dim0,
+                      uint64_t dim1, uint64_t stride1_bytes, uint32_t box0, uint32_t box1,
+                      CUtensorMapSwizzle swz) {
+  PFN_encodeTiled fn = get_encode_fn();
+  if (!fn) return zp_set_error(ZP_ECUDA, "cuTensorMapEncodeTiled entry point unavailable");
+  cuuint64_t dims[2] = {dim0, dim1};
+  cuuint64_t strides[1] = {stride1_bytes};
+  cuuint32_t box[2] = {box0, box1};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map, dt, 2, const_cast<void*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return zp_set_error(ZP_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  return ZP_OK;
+}
+
+// ------------------------------------------------------------------ small host bignum helpers
+// little-endian u32 words
+static void big_mul_small(std::vector<uint32_t>& a, const uint32_t* g, int gw) {
+  std::vector<uint32_t> r(a.size() + gw + 1, 0);
+  for (size_t i = 0; i < a.size(); ++i) {
+    uint64_t carry = 0;
+    for (int j = 0; j < gw; ++j) {
+      uint64_t t = (uint64_t)a[i] * g[j] + r[i + j] + carry;
+      r[i + j] = (uint32_t)t;
+      carry = t >> 32;
+    }
+    size_t k = i + gw;
+    while (carry) {
+      uint64_t t = (uint64_t)r[k] + carry;
+      r[k] = (uint32_t)t;
+      carry = t >> 32;
+      ++k;
+    }
+  }
+  while (r.size() > 1 && r.back() == 0) r.pop_back();
+  a.swap(r);
+}
+
+static uint32_t big_bits(const std::vector<uint32_t>& a) {
+  for (size_t i = a.size(); i-- > 0;)
+    if (a[i]) return (uint32_t)(i * 32 + (32 - __builtin_clz(a[i])));
+  return 0;
+}
+
+// ------------------------------------------------------------------ context
+extern "C" int zp_version(void) { return ZP_VERSION_NUM; }
+
+extern "C" int zp_last_error(char* buf, size_t len) {
+  if (buf && len) {
+    size_t n = g_err.size() < len - 1 ? g_err.size() : len - 1;
+    memcpy(buf, g_err.data(), n);
+    buf[n] = 0;
+  }
+  return (int)g_err.size();
+}
+
+extern "C" int zp_init(int device, const zp_params* P, zp_ctx** out) {
+  try {
+    if (!P || !out) return zp_set_error(ZP_EINVAL, "zp_init: null argument");
+    *out = nullptr;
+    if (P->n < 1 || P->n > 4096) return zp_set_error(ZP_EINVAL, "zp_init: n=%u out of [1,4096]", P->n);
+    if (P->p_bits != 8) return zp_set_error(ZP_EINVAL, "zp_init: p_bits must be 8");
+    if (P->secret != ZP_SECRET_UNIFORM && P->secret != ZP_SECRET_BINARY)
+      return zp_set_error(ZP_EINVAL, "zp_init: bad secret kind %u", P->secret);
+    if (P->key_bits != 32 * ZP_MAX_L)
+      return zp_set_error(ZP_EUNSUPPORTED, "zp_init: key_bits=%u (this build: %d)", P->key_bits,
+                          32 * ZP_MAX_L);
+    ZP_CUDA(cudaSetDevice(device));
+    zp_ctx* c = new zp_ctx();
+    c->device = device;
+    c->P = *P;
+    c->L = P->key_bits / 32;
+    // gamma = q + n q^2 (uniform secret) or q + n q (binary secret), q = 2^32
+    c->gamma_w[0] = 0;
+    if (P->secret == ZP_SECRET_UNIFORM) {
+      c->gamma_w[1] = 1;
+      c->gamma_w[2] = P->n;
+    } else {
+      c->gamma_w[1] = 1 + P->n;
+      c->gamma_w[2] = 0;
+    }
+    // ell = largest integer with gamma^ell < 2^(key_bits - 1)
+    {
+      std::vector<uint32_t> acc(1, 1);
+      uint32_t ell = 0;
+      for (;;) {
+        std::vector<uint32_t> nx = acc;
+        big_mul_small(nx, c->gamma_w, 3);
+        if (big_bits(nx) > P->key_bits - 1) break;  // nx >= 2^(key_bits-1)
+        acc.swap(nx);
+        ++ell;
+      }
+      if (ell == 0) {
+        delete c;
+        return zp_set_error(ZP_EINVAL, "zp_init: key too small for one slot");
+      }
+      c->ell = ell;
+    }
+    cudaDeviceProp prop;
+    cudaError_t e = cudaGetDeviceProperties(&prop, device);
+    if (e != cudaSuccess) {
+      delete c;
+      return zp_cuda_check(e, "cudaGetDeviceProperties");
+    }
+    c->num_sms = prop.multiProcessorCount;
+    c->launches = 0;
+    e = cudaMalloc(&c->d_status, sizeof(uint32_t));
+    if (e != cudaSuccess) {
+      delete c;
+      return zp_set_error(ZP_ENOMEM, "cudaMalloc(status)");
+    }
+    cudaMemset(c->d_status, 0, sizeof(uint32_t));
+    *out = c;
+    return ZP_OK;
+  } catch (const std::bad_alloc&) {
+    return zp_set_error(ZP_ENOMEM, "zp_init: host allocation failed");
+  } catch (...) {
+    return zp_set_error(ZP_EINVAL, "zp_init: unexpected exception");
+  }
+}
+
+extern "C" int zp_ctx_destroy(zp_ctx* c) {
+  if (!c) return ZP_OK;
+  cudaSetDevice(c->device);
+  if (c->d_status) cudaFree(c->d_status);
+  delete c;
+  return ZP_OK;
+}
+
+extern "C" int zp_kernel_launches(const zp_ctx* c, uint64_t* count) {
+  if (!c || !count) return zp_set_error(ZP_EINVAL, "zp_kernel_launches: null argument");
+  *count = c->launches;
+  return ZP_OK;
+}
+
+extern "C" int zp_device_status(zp_ctx* c, uint32_t* code) {
+  if (!c || !code) return zp_set_error(ZP_EINVAL, "zp_device_status: null argument");
+  ZP_CUDA(cudaSetDevice(c->device));
+  ZP_CUDA(cudaDeviceSynchronize());
+  ZP_CUDA(cudaMemcpy(code, c->d_status, sizeof(uint32_t), cudaMemcpyDeviceToHost));
+  ZP_CUDA(cudaMemset(c->d_status, 0, sizeof(uint32_t)));
+  return ZP_OK;
+}
+
+// ------------------------------------------------------------------ database
+extern "C" int zp_setup_db(zp_ctx* c, const uint8_t* dD, uint32_t R, uint32_t C, uint64_t ld,
+                           zp_db** out) {
+  try {
+    if (!c || !dD || !out) return zp_set_error(ZP_EINVAL, "zp_setup_db: null argument");
+    *out = nullptr;
+    if (R < 1 || R > (1u << 20) || C < 1 || C > (1u << 20))
+      return zp_set_error(ZP_EINVAL, "zp_setup_db: R=%u C=%u out of [1, 2^20]", R, C);
+    if (ld < C || ld % 16 != 0)
+      return zp_set_error(ZP_EINVAL, "zp_setup_db: ld_bytes=%llu must be >= C and a multiple of 16",
+                          (unsigned long long)ld);
+    if (reinterpret_cast<uintptr_t>(dD) % 16 != 0)
+      return zp_set_error(ZP_EINVAL, "zp_setup_db: database pointer not 16-byte aligned");
+    ZP_CUDA(cudaSetDevice(c->device));
+    zp_db* db = new zp_db();
+    db->ctx = c;
+    db->dD = dD;
+    db->R = R;
+    db->C = C;
+    db->ld = ld;
+    db->d1p = (R + c->ell - 1) / c->ell;
+    db->d_hneg = nullptr;
+    db->hint_ready = false;
+    db->stale = 0;
+    cudaError_t e = cudaMalloc(&db->d_rowsum, (size_t)R * sizeof(uint32_t));
+    if (e != cudaSuccess) {
+      delete db;
+      return zp_set_error(ZP_ENOMEM, "zp_setup_db: cudaMalloc(rowsum)");
+    }
+    int rc = zp_encode_tmap_2d(&db->tmap_gemv, CU_TENSOR_MAP_DATA_TYPE_UINT8, dD, C, R, ld, 256, 64,
+                               CU_TENSOR_MAP_SWIZZLE_NONE);
+    if (!rc) rc = zp_launch_rowsum(db, nullptr, 0, 0);
+    if (!rc) {
+      e = cudaDeviceSynchronize();
+      if (e != cudaSuccess) rc = zp_cuda_check(e, "zp_setup_db: row sums");
+    }
+    if (rc) {
+      cudaFree(db->d_rowsum);
+      delete db;
+      return rc;
+    }
+    *out = db;
+    return ZP_OK;
+  } catch (const std::bad_alloc&) {
+    return zp_set_error(ZP_ENOMEM, "zp_setup_db: host allocation failed");
+  }
+}
+
+static std::vector<uint8_t>& stale_flags(zp_db* db) {
+  if (db->stale_v.size() != db->R) db->stale_v.assign(db->R, 0);
+  return db->stale_v;
+}
+
+extern "C" int zp_db_info(const zp_db* db, uint32_t* ell, uint32_t* d1p, uint32_t* L) {
+  if (!db) return zp_set_error(ZP_EINVAL, "zp_db_info: null db");
+  if (ell) *ell = db->ctx->ell;
+  if (d1p) *d1p = db->d1p;
+  if (L) *L = db->ctx->L;
+  return ZP_OK;
+}
+
+extern "C" int zp_stale_rows(const zp_db* db, uint32_t* count) {
+  if (!db || !count) return zp_set_error(ZP_EINVAL, "zp_stale_rows: null argument");
+  *count = db->stale;
+  return ZP_OK;
+}
+
+extern "C" int zp_db_destroy(zp_db* db) {
+  if (!db) return ZP_OK;
+  cudaSetDevice(db->ctx->device);
+  cudaDeviceSynchronize();
+  if (db->d_rowsum) cudaFree(db->d_rowsum);
+  if (db->d_hneg) cudaFree(db->d_hneg);
+  zp_scratch* all[] = {&db->s_qplanes, &db->s_v, &db->s_q, &db->s_cko,
+                       &db->s_ans,     &db->s_t, &db->s_clients, &db->s_misc};
+  for (zp_scratch* s : all) scratch_free(s);
+  delete db;
+  return ZP_OK;
+}
+
+// host row list -> validated device copy in db->s_misc (first bytes)
+static int stage_rows(zp_db* db, const uint32_t* hRows, uint32_t k, size_t extra_bytes,
+                      uint32_t** dRows, cudaStream_t st) {
+  for (uint32_t j = 0; j < k; ++j)
+    if (hRows[j] >= db->R) return zp_set_error(ZP_EINVAL, "row index %u >= R=%u", hRows[j], db->R);
+  const size_t rows_bytes = ((size_t)k * 4 + 255) / 256 * 256;
+  int rc = zp_scratch_reserve(&db->s_misc, rows_bytes + extra_bytes);
+  if (rc) return rc;
+  *dRows = static_cast<uint32_t*>(db->s_misc.p);
+  ZP_CUDA(cudaMemcpyAsync(*dRows, hRows, (size_t)k * 4, cudaMemcpyHostToDevice, st));
+  return ZP_OK;
+}
+
+int zp_launch_copy_rows(const uint8_t* src, uint64_t lds, uint8_t* dst, uint64_t ldd, uint32_t C,
+                        const uint32_t* rows, uint32_t cnt, int gather, cudaStream_t st);
+
+extern "C" int zp_gen_hint(zp_db* db, const uint32_t* dA, uint32_t* dH, const uint32_t* hRows,
+                           uint32_t nrows, void* stream) {
+  try {
+    if (!db || !dA) return zp_set_error(ZP_EINVAL, "zp_gen_hint: null argument");
+    if (hRows && (nrows == 0 || nrows > db->R))
+      return zp_set_error(ZP_EINVAL, "zp_gen_hint: nrows=%u out of [1, R]", nrows);
+    zp_ctx* c = db->ctx;
+    ZP_CUDA(cudaSetDevice(c->device));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const uint32_t n = c->P.n;
+    if (!db->d_hneg) {
+      cudaError_t e = cudaMalloc(&db->d_hneg, (size_t)db->R * n * sizeof(uint32_t));
+      if (e != cudaSuccess) {
+        db->d_hneg = nullptr;
+        return zp_set_error(ZP_ENOMEM, "zp_gen_hint: cudaMalloc(hint %zu bytes)",
+                            (size_t)db->R * n * 4);
+      }
+    }
+    std::vector<uint8_t>& stale = stale_flags(db);
+    if (!hRows) {
+      uint32_t* outp = dH;
+      if (!outp) {
+        int rc = zp_scratch_reserve(&db->s_v, (size_t)db->R * n * 4);
+        if (rc) return rc;
+        outp = static_cast<uint32_t*>(db->s_v.p);
+      }
+      int rc = zp_launch_answer_simt(db, dA, n, 0, outp, 1, n, db->dD, db->R, db->ld, st);
+      if (!rc) rc = zp_launch_hint_post(db, outp, nullptr, db->R, dH, st);
+      if (rc) return rc;
+      db->hint_ready = true;
+      stale.assign(db->R, 0);
+      db->stale = 0;
+      return ZP_OK;
+    }
+    const uint64_t ldc = ((uint64_t)db->C + 15) / 16 * 16;
+    const size_t gather_bytes = ((size_t)nrows * ldc + 255) / 256 * 256;
+    const size_t hc_bytes = (size_t)nrows * n * 4;
+    uint32_t* dRows = nullptr;
+    int rc = stage_rows(db, hRows, nrows, gather_bytes + hc_bytes, &dRows, st);
+    if (rc) return rc;
+    uint8_t* base = static_cast<uint8_t*>(db->s_misc.p) + ((size_t)nrows * 4 + 255) / 256 * 256;
+    uint8_t* dG = base;
+    uint32_t* dHc = reinterpret_cast<uint32_t*>(base + gather_bytes);
+    c->launches++;
+    rc = zp_launch_copy_rows(db->dD, db->ld, dG, ldc, db->C, dRows, nrows, 1, st);
+    if (!rc) rc = zp_launch_answer_simt(db, dA, n, 0, dHc, 1, n, dG, nrows, ldc, st);
+    if (!rc) rc = zp_launch_hint_post(db, dHc, dRows, nrows, dH, st);
+    if (rc) return rc;
+    for (uint32_t j = 0; j < nrows; ++j) {
+      if (stale[hRows[j]]) {
+        stale[hRows[j]] = 0;
+        --db->stale;
+      }
+    }
+    return ZP_OK;
+  } catch (const std::bad_alloc&) {
+    return zp_set_error(ZP_ENOMEM, "zp_gen_hint: host allocation failed");
+  }
+}
+
+extern "C" int zp_update_rows(zp_db* db, const uint32_t* hRows, uint32_t k, const uint8_t* dNew,
+                              void* stream) {
+  try {
+    if (!db || !hRows || !dNew) return zp_set_error(ZP_EINVAL, "zp_update_rows: null argument");
+    if (k == 0 || k > db->R) return zp_set_error(ZP_EINVAL, "zp_update_rows: k=%u out of [1, R]", k);
+    ZP_CUDA(cudaSetDevice(db->ctx->device));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    uint32_t* dRows = nullptr;
+    int rc = stage_rows(db, hRows, k, 0, &dRows, st);
+    if (rc) return rc;
+    db->ctx->launches++;
+    rc = zp_launch_copy_rows(dNew, db->C, const_cast<uint8_t*>(db->dD), db->ld, db->C, dRows, k, 0, st);
+    if (!rc) rc = zp_launch_rowsum(db, dRows, k, st);
+    if (rc) return rc;
+    std::vector<uint8_t>& stale = stale_flags(db);
+    for (uint32_t j = 0; j < k; ++j) {
+      if (!stale[hRows[j]]) {
+        stale[hRows[j]] = 1;
+        ++db->stale;
+      }
+    }
+    return ZP_OK;
+  } catch (const std::bad_alloc&) {
+    return zp_set_error(ZP_ENOMEM, "zp_update_rows: host allocation failed");
+  }
+}
+
+// ------------------------------------------------------------------ online Response
+extern "C" int zp_answer(zp_db* db, const uint32_t* dQ, uint32_t B, uint32_t* dAns, void* stream) {
+  if (!db || !dQ || !dAns) return zp_set_error(ZP_EINVAL, "zp_answer: null argument");
+  if (B < 1 || B > 4096) return zp_set_error(ZP_EINVAL, "zp_answer: B=%u out of [1, 4096]", B);
+  ZP_CUDA(cudaSetDevice(db->ctx->device));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (B == 1) return zp_launch_gemv(db, dQ, dAns, st);
+  return zp_launch_answer_simt(db, dQ, B, db->C, dAns, db->R, 1, db->dD, db->R, db->ld, st);
+}
+
+extern "C" int zp_register_client(zp_ctx* c, const uint32_t* hM, uint32_t L, zp_client** out) {
+  try {
+    if (!c || !hM || !out) return zp_set_error(ZP_EINVAL, "zp_register_client: null argument");
+    *out = nullptr;
+    if (L != c->L) return zp_set_error(ZP_EINVAL, "zp_register_client: L=%u, expected %u", L, c->L);
+    std::vector<uint32_t> m(hM, hM + L);
+    if ((m[0] & 1u) == 0) return zp_set_error(ZP_EINVAL, "zp_register_client: m must be odd");
+    if (big_bits(m) != c->P.key_bits)
+      return zp_set_error(ZP_EINVAL, "zp_register_client: m has %u bits, expected %u", big_bits(m),
+                          c->P.key_bits);
+    // mu = floor(2^(64 L) / m) by binary long division (L+1 words)
+    std::vector<uint32_t> mu(L + 1, 0), r(L + 1, 0);
+    const uint32_t nbits = 64 * L + 1;
+    for (int64_t i = nbits - 1; i >= 0; --i) {
+      // r = 2 r + bit(i), bit(i) = 1 only for i = 64 L
+      uint32_t carry = (i == (int64_t)(64 * L)) ? 1u : 0u;
+      for (uint32_t w = 0; w < L + 1; ++w) {
+        const uint32_t nc = r[w] >> 31;
+        r[w] = (r[w] << 1) | carry;
+        carry = nc;
+      }
+      // compare r >= m
+      bool ge = true;
+      for (int64_t w = L; w >= 0; --w) {
+        const uint32_t mw = w < (int64_t)L ? m[w] : 0u;
+        if (r[w] != mw) {
+          ge = r[w] > mw;
+          break;
+        }
+      }
+      if (ge) {
+        uint64_t br = 0;
+        for (uint32_t w = 0; w < L + 1; ++w) {
+          const uint64_t s = (uint64_t)r[w] - (w < L ? m[w] : 0u) - br;
+          r[w] = (uint32_t)s;
+          br = (s >> 63) & 1u;
+        }
+        if (i / 32 < (int64_t)(L + 1)) mu[i / 32] |= 1u << (i % 32);
+      }
+    }
+    ZP_CUDA(cudaSetDevice(c->device));
+    zp_client* cl = new zp_client();
+    cl->ctx = c;
+    cl->L = L;
+    cl->d_m = nullptr;
+    cl->d_mu = nullptr;
+    if (cudaMalloc(&cl->d_m, L * 4) != cudaSuccess || cudaMalloc(&cl->d_mu, (L + 1) * 4) != cudaSuccess) {
+      if (cl->d_m) cudaFree(cl->d_m);
+      delete cl;
+      return zp_set_error(ZP_ENOMEM, "zp_register_client: cudaMalloc");
+    }
+    cudaError_t e = cudaMemcpy(cl->d_m, m.data(), L * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(cl->d_mu, mu.data(), (L + 1) * 4, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      cudaFree(cl->d_m);
+      cudaFree(cl->d_mu);
+      delete cl;
+      return zp_cuda_check(e, "zp_register_client: copy constants");
+    }
+    *out = cl;
+    return ZP_OK;
+  } catch (const std::bad_alloc&) {
+    return zp_set_error(ZP_ENOMEM, "zp_register_client: host allocation failed");
+  }
+}
+
+extern "C" int zp_client_destroy(zp_client* cl) {
+  if (!cl) return ZP_OK;
+  cudaSetDevice(cl->ctx->device);
+  cudaDeviceSynchronize();
+  if (cl->d_m) cudaFree(cl->d_m);
+  if (cl->d_mu) cudaFree(cl->d_mu);
+  delete cl;
+  return ZP_OK;
+}
+
+static int check_compress_args(zp_db* db, zp_client* const* clients, uint32_t B) {
+  if (!clients) return zp_set_error(ZP_EINVAL, "zp_compress: null clients");
+  if (B < 1 || B > 4096) return zp_set_error(ZP_EINVAL, "zp_compress: B=%u out of [1, 4096]", B);
+  if (!db->hint_ready) return zp_set_error(ZP_ESTATE, "zp_compress: no hint (call zp_gen_hint)");
+  if (db->stale) return zp_set_error(ZP_ESTATE, "zp_compress: %u hint rows stale after updates", db->stale);
+  for (uint32_t b = 0; b < B; ++b) {
+    if (!clients[b]) return zp_set_error(ZP_EINVAL, "zp_compress: clients[%u] is null", b);
+    if (clients[b]->ctx != db->ctx) return zp_set_error(ZP_EINVAL, "zp_compress: client %u from another context", b);
+  }
+  return ZP_OK;
+}
+
+extern "C" int zp_compress(zp_db* db, zp_client* const* clients, const uint32_t* dAns,
+                           const uint32_t* dCKO, uint32_t B, uint32_t* dT, void* stream) {
+  try {
+    if (!db || !dAns || !dCKO || !dT) return zp_set_error(ZP_EINVAL, "zp_compress: null argument");
+    int rc = check_compress_args(db, clients, B);
+    if (rc) return rc;
+    ZP_CUDA(cudaSetDevice(db->ctx->device));
+    return zp_launch_compress(db, clients, dAns, dCKO, B, dT, static_cast<cudaStream_t>(stream));
+  } catch (const std::bad_alloc&) {
+    return zp_set_error(ZP_ENOMEM, "zp_compress: host allocation failed");
+  }
+}
+
+extern "C" int zp_respond(zp_db* db, zp_client* const* clients, const uint32_t* dQ,
+                          const uint32_t* dCKO, uint32_t B, uint32_t* dAns, uint32_t* dT,
+                          void* stream) {
+  if (!db || !dQ || !dCKO || !dAns || !dT) return zp_set_error(ZP_EINVAL, "zp_respond: null argument");
+  int rc = check_compress_args(db, clients, B);
+  if (rc) return rc;
+  rc = zp_answer(db, dQ, B, dAns, stream);
+  if (rc) return rc;
+  return zp_compress(db, clients, dAns, dCKO, B, dT, stream);
+}
+
+extern "C" int zp_respond_host(zp_db* db, zp_client* const* clients, const uint32_t* hQ,
+                               const uint32_t* hCKO, uint32_t B, uint32_t* hT, uint32_t* hAns,
+                               void* stream) {
+  if (!db || !hQ || !hCKO || !hT) return zp_set_error(ZP_EINVAL, "zp_respond_host: null argument");
+  int rc = check_compress_args(db, clients, B);
+  if (rc) return rc;
+  zp_ctx* c = db->ctx;
+  ZP_CUDA(cudaSetDevice(c->device));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t qb = (size_t)B * db->C * 4, cb = (size_t)B * c->P.n * c->L * 4;
+  const size_t ab = (size_t)B * db->R * 4, tb = (size_t)B * db->d1p * c->L * 4;
+  if ((rc = zp_scratch_reserve(&db->s_q, qb)) || (rc = zp_scratch_reserve(&db->s_cko, cb)) ||
+      (rc = zp_scratch_reserve(&db->s_ans, ab)) || (rc = zp_scratch_reserve(&db->s_t, tb)))
+    return rc;
+  ZP_CUDA(cudaMemcpyAsync(db->s_q.p, hQ, qb, cudaMemcpyHostToDevice, st));
+  ZP_CUDA(cudaMemcpyAsync(db->s_cko.p, hCKO, cb, cudaMemcpyHostToDevice, st));
+  rc = zp_respond(db, clients, static_cast<uint32_t*>(db->s_q.p), static_cast<uint32_t*>(db->s_cko.p),
+                  B, static_cast<uint32_t*>(db->s_ans.p), static_cast<uint32_t*>(db->s_t.p), stream);
+  if (rc) return rc;
+  ZP_CUDA(cudaMemcpyAsync(hT, db->s_t.p, tb, cudaMemcpyDeviceToHost, st));
+  if (hAns) ZP_CUDA(cudaMemcpyAsync(hAns, db->s_ans.p, ab, cudaMemcpyDeviceToHost, st));
+  ZP_CUDA(cudaStreamSynchronize(st));
+  return ZP_OK;
+}

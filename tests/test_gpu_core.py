@@ -1,0 +1,249 @@
+"""GPU parity of the online Response against the oracle, through the C ABI.
+
+Everything is exact integer work, so every comparison is bit-exact."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import lwe, zippir
+from oracle.params import Params
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def zp():
+    from paper_2603_09190_gb300 import build as b
+    b.build()
+    import paper_2603_09190_gb300 as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def ctx(zp):
+    return zp.Context(0, n=1024, key_bits=2048, secret="uniform")
+
+
+def to_dev_db(zp, D):
+    R, C = D.shape
+    ld = zp.db_pitch(C)
+    buf = np.zeros((R, ld), dtype=np.uint8)
+    buf[:, :C] = D
+    return torch.from_numpy(buf).cuda(), ld
+
+
+def u32_dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.uint32).view(np.int32)).cuda()
+
+
+def u32_host(t):
+    return t.cpu().numpy().view(np.uint32)
+
+
+SHAPES = [(1, 1), (7, 7), (8, 8), (31, 1025), (1024, 1024), (1025, 31), (64, 257), (130, 4096),
+          (333, 9999), (2049, 700)]
+
+
+@pytest.mark.parametrize("R,C", SHAPES)
+def test_gemv_parity(zp, ctx, R, C):
+    D = synth.database(R, C, R * 7 + C)
+    q = synth.uniform_queries(1, C, R + C)[0]
+    dD, ld = to_dev_db(zp, D)
+    db = zp.Database(ctx, dD, R, C, ld)
+    got = u32_host(db.answer(u32_dev(q[None, :])))[0]
+    assert np.array_equal(got, lwe.matvec_mod_q(D, q))
+    db.close()
+
+
+def test_gemv_closed_forms(zp, ctx):
+    R, C = 300, 70000
+    D = np.full((R, C), 255, dtype=np.uint8)
+    dD, ld = to_dev_db(zp, D)
+    db = zp.Database(ctx, dD, R, C, ld)
+    q = np.full(C, 0xFFFFFFFF, dtype=np.uint32)
+    got = u32_host(db.answer(u32_dev(q[None, :])))[0]
+    assert np.all(got == np.uint32((-255 * C) % 2**32))
+    # unit query: column i
+    D2 = synth.database(R, C, 5)
+    dD2, _ = to_dev_db(zp, D2)
+    db2 = zp.Database(ctx, dD2, R, C, ld)
+    for i in (0, 12345, C - 1):
+        e = np.zeros(C, dtype=np.uint32)
+        e[i] = 1
+        got = u32_host(db2.answer(u32_dev(e[None, :])))[0]
+        assert np.array_equal(got, D2[:, i].astype(np.uint32))
+    db.close()
+    db2.close()
+
+
+@pytest.mark.parametrize("R,C,B", [(64, 64, 2), (100, 333, 5), (1024, 1024, 8), (257, 2000, 33)])
+def test_batched_answer_parity(zp, ctx, R, C, B):
+    D = synth.database(R, C, B)
+    Q = synth.uniform_queries(B, C, B + 1)
+    dD, ld = to_dev_db(zp, D)
+    db = zp.Database(ctx, dD, R, C, ld)
+    got = u32_host(db.answer(u32_dev(Q)))
+    assert np.array_equal(got, lwe.matmat_mod_q(D, Q.T).T)
+    db.close()
+
+
+@pytest.mark.parametrize("R,C,n", [(40, 30, 16), (300, 200, 64), (1024, 1024, 1024)])
+def test_hint_parity(zp, R, C, n):
+    c = zp.Context(0, n=n)
+    D = synth.database(R, C, n)
+    A = synth.seed_matrix(C, n, n)
+    dD, ld = to_dev_db(zp, D)
+    db = zp.Database(c, dD, R, C, ld)
+    H = torch.empty((R, n), dtype=torch.int32, device="cuda")
+    db.gen_hint(u32_dev(A), H)
+    assert np.array_equal(u32_host(H), lwe.hint_plus(D, A))
+    db.close()
+    c.close()
+
+
+def _e2e(zp, R, C, n, secret, seed, B=1):
+    P = Params(n=n, key_bits=2048, secret=secret)
+    c = zp.Context(0, n=n, secret=secret)
+    D = synth.database(R, C, seed)
+    A = synth.seed_matrix(C, n, seed)
+    Hn = lwe.hint_neg(D, A)
+    dD, ld = to_dev_db(zp, D)
+    db = zp.Database(c, dD, R, C, ld)
+    assert db.ell == P.ell and db.d1p == P.d1p(R)
+    db.gen_hint(u32_dev(A))
+    clients, qs = [], []
+    for b in range(B):
+        cl = zippir.setup(P, seed * 100 + b, sample_ck_r=False)
+        qy = zippir.query(cl, A, (seed * 31 + 7 * b) % C, seed * 100 + b + 50)
+        clients.append(cl)
+        qs.append(qy)
+    handles = [c.register_client(cl.pk.m) for cl in clients]
+    Q = u32_dev(np.stack([qy.qu for qy in qs]))
+    CKO = u32_dev(np.stack([synth.ints_to_limbs(qy.cko, 64) for qy in qs]))
+    ans, T = db.respond(handles, Q, CKO)
+    ans, T = u32_host(ans), u32_host(T)
+    for b in range(B):
+        want_ans = lwe.matvec_mod_q(D, qs[b].qu)
+        assert np.array_equal(ans[b], want_ans)
+        want_t = zippir.compress_rows(want_ans, Hn, qs[b].cko, clients[b].pk.m, P)
+        got_t = synth.limbs_to_ints(T[b])
+        assert got_t == want_t
+        rows = range(P.d1p(R))
+        rec = zippir.extract(clients[b], zippir.dec_k_shortcut(clients[b], Hn, rows), got_t, R)
+        assert np.array_equal(rec, D[:, qs[b].i0])
+    db.close()
+    c.close()
+
+
+def test_e2e_tiny_config(zp):
+    """1024 x 1024 database, n = 1024, 2048-bit key: ans and t bit-identical to the oracle,
+    and the client recovers its record from the GPU's response."""
+    _e2e(zp, 1024, 1024, 1024, "uniform", 1)
+
+
+@pytest.mark.parametrize("R,C,n,secret,seed,B", [
+    (27, 16, 32, "uniform", 2, 1), (28, 40, 32, "uniform", 3, 2), (100, 64, 48, "binary", 4, 1),
+    (500, 300, 128, "uniform", 5, 3), (49, 33, 1024, "binary", 6, 1)])
+def test_e2e_ragged(zp, R, C, n, secret, seed, B):
+    _e2e(zp, R, C, n, secret, seed, B)
+
+
+def test_compress_edge_values(zp):
+    """cko at its extremes (0 and m - 1) and answers at 2^32 - 1."""
+    R, C, n = 60, 32, 64
+    P = Params(n=n, key_bits=2048)
+    c = zp.Context(0, n=n)
+    D = synth.database(R, C, 8)
+    A = synth.seed_matrix(C, n, 8)
+    Hn = lwe.hint_neg(D, A)
+    dD, ld = to_dev_db(zp, D)
+    db = zp.Database(c, dD, R, C, ld)
+    db.gen_hint(u32_dev(A))
+    from oracle import paillier
+    pk, _ = paillier.keygen(2048, 77)
+    m = pk.m
+    cl = c.register_client(m)
+    ans = np.full(R, 0xFFFFFFFF, dtype=np.uint32)
+    for cko in ([m - 1] * n, [0] * n, [m - 1 if i % 2 else 0 for i in range(n)]):
+        T = db.compress([cl], u32_dev(ans[None, :]), u32_dev(synth.ints_to_limbs(cko, 64)[None]))
+        assert synth.limbs_to_ints(u32_host(T)[0]) == zippir.compress_rows(ans, Hn, cko, m, P)
+    db.close()
+    c.close()
+
+
+def test_update_rows_and_regenerate(zp):
+    R, C, n = 200, 96, 32
+    P = Params(n=n, key_bits=2048)
+    c = zp.Context(0, n=n)
+    D = synth.database(R, C, 9)
+    A = synth.seed_matrix(C, n, 9)
+    dD, ld = to_dev_db(zp, D)
+    db = zp.Database(c, dD, R, C, ld)
+    H = torch.empty((R, n), dtype=torch.int32, device="cuda")
+    db.gen_hint(u32_dev(A), H)
+    rows = np.array([3, 77, 199], dtype=np.uint32)
+    new = synth.database(3, C, 10)
+    db.update_rows(rows, torch.from_numpy(new).cuda())
+    assert db.stale_rows() == 3
+    from oracle import paillier
+    pk, _ = paillier.keygen(2048, 5)
+    cl = c.register_client(pk.m)
+    q = synth.uniform_queries(1, C, 11)
+    cko = synth.uniform_below(pk.m, n, 12)
+    with pytest.raises(zp.ZipPIRError) as ei:
+        db.respond([cl], u32_dev(q), u32_dev(synth.ints_to_limbs(cko, 64)[None]))
+    assert ei.value.code == zp.ZP_ESTATE
+    db.gen_hint(u32_dev(A), H, rows=rows)
+    assert db.stale_rows() == 0
+    D2 = D.copy()
+    D2[rows] = new
+    assert np.array_equal(u32_host(H), lwe.hint_plus(D2, A))
+    ans, T = db.respond([cl], u32_dev(q), u32_dev(synth.ints_to_limbs(cko, 64)[None]))
+    want_ans = lwe.matvec_mod_q(D2, q[0])
+    assert np.array_equal(u32_host(ans)[0], want_ans)
+    assert synth.limbs_to_ints(u32_host(T)[0]) == zippir.compress_rows(
+        want_ans, lwe.hint_neg(D2, A), cko, pk.m, P)
+    db.close()
+    c.close()
+
+
+def test_respond_host_matches_device(zp):
+    R, C, n = 300, 256, 64
+    c = zp.Context(0, n=n)
+    D = synth.database(R, C, 13)
+    A = synth.seed_matrix(C, n, 13)
+    dD, ld = to_dev_db(zp, D)
+    db = zp.Database(c, dD, R, C, ld)
+    db.gen_hint(u32_dev(A))
+    m = synth.random_odd_modulus(2048, 14)
+    cl = c.register_client(m)
+    q = synth.uniform_queries(2, C, 15)
+    cko = np.stack([synth.ints_to_limbs(synth.uniform_below(m, n, 16 + b), 64) for b in range(2)])
+    ans_d, T_d = db.respond([cl, cl], u32_dev(q), u32_dev(cko))
+    hans = np.empty((2, R), dtype=np.uint32)
+    T_h = db.respond_host([cl, cl], q, cko, hAns=hans)
+    assert np.array_equal(T_h, u32_host(T_d)) and np.array_equal(hans, u32_host(ans_d))
+    db.close()
+    c.close()
+
+
+def test_invalid_arguments_fail_loudly(zp, ctx):
+    D = synth.database(10, 16, 1)
+    dD, ld = to_dev_db(zp, D)
+    with pytest.raises(zp.ZipPIRError):
+        zp.zp_setup_db(ctx.handle, dD.data_ptr() + 1, 10, 16, 16)   # misaligned
+    with pytest.raises(zp.ZipPIRError):
+        zp.zp_setup_db(ctx.handle, dD.data_ptr(), 10, 16, 8)        # pitch < C
+    db = zp.Database(ctx, dD, 10, 16, ld)
+    with pytest.raises(zp.ZipPIRError) as ei:                      # no hint yet
+        db.compress([ctx.register_client(synth.random_odd_modulus(2048, 1))],
+                    torch.zeros((1, 10), dtype=torch.int32, device="cuda"),
+                    torch.zeros((1, 1024 * 64), dtype=torch.int32, device="cuda"))
+    assert ei.value.code == zp.ZP_ESTATE
+    with pytest.raises(zp.ZipPIRError):
+        ctx.register_client(2**2047)          # even
+    with pytest.raises(zp.ZipPIRError):
+        ctx.register_client(2**2046 + 1)      # too short
+    assert ctx.device_status() == 0
+    db.close()
