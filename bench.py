@@ -41,6 +41,8 @@ WORKLOADS = {
     "1gib": (32768, 32768, 1024, 1,
              "1 GiB database 32768x32768 u8 uniform mod 256, 1 query, n=1024, 2048-bit Paillier "
              "modulus: GEMV answer + compression"),
+    "256mib": (16384, 16384, 1024, 1,
+               "256 MiB database 16384x16384 u8 uniform mod 256, 1 query, n=1024, 2048-bit modulus"),
     "tiny": (1024, 1024, 1024, 1,
              "1 MiB database 1024x1024, 1 query, n=1024, 2048-bit modulus"),
     "batch64": (32768, 32768, 1024, 64,

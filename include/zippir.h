@@ -23,6 +23,8 @@
  *    launching anything if validation fails, and otherwise enqueue work on
  *    `stream`. Device buffers must not be reused by the caller before that work
  *    completes. The *_host entry points synchronise `stream` before returning.
+ *  - A context must outlive the databases and clients created from it; databases
+ *    and clients may be destroyed before or after one another.
  *  - All arithmetic is exact integer arithmetic; results are bit-identical to the
  *    definitions cited at each call.
  */

@@ -325,12 +325,14 @@ int zp_launch_compress(zp_db* db, zp_client* const* clients, const uint32_t* dAn
   }
   {
     dim3 grid((R + 3) / 4, B);
+    zp_clear_pending_error();
     ctx->launches++;
     k_vmul_simt<<<grid, 256, 0, st>>>(db->d_hneg, R, n, dCKO, V);
     ZP_CUDA(cudaGetLastError());
   }
   {
     dim3 grid((db->d1p + PACK_WARPS - 1) / PACK_WARPS, B);
+    zp_clear_pending_error();
     ctx->launches++;
     k_pack_reduce<<<grid, PACK_WARPS * 32, 0, st>>>(dAns, V, R, ctx->ell, db->d1p, ctx->gamma_w[0],
                                                     ctx->gamma_w[1], ctx->gamma_w[2], dcl, dT);

@@ -172,6 +172,7 @@ int zp_launch_gemv(zp_db* db, const uint32_t* dq, uint32_t* dans, cudaStream_t s
   {
     const uint32_t total = nct * 256u;
     const uint32_t blocks = (total + 255) / 256;
+    zp_clear_pending_error();
     ctx->launches++;
     k_qplanes<<<blocks, 256, 0, st>>>(dq, db->C, nct, qp, dans, db->R);
   }
@@ -182,6 +183,7 @@ int zp_launch_gemv(zp_db* db, const uint32_t* dq, uint32_t* dans, cudaStream_t s
   const uint64_t T = (uint64_t)nrb * nct;
   uint64_t grid = (uint64_t)ctx->num_sms * CTAS_PER_SM;
   if (grid > T) grid = T;
+  zp_clear_pending_error();
   ctx->launches++;
   k_gemv<<<(unsigned)grid, (NCW + 1) * 32, SMEM_BYTES, st>>>(db->tmap_gemv, qp, dans, db->R, nrb,
                                                              nct, ctx->d_status);

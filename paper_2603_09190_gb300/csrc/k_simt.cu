@@ -151,6 +151,7 @@ int zp_launch_rowsum(const zp_db* db, const uint32_t* rows, uint32_t nrows, cuda
   const uint32_t cnt = rows ? nrows : db->R;
   if (cnt == 0) return ZP_OK;
   const uint32_t blocks = (cnt * 32u + 255u) / 256u;
+  zp_clear_pending_error();
   db->ctx->launches++;
   k_rowsum<<<blocks, 256, 0, st>>>(db->dD, db->ld, db->R, db->C, rows, nrows, db->d_rowsum);
   ZP_CUDA(cudaGetLastError());
@@ -164,6 +165,7 @@ int zp_launch_answer_simt(zp_db* db, const uint32_t* dQ, uint32_t B, uint32_t ld
   const uint64_t qsb = ldq ? ldq : 1u;
   const uint64_t qsc = ldq ? 1u : B;
   dim3 grid((Rrows + SB_R - 1) / SB_R, (B + SB_Q - 1) / SB_Q);
+  zp_clear_pending_error();
   db->ctx->launches++;
   k_answer_simt<<<grid, 256, 0, st>>>(dDrows, ld, Rrows, db->C, dQ, qsb, qsc, B, dOut,
                                       out_stride_b, out_stride_r);
@@ -176,6 +178,7 @@ int zp_launch_hint_post(zp_db* db, const uint32_t* src, const uint32_t* rows, ui
   const uint32_t n = db->ctx->P.n;
   const uint64_t total = (uint64_t)cnt * n;
   if (total == 0) return ZP_OK;
+  zp_clear_pending_error();
   db->ctx->launches++;
   k_hint_post<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(src, cnt, n, rows, dH, db->d_hneg);
   ZP_CUDA(cudaGetLastError());

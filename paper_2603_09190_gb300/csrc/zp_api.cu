@@ -235,6 +235,7 @@ extern "C" int zp_setup_db(zp_ctx* c, const uint8_t* dD, uint32_t R, uint32_t C,
     ZP_CUDA(cudaSetDevice(c->device));
     zp_db* db = new zp_db();
     db->ctx = c;
+    db->device = c->device;
     db->dD = dD;
     db->R = R;
     db->C = C;
@@ -288,7 +289,7 @@ extern "C" int zp_stale_rows(const zp_db* db, uint32_t* count) {
 
 extern "C" int zp_db_destroy(zp_db* db) {
   if (!db) return ZP_OK;
-  cudaSetDevice(db->ctx->device);
+  cudaSetDevice(db->device);
   cudaDeviceSynchronize();
   if (db->d_rowsum) cudaFree(db->d_rowsum);
   if (db->d_hneg) cudaFree(db->d_hneg);
@@ -358,6 +359,7 @@ extern "C" int zp_gen_hint(zp_db* db, const uint32_t* dA, uint32_t* dH, const ui
     uint8_t* base = static_cast<uint8_t*>(db->s_misc.p) + ((size_t)nrows * 4 + 255) / 256 * 256;
     uint8_t* dG = base;
     uint32_t* dHc = reinterpret_cast<uint32_t*>(base + gather_bytes);
+    zp_clear_pending_error();
     c->launches++;
     rc = zp_launch_copy_rows(db->dD, db->ld, dG, ldc, db->C, dRows, nrows, 1, st);
     if (!rc) rc = zp_launch_answer_simt(db, dA, n, 0, dHc, 1, n, dG, nrows, ldc, st);
@@ -385,6 +387,7 @@ extern "C" int zp_update_rows(zp_db* db, const uint32_t* hRows, uint32_t k, cons
     uint32_t* dRows = nullptr;
     int rc = stage_rows(db, hRows, k, 0, &dRows, st);
     if (rc) return rc;
+    zp_clear_pending_error();
     db->ctx->launches++;
     rc = zp_launch_copy_rows(dNew, db->C, const_cast<uint8_t*>(db->dD), db->ld, db->C, dRows, k, 0, st);
     if (!rc) rc = zp_launch_rowsum(db, dRows, k, st);
@@ -455,6 +458,7 @@ extern "C" int zp_register_client(zp_ctx* c, const uint32_t* hM, uint32_t L, zp_
     ZP_CUDA(cudaSetDevice(c->device));
     zp_client* cl = new zp_client();
     cl->ctx = c;
+    cl->device = c->device;
     cl->L = L;
     cl->d_m = nullptr;
     cl->d_mu = nullptr;
@@ -480,7 +484,7 @@ extern "C" int zp_register_client(zp_ctx* c, const uint32_t* hM, uint32_t L, zp_
 
 extern "C" int zp_client_destroy(zp_client* cl) {
   if (!cl) return ZP_OK;
-  cudaSetDevice(cl->ctx->device);
+  cudaSetDevice(cl->device);
   cudaDeviceSynchronize();
   if (cl->d_m) cudaFree(cl->d_m);
   if (cl->d_mu) cudaFree(cl->d_mu);

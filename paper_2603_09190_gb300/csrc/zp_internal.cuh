@@ -35,6 +35,7 @@ struct zp_ctx {
 
 struct zp_client {
   zp_ctx* ctx;
+  int device;
   uint32_t L;
   uint32_t* d_m;   // L limbs
   uint32_t* d_mu;  // L+1 limbs: floor(2^(64 L) / m)  (Barrett constant)
@@ -47,6 +48,7 @@ struct zp_scratch {
 
 struct zp_db {
   zp_ctx* ctx;
+  int device;
   const uint8_t* dD;  // caller-owned, R rows of ld bytes
   uint32_t R, C;
   uint64_t ld;
@@ -72,6 +74,10 @@ int zp_cuda_check(cudaError_t e, const char* what);
   } while (0)
 
 int zp_scratch_reserve(zp_scratch* s, size_t bytes);
+
+// Clears a pending runtime error left by an unrelated earlier call, so that the
+// check after a launch reports only that launch.
+static inline void zp_clear_pending_error() { (void)cudaGetLastError(); }
 
 // tensor-map encoding through the driver entry point (no link-time libcuda dependency)
 int zp_encode_tmap_2d(CUtensorMap* map, CUtensorMapDataType dt, const void* base, uint64_t dim0,
