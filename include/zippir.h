@@ -164,6 +164,15 @@ int zp_update_rows(zp_db* db, const uint32_t* hRows, uint32_t k, const uint8_t* 
 /* Number of hint rows marked stale by zp_update_rows and not yet regenerated. */
 int zp_stale_rows(const zp_db* db, uint32_t* count);
 
+/* Selects kernel variants for this context (tuning and cross-checking):
+ *   "answer_path":   0 auto (GEMV for one query, tensor cores otherwise and for the
+ *                    hint), 1 CUDA-core dp4a kernels for every batch and the hint,
+ *                    2 tensor cores also for a single query;
+ *   "compress_path": 0 auto (tensor cores when n <= 1024), 1 CUDA-core products,
+ *                    2 tensor cores (ZP_EUNSUPPORTED at call time if n > 1024).
+ * Every variant computes the same exact result. Errors: ZP_EINVAL (unknown name or value). */
+int zp_set_option(zp_ctx* ctx, const char* name, int64_t value);
+
 /* Number of kernels this context has launched so far (all entry points). */
 int zp_kernel_launches(const zp_ctx* ctx, uint64_t* count);
 

@@ -29,7 +29,7 @@ EXPORTS = [
     "zp_version", "zp_last_error", "zp_init", "zp_ctx_destroy", "zp_setup_db", "zp_db_info",
     "zp_db_destroy", "zp_gen_hint", "zp_answer", "zp_register_client", "zp_client_destroy",
     "zp_compress", "zp_respond", "zp_respond_host", "zp_update_rows", "zp_stale_rows",
-    "zp_device_status", "zp_kernel_launches",
+    "zp_device_status", "zp_kernel_launches", "zp_set_option",
 ]
 
 
@@ -76,6 +76,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "zp_stale_rows": (i32, [vp, ctypes.POINTER(u32)]),
         "zp_device_status": (i32, [vp, ctypes.POINTER(u32)]),
         "zp_kernel_launches": (i32, [vp, ctypes.POINTER(u64)]),
+        "zp_set_option": (i32, [vp, ctypes.c_char_p, ctypes.c_int64]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -228,6 +229,10 @@ def zp_device_status(ctx: int) -> int:
     return c.value
 
 
+def zp_set_option(ctx: int, name: str, value: int):
+    _check(load_library().zp_set_option(ctx, name.encode(), int(value)))
+
+
 def zp_kernel_launches(ctx: int) -> int:
     c = ctypes.c_uint64()
     _check(load_library().zp_kernel_launches(ctx, ctypes.byref(c)))
@@ -251,6 +256,12 @@ class Context:
 
     def kernel_launches(self) -> int:
         return zp_kernel_launches(self.handle)
+
+    def set_option(self, name: str, value):
+        """Kernel-variant selection: name in {"answer_path", "compress_path"},
+        value in {"auto", "simt", "tc"} (or 0/1/2)."""
+        v = {"auto": 0, "simt": 1, "tc": 2}.get(value, value)
+        zp_set_option(self.handle, name, v)
 
     def close(self):
         if self.handle:

@@ -36,7 +36,7 @@ __device__ __forceinline__ void mac96(uint32_t& c0, uint32_t& c1, uint32_t& c2, 
 // ------------------------------------------------------------------ V on CUDA cores
 // grid (ceil(R/4), B), block 256 = 4 rows x 64 limbs.
 __global__ void __launch_bounds__(256)
-    k_vmul_simt(const uint32_t* __restrict__ hneg, uint32_t R, uint32_t n,
+    k_vmul_simt(const uint32_t* __restrict__ hneg, uint32_t R, uint32_t Rp, uint32_t n,
                 const uint32_t* __restrict__ cko, uint32_t* __restrict__ V) {
   __shared__ uint32_t S[4][ZP_MAX_L][3];
   const uint32_t b = blockIdx.y;
@@ -54,7 +54,7 @@ __global__ void __launch_bounds__(256)
   __syncthreads();
   if (l == 0 && row < R) {
     // word w = S[w].lo + S[w-1].mid + S[w-2].hi + carry
-    uint32_t* out = V + ((uint64_t)b * R + row) * VW;
+    uint32_t* out = V + ((uint64_t)b * Rp + row) * VW;
     uint64_t carry = 0;
     for (int w = 0; w < VW; ++w) {
       uint64_t s = carry;
@@ -207,8 +207,9 @@ struct ClientPtrs {
 // grid (ceil(d1p / PACK_WARPS), B), block PACK_WARPS warps. Requires L == ZP_MAX_L.
 __global__ void __launch_bounds__(PACK_WARPS * 32)
     k_pack_reduce(const uint32_t* __restrict__ ans, const uint32_t* __restrict__ V, uint32_t R,
-                  uint32_t ell, uint32_t d1p, uint32_t g0, uint32_t g1, uint32_t g2,
-                  const ClientPtrs* __restrict__ cl, uint32_t* __restrict__ T) {
+                  uint32_t Rp, uint32_t nplanes, uint32_t ell, uint32_t d1p, uint32_t g0,
+                  uint32_t g1, uint32_t g2, const ClientPtrs* __restrict__ cl,
+                  uint32_t* __restrict__ T) {
   __shared__ PackWarpSmem sm[PACK_WARPS];
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t b = blockIdx.y;
@@ -226,7 +227,7 @@ __global__ void __launch_bounds__(PACK_WARPS * 32)
 
   // ---- Horner: X <- X * gamma + W_j, j = ell-1 .. 0 (gamma = g0 + g1 2^32 + g2 2^64)
   const uint32_t* ansb = ans + (uint64_t)b * R;
-  const uint32_t* Vb = V + (uint64_t)b * R * VW;
+  const uint32_t* Vb = V + (uint64_t)b * nplanes * Rp * VW;
   for (int j = (int)ell - 1; j >= 0; --j) {
     const uint32_t row = rp * ell + (uint32_t)j;
     const bool have = row < R;
@@ -246,7 +247,19 @@ __global__ void __launch_bounds__(PACK_WARPS * 32)
       s += (uint32_t)((uint64_t)g2 * x2);
       s += (uint32_t)(((uint64_t)g2 * x3) >> 32);
       if (have) {
-        if (x < VW) s += Vb[(uint64_t)row * VW + x];
+        // W_j = ans + sum_a V_a << 8a  (plane a of the compression product)
+        if (x < VW) {
+          for (uint32_t a = 0; a < nplanes; ++a) {
+            const uint32_t* Vr = Vb + ((uint64_t)a * Rp + row) * VW;
+            const uint32_t cur = Vr[x];
+            if (a == 0) {
+              s += cur;
+            } else {
+              const uint32_t prev = x >= 1 ? Vr[x - 1] : 0u;
+              s += (cur << (8 * a)) | (prev >> (32 - 8 * a));
+            }
+          }
+        }
         if (x == 0) s += ansb[row];
       }
       v[t] = s;
@@ -309,7 +322,11 @@ int zp_launch_compress(zp_db* db, zp_client* const* clients, const uint32_t* dAn
                        const uint32_t* dCKO, uint32_t B, uint32_t* dT, cudaStream_t st) {
   zp_ctx* ctx = db->ctx;
   const uint32_t R = db->R, n = ctx->P.n;
-  int rc = zp_scratch_reserve(&db->s_v, (size_t)B * R * VW * sizeof(uint32_t));
+  if (ctx->compress_path == ZP_PATH_TC && n > 1024)
+    return zp_set_error(ZP_EUNSUPPORTED, "tensor-core compression needs n <= 1024");
+  const bool tc = ctx->compress_path != ZP_PATH_SIMT && n <= 1024;
+  const uint32_t nplanes = tc ? 4u : 1u;
+  int rc = zp_scratch_reserve(&db->s_v, (size_t)B * nplanes * db->Rp * VW * sizeof(uint32_t));
   if (rc) return rc;
   rc = zp_scratch_reserve(&db->s_clients, (size_t)B * sizeof(ClientPtrs));
   if (rc) return rc;
@@ -323,18 +340,22 @@ int zp_launch_compress(zp_db* db, zp_client* const* clients, const uint32_t* dAn
     delete[] h;
     if (e != cudaSuccess) return zp_cuda_check(e, "cudaMemcpyAsync(clients)");
   }
-  {
+  if (tc) {
+    rc = zp_launch_vmul_tc(db, dCKO, B, V, st);
+    if (rc) return rc;
+  } else {
     dim3 grid((R + 3) / 4, B);
     zp_clear_pending_error();
     ctx->launches++;
-    k_vmul_simt<<<grid, 256, 0, st>>>(db->d_hneg, R, n, dCKO, V);
+    k_vmul_simt<<<grid, 256, 0, st>>>(db->d_hneg, R, db->Rp, n, dCKO, V);
     ZP_CUDA(cudaGetLastError());
   }
   {
     dim3 grid((db->d1p + PACK_WARPS - 1) / PACK_WARPS, B);
     zp_clear_pending_error();
     ctx->launches++;
-    k_pack_reduce<<<grid, PACK_WARPS * 32, 0, st>>>(dAns, V, R, ctx->ell, db->d1p, ctx->gamma_w[0],
+    k_pack_reduce<<<grid, PACK_WARPS * 32, 0, st>>>(dAns, V, R, db->Rp, nplanes, ctx->ell, db->d1p,
+                                                    ctx->gamma_w[0],
                                                     ctx->gamma_w[1], ctx->gamma_w[2], dcl, dT);
     ZP_CUDA(cudaGetLastError());
   }

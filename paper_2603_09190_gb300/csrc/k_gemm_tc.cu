@@ -1,0 +1,637 @@
+// k_gemm_tc.cu -- exact integer products of byte matrices on the 5th-generation tensor
+// cores (tcgen05.mma kind::f16, fp32 accumulators in tensor memory).
+//
+//   C[m][n] = sum_k A[m][k] * B[n][k],   A, B with entries in [0, 255].
+//
+// sm_103a has no integer (kind::i8) tensor-core instruction, so the bytes are fed as
+// fp16, which holds every integer of [-2048, 2048] exactly. Both operands are centred,
+// A' = A - 128 and B' = B - 128, so that a product is at most 2^14 in magnitude and a
+// sum of 1024 of them at most 2^24: every partial sum of a 1024-long K chunk is an
+// integer that fp32 represents exactly. The accumulator of each chunk is drained to
+// int32, chunks are summed in 32-bit integers, and the centring is undone with
+//   sum_k A B = sum_k A'B' + 128 sum_k A + 128 sum_k B - 16384 Kp
+// (sums over the zero-padded K range Kp). All integer arithmetic wraps mod 2^32,
+// which is exact for the mod-2^32 answers and, for the compression products, never
+// wraps because every true value is below 2^31.
+//
+// Uses (template MODE):
+//   MODE_ANS  batched LWE answers, ans[b][r] = sum_c D[r][c] Q[b][c] mod 2^32
+//             (Algorithm "ZipPIR", Response, first line): A = D (R x C bytes),
+//             B = the 4 byte planes of BT queries (N = 4 BT rows), recombined as
+//             sum_a 2^(8a) P_a in the epilogue;
+//   MODE_HINT the global hint H+ = D A mod 2^32 (Algorithm "ZipPIR" caption): as
+//             MODE_ANS with the columns of A as queries, written row-major R x n;
+//   MODE_CMP  the compression products V_a[r] = sum_i Hbyte_a[r][i] cko[i]
+//             (Algorithm "ZipPIR", Response, second line): A = the 4 byte planes of
+//             the negated hint, rows ordered (32 rows of plane 0, of plane 1, ...),
+//             B = the 256 bytes of every cko[i] (N = 256), K = n <= 1024; the
+//             epilogue turns the 256 byte-column sums of a row into a 67-word
+//             integer (carry propagation) and writes it.
+//
+// Structure (one CTA per SM, persistent over output tiles of 128 x N):
+//   warp 0      TMA producer: the A tile as bytes (128 x 64, 8 KiB) into a byte ring,
+//               the B tile as fp16 (N x 64, 128-byte swizzle) into the operand ring;
+//   warp 1      allocates 512 TMEM columns (two 256-column accumulators) and one
+//               elected lane issues the MMAs (4 x K=16 per K block) and the commits;
+//   warps 4-7   epilogue: tcgen05.ld of their 32-lane TMEM quarter, int conversion,
+//               chunk accumulation, correction, output;
+//   warps 8-11  converters: byte tile -> centred fp16 in the swizzled operand layout.
+// Every mbarrier wait is bounded; a wait that gives up raises a CTA-wide abort flag and
+// a bit in the context's status word, and every role then leaves its loop.
+#include <cuda_fp16.h>
+
+#include "zp_internal.cuh"
+
+namespace {
+
+constexpr int BM = 128;
+constexpr int BK = 64;
+constexpr int A16_BYTES = BM * BK * 2;       // 16 KiB
+constexpr int B_MAX_BYTES = 256 * BK * 2;    // 32 KiB
+constexpr int OP_STAGE = A16_BYTES + B_MAX_BYTES;
+constexpr int U8_STAGE = BM * BK;            // 8 KiB
+constexpr int SU = 4;
+constexpr int KCHUNK = 16;                   // K blocks per exact fp32 accumulation
+constexpr int NTHREADS = 384;
+constexpr int STG_PITCH = 67;                // words per staged row (odd: no bank conflicts)
+constexpr int STG_BYTES = 4 * 32 * STG_PITCH * 4;
+
+enum { MODE_ANS = 0, MODE_HINT = 1, MODE_CMP = 2 };
+
+template <int MODE>
+struct Cfg {
+  static constexpr int SO = (MODE == MODE_CMP) ? 3 : 4;
+  static constexpr int STG = (MODE == MODE_CMP) ? STG_BYTES : 0;
+  static constexpr int SMEM = SO * OP_STAGE + SU * U8_STAGE + STG + 1024 + 512;
+};
+
+struct GemmArgs {
+  uint32_t num_m_tiles, num_n_tiles, N, nkb, Kp;
+  uint32_t Mvalid;            // ANS/HINT: R (rows of D); CMP: R (answer rows)
+  uint32_t Bvalid;            // ANS: queries; HINT: n; CMP: queries
+  const uint32_t* rowsumA;    // raw byte sums of A rows
+  const uint32_t* colsum;     // ANS/HINT: [b][4] plane sums; CMP: [b][256] byte sums
+  uint32_t* out;
+  uint64_t out_ld;            // ANS: R; HINT: n
+  uint32_t Rp;                // CMP: plane stride (rows) of the output
+  uint32_t* status;
+};
+
+__device__ __forceinline__ uint32_t cvt_rn(uint32_t fbits) {
+  return (uint32_t)__float2int_rn(__uint_as_float(fbits));
+}
+
+// 16 bytes -> 16 centred fp16 (v - 128), exact: (0x6400 | v) is fp16 1024 + v.
+__device__ __forceinline__ void bytes_to_centred_f16(uint32_t w, uint32_t& lo, uint32_t& hi) {
+  const __half2 off = __halves2half2(__ushort_as_half(0x6480), __ushort_as_half(0x6480));  // 1152
+  uint32_t p0 = __byte_perm(w, 0x64646464u, 0x4140);
+  uint32_t p1 = __byte_perm(w, 0x64646464u, 0x4342);
+  __half2 h0 = __hsub2(*reinterpret_cast<__half2*>(&p0), off);
+  __half2 h1 = __hsub2(*reinterpret_cast<__half2*>(&p1), off);
+  lo = *reinterpret_cast<uint32_t*>(&h0);
+  hi = *reinterpret_cast<uint32_t*>(&h1);
+}
+
+// Warp-uniform bounded wait: lane 0 waits, the whole warp takes its verdict (the
+// tcgen05.ld that follows must be executed by all 32 lanes).
+__device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity,
+                                          volatile uint32_t* abort_flag, uint32_t* status) {
+  uint32_t ok = 1;
+  if ((threadIdx.x & 31) == 0)
+    ok = mbar_wait_abortable(bar, parity, abort_flag, status, ZP_DEV_TIMEOUT_GEMM) ? 1u : 0u;
+  ok = __shfl_sync(0xffffffffu, ok, 0);
+  if (ok) (void)mbar_try_wait(bar, parity);  // each lane observes the completed phase itself
+  return ok != 0;
+}
+
+template <int MODE, int BT>
+__global__ void __launch_bounds__(NTHREADS, 1)
+    k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+              const GemmArgs args) {
+  using C = Cfg<MODE>;
+  constexpr int SO = C::SO;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                             ~static_cast<uintptr_t>(1023));
+  uint8_t* op_ring = smem;                                   // SO x (A16 | B)
+  uint8_t* u8_ring = op_ring + SO * OP_STAGE;                // SU x 8 KiB
+  uint32_t* stg = reinterpret_cast<uint32_t*>(u8_ring + SU * U8_STAGE);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(u8_ring + SU * U8_STAGE + C::STG);
+  uint64_t* u8_full = bars;
+  uint64_t* u8_empty = u8_full + SU;
+  uint64_t* op_full = u8_empty + SU;
+  uint64_t* op_empty = op_full + SO;
+  uint64_t* acc_full = op_empty + SO;
+  uint64_t* acc_empty = acc_full + 2;
+  uint64_t* mma_done = acc_empty + 2;
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(mma_done + 1);
+  volatile uint32_t* abort_flag = tmem_holder + 1;
+
+  const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t num_tiles = args.num_m_tiles * args.num_n_tiles;
+  const uint32_t N = args.N, nkb = args.nkb;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < SU; ++s) {
+      mbar_init(&u8_full[s], 1);
+      mbar_init(&u8_empty[s], 4);
+    }
+    for (int s = 0; s < SO; ++s) {
+      mbar_init(&op_full[s], 1 + 4);
+      mbar_init(&op_empty[s], 1);
+    }
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(&acc_full[s], 1);
+      mbar_init(&acc_empty[s], 4);
+    }
+    mbar_init(mma_done, 1);
+    *abort_flag = 0u;
+    fence_mbar_init();
+  }
+  if (warp == 1) {
+    tmem_alloc(tmem_holder, 512);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_holder;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ TMA producer
+    if (lane == 0) {
+      prefetch_tmap(&tmA);
+      prefetch_tmap(&tmB);
+      uint32_t cnt = 0;
+      bool ok = true;
+      for (uint32_t tile = blockIdx.x; ok && tile < num_tiles; tile += gridDim.x) {
+        const uint32_t nt = tile % args.num_n_tiles, mt = tile / args.num_n_tiles;
+        for (uint32_t kb = 0; kb < nkb; ++kb, ++cnt) {
+          const uint32_t su = cnt % SU, ru = cnt / SU;
+          if (ru > 0 && !mbar_wait_abortable(&u8_empty[su], (ru - 1) & 1u, abort_flag,
+                                             args.status, ZP_DEV_TIMEOUT_GEMM)) {
+            ok = false;
+            break;
+          }
+          mbar_arrive_expect_tx(&u8_full[su], U8_STAGE);
+          tma_load_2d(u8_ring + su * U8_STAGE, &tmA, (int32_t)(kb * BK), (int32_t)(mt * BM),
+                      &u8_full[su]);
+          const uint32_t so = cnt % SO, ro = cnt / SO;
+          if (ro > 0 && !mbar_wait_abortable(&op_empty[so], (ro - 1) & 1u, abort_flag,
+                                             args.status, ZP_DEV_TIMEOUT_GEMM)) {
+            ok = false;
+            ++cnt;
+            break;
+          }
+          mbar_arrive_expect_tx(&op_full[so], N * BK * 2);
+          tma_load_2d(op_ring + so * OP_STAGE + A16_BYTES, &tmB, (int32_t)(kb * BK),
+                      (int32_t)(nt * N), &op_full[so]);
+        }
+      }
+      // Stay until the copies issued last have landed (bounded, ignores the abort flag).
+      const uint32_t f_u = cnt > (uint32_t)SU ? cnt - SU : 0;
+      for (uint32_t i = f_u; i < cnt; ++i)
+        mbar_wait_bounded(&u8_full[i % SU], (i / SU) & 1u, args.status, ZP_DEV_TIMEOUT_GEMM);
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      const uint32_t idesc = idesc_f16_f32(BM, N);
+      uint32_t cnt = 0, acc_cnt = 0;
+      bool ok = true;
+      for (uint32_t tile = blockIdx.x; ok && tile < num_tiles; tile += gridDim.x) {
+        uint32_t a = 0;
+        for (uint32_t kb = 0; kb < nkb; ++kb, ++cnt) {
+          const uint32_t kin = kb % KCHUNK;
+          if (kin == 0) {
+            a = acc_cnt & 1u;
+            const uint32_t ra = acc_cnt >> 1;
+            if (ra > 0 && !mbar_wait_abortable(&acc_empty[a], (ra - 1) & 1u, abort_flag,
+                                               args.status, ZP_DEV_TIMEOUT_GEMM)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+          }
+          const uint32_t so = cnt % SO, ro = cnt / SO;
+          if (!mbar_wait_abortable(&op_full[so], ro & 1u, abort_flag, args.status,
+                                   ZP_DEV_TIMEOUT_GEMM)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t abase = smem_u32(op_ring + so * OP_STAGE);
+          const uint32_t bbase = abase + A16_BYTES;
+          const uint64_t ad = sdesc_k_sw128(abase), bd = sdesc_k_sw128(bbase);
+#pragma unroll
+          for (uint32_t kk = 0; kk < BK / 16; ++kk)
+            umma_f16(tmem_base + a * 256u, ad + 2u * kk, bd + 2u * kk, idesc,
+                     (kin > 0 || kk > 0) ? 1u : 0u);
+          umma_commit(&op_empty[so]);
+          if (kin == KCHUNK - 1 || kb == nkb - 1) {
+            umma_commit(&acc_full[a]);
+            ++acc_cnt;
+          }
+        }
+      }
+      // every MMA issued has completed before TMEM is released
+      umma_commit(mma_done);
+      mbar_wait_bounded(mma_done, 0, args.status, ZP_DEV_TIMEOUT_GEMM);
+    }
+    __syncwarp();
+  } else if (warp >= 8) {
+    // ------------------------------------------------------------ converters
+    const uint32_t ct = threadIdx.x - 256;  // 0..127
+    uint32_t cnt = 0;
+    bool ok = true;
+    for (uint32_t tile = blockIdx.x; ok && tile < num_tiles; tile += gridDim.x) {
+      for (uint32_t kb = 0; kb < nkb; ++kb, ++cnt) {
+        const uint32_t su = cnt % SU, ru = cnt / SU;
+        const uint32_t so = cnt % SO, ro = cnt / SO;
+        if (!mbar_wait_abortable(&u8_full[su], ru & 1u, abort_flag, args.status,
+                                 ZP_DEV_TIMEOUT_GEMM) ||
+            (ro > 0 && !mbar_wait_abortable(&op_empty[so], (ro - 1) & 1u, abort_flag,
+                                            args.status, ZP_DEV_TIMEOUT_GEMM))) {
+          ok = false;
+          break;
+        }
+        const uint8_t* src = u8_ring + su * U8_STAGE;
+        uint8_t* dst = op_ring + so * OP_STAGE;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const uint32_t idx = ct + 128u * i;
+          const uint32_t row = idx >> 2, ch = idx & 3u;
+          const uint4 v = *reinterpret_cast<const uint4*>(src + row * 64 + ch * 16);
+          uint4 o0, o1;
+          bytes_to_centred_f16(v.x, o0.x, o0.y);
+          bytes_to_centred_f16(v.y, o0.z, o0.w);
+          bytes_to_centred_f16(v.z, o1.x, o1.y);
+          bytes_to_centred_f16(v.w, o1.z, o1.w);
+          const uint32_t sw = row & 7u;
+          *reinterpret_cast<uint4*>(dst + row * 128 + (((2 * ch) ^ sw) << 4)) = o0;
+          *reinterpret_cast<uint4*>(dst + row * 128 + (((2 * ch + 1) ^ sw) << 4)) = o1;
+        }
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) {
+          mbar_arrive(&op_full[so]);
+          mbar_arrive(&u8_empty[su]);
+        }
+      }
+    }
+  } else if (warp >= 4) {
+    // ------------------------------------------------------------ epilogue
+    const uint32_t e = warp - 4;  // TMEM lane quarter
+    const uint32_t lane_addr = (32u * e) << 16;
+    uint32_t acc_cnt = 0;
+    bool ok = true;
+    const uint32_t nchunks = (nkb + KCHUNK - 1) / KCHUNK;
+    for (uint32_t tile = blockIdx.x; ok && tile < num_tiles; tile += gridDim.x) {
+      const uint32_t nt = tile % args.num_n_tiles, mt = tile / args.num_n_tiles;
+      if constexpr (MODE == MODE_CMP) {
+        // single chunk (n <= 1024): byte-column sums -> 67-word integer
+        const uint32_t a = acc_cnt & 1u, ra = acc_cnt >> 1;
+        if (!warp_wait(&acc_full[a], ra & 1u, abort_flag, args.status)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t m = mt * BM + e * 32 + lane;  // row of A (plane e of answer row 32 mt + lane)
+        const uint32_t b = nt;
+        const uint32_t corr_row = 128u * __ldg(args.rowsumA + m) - 16384u * args.Kp;
+        const uint32_t* cs = args.colsum + (uint64_t)b * 256;
+        uint32_t* myst = stg + (e * 32 + lane) * STG_PITCH;
+        uint64_t carry = 0;
+#pragma unroll 1
+        for (int g = 0; g < 8; ++g) {
+          uint32_t r[32];
+          tmem_ld32(tmem_base + lane_addr + a * 256u + 32u * g, r);
+          tmem_wait_ld();
+#pragma unroll
+          for (int w = 0; w < 8; ++w) {
+            uint64_t s = carry;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              const int col = 32 * g + 4 * w + j;
+              const uint32_t p = cvt_rn(r[4 * w + j]) + corr_row + 128u * __ldg(cs + col);
+              s += (uint64_t)p << (8 * j);
+            }
+            myst[8 * g + w] = (uint32_t)s;
+            carry = s >> 32;
+          }
+        }
+        myst[64] = (uint32_t)carry;
+        myst[65] = (uint32_t)(carry >> 32);
+        myst[66] = 0u;
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&acc_empty[a]);
+        ++acc_cnt;
+        // coalesced copy of this warp's 32 rows x 67 words
+        uint32_t* dst = args.out + (((uint64_t)b * 4 + e) * args.Rp + (uint64_t)mt * 32) * ZP_VW;
+        const uint32_t* src = stg + e * 32 * STG_PITCH;
+        for (uint32_t idx = lane; idx < 32u * ZP_VW; idx += 32) {
+          const uint32_t rr = idx / ZP_VW, ww = idx % ZP_VW;
+          dst[idx] = src[rr * STG_PITCH + ww];
+        }
+        __syncwarp();
+      } else {
+        uint32_t acc[BT];
+#pragma unroll
+        for (int i = 0; i < BT; ++i) acc[i] = 0u;
+        for (uint32_t c = 0; c < nchunks; ++c) {
+          const uint32_t a = acc_cnt & 1u, ra = acc_cnt >> 1;
+          if (!warp_wait(&acc_full[a], ra & 1u, abort_flag, args.status)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+#pragma unroll
+          for (int g = 0; g < (4 * BT) / 32; ++g) {
+            uint32_t r[32];
+            tmem_ld32(tmem_base + lane_addr + a * 256u + 32u * g, r);
+            tmem_wait_ld();
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              const int col = 32 * g + j;
+              const int pl = col / BT, bl = col % BT;
+              acc[bl] += cvt_rn(r[j]) << (8 * pl);
+            }
+          }
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&acc_empty[a]);
+          ++acc_cnt;
+        }
+        if (!ok) break;
+        const uint32_t r = mt * BM + e * 32 + lane;
+        if (r < args.Mvalid) {
+          const uint32_t rowterm = 128u * __ldg(args.rowsumA + r) * 0x01010101u;
+          const uint32_t kterm = 16384u * args.Kp * 0x01010101u;
+          if constexpr (MODE == MODE_ANS) {
+#pragma unroll
+            for (int bl = 0; bl < BT; ++bl) {
+              const uint32_t b = nt * BT + bl;
+              if (b < args.Bvalid) {
+                const uint4 cq = *reinterpret_cast<const uint4*>(args.colsum + (uint64_t)b * 4);
+                const uint32_t qterm =
+                    128u * (cq.x + (cq.y << 8) + (cq.z << 16) + (cq.w << 24)) - kterm;
+                args.out[(uint64_t)b * args.out_ld + r] = acc[bl] + rowterm + qterm;
+              }
+            }
+          } else {
+            uint32_t* orow = args.out + (uint64_t)r * args.out_ld + (uint64_t)nt * BT;
+#pragma unroll
+            for (int bl = 0; bl < BT; ++bl) {
+              const uint32_t b = nt * BT + bl;
+              if (b < args.Bvalid) {
+                const uint4 cq = *reinterpret_cast<const uint4*>(args.colsum + (uint64_t)b * 4);
+                const uint32_t qterm =
+                    128u * (cq.x + (cq.y << 8) + (cq.z << 16) + (cq.w << 24)) - kterm;
+                orow[bl] = acc[bl] + rowterm + qterm;
+              }
+            }
+          }
+        }
+      }
+    }
+  }
+  // warps 2-3 have no role
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) tmem_dealloc(tmem_base, 512);
+}
+
+// ---------------------------------------------------------------------- operand preparation
+// Query byte planes as centred fp16 for MODE_ANS / MODE_HINT. Row (nt*N + a*BT + bl) of
+// Qc holds plane a of query b = nt*BT + bl over k < Kp: byte a of Q(b, k) - 128, with
+// Q(b, k) = 0 for b >= B or k >= C. colsum[b][a] += sum_k byte a of Q(b, k).
+// Variant "rows": Q(b, k) = Q[b*C + k]; one CTA per (query, 2048-wide K range).
+__global__ void k_prep_q_rows(const uint32_t* __restrict__ Q, uint32_t B, uint32_t C, uint32_t Kp,
+                              uint32_t BT, uint32_t N, __half* __restrict__ Qc,
+                              uint32_t* __restrict__ colsum) {
+  const uint32_t b = blockIdx.y;
+  const uint32_t nt = b / BT, bl = b % BT;
+  const uint32_t k0 = blockIdx.x * 2048 + threadIdx.x * 8;
+  uint32_t s[4] = {0, 0, 0, 0};
+  if (k0 < Kp) {
+    uint32_t x[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const uint32_t k = k0 + i;
+      x[i] = (b < B && k < C) ? Q[(uint64_t)b * C + k] : 0u;
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      uint32_t h[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const uint32_t lo = (x[2 * i] >> (8 * a)) & 0xFFu, hi = (x[2 * i + 1] >> (8 * a)) & 0xFFu;
+        s[a] += lo + hi;
+        const __half2 hv = __halves2half2(__int2half_rn((int)lo - 128), __int2half_rn((int)hi - 128));
+        h[i] = *reinterpret_cast<const uint32_t*>(&hv);
+      }
+      __half* dst = Qc + ((uint64_t)nt * N + a * BT + bl) * Kp + k0;
+      *reinterpret_cast<uint4*>(dst) = make_uint4(h[0], h[1], h[2], h[3]);
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    uint32_t v = s[a];
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0 && b < B && v) atomicAdd(&colsum[b * 4 + a], v);
+  }
+}
+
+// Variant "cols": Q(b, k) = A[k*B + b] (the hint's queries are the columns of A).
+// CTA: 32 queries x 64 k, transposed through shared memory.
+__global__ void k_prep_q_cols(const uint32_t* __restrict__ A, uint32_t B, uint32_t Bpad, uint32_t C,
+                              uint32_t Kp, uint32_t BT, uint32_t N, __half* __restrict__ Qc,
+                              uint32_t* __restrict__ colsum) {
+  __shared__ uint32_t tile[64][33];
+  const uint32_t b0 = blockIdx.y * 32, k0 = blockIdx.x * 64;
+  const uint32_t tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 256 threads: 8 rows per pass
+  for (uint32_t kk = ty; kk < 64; kk += 8) {
+    const uint32_t k = k0 + kk, b = b0 + tx;
+    tile[kk][tx] = (k < C && b < B) ? A[(uint64_t)k * B + b] : 0u;
+  }
+  __syncthreads();
+  // thread -> (query bq = threadIdx.x / 8, 8-wide k group kg = threadIdx.x % 8)
+  const uint32_t bq = threadIdx.x >> 3, kg = threadIdx.x & 7;
+  const uint32_t b = b0 + bq;
+  const uint32_t nt = b / BT, bl = b % BT;
+  const bool row_exists = b < Bpad;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    uint32_t h[4], s = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const uint32_t lo = (tile[kg * 8 + 2 * i][bq] >> (8 * a)) & 0xFFu;
+      const uint32_t hi = (tile[kg * 8 + 2 * i + 1][bq] >> (8 * a)) & 0xFFu;
+      s += lo + hi;
+      const __half2 hv = __halves2half2(__int2half_rn((int)lo - 128), __int2half_rn((int)hi - 128));
+      h[i] = *reinterpret_cast<const uint32_t*>(&hv);
+    }
+    if (row_exists) {
+      __half* dst = Qc + ((uint64_t)nt * N + a * BT + bl) * Kp + k0 + kg * 8;
+      *reinterpret_cast<uint4*>(dst) = make_uint4(h[0], h[1], h[2], h[3]);
+    }
+    // reduce s over the 8 k-groups of this query (8 consecutive lanes)
+    s += __shfl_xor_sync(0xffffffffu, s, 4);
+    s += __shfl_xor_sync(0xffffffffu, s, 2);
+    s += __shfl_xor_sync(0xffffffffu, s, 1);
+    if (kg == 0 && b < B && s) atomicAdd(&colsum[b * 4 + a], s);
+  }
+}
+
+// Compression operand: row (b*256 + beta) of Bc holds byte beta of cko[b][i] - 128 for
+// i < n (raw 0 for n <= i < Kp). colsum[b][beta] += sum_i byte beta of cko[b][i].
+// CTA: one query, 64 offsets; 256 threads.
+__global__ void k_prep_cko(const uint32_t* __restrict__ cko, uint32_t n, uint32_t Kp,
+                           __half* __restrict__ Bc, uint32_t* __restrict__ colsum) {
+  __shared__ uint32_t tile[64][ZP_MAX_L + 1];
+  const uint32_t b = blockIdx.y, i0 = blockIdx.x * 64;
+  for (uint32_t idx = threadIdx.x; idx < 64u * ZP_MAX_L; idx += blockDim.x) {
+    const uint32_t ii = idx / ZP_MAX_L, w = idx % ZP_MAX_L;
+    const uint32_t i = i0 + ii;
+    tile[ii][w] = i < n ? cko[((uint64_t)b * n + i) * ZP_MAX_L + w] : 0u;
+  }
+  __syncthreads();
+  const uint32_t beta = threadIdx.x;  // 0..255
+  const uint32_t w = beta >> 2, sh = 8 * (beta & 3);
+  uint32_t s = 0;
+  __half* dst = Bc + ((uint64_t)b * 256 + beta) * Kp + i0;
+#pragma unroll
+  for (int g = 0; g < 8; ++g) {
+    uint32_t h[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const uint32_t lo = (tile[g * 8 + 2 * i][w] >> sh) & 0xFFu;
+      const uint32_t hi = (tile[g * 8 + 2 * i + 1][w] >> sh) & 0xFFu;
+      s += lo + hi;
+      const __half2 hv = __halves2half2(__int2half_rn((int)lo - 128), __int2half_rn((int)hi - 128));
+      h[i] = *reinterpret_cast<const uint32_t*>(&hv);
+    }
+    *reinterpret_cast<uint4*>(dst + g * 8) = make_uint4(h[0], h[1], h[2], h[3]);
+  }
+  if (s) atomicAdd(&colsum[(uint64_t)b * 256 + beta], s);
+}
+
+bool g_attr[3][3] = {{false}};
+
+template <int MODE, int BT>
+int launch_gemm(zp_ctx* ctx, const CUtensorMap& tmA, const CUtensorMap& tmB, const GemmArgs& ga,
+                cudaStream_t st) {
+  constexpr int bi = BT == 16 ? 0 : (BT == 32 ? 1 : 2);
+  if (!g_attr[MODE][bi]) {
+    ZP_CUDA(cudaFuncSetAttribute(k_gemm_tc<MODE, BT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 Cfg<MODE>::SMEM));
+    g_attr[MODE][bi] = true;
+  }
+  uint32_t tiles = ga.num_m_tiles * ga.num_n_tiles;
+  uint32_t grid = tiles < (uint32_t)ctx->num_sms ? tiles : (uint32_t)ctx->num_sms;
+  zp_clear_pending_error();
+  ctx->launches++;
+  k_gemm_tc<MODE, BT><<<grid, NTHREADS, Cfg<MODE>::SMEM, st>>>(tmA, tmB, ga);
+  ZP_CUDA(cudaGetLastError());
+  return ZP_OK;
+}
+
+}  // namespace
+
+// Queries per N tile for a batch of B queries (N = 4 * BT rows of the B operand).
+static uint32_t pick_bt(uint32_t B) { return B <= 16 ? 16u : (B <= 32 ? 32u : 64u); }
+
+// Batched product out = D . Q^T (MODE_ANS: out[b][r]) or D . A (MODE_HINT: out[r][i]).
+// Q(b, k) = dQ[b*C + k] (rows) or dQ[k*B + b] (cols). D given by its tensor map.
+int zp_launch_answer_tc(zp_db* db, const CUtensorMap& tmD, uint32_t Rrows, const uint32_t* dQ,
+                        uint32_t B, bool q_cols, uint32_t* dOut, uint64_t out_ld, bool hint,
+                        const uint32_t* rowsum, cudaStream_t st) {
+  zp_ctx* ctx = db->ctx;
+  const uint32_t C = db->C;
+  const uint32_t Kp = (C + 63) / 64 * 64;
+  const uint32_t BT = pick_bt(B);
+  const uint32_t N = 4 * BT;
+  const uint32_t nnt = (B + BT - 1) / BT;
+  const size_t qc_bytes = (size_t)nnt * N * Kp * 2;
+  const size_t cs_bytes = (size_t)nnt * BT * 4 * 4;
+  int rc = zp_scratch_reserve(&db->s_tcq, qc_bytes + cs_bytes + 256);
+  if (rc) return rc;
+  __half* Qc = static_cast<__half*>(db->s_tcq.p);
+  uint32_t* colsum = reinterpret_cast<uint32_t*>(static_cast<uint8_t*>(db->s_tcq.p) + qc_bytes);
+  ZP_CUDA(cudaMemsetAsync(colsum, 0, cs_bytes, st));
+  zp_clear_pending_error();
+  ctx->launches++;
+  if (!q_cols) {
+    dim3 grid((Kp + 2047) / 2048, nnt * BT);
+    k_prep_q_rows<<<grid, 256, 0, st>>>(dQ, B, C, Kp, BT, N, Qc, colsum);
+  } else {
+    dim3 grid(Kp / 64, (nnt * BT + 31) / 32);
+    k_prep_q_cols<<<grid, 256, 0, st>>>(dQ, B, nnt * BT, C, Kp, BT, N, Qc, colsum);
+  }
+  ZP_CUDA(cudaGetLastError());
+  CUtensorMap tmB;
+  rc = zp_encode_tmap_2d(&tmB, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, Qc, Kp, (uint64_t)nnt * N,
+                         (uint64_t)Kp * 2, 64, N, CU_TENSOR_MAP_SWIZZLE_128B);
+  if (rc) return rc;
+  GemmArgs ga{};
+  ga.num_m_tiles = (Rrows + BM - 1) / BM;
+  ga.num_n_tiles = nnt;
+  ga.N = N;
+  ga.nkb = Kp / BK;
+  ga.Kp = Kp;
+  ga.Mvalid = Rrows;
+  ga.Bvalid = B;
+  ga.rowsumA = rowsum;
+  ga.colsum = colsum;
+  ga.out = dOut;
+  ga.out_ld = out_ld;
+  ga.status = ctx->d_status;
+  if (hint) {
+    if (BT == 16) return launch_gemm<MODE_HINT, 16>(ctx, tmD, tmB, ga, st);
+    if (BT == 32) return launch_gemm<MODE_HINT, 32>(ctx, tmD, tmB, ga, st);
+    return launch_gemm<MODE_HINT, 64>(ctx, tmD, tmB, ga, st);
+  }
+  if (BT == 16) return launch_gemm<MODE_ANS, 16>(ctx, tmD, tmB, ga, st);
+  if (BT == 32) return launch_gemm<MODE_ANS, 32>(ctx, tmD, tmB, ga, st);
+  return launch_gemm<MODE_ANS, 64>(ctx, tmD, tmB, ga, st);
+}
+
+// Compression products V4[b][a][r][67] = sum_i Hbyte_a[r][i] cko[b][i] (n <= 1024).
+int zp_launch_vmul_tc(zp_db* db, const uint32_t* dCKO, uint32_t B, uint32_t* V4, cudaStream_t st) {
+  zp_ctx* ctx = db->ctx;
+  const uint32_t n = ctx->P.n;
+  const uint32_t Kp = (n + 63) / 64 * 64;
+  const size_t bc_bytes = (size_t)B * 256 * Kp * 2;
+  const size_t cs_bytes = (size_t)B * 256 * 4;
+  int rc = zp_scratch_reserve(&db->s_cko, bc_bytes + cs_bytes + 256);
+  if (rc) return rc;
+  __half* Bc = static_cast<__half*>(db->s_cko.p);
+  uint32_t* colsum = reinterpret_cast<uint32_t*>(static_cast<uint8_t*>(db->s_cko.p) + bc_bytes);
+  ZP_CUDA(cudaMemsetAsync(colsum, 0, cs_bytes, st));
+  zp_clear_pending_error();
+  ctx->launches++;
+  k_prep_cko<<<dim3(Kp / 64, B), 256, 0, st>>>(dCKO, n, Kp, Bc, colsum);
+  ZP_CUDA(cudaGetLastError());
+  CUtensorMap tmB;
+  rc = zp_encode_tmap_2d(&tmB, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, Bc, Kp, (uint64_t)B * 256,
+                         (uint64_t)Kp * 2, 64, 256, CU_TENSOR_MAP_SWIZZLE_128B);
+  if (rc) return rc;
+  GemmArgs ga{};
+  ga.num_m_tiles = db->Rp / 32;
+  ga.num_n_tiles = B;
+  ga.N = 256;
+  ga.nkb = Kp / BK;
+  ga.Kp = Kp;
+  ga.Mvalid = db->R;
+  ga.Bvalid = B;
+  ga.rowsumA = db->d_hpl_rowsum;
+  ga.colsum = colsum;
+  ga.out = V4;
+  ga.out_ld = 0;
+  ga.Rp = db->Rp;
+  ga.status = ctx->d_status;
+  return launch_gemm<MODE_CMP, 64>(ctx, db->tmap_hpl, tmB, ga, st);
+}

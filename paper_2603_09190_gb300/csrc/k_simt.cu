@@ -122,7 +122,8 @@ __global__ void __launch_bounds__(256)
 // -H+ mod 2^32 into hneg, both R x n row-major.
 __global__ void k_hint_post(const uint32_t* __restrict__ src, uint32_t cnt, uint32_t n,
                             const uint32_t* __restrict__ rows, uint32_t* __restrict__ dH,
-                            uint32_t* __restrict__ hneg) {
+                            uint32_t* __restrict__ hneg, uint8_t* __restrict__ hpl,
+                            uint64_t hpl_ld) {
   const uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (uint64_t)cnt * n) return;
   const uint32_t j = (uint32_t)(idx / n), i = (uint32_t)(idx % n);
@@ -130,7 +131,30 @@ __global__ void k_hint_post(const uint32_t* __restrict__ src, uint32_t cnt, uint
   const uint32_t v = src[idx];
   const uint64_t o = (uint64_t)r * n + i;
   if (dH && (rows || dH != src)) dH[o] = v;
-  hneg[o] = 0u - v;
+  const uint32_t h = 0u - v;
+  hneg[o] = h;
+  // byte planes: row 128 g + 32 a + t of hpl holds byte a of hint row 32 g + t
+  const uint64_t base = (uint64_t)(r >> 5) * 128 + (r & 31);
+#pragma unroll
+  for (uint32_t a = 0; a < 4; ++a) hpl[(base + 32 * a) * hpl_ld + i] = (uint8_t)(h >> (8 * a));
+}
+
+// Byte sums of the 4 plane rows of each listed hint row (all rows if rows == NULL).
+__global__ void k_hpl_rowsum(const uint8_t* __restrict__ hpl, uint64_t ld, uint32_t n,
+                             const uint32_t* __restrict__ rows, uint32_t cnt,
+                             uint32_t* __restrict__ out) {
+  const uint32_t wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t lane = threadIdx.x & 31;
+  if (wid >= cnt * 4u) return;
+  const uint32_t j = wid >> 2, a = wid & 3;
+  const uint32_t r = rows ? rows[j] : j;
+  const uint64_t m = (uint64_t)(r >> 5) * 128 + 32 * a + (r & 31);
+  const uint8_t* row = hpl + m * ld;
+  uint32_t s = 0;
+  for (uint32_t i = lane; i < n; i += 32) s += row[i];
+#pragma unroll
+  for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) out[m] = s;
 }
 
 // Gather rows of D into a compact buffer (pitch ldc), or scatter new rows into D.
@@ -158,6 +182,29 @@ int zp_launch_rowsum(const zp_db* db, const uint32_t* rows, uint32_t nrows, cuda
   return ZP_OK;
 }
 
+int zp_launch_rowsum_buf(zp_ctx* ctx, const uint8_t* M, uint64_t ld, uint32_t rows, uint32_t cols,
+                         uint32_t* out, cudaStream_t st) {
+  if (rows == 0) return ZP_OK;
+  const uint32_t blocks = (rows * 32u + 255u) / 256u;
+  zp_clear_pending_error();
+  ctx->launches++;
+  k_rowsum<<<blocks, 256, 0, st>>>(M, ld, rows, cols, nullptr, 0, out);
+  ZP_CUDA(cudaGetLastError());
+  return ZP_OK;
+}
+
+int zp_launch_hint_planes_rowsum(zp_db* db, const uint32_t* rows, uint32_t nrows, cudaStream_t st) {
+  const uint32_t cnt = rows ? nrows : db->R;
+  if (cnt == 0) return ZP_OK;
+  const uint32_t blocks = (cnt * 4u * 32u + 255u) / 256u;
+  zp_clear_pending_error();
+  db->ctx->launches++;
+  k_hpl_rowsum<<<blocks, 256, 0, st>>>(db->d_hpl, db->hpl_ld, db->ctx->P.n, rows, cnt,
+                                        db->d_hpl_rowsum);
+  ZP_CUDA(cudaGetLastError());
+  return ZP_OK;
+}
+
 int zp_launch_answer_simt(zp_db* db, const uint32_t* dQ, uint32_t B, uint32_t ldq,
                           uint32_t* dOut, uint64_t out_stride_b, uint64_t out_stride_r,
                           const uint8_t* dDrows, uint32_t Rrows, uint64_t ld, cudaStream_t st) {
@@ -180,7 +227,8 @@ int zp_launch_hint_post(zp_db* db, const uint32_t* src, const uint32_t* rows, ui
   if (total == 0) return ZP_OK;
   zp_clear_pending_error();
   db->ctx->launches++;
-  k_hint_post<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(src, cnt, n, rows, dH, db->d_hneg);
+  k_hint_post<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(src, cnt, n, rows, dH, db->d_hneg,
+                                                              db->d_hpl, db->hpl_ld);
   ZP_CUDA(cudaGetLastError());
   return ZP_OK;
 }

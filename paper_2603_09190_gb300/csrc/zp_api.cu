@@ -181,6 +181,8 @@ extern "C" int zp_init(int device, const zp_params* P, zp_ctx** out) {
     }
     c->num_sms = prop.multiProcessorCount;
     c->launches = 0;
+    c->answer_path = ZP_PATH_AUTO;
+    c->compress_path = ZP_PATH_AUTO;
     e = cudaMalloc(&c->d_status, sizeof(uint32_t));
     if (e != cudaSuccess) {
       delete c;
@@ -202,6 +204,18 @@ extern "C" int zp_ctx_destroy(zp_ctx* c) {
   if (c->d_status) cudaFree(c->d_status);
   delete c;
   return ZP_OK;
+}
+
+extern "C" int zp_set_option(zp_ctx* c, const char* name, int64_t value) {
+  if (!c || !name) return zp_set_error(ZP_EINVAL, "zp_set_option: null argument");
+  const std::string k(name);
+  if (k == "answer_path" || k == "compress_path") {
+    if (value < ZP_PATH_AUTO || value > ZP_PATH_TC)
+      return zp_set_error(ZP_EINVAL, "zp_set_option: %s=%lld out of range", name, (long long)value);
+    (k == "answer_path" ? c->answer_path : c->compress_path) = (int)value;
+    return ZP_OK;
+  }
+  return zp_set_error(ZP_EINVAL, "zp_set_option: unknown option '%s'", name);
 }
 
 extern "C" int zp_kernel_launches(const zp_ctx* c, uint64_t* count) {
@@ -241,7 +255,11 @@ extern "C" int zp_setup_db(zp_ctx* c, const uint8_t* dD, uint32_t R, uint32_t C,
     db->C = C;
     db->ld = ld;
     db->d1p = (R + c->ell - 1) / c->ell;
+    db->Rp = (R + 31) / 32 * 32;
     db->d_hneg = nullptr;
+    db->d_hpl = nullptr;
+    db->d_hpl_rowsum = nullptr;
+    db->hpl_ld = ((uint64_t)c->P.n + 15) / 16 * 16;
     db->hint_ready = false;
     db->stale = 0;
     cudaError_t e = cudaMalloc(&db->d_rowsum, (size_t)R * sizeof(uint32_t));
@@ -251,6 +269,9 @@ extern "C" int zp_setup_db(zp_ctx* c, const uint8_t* dD, uint32_t R, uint32_t C,
     }
     int rc = zp_encode_tmap_2d(&db->tmap_gemv, CU_TENSOR_MAP_DATA_TYPE_UINT8, dD, C, R, ld, 256, 64,
                                CU_TENSOR_MAP_SWIZZLE_NONE);
+    if (!rc)
+      rc = zp_encode_tmap_2d(&db->tmap_gemm, CU_TENSOR_MAP_DATA_TYPE_UINT8, dD, C, R, ld, 64, 128,
+                             CU_TENSOR_MAP_SWIZZLE_NONE);
     if (!rc) rc = zp_launch_rowsum(db, nullptr, 0, 0);
     if (!rc) {
       e = cudaDeviceSynchronize();
@@ -293,8 +314,11 @@ extern "C" int zp_db_destroy(zp_db* db) {
   cudaDeviceSynchronize();
   if (db->d_rowsum) cudaFree(db->d_rowsum);
   if (db->d_hneg) cudaFree(db->d_hneg);
-  zp_scratch* all[] = {&db->s_qplanes, &db->s_v, &db->s_q, &db->s_cko,
-                       &db->s_ans,     &db->s_t, &db->s_clients, &db->s_misc};
+  if (db->d_hpl) cudaFree(db->d_hpl);
+  if (db->d_hpl_rowsum) cudaFree(db->d_hpl_rowsum);
+  zp_scratch* all[] = {&db->s_qplanes, &db->s_v,   &db->s_q,   &db->s_cko,  &db->s_ans,
+                       &db->s_t,       &db->s_clients, &db->s_misc, &db->s_tcq, &db->s_hq,
+                       &db->s_hcko};
   for (zp_scratch* s : all) scratch_free(s);
   delete db;
   return ZP_OK;
@@ -313,8 +337,34 @@ static int stage_rows(zp_db* db, const uint32_t* hRows, uint32_t k, size_t extra
   return ZP_OK;
 }
 
-int zp_launch_copy_rows(const uint8_t* src, uint64_t lds, uint8_t* dst, uint64_t ldd, uint32_t C,
-                        const uint32_t* rows, uint32_t cnt, int gather, cudaStream_t st);
+static int alloc_hint_state(zp_db* db) {
+  const uint32_t n = db->ctx->P.n;
+  if (!db->d_hneg) {
+    if (cudaMalloc(&db->d_hneg, (size_t)db->R * n * 4) != cudaSuccess) {
+      db->d_hneg = nullptr;
+      return zp_set_error(ZP_ENOMEM, "zp_gen_hint: cudaMalloc(hint %zu bytes)", (size_t)db->R * n * 4);
+    }
+  }
+  if (!db->d_hpl) {
+    const size_t bytes = (size_t)4 * db->Rp * db->hpl_ld;
+    if (cudaMalloc(&db->d_hpl, bytes) != cudaSuccess) {
+      db->d_hpl = nullptr;
+      return zp_set_error(ZP_ENOMEM, "zp_gen_hint: cudaMalloc(hint planes %zu bytes)", bytes);
+    }
+    cudaError_t e = cudaMemset(db->d_hpl, 0, bytes);
+    if (e != cudaSuccess) return zp_cuda_check(e, "cudaMemset(hint planes)");
+    if (cudaMalloc(&db->d_hpl_rowsum, (size_t)4 * db->Rp * 4) != cudaSuccess) {
+      db->d_hpl_rowsum = nullptr;
+      return zp_set_error(ZP_ENOMEM, "zp_gen_hint: cudaMalloc(plane sums)");
+    }
+    e = cudaMemset(db->d_hpl_rowsum, 0, (size_t)4 * db->Rp * 4);
+    if (e != cudaSuccess) return zp_cuda_check(e, "cudaMemset(plane sums)");
+    int rc = zp_encode_tmap_2d(&db->tmap_hpl, CU_TENSOR_MAP_DATA_TYPE_UINT8, db->d_hpl, n,
+                               (uint64_t)4 * db->Rp, db->hpl_ld, 64, 128, CU_TENSOR_MAP_SWIZZLE_NONE);
+    if (rc) return rc;
+  }
+  return ZP_OK;
+}
 
 extern "C" int zp_gen_hint(zp_db* db, const uint32_t* dA, uint32_t* dH, const uint32_t* hRows,
                            uint32_t nrows, void* stream) {
@@ -326,24 +376,22 @@ extern "C" int zp_gen_hint(zp_db* db, const uint32_t* dA, uint32_t* dH, const ui
     ZP_CUDA(cudaSetDevice(c->device));
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const uint32_t n = c->P.n;
-    if (!db->d_hneg) {
-      cudaError_t e = cudaMalloc(&db->d_hneg, (size_t)db->R * n * sizeof(uint32_t));
-      if (e != cudaSuccess) {
-        db->d_hneg = nullptr;
-        return zp_set_error(ZP_ENOMEM, "zp_gen_hint: cudaMalloc(hint %zu bytes)",
-                            (size_t)db->R * n * 4);
-      }
-    }
+    int rc = alloc_hint_state(db);
+    if (rc) return rc;
+    const bool tc = c->answer_path != ZP_PATH_SIMT;
     std::vector<uint8_t>& stale = stale_flags(db);
     if (!hRows) {
       uint32_t* outp = dH;
       if (!outp) {
-        int rc = zp_scratch_reserve(&db->s_v, (size_t)db->R * n * 4);
+        rc = zp_scratch_reserve(&db->s_v, (size_t)db->R * n * 4);
         if (rc) return rc;
         outp = static_cast<uint32_t*>(db->s_v.p);
       }
-      int rc = zp_launch_answer_simt(db, dA, n, 0, outp, 1, n, db->dD, db->R, db->ld, st);
+      rc = tc ? zp_launch_answer_tc(db, db->tmap_gemm, db->R, dA, n, true, outp, n, true,
+                                    db->d_rowsum, st)
+              : zp_launch_answer_simt(db, dA, n, 0, outp, 1, n, db->dD, db->R, db->ld, st);
       if (!rc) rc = zp_launch_hint_post(db, outp, nullptr, db->R, dH, st);
+      if (!rc) rc = zp_launch_hint_planes_rowsum(db, nullptr, 0, st);
       if (rc) return rc;
       db->hint_ready = true;
       stale.assign(db->R, 0);
@@ -352,18 +400,30 @@ extern "C" int zp_gen_hint(zp_db* db, const uint32_t* dA, uint32_t* dH, const ui
     }
     const uint64_t ldc = ((uint64_t)db->C + 15) / 16 * 16;
     const size_t gather_bytes = ((size_t)nrows * ldc + 255) / 256 * 256;
+    const size_t rs_bytes = ((size_t)nrows * 4 + 255) / 256 * 256;
     const size_t hc_bytes = (size_t)nrows * n * 4;
     uint32_t* dRows = nullptr;
-    int rc = stage_rows(db, hRows, nrows, gather_bytes + hc_bytes, &dRows, st);
+    rc = stage_rows(db, hRows, nrows, gather_bytes + rs_bytes + hc_bytes, &dRows, st);
     if (rc) return rc;
     uint8_t* base = static_cast<uint8_t*>(db->s_misc.p) + ((size_t)nrows * 4 + 255) / 256 * 256;
     uint8_t* dG = base;
-    uint32_t* dHc = reinterpret_cast<uint32_t*>(base + gather_bytes);
+    uint32_t* dGsum = reinterpret_cast<uint32_t*>(base + gather_bytes);
+    uint32_t* dHc = reinterpret_cast<uint32_t*>(base + gather_bytes + rs_bytes);
     zp_clear_pending_error();
     c->launches++;
     rc = zp_launch_copy_rows(db->dD, db->ld, dG, ldc, db->C, dRows, nrows, 1, st);
-    if (!rc) rc = zp_launch_answer_simt(db, dA, n, 0, dHc, 1, n, dG, nrows, ldc, st);
+    if (rc) return rc;
+    if (tc) {
+      CUtensorMap tmG;
+      rc = zp_encode_tmap_2d(&tmG, CU_TENSOR_MAP_DATA_TYPE_UINT8, dG, db->C, nrows, ldc, 64, 128,
+                             CU_TENSOR_MAP_SWIZZLE_NONE);
+      if (!rc) rc = zp_launch_rowsum_buf(c, dG, ldc, nrows, db->C, dGsum, st);
+      if (!rc) rc = zp_launch_answer_tc(db, tmG, nrows, dA, n, true, dHc, n, true, dGsum, st);
+    } else {
+      rc = zp_launch_answer_simt(db, dA, n, 0, dHc, 1, n, dG, nrows, ldc, st);
+    }
     if (!rc) rc = zp_launch_hint_post(db, dHc, dRows, nrows, dH, st);
+    if (!rc) rc = zp_launch_hint_planes_rowsum(db, dRows, nrows, st);
     if (rc) return rc;
     for (uint32_t j = 0; j < nrows; ++j) {
       if (stale[hRows[j]]) {
@@ -411,8 +471,13 @@ extern "C" int zp_answer(zp_db* db, const uint32_t* dQ, uint32_t B, uint32_t* dA
   if (B < 1 || B > 4096) return zp_set_error(ZP_EINVAL, "zp_answer: B=%u out of [1, 4096]", B);
   ZP_CUDA(cudaSetDevice(db->ctx->device));
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if (B == 1) return zp_launch_gemv(db, dQ, dAns, st);
-  return zp_launch_answer_simt(db, dQ, B, db->C, dAns, db->R, 1, db->dD, db->R, db->ld, st);
+  zp_ctx* c = db->ctx;
+  if (B == 1 && c->answer_path != ZP_PATH_SIMT && c->answer_path != ZP_PATH_TC)
+    return zp_launch_gemv(db, dQ, dAns, st);
+  if (c->answer_path == ZP_PATH_SIMT)
+    return zp_launch_answer_simt(db, dQ, B, db->C, dAns, db->R, 1, db->dD, db->R, db->ld, st);
+  return zp_launch_answer_tc(db, db->tmap_gemm, db->R, dQ, B, false, dAns, db->R, false,
+                             db->d_rowsum, st);
 }
 
 extern "C" int zp_register_client(zp_ctx* c, const uint32_t* hM, uint32_t L, zp_client** out) {

@@ -22,9 +22,16 @@
 #define ZP_DEV_TIMEOUT_GEMM 0x2u
 #define ZP_DEV_TIMEOUT_MISC 0x4u
 
+// kernel-path options (zp_set_option)
+#define ZP_PATH_AUTO 0
+#define ZP_PATH_SIMT 1
+#define ZP_PATH_TC 2
+
 struct zp_ctx {
   int device;
   zp_params P;
+  int answer_path;     // ZP_PATH_* for batched answers and the hint
+  int compress_path;   // ZP_PATH_* for the compression products
   uint32_t ell;        // slots per packed row
   uint32_t L;          // limbs per element of Z_m
   uint32_t gamma_w[3]; // packing scale gamma, little-endian 32-bit words (gamma < 2^96)
@@ -53,15 +60,21 @@ struct zp_db {
   uint32_t R, C;
   uint64_t ld;
   uint32_t d1p;
+  uint32_t Rp;             // R rounded up to 32 (rows of the hint byte-plane layout)
   uint32_t* d_rowsum;      // R: sum_c D[r][c]
-  CUtensorMap tmap_gemv;   // D as a 2-D u8 tensor, box 256 x 64
+  CUtensorMap tmap_gemv;   // D as a 2-D u8 tensor, box 256 x 64 (GEMV)
+  CUtensorMap tmap_gemm;   // D as a 2-D u8 tensor, box 64 x 128 (tensor-core products)
   // hint in compression layout (library-owned)
   uint32_t* d_hneg;        // R x n u32: -D.A mod 2^32
+  uint8_t* d_hpl;          // 4 Rp x lda bytes: row 128 g + 32 a + t = byte a of d_hneg row 32 g + t
+  uint32_t* d_hpl_rowsum;  // 4 Rp: byte sums of d_hpl rows
+  uint64_t hpl_ld;         // row pitch of d_hpl (n rounded up to 16)
+  CUtensorMap tmap_hpl;    // d_hpl as a 2-D u8 tensor, box 64 x 128
   bool hint_ready;
   uint32_t stale;          // rows updated since the last hint generation
   std::vector<uint8_t> stale_v;  // per-row stale flags (host)
   // scratch, grown on demand (never shrunk before zp_db_destroy)
-  zp_scratch s_qplanes, s_v, s_q, s_cko, s_ans, s_t, s_clients, s_misc;
+  zp_scratch s_qplanes, s_v, s_q, s_cko, s_ans, s_t, s_clients, s_misc, s_tcq, s_hq, s_hcko;
 };
 
 // error reporting (thread-local message)
@@ -87,6 +100,15 @@ int zp_encode_tmap_2d(CUtensorMap* map, CUtensorMapDataType dt, const void* base
 // ------------------------------------------------------------------ kernel launchers
 // (defined in the k_*.cu translation units; all asynchronous on `st`)
 int zp_launch_rowsum(const zp_db* db, const uint32_t* rows, uint32_t nrows, cudaStream_t st);
+int zp_launch_rowsum_buf(zp_ctx* ctx, const uint8_t* M, uint64_t ld, uint32_t rows, uint32_t cols,
+                         uint32_t* out, cudaStream_t st);
+int zp_launch_copy_rows(const uint8_t* src, uint64_t lds, uint8_t* dst, uint64_t ldd, uint32_t C,
+                        const uint32_t* rows, uint32_t cnt, int gather, cudaStream_t st);
+int zp_launch_answer_tc(zp_db* db, const CUtensorMap& tmD, uint32_t Rrows, const uint32_t* dQ,
+                        uint32_t B, bool q_cols, uint32_t* dOut, uint64_t out_ld, bool hint,
+                        const uint32_t* rowsum, cudaStream_t st);
+int zp_launch_vmul_tc(zp_db* db, const uint32_t* dCKO, uint32_t B, uint32_t* V4, cudaStream_t st);
+int zp_launch_hint_planes_rowsum(zp_db* db, const uint32_t* rows, uint32_t nrows, cudaStream_t st);
 int zp_launch_gemv(zp_db* db, const uint32_t* dq, uint32_t* dans, cudaStream_t st);
 int zp_launch_answer_simt(zp_db* db, const uint32_t* dQ, uint32_t B, uint32_t ldq,
                           uint32_t* dOut, uint64_t out_stride_b, uint64_t out_stride_r,
@@ -202,5 +224,100 @@ __device__ __forceinline__ uint64_t l2_policy_evict_first() {
 }
 
 __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31; }
+
+// ---- bounded waits that also give up when another role of the CTA has aborted
+__device__ __forceinline__ bool mbar_wait_abortable(uint64_t* bar, uint32_t parity,
+                                                    volatile uint32_t* abort_flag,
+                                                    uint32_t* status, uint32_t flag) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = clock64();
+  for (;;) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (*abort_flag) return false;
+    if ((unsigned long long)(clock64() - t0) > ZP_WAIT_CYCLES) {
+      *abort_flag = 1u;
+      if (status) atomicOr(status, flag);
+      return false;
+    }
+  }
+}
+
+// ---- tcgen05 (5th-generation tensor cores, tensor memory)
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst_smem, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                   smem_u32(dst_smem)),
+               "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+// D[tmem] (+)= A[smem] * B[smem]^T, fp16 inputs, fp32 accumulators, one CTA.
+__device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n"
+      ".reg .pred p;\n"
+      "setp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n"
+      "}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+// Arrives on `bar` once every tcgen05 operation issued so far by this thread completes.
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+// 32 consecutive 32-bit columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr)
+      : "memory");
+}
+__device__ __forceinline__ void tmem_wait_ld() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+// Shared-memory matrix descriptor for a K-major operand stored with the 128-byte
+// swizzle (8-row atoms of 128-byte rows, atoms 1024 bytes apart). Fields: start
+// address >> 4 (bits 0-13), leading-dimension offset >> 4 (bits 16-29; unused for
+// this layout, 1), stride-dimension offset >> 4 (bits 32-45: 1024 bytes between
+// 8-row groups), descriptor version 1 (bits 46-47), swizzle mode 2 = 128-byte
+// (bits 61-63).
+__device__ __forceinline__ uint64_t sdesc_k_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1u << 16;
+  d |= (uint64_t)(1024u >> 4) << 32;
+  d |= (uint64_t)1u << 46;
+  d |= (uint64_t)2u << 61;
+  return d;
+}
+// Instruction descriptor of kind::f16 with fp16 A and B, fp32 accumulators, both
+// operands K-major: D format F32 (bits 4-5 = 1), A/B format F16 (bits 7-9, 10-12 = 0),
+// N >> 3 in bits 17-22, M >> 4 in bits 24-28.
+__host__ __device__ __forceinline__ uint32_t idesc_f16_f32(uint32_t M, uint32_t N) {
+  return (1u << 4) | ((N >> 3) << 17) | ((M >> 4) << 24);
+}
 
 #endif  // __CUDACC__

@@ -77,8 +77,11 @@ def test_gemv_closed_forms(zp, ctx):
     db2.close()
 
 
-@pytest.mark.parametrize("R,C,B", [(64, 64, 2), (100, 333, 5), (1024, 1024, 8), (257, 2000, 33)])
+@pytest.mark.parametrize("R,C,B", [(64, 64, 2), (100, 333, 5), (1024, 1024, 8), (257, 2000, 33),
+                                   (1000, 4097, 17), (130, 1030, 64), (300, 3000, 65),
+                                   (129, 700, 100)])
 def test_batched_answer_parity(zp, ctx, R, C, B):
+    """Batched answers on the tensor cores (byte planes, centred fp16, chunked exact sums)."""
     D = synth.database(R, C, B)
     Q = synth.uniform_queries(B, C, B + 1)
     dD, ld = to_dev_db(zp, D)
@@ -88,9 +91,46 @@ def test_batched_answer_parity(zp, ctx, R, C, B):
     db.close()
 
 
-@pytest.mark.parametrize("R,C,n", [(40, 30, 16), (300, 200, 64), (1024, 1024, 1024)])
-def test_hint_parity(zp, R, C, n):
+@pytest.mark.parametrize("dval,qval", [(0, 0), (255, 0xFFFFFFFF), (0, 0xFFFFFFFF), (255, 0),
+                                       ("alt", 0xFF00FF00)])
+def test_batched_answer_extremes(zp, ctx, dval, qval):
+    """Centred products at their extremes: |A'B'| = 2^14 for every term, so each 1024-long
+    chunk sum sits exactly at the fp32 exactness limit 2^24."""
+    R, C, B = 256, 3072, 20
+    if dval == "alt":
+        D = np.tile(np.array([0, 255], dtype=np.uint8), (R, C // 2))
+    else:
+        D = np.full((R, C), dval, dtype=np.uint8)
+    Q = np.full((B, C), qval, dtype=np.uint32)
+    Q[1::2] = ~Q[1::2]
+    dD, ld = to_dev_db(zp, D)
+    db = zp.Database(ctx, dD, R, C, ld)
+    got = u32_host(db.answer(u32_dev(Q)))
+    assert np.array_equal(got, lwe.matmat_mod_q(D, Q.T).T)
+    db.close()
+
+
+@pytest.mark.parametrize("path", ["simt", "tc"])
+def test_single_query_other_paths(zp, path):
+    """The CUDA-core and tensor-core kernels also serve B = 1 and agree with the GEMV."""
+    c = zp.Context(0, n=64)
+    c.set_option("answer_path", path)
+    R, C = 700, 1500
+    D = synth.database(R, C, 3)
+    q = synth.uniform_queries(1, C, 4)
+    dD, ld = to_dev_db(zp, D)
+    db = zp.Database(c, dD, R, C, ld)
+    assert np.array_equal(u32_host(db.answer(u32_dev(q)))[0], lwe.matvec_mod_q(D, q[0]))
+    db.close()
+    c.close()
+
+
+@pytest.mark.parametrize("R,C,n,path", [(40, 30, 16, "auto"), (300, 200, 64, "auto"),
+                                        (1024, 1024, 1024, "auto"), (300, 200, 64, "simt"),
+                                        (513, 1100, 96, "auto"), (70, 5000, 40, "auto")])
+def test_hint_parity(zp, R, C, n, path):
     c = zp.Context(0, n=n)
+    c.set_option("answer_path", path)
     D = synth.database(R, C, n)
     A = synth.seed_matrix(C, n, n)
     dD, ld = to_dev_db(zp, D)
@@ -247,3 +287,49 @@ def test_invalid_arguments_fail_loudly(zp, ctx):
         ctx.register_client(2**2046 + 1)      # too short
     assert ctx.device_status() == 0
     db.close()
+
+
+@pytest.mark.parametrize("n", [64, 1000, 1024])
+def test_compress_tc_equals_simt(zp, n):
+    """The tensor-core and CUDA-core compression products give identical t."""
+    R, C = 333, 128
+    D = synth.database(R, C, n)
+    A = synth.seed_matrix(C, n, n)
+    dD, ld = to_dev_db(zp, D)
+    m = synth.random_odd_modulus(2048, n)
+    cko = u32_dev(np.stack([synth.ints_to_limbs(synth.uniform_below(m, n, 7 + b), 64) for b in range(3)]))
+    ans = u32_dev(synth.uniform_queries(3, R, 9))
+    outs = []
+    for path in ("simt", "tc"):
+        c = zp.Context(0, n=n)
+        c.set_option("compress_path", path)
+        db = zp.Database(c, dD, R, C, ld)
+        db.gen_hint(u32_dev(A))
+        cl = c.register_client(m)
+        outs.append(u32_host(db.compress([cl, cl, cl], ans, cko)))
+        db.close()
+        cl.close()
+        c.close()
+    assert np.array_equal(outs[0], outs[1])
+
+
+def test_compress_zero_database(zp):
+    """D = 0 gives H = 0: every hint byte centres to -128 and, with cko = 0, each product sum
+    is exactly 2^24 before the correction; t must equal b' mod m."""
+    R, C, n = 100, 64, 1024
+    P = Params(n=n, key_bits=2048)
+    c = zp.Context(0, n=n)
+    D = np.zeros((R, C), dtype=np.uint8)
+    A = synth.seed_matrix(C, n, 1)
+    dD, ld = to_dev_db(zp, D)
+    db = zp.Database(c, dD, R, C, ld)
+    db.gen_hint(u32_dev(A))
+    m = synth.random_odd_modulus(2048, 3)
+    cl = c.register_client(m)
+    ans = synth.uniform_queries(1, R, 4)
+    for cko in ([0] * n, [m - 1] * n):
+        T = db.compress([cl], u32_dev(ans), u32_dev(synth.ints_to_limbs(cko, 64)[None]))
+        assert synth.limbs_to_ints(u32_host(T)[0]) == zippir.compress_rows(
+            ans[0], np.zeros((R, n), dtype=np.uint32), cko, m, P)
+    db.close()
+    c.close()
