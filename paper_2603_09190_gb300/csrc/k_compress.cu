@@ -9,9 +9,10 @@
 // Two kernels:
 //  * k_vmul_simt: V on CUDA cores, one thread per (row, limb of cko), 96-bit
 //    column accumulators, then one carry-propagation pass per row;
-//  * k_pack_reduce: one warp per (query, packed row): Horner evaluation
+//  * k_pack_reduce: one warp per (query, packed row): the ell rows of V are staged
+//    in shared memory, then Horner evaluation
 //    X = (..((W_{ell-1}) gamma + W_{ell-2}) gamma + ..) gamma + W_0 with
-//    W_j = ans + V of row r' ell + j (X < 2^4064), then Barrett reduction mod m
+//    W_j = ans + V of row r' ell + j (X < 2^4064) in registers, then Barrett reduction mod m
 //    (Barrett, CRYPTO '86; the quotient-estimate form of the Handbook of Applied
 //    Cryptography, Alg. 14.42) with the per-client constant mu = floor(2^(64 L) / m).
 //    Big integers live in shared memory; products are summed per output column in
@@ -188,8 +189,8 @@ __device__ __forceinline__ void warp_cols_to_words(const uint32_t (*col)[3], int
   warp_normalize<WPL>(v, w);
 }
 
-struct PackWarpSmem {
-  uint32_t X[ZP_XW];        // Horner accumulator (< 2^4064)
+struct PackBarrett {
+  uint32_t X[ZP_XW];        // the packed sum before reduction (< 2^4064)
   uint32_t col[160][3];     // product columns
   uint32_t q1[ZP_MAX_L + 1];
   uint32_t q3[ZP_MAX_L + 1];
@@ -204,73 +205,74 @@ struct ClientPtrs {
   const uint32_t* mu;
 };
 
-// grid (ceil(d1p / PACK_WARPS), B), block PACK_WARPS warps. Requires L == ZP_MAX_L.
+// grid (ceil(d1p / PACK_WARPS), B), block PACK_WARPS warps, dynamic shared memory
+// PACK_WARPS x (PackBarrett + ell x VW words). Requires L == ZP_MAX_L.
+// V: [b][Rp][VW] words, the exact products V[row] = H[row,:] . cko[b].
 __global__ void __launch_bounds__(PACK_WARPS * 32)
     k_pack_reduce(const uint32_t* __restrict__ ans, const uint32_t* __restrict__ V, uint32_t R,
-                  uint32_t Rp, uint32_t nplanes, uint32_t ell, uint32_t d1p, uint32_t g0,
-                  uint32_t g1, uint32_t g2, const ClientPtrs* __restrict__ cl,
-                  uint32_t* __restrict__ T) {
-  __shared__ PackWarpSmem sm[PACK_WARPS];
+                  uint32_t Rp, uint32_t ell, uint32_t d1p, uint32_t g1, uint32_t g2,
+                  const ClientPtrs* __restrict__ cl, uint32_t* __restrict__ T) {
+  extern __shared__ __align__(16) uint32_t pack_smem[];
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t b = blockIdx.y;
   const uint32_t rp = blockIdx.x * PACK_WARPS + warp;
   if (rp >= d1p) return;
-  PackWarpSmem& S = sm[warp];
+  const uint32_t per_warp = (uint32_t)(sizeof(PackBarrett) / 4) + ell * VW;
+  PackBarrett& S = *reinterpret_cast<PackBarrett*>(pack_smem + warp * per_warp);
+  uint32_t* Vs = pack_smem + warp * per_warp + sizeof(PackBarrett) / 4;  // ell x VW
   constexpr int L = ZP_MAX_L;
 
+  // ---- stage the rows r' ell .. r' ell + ell - 1 of V (contiguous) and the client constants
+  const uint32_t row0 = rp * ell;
+  const uint32_t nrows = R - row0 < ell ? R - row0 : ell;
+  const uint32_t* src = V + ((uint64_t)b * Rp + row0) * VW;
+  for (uint32_t idx = lane; idx < nrows * VW; idx += 32) Vs[idx] = __ldg(src + idx);
   for (int x = lane; x < L + 1; x += 32) {
     S.m[x] = x < L ? cl[b].m[x] : 0u;
     S.mu[x] = cl[b].mu[x];
   }
-  for (int x = lane; x < ZP_XW; x += 32) S.X[x] = 0u;
+  const uint32_t* ansb = ans + (uint64_t)b * R + row0;
   __syncwarp();
 
-  // ---- Horner: X <- X * gamma + W_j, j = ell-1 .. 0 (gamma = g0 + g1 2^32 + g2 2^64)
-  const uint32_t* ansb = ans + (uint64_t)b * R;
-  const uint32_t* Vb = V + (uint64_t)b * nplanes * Rp * VW;
-  for (int j = (int)ell - 1; j >= 0; --j) {
-    const uint32_t row = rp * ell + (uint32_t)j;
-    const bool have = row < R;
+  // ---- Horner: X <- X gamma + W_j (j = ell-1 .. 0), gamma = g1 2^32 + g2 2^64,
+  // W_j = ans[row] + V[row]. X is kept with lazy carries: four 64-bit words per lane
+  // (words 4 lane .. 4 lane + 3), each below 2^33, so one step needs a local carry
+  // pass and one shuffle instead of a full carry resolution.
+  uint64_t xv[4] = {0, 0, 0, 0};
+  for (int j = (int)nrows - 1; j >= 0; --j) {
+    const uint64_t pm1 = __shfl_up_sync(0xffffffffu, xv[3], 1);  // word 4 lane - 1
+    const uint64_t pm2 = __shfl_up_sync(0xffffffffu, xv[2], 1);  // word 4 lane - 2
+    const uint64_t xm1 = lane ? pm1 : 0, xm2 = lane ? pm2 : 0;
+    const uint32_t* Wj = Vs + (uint32_t)j * VW;
     uint64_t v[4];
+    v[0] = (uint64_t)g1 * xm1 + (uint64_t)g2 * xm2;
+    v[1] = (uint64_t)g1 * xv[0] + (uint64_t)g2 * xm1;
+    v[2] = (uint64_t)g1 * xv[1] + (uint64_t)g2 * xv[0];
+    v[3] = (uint64_t)g1 * xv[2] + (uint64_t)g2 * xv[1];
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
-      const int x = (int)lane * 4 + t;
-      const uint32_t x0 = S.X[x];
-      const uint32_t x1 = x >= 1 ? S.X[x - 1] : 0u;
-      const uint32_t x2 = x >= 2 ? S.X[x - 2] : 0u;
-      const uint32_t x3 = x >= 3 ? S.X[x - 3] : 0u;
-      uint64_t s = 0;
-      s += (uint32_t)((uint64_t)g0 * x0);
-      s += (uint32_t)(((uint64_t)g0 * x1) >> 32);
-      s += (uint32_t)((uint64_t)g1 * x1);
-      s += (uint32_t)(((uint64_t)g1 * x2) >> 32);
-      s += (uint32_t)((uint64_t)g2 * x2);
-      s += (uint32_t)(((uint64_t)g2 * x3) >> 32);
-      if (have) {
-        // W_j = ans + sum_a V_a << 8a  (plane a of the compression product)
-        if (x < VW) {
-          for (uint32_t a = 0; a < nplanes; ++a) {
-            const uint32_t* Vr = Vb + ((uint64_t)a * Rp + row) * VW;
-            const uint32_t cur = Vr[x];
-            if (a == 0) {
-              s += cur;
-            } else {
-              const uint32_t prev = x >= 1 ? Vr[x - 1] : 0u;
-              s += (cur << (8 * a)) | (prev >> (32 - 8 * a));
-            }
-          }
-        }
-        if (x == 0) s += ansb[row];
-      }
-      v[t] = s;
+      const uint32_t x = lane * 4 + t;
+      if (x < VW) v[t] += Wj[x];
     }
-    __syncwarp();
+    if (lane == 0) v[0] += __ldg(ansb + j);
+    uint64_t c = 0;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const uint64_t sum = v[t] + c;
+      xv[t] = sum & 0xFFFFFFFFull;
+      c = sum >> 32;
+    }
+    const uint64_t cin = __shfl_up_sync(0xffffffffu, c, 1);
+    if (lane) xv[0] += cin;
+  }
+  // final carry resolution, then X to shared memory
+  {
     uint32_t w[4];
-    warp_normalize<4>(v, w);
+    warp_normalize<4>(xv, w);
 #pragma unroll
     for (int t = 0; t < 4; ++t) S.X[lane * 4 + t] = w[t];
-    __syncwarp();
   }
+  __syncwarp();
 
   // ---- Barrett: q1 = floor(X / b^(L-1)), q3 = floor(q1 mu / b^(L+1)),
   //      r = (X mod b^(L+1)) - (q3 m mod b^(L+1)), then r -= m while r >= m.
@@ -325,8 +327,7 @@ int zp_launch_compress(zp_db* db, zp_client* const* clients, const uint32_t* dAn
   if (ctx->compress_path == ZP_PATH_TC && n > 1024)
     return zp_set_error(ZP_EUNSUPPORTED, "tensor-core compression needs n <= 1024");
   const bool tc = ctx->compress_path != ZP_PATH_SIMT && n <= 1024;
-  const uint32_t nplanes = tc ? 4u : 1u;
-  int rc = zp_scratch_reserve(&db->s_v, (size_t)B * nplanes * db->Rp * VW * sizeof(uint32_t));
+  int rc = zp_scratch_reserve(&db->s_v, (size_t)B * db->Rp * VW * sizeof(uint32_t));
   if (rc) return rc;
   rc = zp_scratch_reserve(&db->s_clients, (size_t)B * sizeof(ClientPtrs));
   if (rc) return rc;
@@ -351,12 +352,18 @@ int zp_launch_compress(zp_db* db, zp_client* const* clients, const uint32_t* dAn
     ZP_CUDA(cudaGetLastError());
   }
   {
+    const size_t smem = (size_t)PACK_WARPS * (sizeof(PackBarrett) + (size_t)ctx->ell * VW * 4);
+    static bool attr = false;
+    if (!attr) {
+      ZP_CUDA(cudaFuncSetAttribute(k_pack_reduce, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)(PACK_WARPS * (sizeof(PackBarrett) + 64 * VW * 4))));
+      attr = true;
+    }
     dim3 grid((db->d1p + PACK_WARPS - 1) / PACK_WARPS, B);
     zp_clear_pending_error();
     ctx->launches++;
-    k_pack_reduce<<<grid, PACK_WARPS * 32, 0, st>>>(dAns, V, R, db->Rp, nplanes, ctx->ell, db->d1p,
-                                                    ctx->gamma_w[0],
-                                                    ctx->gamma_w[1], ctx->gamma_w[2], dcl, dT);
+    k_pack_reduce<<<grid, PACK_WARPS * 32, smem, st>>>(dAns, V, R, db->Rp, ctx->ell, db->d1p,
+                                                       ctx->gamma_w[1], ctx->gamma_w[2], dcl, dT);
     ZP_CUDA(cudaGetLastError());
   }
   return ZP_OK;

@@ -21,16 +21,19 @@
 //             sum_a 2^(8a) P_a in the epilogue;
 //   MODE_HINT the global hint H+ = D A mod 2^32 (Algorithm "ZipPIR" caption): as
 //             MODE_ANS with the columns of A as queries, written row-major R x n;
-//   MODE_CMP  the compression products V_a[r] = sum_i Hbyte_a[r][i] cko[i]
-//             (Algorithm "ZipPIR", Response, second line): A = the 4 byte planes of
-//             the negated hint, rows ordered (32 rows of plane 0, of plane 1, ...),
-//             B = the 256 bytes of every cko[i] (N = 256), K = n <= 1024; the
-//             epilogue turns the 256 byte-column sums of a row into a 67-word
-//             integer (carry propagation) and writes it.
+//   MODE_CMP  the compression products V[r] = sum_i H[r][i] cko[i] (Algorithm
+//             "ZipPIR", Response, second line): A = the 4 byte planes of the negated
+//             hint, rows ordered (32 rows of plane 0, of plane 1, ...), B = the 256
+//             bytes of every cko[i] (N = 256), K = n <= 1024; the epilogue turns the
+//             256 byte-column sums of a row into a 67-word integer V_a (carry
+//             propagation), adds the four planes as V = sum_a V_a 2^(8a) and writes
+//             V (67 words per row).
 //
 // Structure (one CTA per SM, persistent over output tiles of 128 x N):
-//   warp 0      TMA producer: the A tile as bytes (128 x 64, 8 KiB) into a byte ring,
-//               the B tile as fp16 (N x 64, 128-byte swizzle) into the operand ring;
+//   warp 0      TMA producer of A: the A tile as bytes (128 x 64, 8 KiB) into a deep
+//               byte ring (its source is HBM);
+//   warp 2      TMA producer of B: the B tile as fp16 (N x 64, 128-byte swizzle) into
+//               the operand ring;
 //   warp 1      allocates 512 TMEM columns (two 256-column accumulators) and one
 //               elected lane issues the MMAs (4 x K=16 per K block) and the commits;
 //   warps 4-7   epilogue: tcgen05.ld of their 32-lane TMEM quarter, int conversion,
@@ -50,7 +53,6 @@ constexpr int A16_BYTES = BM * BK * 2;       // 16 KiB
 constexpr int B_MAX_BYTES = 256 * BK * 2;    // 32 KiB
 constexpr int OP_STAGE = A16_BYTES + B_MAX_BYTES;
 constexpr int U8_STAGE = BM * BK;            // 8 KiB
-constexpr int SU = 4;
 constexpr int KCHUNK = 16;                   // K blocks per exact fp32 accumulation
 constexpr int NTHREADS = 384;
 constexpr int STG_PITCH = 67;                // words per staged row (odd: no bank conflicts)
@@ -60,7 +62,8 @@ enum { MODE_ANS = 0, MODE_HINT = 1, MODE_CMP = 2 };
 
 template <int MODE>
 struct Cfg {
-  static constexpr int SO = (MODE == MODE_CMP) ? 3 : 4;
+  static constexpr int SO = 3;                          // operand stages (fp16 A | B)
+  static constexpr int SU = (MODE == MODE_CMP) ? 5 : 8;  // byte stages of A (HBM-latency bound)
   static constexpr int STG = (MODE == MODE_CMP) ? STG_BYTES : 0;
   static constexpr int SMEM = SO * OP_STAGE + SU * U8_STAGE + STG + 1024 + 512;
 };
@@ -104,12 +107,29 @@ __device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity,
   return ok != 0;
 }
 
+// AND of `pred` over the 128 threads of the four epilogue warps (named barrier 1).
+__device__ __forceinline__ bool bar_and_128(bool pred) {
+  uint32_t r;
+  asm volatile(
+      "{\n"
+      ".reg .pred p, q;\n"
+      "setp.ne.u32 p, %1, 0;\n"
+      "bar.red.and.pred q, 1, 128, p;\n"
+      "selp.u32 %0, 1, 0, q;\n"
+      "}\n"
+      : "=r"(r)
+      : "r"((uint32_t)pred)
+      : "memory");
+  return r != 0;
+}
+
 template <int MODE, int BT>
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
               const GemmArgs args) {
   using C = Cfg<MODE>;
   constexpr int SO = C::SO;
+  constexpr int SU = C::SU;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~static_cast<uintptr_t>(1023));
@@ -158,14 +178,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const uint32_t tmem_base = *tmem_holder;
 
   if (warp == 0) {
-    // ------------------------------------------------------------ TMA producer
+    // ------------------------------------------------------------ TMA producer of A (bytes)
     if (lane == 0) {
       prefetch_tmap(&tmA);
-      prefetch_tmap(&tmB);
       uint32_t cnt = 0;
       bool ok = true;
       for (uint32_t tile = blockIdx.x; ok && tile < num_tiles; tile += gridDim.x) {
-        const uint32_t nt = tile % args.num_n_tiles, mt = tile / args.num_n_tiles;
+        const uint32_t mt = tile / args.num_n_tiles;
         for (uint32_t kb = 0; kb < nkb; ++kb, ++cnt) {
           const uint32_t su = cnt % SU, ru = cnt / SU;
           if (ru > 0 && !mbar_wait_abortable(&u8_empty[su], (ru - 1) & 1u, abort_flag,
@@ -176,11 +195,26 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           mbar_arrive_expect_tx(&u8_full[su], U8_STAGE);
           tma_load_2d(u8_ring + su * U8_STAGE, &tmA, (int32_t)(kb * BK), (int32_t)(mt * BM),
                       &u8_full[su]);
+        }
+      }
+      // Stay until the copies issued last have landed (bounded, ignores the abort flag).
+      const uint32_t f_u = cnt > (uint32_t)SU ? cnt - SU : 0;
+      for (uint32_t i = f_u; i < cnt; ++i)
+        mbar_wait_bounded(&u8_full[i % SU], (i / SU) & 1u, args.status, ZP_DEV_TIMEOUT_GEMM);
+    }
+  } else if (warp == 2) {
+    // ------------------------------------------------------------ TMA producer of B (fp16)
+    if (lane == 0) {
+      prefetch_tmap(&tmB);
+      uint32_t cnt = 0;
+      bool ok = true;
+      for (uint32_t tile = blockIdx.x; ok && tile < num_tiles; tile += gridDim.x) {
+        const uint32_t nt = tile % args.num_n_tiles;
+        for (uint32_t kb = 0; kb < nkb; ++kb, ++cnt) {
           const uint32_t so = cnt % SO, ro = cnt / SO;
           if (ro > 0 && !mbar_wait_abortable(&op_empty[so], (ro - 1) & 1u, abort_flag,
                                              args.status, ZP_DEV_TIMEOUT_GEMM)) {
             ok = false;
-            ++cnt;
             break;
           }
           mbar_arrive_expect_tx(&op_full[so], N * BK * 2);
@@ -188,10 +222,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                       (int32_t)(nt * N), &op_full[so]);
         }
       }
-      // Stay until the copies issued last have landed (bounded, ignores the abort flag).
-      const uint32_t f_u = cnt > (uint32_t)SU ? cnt - SU : 0;
-      for (uint32_t i = f_u; i < cnt; ++i)
-        mbar_wait_bounded(&u8_full[i % SU], (i / SU) & 1u, args.status, ZP_DEV_TIMEOUT_GEMM);
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
@@ -291,7 +321,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       if constexpr (MODE == MODE_CMP) {
         // single chunk (n <= 1024): byte-column sums -> 67-word integer
         const uint32_t a = acc_cnt & 1u, ra = acc_cnt >> 1;
-        if (!warp_wait(&acc_full[a], ra & 1u, abort_flag, args.status)) {
+        // the four epilogue warps agree on the verdict before their named barriers
+        if (!bar_and_128(warp_wait(&acc_full[a], ra & 1u, abort_flag, args.status))) {
           ok = false;
           break;
         }
@@ -327,14 +358,37 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         __syncwarp();
         if (lane == 0) mbar_arrive(&acc_empty[a]);
         ++acc_cnt;
-        // coalesced copy of this warp's 32 rows x 67 words
-        uint32_t* dst = args.out + (((uint64_t)b * 4 + e) * args.Rp + (uint64_t)mt * 32) * ZP_VW;
-        const uint32_t* src = stg + e * 32 * STG_PITCH;
-        for (uint32_t idx = lane; idx < 32u * ZP_VW; idx += 32) {
-          const uint32_t rr = idx / ZP_VW, ww = idx % ZP_VW;
-          dst[idx] = src[rr * STG_PITCH + ww];
+        // V = sum_a V_a 2^(8a): warp 0 adds the four staged planes of its row (exact,
+        // sequential carries), then all four warps copy the 32 rows out coalesced.
+        asm volatile("bar.sync 1, 128;" ::: "memory");
+        if (e == 0) {
+          const uint32_t* p1 = stg + (1 * 32 + lane) * STG_PITCH;
+          const uint32_t* p2 = stg + (2 * 32 + lane) * STG_PITCH;
+          const uint32_t* p3 = stg + (3 * 32 + lane) * STG_PITCH;
+          uint64_t c = 0;
+          uint32_t q1 = 0, q2 = 0, q3 = 0;  // previous words of planes 1..3
+#pragma unroll 4
+          for (int w = 0; w < ZP_VW; ++w) {
+            const uint32_t w1 = p1[w], w2 = p2[w], w3 = p3[w];
+            uint64_t s = c + myst[w];
+            s += (w1 << 8) | (q1 >> 24);
+            s += (w2 << 16) | (q2 >> 16);
+            s += (w3 << 24) | (q3 >> 8);
+            myst[w] = (uint32_t)s;
+            c = s >> 32;
+            q1 = w1;
+            q2 = w2;
+            q3 = w3;
+          }
         }
-        __syncwarp();
+        asm volatile("bar.sync 1, 128;" ::: "memory");
+        uint32_t* dst = args.out + ((uint64_t)b * args.Rp + (uint64_t)mt * 32) * ZP_VW;
+        const uint32_t tid = e * 32 + lane;
+        for (uint32_t idx = tid; idx < 32u * ZP_VW; idx += 128) {
+          const uint32_t rr = idx / ZP_VW, ww = idx % ZP_VW;
+          dst[idx] = stg[rr * STG_PITCH + ww];
+        }
+        asm volatile("bar.sync 1, 128;" ::: "memory");
       } else {
         uint32_t acc[BT];
 #pragma unroll
@@ -396,7 +450,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       }
     }
   }
-  // warps 2-3 have no role
+  // warp 3 has no role
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
