@@ -139,8 +139,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   uint64_t* bars = reinterpret_cast<uint64_t*>(u8_ring + SU * U8_STAGE + C::STG);
   uint64_t* u8_full = bars;
   uint64_t* u8_empty = u8_full + SU;
-  uint64_t* op_full = u8_empty + SU;
-  uint64_t* op_empty = op_full + SO;
+  uint64_t* b_full = u8_empty + SU;     // B tile landed (TMA transaction count)
+  uint64_t* a_ready = b_full + SO;      // fp16 A tile written by the four converter warps
+  uint64_t* op_empty = a_ready + SO;
   uint64_t* acc_full = op_empty + SO;
   uint64_t* acc_empty = acc_full + 2;
   uint64_t* mma_done = acc_empty + 2;
@@ -157,7 +158,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       mbar_init(&u8_empty[s], 4);
     }
     for (int s = 0; s < SO; ++s) {
-      mbar_init(&op_full[s], 1 + 4);
+      mbar_init(&b_full[s], 1);
+      mbar_init(&a_ready[s], 4);
       mbar_init(&op_empty[s], 1);
     }
     for (int s = 0; s < 2; ++s) {
@@ -183,9 +185,24 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       prefetch_tmap(&tmA);
       uint32_t cnt = 0;
       bool ok = true;
+      // L2 prefetch runs PF K blocks ahead of the loads, so that the loads that fill
+      // the byte ring hit L2 instead of waiting for HBM.
+      constexpr uint32_t PF = 16;
+      for (uint32_t f = 0; f < PF; ++f) {
+        const uint32_t t = blockIdx.x + (f / nkb) * gridDim.x;
+        if (t < num_tiles)
+          tma_prefetch_l2_2d(&tmA, (int32_t)((f % nkb) * BK), (int32_t)((t / args.num_n_tiles) * BM));
+      }
       for (uint32_t tile = blockIdx.x; ok && tile < num_tiles; tile += gridDim.x) {
         const uint32_t mt = tile / args.num_n_tiles;
         for (uint32_t kb = 0; kb < nkb; ++kb, ++cnt) {
+          {
+            const uint32_t f = cnt + PF;
+            const uint32_t t = blockIdx.x + (f / nkb) * gridDim.x;
+            if (t < num_tiles)
+              tma_prefetch_l2_2d(&tmA, (int32_t)((f % nkb) * BK),
+                                 (int32_t)((t / args.num_n_tiles) * BM));
+          }
           const uint32_t su = cnt % SU, ru = cnt / SU;
           if (ru > 0 && !mbar_wait_abortable(&u8_empty[su], (ru - 1) & 1u, abort_flag,
                                              args.status, ZP_DEV_TIMEOUT_GEMM)) {
@@ -217,11 +234,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             ok = false;
             break;
           }
-          mbar_arrive_expect_tx(&op_full[so], N * BK * 2);
+          mbar_arrive_expect_tx(&b_full[so], N * BK * 2);
           tma_load_2d(op_ring + so * OP_STAGE + A16_BYTES, &tmB, (int32_t)(kb * BK),
-                      (int32_t)(nt * N), &op_full[so]);
+                      (int32_t)(nt * N), &b_full[so]);
         }
       }
+      // Stay until the copies issued last have landed (bounded, ignores the abort flag).
+      const uint32_t f_o = cnt > (uint32_t)SO ? cnt - SO : 0;
+      for (uint32_t i = f_o; i < cnt; ++i)
+        mbar_wait_bounded(&b_full[i % SO], (i / SO) & 1u, args.status, ZP_DEV_TIMEOUT_GEMM);
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
@@ -244,7 +265,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             tc_fence_after();
           }
           const uint32_t so = cnt % SO, ro = cnt / SO;
-          if (!mbar_wait_abortable(&op_full[so], ro & 1u, abort_flag, args.status,
+          if (!mbar_wait_abortable(&b_full[so], ro & 1u, abort_flag, args.status,
+                                   ZP_DEV_TIMEOUT_GEMM) ||
+              !mbar_wait_abortable(&a_ready[so], ro & 1u, abort_flag, args.status,
                                    ZP_DEV_TIMEOUT_GEMM)) {
             ok = false;
             break;
@@ -304,7 +327,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0) {
-          mbar_arrive(&op_full[so]);
+          mbar_arrive(&a_ready[so]);
           mbar_arrive(&u8_empty[su]);
         }
       }
