@@ -114,6 +114,24 @@ int zp_gen_hint(zp_db* db, const uint32_t* dA, uint32_t* dH, const uint32_t* hRo
  * 1 <= B <= 4096. Asynchronous on `stream`. Errors: ZP_EINVAL, ZP_ENOMEM, ZP_ECUDA. */
 int zp_answer(zp_db* db, const uint32_t* dQ, uint32_t B, uint32_t* dAns, void* stream);
 
+/* Single-query answer that allocates no device memory (the paper has no
+ * counterpart; it serves callers of this library that cannot allocate). Same result
+ * as zp_answer with B = 1: ans[r] = sum_c D[r][c] * q[c] mod 2^32, dQ: C u32, dAns:
+ * R u32 (device). Some callers may not call cudaMalloc at all: code recorded into a
+ * CUDA graph, latency-critical serving threads that must never block on the device
+ * allocator (cudaMalloc can synchronise the device), and hosts whose memory manager
+ * owns every byte of HBM. zp_answer grows library scratch on demand; this entry
+ * point instead keeps its scratch (the query byte planes) in a 1 MiB array compiled
+ * into the library, which every GPU that loads the library holds until the process
+ * exits. Limit: C <= 262144 columns (ZP_EINVAL above it, before any work). The first
+ * call on a device looks up that array's device address (cudaGetSymbolAddress); make
+ * that first call before any stream capture. All calls on a device share the array,
+ * so calls that overlap on the GPU (different streams, no ordering) race and give
+ * wrong answers; calls ordered on one stream are safe, and each call rewrites every
+ * plane it reads and zeroes dAns itself. Asynchronous on `stream`.
+ * Errors: ZP_EINVAL, ZP_ECUDA. */
+int zp_answer_noalloc(zp_db* db, const uint32_t* dQ, uint32_t* dAns, void* stream);
+
 /* Registers a client's public Paillier modulus m (Algorithm "ZipPIR", Setup: the
  * client sends m). hM: HOST array of L = key_bits/32 little-endian u32 limbs; m
  * must be odd with exactly key_bits bits. The library derives the Barrett constant

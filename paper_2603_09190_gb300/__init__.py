@@ -29,7 +29,7 @@ EXPORTS = [
     "zp_version", "zp_last_error", "zp_init", "zp_ctx_destroy", "zp_setup_db", "zp_db_info",
     "zp_db_destroy", "zp_gen_hint", "zp_answer", "zp_register_client", "zp_client_destroy",
     "zp_compress", "zp_respond", "zp_respond_host", "zp_update_rows", "zp_stale_rows",
-    "zp_device_status", "zp_kernel_launches", "zp_set_option",
+    "zp_device_status", "zp_kernel_launches", "zp_set_option", "zp_answer_noalloc",
 ]
 
 
@@ -77,6 +77,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "zp_device_status": (i32, [vp, ctypes.POINTER(u32)]),
         "zp_kernel_launches": (i32, [vp, ctypes.POINTER(u64)]),
         "zp_set_option": (i32, [vp, ctypes.c_char_p, ctypes.c_int64]),
+        "zp_answer_noalloc": (i32, [vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -172,6 +173,12 @@ def zp_gen_hint(db: int, dA: int, dH: int | None, hRows: np.ndarray | None, stre
 
 def zp_answer(db: int, dQ: int, B: int, dAns: int, stream: int | None):
     _check(load_library().zp_answer(db, dQ, B, dAns, stream))
+
+
+def zp_answer_noalloc(db: int, dQ: int, dAns: int, stream: int | None):
+    """Single-query answer without any device allocation (fixed 1 MiB static scratch,
+    C <= 262144); see include/zippir.h."""
+    _check(load_library().zp_answer_noalloc(db, dQ, dAns, stream))
 
 
 def zp_register_client(ctx: int, m: int, L: int) -> int:

@@ -11,6 +11,7 @@
 // number of bytes; a CTA adds its partial row sums to ans with atomicAdd, which is
 // order-independent under wrap-around, so the result is deterministic.
 #include <cstdio>
+#include <mutex>
 
 #include "zp_internal.cuh"
 
@@ -186,6 +187,64 @@ int zp_launch_gemv(zp_db* db, const uint32_t* dq, uint32_t* dans, cudaStream_t s
   zp_clear_pending_error();
   ctx->launches++;
   k_gemv<<<(unsigned)grid, (NCW + 1) * 32, SMEM_BYTES, st>>>(db->tmap_gemv, qp, dans, db->R, nrb,
+                                                             nct, ctx->d_status);
+  ZP_CUDA(cudaGetLastError());
+  return ZP_OK;
+}
+
+// ---------------------------------------------------------------------------------
+// zp_answer_noalloc: the single-query answer for callers that must not allocate
+// device memory. Its only scratch, the query byte planes, lives in this file-scope
+// device array instead of library-allocated memory; every GPU that loads the
+// library holds these 1 MiB until the process exits. In host code the array's name
+// is only a host-side stand-in, so its device address is looked up once per device
+// (cudaGetSymbolAddress, with that device current) and passed to the kernels.
+#define ZP_NOALLOC_MAX_C (1u << 18)  // columns: 1024 tiles x 1 KiB of planes = 1 MiB
+static __device__ __align__(256) uint32_t g_noalloc_qplanes[(ZP_NOALLOC_MAX_C / TCB) * 256];
+
+namespace {
+std::mutex g_noalloc_mu;
+uint32_t* g_noalloc_planes[64] = {nullptr};
+}  // namespace
+
+extern "C" int zp_answer_noalloc(zp_db* db, const uint32_t* dQ, uint32_t* dAns, void* stream) {
+  if (!db || !dQ || !dAns) return zp_set_error(ZP_EINVAL, "zp_answer_noalloc: null argument");
+  if (db->C > ZP_NOALLOC_MAX_C)
+    return zp_set_error(ZP_EINVAL,
+                        "zp_answer_noalloc: C=%u exceeds the %u columns its static buffer holds",
+                        db->C, ZP_NOALLOC_MAX_C);
+  const int dev = db->device;
+  if (dev < 0 || dev >= 64) return zp_set_error(ZP_EINVAL, "zp_answer_noalloc: device %d", dev);
+  ZP_CUDA(cudaSetDevice(dev));
+  uint32_t* qp;
+  {
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_planes[dev]) {
+      void* p = nullptr;
+      cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_qplanes);
+      if (e != cudaSuccess) return zp_cuda_check(e, "zp_answer_noalloc: cudaGetSymbolAddress");
+      g_noalloc_planes[dev] = static_cast<uint32_t*>(p);
+    }
+    qp = g_noalloc_planes[dev];
+  }
+  zp_ctx* ctx = db->ctx;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const uint32_t nct = (db->C + TCB - 1) / TCB;
+  const uint32_t nrb = (db->R + TR - 1) / TR;
+  zp_clear_pending_error();
+  ctx->launches++;
+  k_qplanes<<<(nct * 256u + 255) / 256, 256, 0, st>>>(dQ, db->C, nct, qp, dAns, db->R);
+  ZP_CUDA(cudaGetLastError());
+  if (!g_attr_done[dev & 63]) {
+    ZP_CUDA(cudaFuncSetAttribute(k_gemv, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    g_attr_done[dev & 63] = true;
+  }
+  const uint64_t T = (uint64_t)nrb * nct;
+  uint64_t grid = (uint64_t)ctx->num_sms * CTAS_PER_SM;
+  if (grid > T) grid = T;
+  zp_clear_pending_error();
+  ctx->launches++;
+  k_gemv<<<(unsigned)grid, (NCW + 1) * 32, SMEM_BYTES, st>>>(db->tmap_gemv, qp, dAns, db->R, nrb,
                                                              nct, ctx->d_status);
   ZP_CUDA(cudaGetLastError());
   return ZP_OK;
