@@ -155,8 +155,24 @@ int zp_client_destroy(zp_client* cl);
 int zp_compress(zp_db* db, zp_client* const* clients, const uint32_t* dAns,
                 const uint32_t* dCKO, uint32_t B, uint32_t* dT, void* stream);
 
+/* The two halves of zp_compress, for callers that schedule them themselves.
+ * zp_compress_products computes, for each query b, the exact row products
+ * V[b][r] = sum_i H[r][i] * cko[b][i] (no dependence on the answers) into library
+ * scratch; zp_compress_finish packs ans + V and reduces mod m_b into dT, exactly as
+ * zp_compress. The products of one call are consumed by the next finish call with the
+ * same B (ZP_ESTATE otherwise); both must be ordered on the caller's streams (the
+ * finish after the products). With the "overlap_sms" option set, the products use only
+ * that many SMs so that they can run concurrently with a single-query zp_answer.
+ * Errors as zp_compress. */
+int zp_compress_products(zp_db* db, const uint32_t* dCKO, uint32_t B, void* stream);
+int zp_compress_finish(zp_db* db, zp_client* const* clients, const uint32_t* dAns, uint32_t B,
+                       uint32_t* dT, void* stream);
+
 /* The whole online Response for B queries on DEVICE buffers: zp_answer into dAns,
- * then zp_compress into dT. Asynchronous on `stream`. */
+ * then zp_compress into dT. Asynchronous on `stream`. For one query with the
+ * "overlap_sms" option set, the compression products run on an internal stream
+ * (forked from and joined back to `stream` with events) on overlap_sms SMs while the
+ * answer streams the database on the remaining SMs. */
 int zp_respond(zp_db* db, zp_client* const* clients, const uint32_t* dQ, const uint32_t* dCKO,
                uint32_t B, uint32_t* dAns, uint32_t* dT, void* stream);
 
@@ -187,7 +203,10 @@ int zp_stale_rows(const zp_db* db, uint32_t* count);
  *                    hint), 1 CUDA-core dp4a kernels for every batch and the hint,
  *                    2 tensor cores also for a single query;
  *   "compress_path": 0 auto (tensor cores when n <= 1024), 1 CUDA-core products,
- *                    2 tensor cores (ZP_EUNSUPPORTED at call time if n > 1024).
+ *                    2 tensor cores (ZP_EUNSUPPORTED at call time if n > 1024);
+ *   "overlap_sms":   0 (default) or the number of SMs on which the compression products
+ *                    of a single query run while the answer uses the other SMs
+ *                    (zp_respond, zp_compress_products, single-query zp_answer).
  * Every variant computes the same exact result. Errors: ZP_EINVAL (unknown name or value). */
 int zp_set_option(zp_ctx* ctx, const char* name, int64_t value);
 

@@ -30,6 +30,7 @@ EXPORTS = [
     "zp_db_destroy", "zp_gen_hint", "zp_answer", "zp_register_client", "zp_client_destroy",
     "zp_compress", "zp_respond", "zp_respond_host", "zp_update_rows", "zp_stale_rows",
     "zp_device_status", "zp_kernel_launches", "zp_set_option", "zp_answer_noalloc",
+    "zp_compress_products", "zp_compress_finish",
 ]
 
 
@@ -78,6 +79,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "zp_kernel_launches": (i32, [vp, ctypes.POINTER(u64)]),
         "zp_set_option": (i32, [vp, ctypes.c_char_p, ctypes.c_int64]),
         "zp_answer_noalloc": (i32, [vp, vp, vp, vp]),
+        "zp_compress_products": (i32, [vp, vp, u32, vp]),
+        "zp_compress_finish": (i32, [vp, vp, vp, u32, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -202,6 +205,15 @@ def _client_array(clients) -> ctypes.Array:
 def zp_compress(db: int, clients, dAns: int, dCKO: int, B: int, dT: int, stream: int | None):
     _check(load_library().zp_compress(db, ctypes.cast(_client_array(clients), ctypes.c_void_p),
                                       dAns, dCKO, B, dT, stream))
+
+
+def zp_compress_products(db: int, dCKO: int, B: int, stream: int | None):
+    _check(load_library().zp_compress_products(db, dCKO, B, stream))
+
+
+def zp_compress_finish(db: int, clients, dAns: int, B: int, dT: int, stream: int | None):
+    _check(load_library().zp_compress_finish(db, ctypes.cast(_client_array(clients), ctypes.c_void_p),
+                                             dAns, B, dT, stream))
 
 
 def zp_respond(db: int, clients, dQ: int, dCKO: int, B: int, dAns: int, dT: int, stream: int | None):

@@ -320,8 +320,8 @@ __global__ void __launch_bounds__(PACK_WARPS * 32)
 
 }  // namespace
 
-int zp_launch_compress(zp_db* db, zp_client* const* clients, const uint32_t* dAns,
-                       const uint32_t* dCKO, uint32_t B, uint32_t* dT, cudaStream_t st) {
+int zp_launch_compress_products(zp_db* db, const uint32_t* dCKO, uint32_t B, cudaStream_t st,
+                                uint32_t max_ctas) {
   zp_ctx* ctx = db->ctx;
   const uint32_t R = db->R, n = ctx->P.n;
   if (ctx->compress_path == ZP_PATH_TC && n > 1024)
@@ -329,20 +329,9 @@ int zp_launch_compress(zp_db* db, zp_client* const* clients, const uint32_t* dAn
   const bool tc = ctx->compress_path != ZP_PATH_SIMT && n <= 1024;
   int rc = zp_scratch_reserve(&db->s_v, (size_t)B * db->Rp * VW * sizeof(uint32_t));
   if (rc) return rc;
-  rc = zp_scratch_reserve(&db->s_clients, (size_t)B * sizeof(ClientPtrs));
-  if (rc) return rc;
   uint32_t* V = static_cast<uint32_t*>(db->s_v.p);
-  ClientPtrs* dcl = static_cast<ClientPtrs*>(db->s_clients.p);
-  {
-    ClientPtrs* h = new ClientPtrs[B];
-    for (uint32_t b = 0; b < B; ++b) h[b] = ClientPtrs{clients[b]->d_m, clients[b]->d_mu};
-    // pageable source: the copy is staged before cudaMemcpyAsync returns
-    cudaError_t e = cudaMemcpyAsync(dcl, h, B * sizeof(ClientPtrs), cudaMemcpyHostToDevice, st);
-    delete[] h;
-    if (e != cudaSuccess) return zp_cuda_check(e, "cudaMemcpyAsync(clients)");
-  }
   if (tc) {
-    rc = zp_launch_vmul_tc(db, dCKO, B, V, st);
+    rc = zp_launch_vmul_tc(db, dCKO, B, V, st, max_ctas);
     if (rc) return rc;
   } else {
     dim3 grid((R + 3) / 4, B);
@@ -351,20 +340,51 @@ int zp_launch_compress(zp_db* db, zp_client* const* clients, const uint32_t* dAn
     k_vmul_simt<<<grid, 256, 0, st>>>(db->d_hneg, R, db->Rp, n, dCKO, V);
     ZP_CUDA(cudaGetLastError());
   }
-  {
-    const size_t smem = (size_t)PACK_WARPS * (sizeof(PackBarrett) + (size_t)ctx->ell * VW * 4);
-    static bool attr = false;
-    if (!attr) {
-      ZP_CUDA(cudaFuncSetAttribute(k_pack_reduce, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)(PACK_WARPS * (sizeof(PackBarrett) + 64 * VW * 4))));
-      attr = true;
+  db->v_batch = B;
+  return ZP_OK;
+}
+
+int zp_launch_compress_finish(zp_db* db, zp_client* const* clients, const uint32_t* dAns,
+                              uint32_t B, uint32_t* dT, cudaStream_t st) {
+  zp_ctx* ctx = db->ctx;
+  if (db->v_batch != B)
+    return zp_set_error(ZP_ESTATE, "compression finish for %u queries, products hold %u", B,
+                        db->v_batch);
+  uint32_t* V = static_cast<uint32_t*>(db->s_v.p);
+  int rc = zp_scratch_reserve(&db->s_clients, (size_t)B * sizeof(ClientPtrs));
+  if (rc) return rc;
+  ClientPtrs* dcl = static_cast<ClientPtrs*>(db->s_clients.p);
+  // upload the per-query client constants only when the list changed
+  bool same = db->cl_cache.size() == 2 * (size_t)B;
+  for (uint32_t b = 0; same && b < B; ++b)
+    same = db->cl_cache[2 * b] == clients[b]->d_m && db->cl_cache[2 * b + 1] == clients[b]->d_mu;
+  if (!same) {
+    std::vector<ClientPtrs> h(B);
+    db->cl_cache.resize(2 * (size_t)B);
+    for (uint32_t b = 0; b < B; ++b) {
+      h[b] = ClientPtrs{clients[b]->d_m, clients[b]->d_mu};
+      db->cl_cache[2 * b] = clients[b]->d_m;
+      db->cl_cache[2 * b + 1] = clients[b]->d_mu;
     }
-    dim3 grid((db->d1p + PACK_WARPS - 1) / PACK_WARPS, B);
-    zp_clear_pending_error();
-    ctx->launches++;
-    k_pack_reduce<<<grid, PACK_WARPS * 32, smem, st>>>(dAns, V, R, db->Rp, ctx->ell, db->d1p,
-                                                       ctx->gamma_w[1], ctx->gamma_w[2], dcl, dT);
-    ZP_CUDA(cudaGetLastError());
+    // pageable source: the copy is staged before cudaMemcpyAsync returns
+    cudaError_t e = cudaMemcpyAsync(dcl, h.data(), B * sizeof(ClientPtrs), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) {
+      db->cl_cache.clear();
+      return zp_cuda_check(e, "cudaMemcpyAsync(clients)");
+    }
   }
+  const size_t smem = (size_t)PACK_WARPS * (sizeof(PackBarrett) + (size_t)ctx->ell * VW * 4);
+  static bool attr = false;
+  if (!attr) {
+    ZP_CUDA(cudaFuncSetAttribute(k_pack_reduce, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(PACK_WARPS * (sizeof(PackBarrett) + 64 * VW * 4))));
+    attr = true;
+  }
+  dim3 grid((db->d1p + PACK_WARPS - 1) / PACK_WARPS, B);
+  zp_clear_pending_error();
+  ctx->launches++;
+  k_pack_reduce<<<grid, PACK_WARPS * 32, smem, st>>>(dAns, V, db->R, db->Rp, ctx->ell, db->d1p,
+                                                     ctx->gamma_w[1], ctx->gamma_w[2], dcl, dT);
+  ZP_CUDA(cudaGetLastError());
   return ZP_OK;
 }

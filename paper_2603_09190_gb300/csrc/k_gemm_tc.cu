@@ -600,7 +600,7 @@ bool g_attr[3][3] = {{false}};
 
 template <int MODE, int BT>
 int launch_gemm(zp_ctx* ctx, const CUtensorMap& tmA, const CUtensorMap& tmB, const GemmArgs& ga,
-                cudaStream_t st) {
+                cudaStream_t st, uint32_t max_ctas = 0) {
   constexpr int bi = BT == 16 ? 0 : (BT == 32 ? 1 : 2);
   if (!g_attr[MODE][bi]) {
     ZP_CUDA(cudaFuncSetAttribute(k_gemm_tc<MODE, BT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -609,6 +609,7 @@ int launch_gemm(zp_ctx* ctx, const CUtensorMap& tmA, const CUtensorMap& tmB, con
   }
   uint32_t tiles = ga.num_m_tiles * ga.num_n_tiles;
   uint32_t grid = tiles < (uint32_t)ctx->num_sms ? tiles : (uint32_t)ctx->num_sms;
+  if (max_ctas && grid > max_ctas) grid = max_ctas;
   zp_clear_pending_error();
   ctx->launches++;
   k_gemm_tc<MODE, BT><<<grid, NTHREADS, Cfg<MODE>::SMEM, st>>>(tmA, tmB, ga);
@@ -677,7 +678,8 @@ int zp_launch_answer_tc(zp_db* db, const CUtensorMap& tmD, uint32_t Rrows, const
 }
 
 // Compression products V4[b][a][r][67] = sum_i Hbyte_a[r][i] cko[b][i] (n <= 1024).
-int zp_launch_vmul_tc(zp_db* db, const uint32_t* dCKO, uint32_t B, uint32_t* V4, cudaStream_t st) {
+int zp_launch_vmul_tc(zp_db* db, const uint32_t* dCKO, uint32_t B, uint32_t* V4, cudaStream_t st,
+                      uint32_t max_ctas) {
   zp_ctx* ctx = db->ctx;
   const uint32_t n = ctx->P.n;
   const uint32_t Kp = (n + 63) / 64 * 64;
@@ -710,5 +712,5 @@ int zp_launch_vmul_tc(zp_db* db, const uint32_t* dCKO, uint32_t B, uint32_t* V4,
   ga.out_ld = 0;
   ga.Rp = db->Rp;
   ga.status = ctx->d_status;
-  return launch_gemm<MODE_CMP, 64>(ctx, db->tmap_hpl, tmB, ga, st);
+  return launch_gemm<MODE_CMP, 64>(ctx, db->tmap_hpl, tmB, ga, st, max_ctas);
 }

@@ -23,9 +23,9 @@ constexpr int NCW = 8;                   // consumer warps
 constexpr int TILE_BYTES = TR * TCB;     // 16 KiB
 constexpr int QT_BYTES = 4 * 16 * 16;    // q planes of one column tile: 4 planes x 16 chunks x 16 B
 constexpr int STAGE_BYTES = TILE_BYTES + QT_BYTES;
-constexpr int STAGES = 6;
+constexpr int STAGES = 12;
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 2 * STAGES * 8;
-constexpr int CTAS_PER_SM = 2;
+constexpr int CTAS_PER_SM = 1;  // > 114 KiB of shared memory: an SM runs one GEMV CTA and nothing else
 
 // Byte planes of the query for the GEMV tile layout. Word index
 //   ((ct * 4 + k) * 16 + j) * 4 + w
@@ -162,7 +162,8 @@ bool g_attr_done[64] = {false};
 
 }  // namespace
 
-int zp_launch_gemv(zp_db* db, const uint32_t* dq, uint32_t* dans, cudaStream_t st) {
+int zp_launch_gemv(zp_db* db, const uint32_t* dq, uint32_t* dans, cudaStream_t st,
+                   uint32_t max_ctas) {
   zp_ctx* ctx = db->ctx;
   const uint32_t nct = (db->C + TCB - 1) / TCB;
   const uint32_t nrb = (db->R + TR - 1) / TR;
@@ -183,6 +184,7 @@ int zp_launch_gemv(zp_db* db, const uint32_t* dq, uint32_t* dans, cudaStream_t s
   }
   const uint64_t T = (uint64_t)nrb * nct;
   uint64_t grid = (uint64_t)ctx->num_sms * CTAS_PER_SM;
+  if (max_ctas && grid > max_ctas) grid = max_ctas;
   if (grid > T) grid = T;
   zp_clear_pending_error();
   ctx->launches++;

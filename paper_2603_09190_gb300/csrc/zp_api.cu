@@ -183,6 +183,7 @@ extern "C" int zp_init(int device, const zp_params* P, zp_ctx** out) {
     c->launches = 0;
     c->answer_path = ZP_PATH_AUTO;
     c->compress_path = ZP_PATH_AUTO;
+    c->overlap_sms = 0;
     e = cudaMalloc(&c->d_status, sizeof(uint32_t));
     if (e != cudaSuccess) {
       delete c;
@@ -213,6 +214,13 @@ extern "C" int zp_set_option(zp_ctx* c, const char* name, int64_t value) {
     if (value < ZP_PATH_AUTO || value > ZP_PATH_TC)
       return zp_set_error(ZP_EINVAL, "zp_set_option: %s=%lld out of range", name, (long long)value);
     (k == "answer_path" ? c->answer_path : c->compress_path) = (int)value;
+    return ZP_OK;
+  }
+  if (k == "overlap_sms") {
+    if (value < 0 || value >= c->num_sms)
+      return zp_set_error(ZP_EINVAL, "zp_set_option: overlap_sms=%lld out of [0, %d)",
+                          (long long)value, c->num_sms);
+    c->overlap_sms = (uint32_t)value;
     return ZP_OK;
   }
   return zp_set_error(ZP_EINVAL, "zp_set_option: unknown option '%s'", name);
@@ -262,6 +270,9 @@ extern "C" int zp_setup_db(zp_ctx* c, const uint8_t* dD, uint32_t R, uint32_t C,
     db->hpl_ld = ((uint64_t)c->P.n + 15) / 16 * 16;
     db->hint_ready = false;
     db->stale = 0;
+    db->v_batch = 0;
+    db->side = nullptr;
+    db->ev_fork = db->ev_join = nullptr;
     cudaError_t e = cudaMalloc(&db->d_rowsum, (size_t)R * sizeof(uint32_t));
     if (e != cudaSuccess) {
       delete db;
@@ -316,6 +327,11 @@ extern "C" int zp_db_destroy(zp_db* db) {
   if (db->d_hneg) cudaFree(db->d_hneg);
   if (db->d_hpl) cudaFree(db->d_hpl);
   if (db->d_hpl_rowsum) cudaFree(db->d_hpl_rowsum);
+  if (db->side) {
+    cudaStreamDestroy(db->side);
+    cudaEventDestroy(db->ev_fork);
+    cudaEventDestroy(db->ev_join);
+  }
   zp_scratch* all[] = {&db->s_qplanes, &db->s_v,   &db->s_q,   &db->s_cko,  &db->s_ans,
                        &db->s_t,       &db->s_clients, &db->s_misc, &db->s_tcq, &db->s_hq,
                        &db->s_hcko};
@@ -473,7 +489,8 @@ extern "C" int zp_answer(zp_db* db, const uint32_t* dQ, uint32_t B, uint32_t* dA
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   zp_ctx* c = db->ctx;
   if (B == 1 && c->answer_path != ZP_PATH_SIMT && c->answer_path != ZP_PATH_TC)
-    return zp_launch_gemv(db, dQ, dAns, st);
+    return zp_launch_gemv(db, dQ, dAns, st,
+                          c->overlap_sms ? (uint32_t)c->num_sms - c->overlap_sms : 0u);
   if (c->answer_path == ZP_PATH_SIMT)
     return zp_launch_answer_simt(db, dQ, B, db->C, dAns, db->R, 1, db->dD, db->R, db->ld, st);
   return zp_launch_answer_tc(db, db->tmap_gemm, db->R, dQ, B, false, dAns, db->R, false,
@@ -576,21 +593,83 @@ extern "C" int zp_compress(zp_db* db, zp_client* const* clients, const uint32_t*
     int rc = check_compress_args(db, clients, B);
     if (rc) return rc;
     ZP_CUDA(cudaSetDevice(db->ctx->device));
-    return zp_launch_compress(db, clients, dAns, dCKO, B, dT, static_cast<cudaStream_t>(stream));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    rc = zp_launch_compress_products(db, dCKO, B, st, 0);
+    if (rc) return rc;
+    return zp_launch_compress_finish(db, clients, dAns, B, dT, st);
   } catch (const std::bad_alloc&) {
     return zp_set_error(ZP_ENOMEM, "zp_compress: host allocation failed");
   }
 }
 
+extern "C" int zp_compress_products(zp_db* db, const uint32_t* dCKO, uint32_t B, void* stream) {
+  try {
+    if (!db || !dCKO) return zp_set_error(ZP_EINVAL, "zp_compress_products: null argument");
+    if (B < 1 || B > 4096) return zp_set_error(ZP_EINVAL, "zp_compress_products: B=%u out of [1, 4096]", B);
+    if (!db->hint_ready) return zp_set_error(ZP_ESTATE, "zp_compress_products: no hint (call zp_gen_hint)");
+    if (db->stale) return zp_set_error(ZP_ESTATE, "zp_compress_products: %u hint rows stale", db->stale);
+    ZP_CUDA(cudaSetDevice(db->ctx->device));
+    return zp_launch_compress_products(db, dCKO, B, static_cast<cudaStream_t>(stream),
+                                       db->ctx->overlap_sms);
+  } catch (const std::bad_alloc&) {
+    return zp_set_error(ZP_ENOMEM, "zp_compress_products: host allocation failed");
+  }
+}
+
+extern "C" int zp_compress_finish(zp_db* db, zp_client* const* clients, const uint32_t* dAns,
+                                  uint32_t B, uint32_t* dT, void* stream) {
+  try {
+    if (!db || !dAns || !dT) return zp_set_error(ZP_EINVAL, "zp_compress_finish: null argument");
+    int rc = check_compress_args(db, clients, B);
+    if (rc) return rc;
+    ZP_CUDA(cudaSetDevice(db->ctx->device));
+    return zp_launch_compress_finish(db, clients, dAns, B, dT, static_cast<cudaStream_t>(stream));
+  } catch (const std::bad_alloc&) {
+    return zp_set_error(ZP_ENOMEM, "zp_compress_finish: host allocation failed");
+  }
+}
+
+static int ensure_side_stream(zp_db* db) {
+  if (db->side) return ZP_OK;
+  ZP_CUDA(cudaStreamCreateWithFlags(&db->side, cudaStreamNonBlocking));
+  ZP_CUDA(cudaEventCreateWithFlags(&db->ev_fork, cudaEventDisableTiming));
+  ZP_CUDA(cudaEventCreateWithFlags(&db->ev_join, cudaEventDisableTiming));
+  return ZP_OK;
+}
+
 extern "C" int zp_respond(zp_db* db, zp_client* const* clients, const uint32_t* dQ,
                           const uint32_t* dCKO, uint32_t B, uint32_t* dAns, uint32_t* dT,
                           void* stream) {
-  if (!db || !dQ || !dCKO || !dAns || !dT) return zp_set_error(ZP_EINVAL, "zp_respond: null argument");
-  int rc = check_compress_args(db, clients, B);
-  if (rc) return rc;
-  rc = zp_answer(db, dQ, B, dAns, stream);
-  if (rc) return rc;
-  return zp_compress(db, clients, dAns, dCKO, B, dT, stream);
+  try {
+    if (!db || !dQ || !dCKO || !dAns || !dT) return zp_set_error(ZP_EINVAL, "zp_respond: null argument");
+    int rc = check_compress_args(db, clients, B);
+    if (rc) return rc;
+    zp_ctx* c = db->ctx;
+    ZP_CUDA(cudaSetDevice(c->device));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const bool overlap = B == 1 && c->overlap_sms > 0 && c->answer_path == ZP_PATH_AUTO &&
+                         c->compress_path != ZP_PATH_SIMT && c->P.n <= 1024;
+    if (!overlap) {
+      rc = zp_answer(db, dQ, B, dAns, stream);
+      if (rc) return rc;
+      return zp_compress(db, clients, dAns, dCKO, B, dT, stream);
+    }
+    // The products V = H.cko do not depend on the answer: they run on `overlap_sms` SMs
+    // of an internal stream while the HBM-bound GEMV streams the database on the rest.
+    rc = ensure_side_stream(db);
+    if (rc) return rc;
+    ZP_CUDA(cudaEventRecord(db->ev_fork, st));
+    ZP_CUDA(cudaStreamWaitEvent(db->side, db->ev_fork, 0));
+    rc = zp_launch_compress_products(db, dCKO, B, db->side, c->overlap_sms);
+    if (rc) return rc;
+    rc = zp_launch_gemv(db, dQ, dAns, st, (uint32_t)c->num_sms - c->overlap_sms);
+    if (rc) return rc;
+    ZP_CUDA(cudaEventRecord(db->ev_join, db->side));
+    ZP_CUDA(cudaStreamWaitEvent(st, db->ev_join, 0));
+    return zp_launch_compress_finish(db, clients, dAns, B, dT, st);
+  } catch (const std::bad_alloc&) {
+    return zp_set_error(ZP_ENOMEM, "zp_respond: host allocation failed");
+  }
 }
 
 extern "C" int zp_respond_host(zp_db* db, zp_client* const* clients, const uint32_t* hQ,

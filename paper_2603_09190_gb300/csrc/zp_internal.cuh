@@ -32,6 +32,8 @@ struct zp_ctx {
   zp_params P;
   int answer_path;     // ZP_PATH_* for batched answers and the hint
   int compress_path;   // ZP_PATH_* for the compression products
+  uint32_t overlap_sms;  // SMs given to the compression products while a single-query
+                         // answer runs on the others (0: no overlap)
   uint32_t ell;        // slots per packed row
   uint32_t L;          // limbs per element of Z_m
   uint32_t gamma_w[3]; // packing scale gamma, little-endian 32-bit words (gamma < 2^96)
@@ -73,6 +75,10 @@ struct zp_db {
   bool hint_ready;
   uint32_t stale;          // rows updated since the last hint generation
   std::vector<uint8_t> stale_v;  // per-row stale flags (host)
+  uint32_t v_batch;        // queries whose products are in s_v (0: none)
+  std::vector<const uint32_t*> cl_cache;  // client constants last uploaded to s_clients
+  cudaStream_t side;       // internal stream of zp_respond's overlap (lazily created)
+  cudaEvent_t ev_fork, ev_join;
   // scratch, grown on demand (never shrunk before zp_db_destroy)
   zp_scratch s_qplanes, s_v, s_q, s_cko, s_ans, s_t, s_clients, s_misc, s_tcq, s_hq, s_hcko;
 };
@@ -107,16 +113,20 @@ int zp_launch_copy_rows(const uint8_t* src, uint64_t lds, uint8_t* dst, uint64_t
 int zp_launch_answer_tc(zp_db* db, const CUtensorMap& tmD, uint32_t Rrows, const uint32_t* dQ,
                         uint32_t B, bool q_cols, uint32_t* dOut, uint64_t out_ld, bool hint,
                         const uint32_t* rowsum, cudaStream_t st);
-int zp_launch_vmul_tc(zp_db* db, const uint32_t* dCKO, uint32_t B, uint32_t* V4, cudaStream_t st);
+int zp_launch_vmul_tc(zp_db* db, const uint32_t* dCKO, uint32_t B, uint32_t* V4, cudaStream_t st,
+                      uint32_t max_ctas);
 int zp_launch_hint_planes_rowsum(zp_db* db, const uint32_t* rows, uint32_t nrows, cudaStream_t st);
-int zp_launch_gemv(zp_db* db, const uint32_t* dq, uint32_t* dans, cudaStream_t st);
+int zp_launch_gemv(zp_db* db, const uint32_t* dq, uint32_t* dans, cudaStream_t st,
+                   uint32_t max_ctas);
 int zp_launch_answer_simt(zp_db* db, const uint32_t* dQ, uint32_t B, uint32_t ldq,
                           uint32_t* dOut, uint64_t out_stride_b, uint64_t out_stride_r,
                           const uint8_t* dDrows, uint32_t Rrows, uint64_t ld, cudaStream_t st);
 int zp_launch_hint_post(zp_db* db, const uint32_t* dHplus_compact, const uint32_t* rows,
                         uint32_t nrows, uint32_t* dH, cudaStream_t st);
-int zp_launch_compress(zp_db* db, zp_client* const* clients, const uint32_t* dAns,
-                       const uint32_t* dCKO, uint32_t B, uint32_t* dT, cudaStream_t st);
+int zp_launch_compress_products(zp_db* db, const uint32_t* dCKO, uint32_t B, cudaStream_t st,
+                                uint32_t max_ctas);
+int zp_launch_compress_finish(zp_db* db, zp_client* const* clients, const uint32_t* dAns,
+                              uint32_t B, uint32_t* dT, cudaStream_t st);
 int zp_launch_update_rows(zp_db* db, const uint32_t* rows, uint32_t k, const uint8_t* dNew,
                           cudaStream_t st);
 

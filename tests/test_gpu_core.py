@@ -333,3 +333,58 @@ def test_compress_zero_database(zp):
             ans[0], np.zeros((R, n), dtype=np.uint32), cko, m, P)
     db.close()
     c.close()
+
+
+@pytest.mark.parametrize("overlap", [0, 40, 100])
+def test_respond_overlap_identical(zp, overlap):
+    """With the compression products running concurrently on a subset of SMs, the single-query
+    Response is identical to the oracle (and to the sequential one)."""
+    R, C, n = 2000, 3000, 1024
+    P = Params(n=n, key_bits=2048)
+    c = zp.Context(0, n=n)
+    c.set_option("overlap_sms", overlap)
+    D = synth.database(R, C, 21)
+    A = synth.seed_matrix(C, n, 21)
+    Hn = lwe.hint_neg(D, A)
+    dD, ld = to_dev_db(zp, D)
+    db = zp.Database(c, dD, R, C, ld)
+    db.gen_hint(u32_dev(A))
+    m = synth.random_odd_modulus(2048, 22)
+    cl = c.register_client(m)
+    q = synth.uniform_queries(1, C, 23)
+    cko = synth.uniform_below(m, n, 24)
+    for rep in range(2):
+        ans, T = db.respond([cl], u32_dev(q), u32_dev(synth.ints_to_limbs(cko, 64)[None]))
+        want = lwe.matvec_mod_q(D, q[0])
+        assert np.array_equal(u32_host(ans)[0], want)
+        assert synth.limbs_to_ints(u32_host(T)[0]) == zippir.compress_rows(want, Hn, cko, m, P)
+    assert c.device_status() == 0
+    db.close()
+    c.close()
+
+
+def test_split_compress_api(zp):
+    """zp_compress_products + zp_compress_finish equal zp_compress; a finish whose batch
+    does not match the products is refused."""
+    R, C, n = 300, 200, 128
+    c = zp.Context(0, n=n)
+    D = synth.database(R, C, 31)
+    A = synth.seed_matrix(C, n, 31)
+    dD, ld = to_dev_db(zp, D)
+    db = zp.Database(c, dD, R, C, ld)
+    db.gen_hint(u32_dev(A))
+    m = synth.random_odd_modulus(2048, 32)
+    cl = c.register_client(m)
+    cko = u32_dev(np.stack([synth.ints_to_limbs(synth.uniform_below(m, n, 33 + b), 64) for b in range(2)]))
+    ans = u32_dev(synth.uniform_queries(2, R, 34))
+    ref = db.compress([cl, cl], ans, cko)
+    st = torch.cuda.current_stream().cuda_stream
+    T = torch.empty_like(ref)
+    zp.zp_compress_products(db.handle, cko.data_ptr(), 2, st)
+    zp.zp_compress_finish(db.handle, [cl, cl], ans.data_ptr(), 2, T.data_ptr(), st)
+    assert torch.equal(T, ref)
+    with pytest.raises(zp.ZipPIRError) as ei:
+        zp.zp_compress_finish(db.handle, [cl], ans.data_ptr(), 1, T.data_ptr(), st)
+    assert ei.value.code == zp.ZP_ESTATE
+    db.close()
+    c.close()
