@@ -204,11 +204,14 @@ int zp_stale_rows(const zp_db* db, uint32_t* count);
  *                    2 tensor cores also for a single query;
  *   "compress_path": 0 auto (tensor cores when n <= 1024), 1 CUDA-core products,
  *                    2 tensor cores (ZP_EUNSUPPORTED at call time if n > 1024);
- *   "overlap_sms":   0 (default) or the number of SMs on which the compression products
- *                    of a single query run while the answer uses the other SMs
- *                    (zp_respond, zp_compress_products, single-query zp_answer).
+ *   "overlap_sms":   the number of SMs on which the compression products of a single
+ *                    query run while the answer uses the other SMs (zp_respond,
+ *                    zp_compress_products, single-query zp_answer); 0 = no overlap.
+ *                    Default: about 3/8 of the SMs (56 of 152) on GPUs with >= 64 SMs.
  * Every variant computes the same exact result. Errors: ZP_EINVAL (unknown name or value). */
 int zp_set_option(zp_ctx* ctx, const char* name, int64_t value);
+/* Reads an option set by zp_set_option (or its default). Errors: ZP_EINVAL. */
+int zp_get_option(const zp_ctx* ctx, const char* name, int64_t* value);
 
 /* Number of kernels this context has launched so far (all entry points). */
 int zp_kernel_launches(const zp_ctx* ctx, uint64_t* count);

@@ -30,7 +30,7 @@ EXPORTS = [
     "zp_db_destroy", "zp_gen_hint", "zp_answer", "zp_register_client", "zp_client_destroy",
     "zp_compress", "zp_respond", "zp_respond_host", "zp_update_rows", "zp_stale_rows",
     "zp_device_status", "zp_kernel_launches", "zp_set_option", "zp_answer_noalloc",
-    "zp_compress_products", "zp_compress_finish",
+    "zp_compress_products", "zp_compress_finish", "zp_get_option",
 ]
 
 
@@ -81,6 +81,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "zp_answer_noalloc": (i32, [vp, vp, vp, vp]),
         "zp_compress_products": (i32, [vp, vp, u32, vp]),
         "zp_compress_finish": (i32, [vp, vp, vp, u32, vp, vp]),
+        "zp_get_option": (i32, [vp, ctypes.c_char_p, ctypes.POINTER(ctypes.c_int64)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -250,6 +251,14 @@ def zp_device_status(ctx: int) -> int:
 
 def zp_set_option(ctx: int, name: str, value: int):
     _check(load_library().zp_set_option(ctx, name.encode(), int(value)))
+
+
+def zp_get_overlap(ctx) -> int:
+    """Current "overlap_sms" option of a context (Context or handle)."""
+    h = ctx.handle if isinstance(ctx, Context) else ctx
+    v = ctypes.c_int64()
+    _check(load_library().zp_get_option(h, b"overlap_sms", ctypes.byref(v)))
+    return v.value
 
 
 def zp_kernel_launches(ctx: int) -> int:

@@ -216,8 +216,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       }
       // Stay until the copies issued last have landed (bounded, ignores the abort flag).
       const uint32_t f_u = cnt > (uint32_t)SU ? cnt - SU : 0;
+      const unsigned long long deadline = clock64() + ZP_WAIT_CYCLES;
       for (uint32_t i = f_u; i < cnt; ++i)
-        mbar_wait_bounded(&u8_full[i % SU], (i / SU) & 1u, args.status, ZP_DEV_TIMEOUT_GEMM);
+        if (!mbar_wait_until(&u8_full[i % SU], (i / SU) & 1u, deadline)) {
+          atomicOr(args.status, ZP_DEV_TIMEOUT_GEMM);
+          break;
+        }
     }
   } else if (warp == 2) {
     // ------------------------------------------------------------ TMA producer of B (fp16)
@@ -241,8 +245,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       }
       // Stay until the copies issued last have landed (bounded, ignores the abort flag).
       const uint32_t f_o = cnt > (uint32_t)SO ? cnt - SO : 0;
+      const unsigned long long deadline = clock64() + ZP_WAIT_CYCLES;
       for (uint32_t i = f_o; i < cnt; ++i)
-        mbar_wait_bounded(&b_full[i % SO], (i / SO) & 1u, args.status, ZP_DEV_TIMEOUT_GEMM);
+        if (!mbar_wait_until(&b_full[i % SO], (i / SO) & 1u, deadline)) {
+          atomicOr(args.status, ZP_DEV_TIMEOUT_GEMM);
+          break;
+        }
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
@@ -289,7 +297,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       }
       // every MMA issued has completed before TMEM is released
       umma_commit(mma_done);
-      mbar_wait_bounded(mma_done, 0, args.status, ZP_DEV_TIMEOUT_GEMM);
+      if (!mbar_wait_until(mma_done, 0, clock64() + ZP_WAIT_CYCLES))
+        atomicOr(args.status, ZP_DEV_TIMEOUT_GEMM);
     }
     __syncwarp();
   } else if (warp >= 8) {

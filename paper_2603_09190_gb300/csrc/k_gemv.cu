@@ -17,15 +17,25 @@
 
 namespace {
 
-constexpr int TR = 64;                   // rows per tile
 constexpr int TCB = 256;                 // bytes (= columns) per tile row
-constexpr int NCW = 8;                   // consumer warps
-constexpr int TILE_BYTES = TR * TCB;     // 16 KiB
 constexpr int QT_BYTES = 4 * 16 * 16;    // q planes of one column tile: 4 planes x 16 chunks x 16 B
-constexpr int STAGE_BYTES = TILE_BYTES + QT_BYTES;
-constexpr int STAGES = 12;
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 2 * STAGES * 8;
-constexpr int CTAS_PER_SM = 1;  // > 114 KiB of shared memory: an SM runs one GEMV CTA and nothing else
+
+// Two configurations, both with more than 114 KiB of shared memory so that an SM runs
+// one GEMV CTA and nothing else (which also keeps the SM split of zp_respond clean):
+//   <8 consumer warps, 12 stages of 64 x 256 bytes>   fastest on the whole GPU;
+//   <16 consumer warps, 6 stages of 128 x 256 bytes>  larger TMA boxes and more warps,
+//     about 40% more bytes per SM per second, used when the GEMV shares the GPU with
+//     the compression products.
+template <int NCW, int STAGES>
+struct GemvCfg {
+  static constexpr int TR = NCW * 8;  // rows per tile: 2 row groups of 4 rows per warp
+  static constexpr int TILE_BYTES = TR * TCB;
+  static constexpr int STAGE_BYTES = TILE_BYTES + QT_BYTES;
+  static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 2 * STAGES * 8 + 16;
+};
+// rows per tile of the whole-GPU configuration (the tensor map db->tmap_gemv)
+constexpr int TR = GemvCfg<8, 12>::TR;
+constexpr int CTAS_PER_SM = 1;
 
 // Byte planes of the query for the GEMV tile layout. Word index
 //   ((ct * 4 + k) * 16 + j) * 4 + w
@@ -50,13 +60,17 @@ __global__ void k_qplanes(const uint32_t* __restrict__ q, uint32_t C, uint32_t n
   for (uint32_t r = tid; r < R; r += gridDim.x * blockDim.x) ans[r] = 0u;
 }
 
+template <int NCW, int STAGES>
 __global__ void __launch_bounds__((NCW + 1) * 32, 1)
     k_gemv(const __grid_constant__ CUtensorMap tmap, const uint32_t* __restrict__ qp,
            uint32_t* __restrict__ ans, uint32_t R, uint32_t nrb, uint32_t nct,
            uint32_t* status) {
+  using G = GemvCfg<NCW, STAGES>;
+  constexpr int TR = G::TR, TILE_BYTES = G::TILE_BYTES, STAGE_BYTES = G::STAGE_BYTES;
   extern __shared__ __align__(1024) uint8_t smem[];
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
   uint64_t* empty = full + STAGES;
+  volatile uint32_t* abort_flag = reinterpret_cast<volatile uint32_t*>(empty + STAGES);
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint64_t T = (uint64_t)nrb * nct;
   const uint64_t t_begin = T * blockIdx.x / gridDim.x;
@@ -67,6 +81,7 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1)
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], NCW);
     }
+    *abort_flag = 0u;
     fence_mbar_init();
   }
   __syncthreads();
@@ -79,8 +94,8 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1)
       uint32_t issued = 0;
       for (uint64_t t = t_begin; t < t_end; ++t, ++issued) {
         const uint32_t s = issued % STAGES, round = issued / STAGES;
-        if (round > 0 &&
-            !mbar_wait_bounded(&empty[s], (round - 1) & 1u, status, ZP_DEV_TIMEOUT_GEMV))
+        if (round > 0 && !mbar_wait_abortable(&empty[s], (round - 1) & 1u, abort_flag, status,
+                                              ZP_DEV_TIMEOUT_GEMV))
           break;
         const uint32_t rb = (uint32_t)(t / nct), ct = (uint32_t)(t % nct);
         uint8_t* st = smem + s * STAGE_BYTES;
@@ -88,10 +103,14 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1)
         tma_load_2d_hint(st, &tmap, (int32_t)(ct * TCB), (int32_t)(rb * TR), &full[s], pol);
         bulk_load(st + TILE_BYTES, qp + (size_t)ct * 256u, QT_BYTES, &full[s]);
       }
-      // Stay alive until every copy this thread issued has landed (bounded).
+      // Stay alive until every copy this thread issued has landed (one bounded deadline).
       const uint32_t first = issued > STAGES ? issued - STAGES : 0;
+      const unsigned long long deadline = clock64() + ZP_WAIT_CYCLES;
       for (uint32_t i = first; i < issued; ++i)
-        mbar_wait_bounded(&full[i % STAGES], (i / STAGES) & 1u, status, ZP_DEV_TIMEOUT_GEMV);
+        if (!mbar_wait_until(&full[i % STAGES], (i / STAGES) & 1u, deadline)) {
+          atomicOr(status, ZP_DEV_TIMEOUT_GEMV);
+          break;
+        }
     }
     return;
   }
@@ -130,7 +149,7 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1)
       cur_rb = rb;
     }
     const uint32_t s = consumed % STAGES, round = consumed / STAGES;
-    if (!mbar_wait_bounded(&full[s], round & 1u, status, ZP_DEV_TIMEOUT_GEMV)) {
+    if (!mbar_wait_abortable(&full[s], round & 1u, abort_flag, status, ZP_DEV_TIMEOUT_GEMV)) {
       ok = false;
       break;
     }
@@ -166,7 +185,6 @@ int zp_launch_gemv(zp_db* db, const uint32_t* dq, uint32_t* dans, cudaStream_t s
                    uint32_t max_ctas) {
   zp_ctx* ctx = db->ctx;
   const uint32_t nct = (db->C + TCB - 1) / TCB;
-  const uint32_t nrb = (db->R + TR - 1) / TR;
   const size_t qp_bytes = (size_t)nct * QT_BYTES;
   int rc = zp_scratch_reserve(&db->s_qplanes, qp_bytes);
   if (rc) return rc;
@@ -178,18 +196,28 @@ int zp_launch_gemv(zp_db* db, const uint32_t* dq, uint32_t* dans, cudaStream_t s
     ctx->launches++;
     k_qplanes<<<blocks, 256, 0, st>>>(dq, db->C, nct, qp, dans, db->R);
   }
+  const bool shared_gpu = max_ctas && max_ctas < (uint32_t)ctx->num_sms;
   if (!g_attr_done[ctx->device & 63]) {
-    ZP_CUDA(cudaFuncSetAttribute(k_gemv, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    ZP_CUDA(cudaFuncSetAttribute(k_gemv<8, 12>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 GemvCfg<8, 12>::SMEM_BYTES));
+    ZP_CUDA(cudaFuncSetAttribute(k_gemv<16, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 GemvCfg<16, 6>::SMEM_BYTES));
     g_attr_done[ctx->device & 63] = true;
   }
-  const uint64_t T = (uint64_t)nrb * nct;
+  const uint32_t tr = shared_gpu ? GemvCfg<16, 6>::TR : GemvCfg<8, 12>::TR;
+  const uint32_t nrbs = (db->R + tr - 1) / tr;
+  const uint64_t T = (uint64_t)nrbs * nct;
   uint64_t grid = (uint64_t)ctx->num_sms * CTAS_PER_SM;
   if (max_ctas && grid > max_ctas) grid = max_ctas;
   if (grid > T) grid = T;
   zp_clear_pending_error();
   ctx->launches++;
-  k_gemv<<<(unsigned)grid, (NCW + 1) * 32, SMEM_BYTES, st>>>(db->tmap_gemv, qp, dans, db->R, nrb,
-                                                             nct, ctx->d_status);
+  if (shared_gpu)
+    k_gemv<16, 6><<<(unsigned)grid, 17 * 32, GemvCfg<16, 6>::SMEM_BYTES, st>>>(
+        db->tmap_gemv128, qp, dans, db->R, nrbs, nct, ctx->d_status);
+  else
+    k_gemv<8, 12><<<(unsigned)grid, 9 * 32, GemvCfg<8, 12>::SMEM_BYTES, st>>>(
+        db->tmap_gemv, qp, dans, db->R, nrbs, nct, ctx->d_status);
   ZP_CUDA(cudaGetLastError());
   return ZP_OK;
 }
@@ -238,7 +266,10 @@ extern "C" int zp_answer_noalloc(zp_db* db, const uint32_t* dQ, uint32_t* dAns, 
   k_qplanes<<<(nct * 256u + 255) / 256, 256, 0, st>>>(dQ, db->C, nct, qp, dAns, db->R);
   ZP_CUDA(cudaGetLastError());
   if (!g_attr_done[dev & 63]) {
-    ZP_CUDA(cudaFuncSetAttribute(k_gemv, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    ZP_CUDA(cudaFuncSetAttribute(k_gemv<8, 12>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 GemvCfg<8, 12>::SMEM_BYTES));
+    ZP_CUDA(cudaFuncSetAttribute(k_gemv<16, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 GemvCfg<16, 6>::SMEM_BYTES));
     g_attr_done[dev & 63] = true;
   }
   const uint64_t T = (uint64_t)nrb * nct;
@@ -246,8 +277,8 @@ extern "C" int zp_answer_noalloc(zp_db* db, const uint32_t* dQ, uint32_t* dAns, 
   if (grid > T) grid = T;
   zp_clear_pending_error();
   ctx->launches++;
-  k_gemv<<<(unsigned)grid, (NCW + 1) * 32, SMEM_BYTES, st>>>(db->tmap_gemv, qp, dAns, db->R, nrb,
-                                                             nct, ctx->d_status);
+  k_gemv<8, 12><<<(unsigned)grid, 9 * 32, GemvCfg<8, 12>::SMEM_BYTES, st>>>(
+      db->tmap_gemv, qp, dAns, db->R, nrb, nct, ctx->d_status);
   ZP_CUDA(cudaGetLastError());
   return ZP_OK;
 }

@@ -183,7 +183,9 @@ extern "C" int zp_init(int device, const zp_params* P, zp_ctx** out) {
     c->launches = 0;
     c->answer_path = ZP_PATH_AUTO;
     c->compress_path = ZP_PATH_AUTO;
-    c->overlap_sms = 0;
+    // default SM split of zp_respond for one query: about 3/8 of the SMs run the
+    // compression products beside the GEMV (56 of 152 on GB300)
+    c->overlap_sms = c->num_sms >= 64 ? (uint32_t)(c->num_sms * 3 + 4) / 8 : 0u;
     e = cudaMalloc(&c->d_status, sizeof(uint32_t));
     if (e != cudaSuccess) {
       delete c;
@@ -224,6 +226,16 @@ extern "C" int zp_set_option(zp_ctx* c, const char* name, int64_t value) {
     return ZP_OK;
   }
   return zp_set_error(ZP_EINVAL, "zp_set_option: unknown option '%s'", name);
+}
+
+extern "C" int zp_get_option(const zp_ctx* c, const char* name, int64_t* value) {
+  if (!c || !name || !value) return zp_set_error(ZP_EINVAL, "zp_get_option: null argument");
+  const std::string k(name);
+  if (k == "answer_path") *value = c->answer_path;
+  else if (k == "compress_path") *value = c->compress_path;
+  else if (k == "overlap_sms") *value = c->overlap_sms;
+  else return zp_set_error(ZP_EINVAL, "zp_get_option: unknown option '%s'", name);
+  return ZP_OK;
 }
 
 extern "C" int zp_kernel_launches(const zp_ctx* c, uint64_t* count) {
@@ -280,6 +292,9 @@ extern "C" int zp_setup_db(zp_ctx* c, const uint8_t* dD, uint32_t R, uint32_t C,
     }
     int rc = zp_encode_tmap_2d(&db->tmap_gemv, CU_TENSOR_MAP_DATA_TYPE_UINT8, dD, C, R, ld, 256, 64,
                                CU_TENSOR_MAP_SWIZZLE_NONE);
+    if (!rc)
+      rc = zp_encode_tmap_2d(&db->tmap_gemv128, CU_TENSOR_MAP_DATA_TYPE_UINT8, dD, C, R, ld, 256, 128,
+                             CU_TENSOR_MAP_SWIZZLE_NONE);
     if (!rc)
       rc = zp_encode_tmap_2d(&db->tmap_gemm, CU_TENSOR_MAP_DATA_TYPE_UINT8, dD, C, R, ld, 64, 128,
                              CU_TENSOR_MAP_SWIZZLE_NONE);

@@ -64,7 +64,8 @@ struct zp_db {
   uint32_t d1p;
   uint32_t Rp;             // R rounded up to 32 (rows of the hint byte-plane layout)
   uint32_t* d_rowsum;      // R: sum_c D[r][c]
-  CUtensorMap tmap_gemv;   // D as a 2-D u8 tensor, box 256 x 64 (GEMV)
+  CUtensorMap tmap_gemv;   // D as a 2-D u8 tensor, box 256 x 64 (GEMV on the whole GPU)
+  CUtensorMap tmap_gemv128;  // box 256 x 128 (GEMV beside the compression products)
   CUtensorMap tmap_gemm;   // D as a 2-D u8 tensor, box 64 x 128 (tensor-core products)
   // hint in compression layout (library-owned)
   uint32_t* d_hneg;        // R x n u32: -D.A mod 2^32
@@ -242,6 +243,15 @@ __device__ __forceinline__ uint64_t l2_policy_evict_first() {
 }
 
 __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31; }
+
+// Waits for phase `parity` of `bar` until the absolute clock64 deadline; false when it
+// passes (used to drain copies in flight before a CTA leaves).
+__device__ __forceinline__ bool mbar_wait_until(uint64_t* bar, uint32_t parity,
+                                                unsigned long long deadline) {
+  while (!mbar_try_wait(bar, parity))
+    if ((unsigned long long)clock64() > deadline) return false;
+  return true;
+}
 
 // ---- bounded waits that also give up when another role of the CTA has aborted
 __device__ __forceinline__ bool mbar_wait_abortable(uint64_t* bar, uint32_t parity,
