@@ -161,8 +161,9 @@ int zp_compress(zp_db* db, zp_client* const* clients, const uint32_t* dAns,
  * scratch; zp_compress_finish packs ans + V and reduces mod m_b into dT, exactly as
  * zp_compress. The products of one call are consumed by the next finish call with the
  * same B (ZP_ESTATE otherwise); both must be ordered on the caller's streams (the
- * finish after the products). With the "overlap_sms" option set, the products use only
- * that many SMs so that they can run concurrently with a single-query zp_answer.
+ * finish after the products). For B = 1 with the "overlap_sms" option set, the products
+ * use only that many SMs so that they can run concurrently with a single-query
+ * zp_answer (which then leaves those SMs free).
  * Errors as zp_compress. */
 int zp_compress_products(zp_db* db, const uint32_t* dCKO, uint32_t B, void* stream);
 int zp_compress_finish(zp_db* db, zp_client* const* clients, const uint32_t* dAns, uint32_t B,

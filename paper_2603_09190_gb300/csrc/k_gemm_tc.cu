@@ -51,7 +51,6 @@ constexpr int BM = 128;
 constexpr int BK = 64;
 constexpr int A16_BYTES = BM * BK * 2;       // 16 KiB
 constexpr int B_MAX_BYTES = 256 * BK * 2;    // 32 KiB
-constexpr int OP_STAGE = A16_BYTES + B_MAX_BYTES;
 constexpr int U8_STAGE = BM * BK;            // 8 KiB
 constexpr int KCHUNK = 16;                   // K blocks per exact fp32 accumulation
 constexpr int NTHREADS = 384;
@@ -60,12 +59,15 @@ constexpr int STG_BYTES = 4 * 32 * STG_PITCH * 4;
 
 enum { MODE_ANS = 0, MODE_HINT = 1, MODE_CMP = 2 };
 
+// Three rings: B (fp16, from L2: deep, it is the largest operand), A as bytes (from
+// HBM, L2-prefetched) and A as fp16 (written by the converters just before the MMA).
 template <int MODE>
 struct Cfg {
-  static constexpr int SO = 3;                          // operand stages (fp16 A | B)
-  static constexpr int SU = (MODE == MODE_CMP) ? 5 : 8;  // byte stages of A (HBM-latency bound)
+  static constexpr int SB = (MODE == MODE_CMP) ? 4 : 5;
+  static constexpr int SA = 2;
+  static constexpr int SU = (MODE == MODE_CMP) ? 3 : 4;
   static constexpr int STG = (MODE == MODE_CMP) ? STG_BYTES : 0;
-  static constexpr int SMEM = SO * OP_STAGE + SU * U8_STAGE + STG + 1024 + 512;
+  static constexpr int SMEM = SB * B_MAX_BYTES + SA * A16_BYTES + SU * U8_STAGE + STG + 1024 + 512;
 };
 
 struct GemmArgs {
@@ -128,21 +130,22 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
               const GemmArgs args) {
   using C = Cfg<MODE>;
-  constexpr int SO = C::SO;
-  constexpr int SU = C::SU;
+  constexpr int SB = C::SB, SA = C::SA, SU = C::SU;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~static_cast<uintptr_t>(1023));
-  uint8_t* op_ring = smem;                                   // SO x (A16 | B)
-  uint8_t* u8_ring = op_ring + SO * OP_STAGE;                // SU x 8 KiB
+  uint8_t* b_ring = smem;                                    // SB x 32 KiB (1024-aligned)
+  uint8_t* a_ring = b_ring + SB * B_MAX_BYTES;               // SA x 16 KiB (1024-aligned)
+  uint8_t* u8_ring = a_ring + SA * A16_BYTES;                // SU x 8 KiB
   uint32_t* stg = reinterpret_cast<uint32_t*>(u8_ring + SU * U8_STAGE);
   uint64_t* bars = reinterpret_cast<uint64_t*>(u8_ring + SU * U8_STAGE + C::STG);
   uint64_t* u8_full = bars;
   uint64_t* u8_empty = u8_full + SU;
   uint64_t* b_full = u8_empty + SU;     // B tile landed (TMA transaction count)
-  uint64_t* a_ready = b_full + SO;      // fp16 A tile written by the four converter warps
-  uint64_t* op_empty = a_ready + SO;
-  uint64_t* acc_full = op_empty + SO;
+  uint64_t* b_empty = b_full + SB;      // MMAs reading the B stage are done
+  uint64_t* a_ready = b_empty + SB;     // fp16 A tile written by the four converter warps
+  uint64_t* a_empty = a_ready + SA;     // MMAs reading the A stage are done
+  uint64_t* acc_full = a_empty + SA;
   uint64_t* acc_empty = acc_full + 2;
   uint64_t* mma_done = acc_empty + 2;
   uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(mma_done + 1);
@@ -157,10 +160,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       mbar_init(&u8_full[s], 1);
       mbar_init(&u8_empty[s], 4);
     }
-    for (int s = 0; s < SO; ++s) {
+    for (int s = 0; s < SB; ++s) {
       mbar_init(&b_full[s], 1);
+      mbar_init(&b_empty[s], 1);
+    }
+    for (int s = 0; s < SA; ++s) {
       mbar_init(&a_ready[s], 4);
-      mbar_init(&op_empty[s], 1);
+      mbar_init(&a_empty[s], 1);
     }
     for (int s = 0; s < 2; ++s) {
       mbar_init(&acc_full[s], 1);
@@ -232,22 +238,22 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       for (uint32_t tile = blockIdx.x; ok && tile < num_tiles; tile += gridDim.x) {
         const uint32_t nt = tile % args.num_n_tiles;
         for (uint32_t kb = 0; kb < nkb; ++kb, ++cnt) {
-          const uint32_t so = cnt % SO, ro = cnt / SO;
-          if (ro > 0 && !mbar_wait_abortable(&op_empty[so], (ro - 1) & 1u, abort_flag,
+          const uint32_t sb = cnt % SB, rb = cnt / SB;
+          if (rb > 0 && !mbar_wait_abortable(&b_empty[sb], (rb - 1) & 1u, abort_flag,
                                              args.status, ZP_DEV_TIMEOUT_GEMM)) {
             ok = false;
             break;
           }
-          mbar_arrive_expect_tx(&b_full[so], N * BK * 2);
-          tma_load_2d(op_ring + so * OP_STAGE + A16_BYTES, &tmB, (int32_t)(kb * BK),
-                      (int32_t)(nt * N), &b_full[so]);
+          mbar_arrive_expect_tx(&b_full[sb], N * BK * 2);
+          tma_load_2d(b_ring + sb * B_MAX_BYTES, &tmB, (int32_t)(kb * BK), (int32_t)(nt * N),
+                      &b_full[sb]);
         }
       }
       // Stay until the copies issued last have landed (bounded, ignores the abort flag).
-      const uint32_t f_o = cnt > (uint32_t)SO ? cnt - SO : 0;
+      const uint32_t f_o = cnt > (uint32_t)SB ? cnt - SB : 0;
       const unsigned long long deadline = clock64() + ZP_WAIT_CYCLES;
       for (uint32_t i = f_o; i < cnt; ++i)
-        if (!mbar_wait_until(&b_full[i % SO], (i / SO) & 1u, deadline)) {
+        if (!mbar_wait_until(&b_full[i % SB], (i / SB) & 1u, deadline)) {
           atomicOr(args.status, ZP_DEV_TIMEOUT_GEMM);
           break;
         }
@@ -272,23 +278,25 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             }
             tc_fence_after();
           }
-          const uint32_t so = cnt % SO, ro = cnt / SO;
-          if (!mbar_wait_abortable(&b_full[so], ro & 1u, abort_flag, args.status,
+          const uint32_t sb = cnt % SB, rb = cnt / SB;
+          const uint32_t sa = cnt % SA, rra = cnt / SA;
+          if (!mbar_wait_abortable(&b_full[sb], rb & 1u, abort_flag, args.status,
                                    ZP_DEV_TIMEOUT_GEMM) ||
-              !mbar_wait_abortable(&a_ready[so], ro & 1u, abort_flag, args.status,
+              !mbar_wait_abortable(&a_ready[sa], rra & 1u, abort_flag, args.status,
                                    ZP_DEV_TIMEOUT_GEMM)) {
             ok = false;
             break;
           }
           tc_fence_after();
-          const uint32_t abase = smem_u32(op_ring + so * OP_STAGE);
-          const uint32_t bbase = abase + A16_BYTES;
+          const uint32_t abase = smem_u32(a_ring + sa * A16_BYTES);
+          const uint32_t bbase = smem_u32(b_ring + sb * B_MAX_BYTES);
           const uint64_t ad = sdesc_k_sw128(abase), bd = sdesc_k_sw128(bbase);
 #pragma unroll
           for (uint32_t kk = 0; kk < BK / 16; ++kk)
             umma_f16(tmem_base + a * 256u, ad + 2u * kk, bd + 2u * kk, idesc,
                      (kin > 0 || kk > 0) ? 1u : 0u);
-          umma_commit(&op_empty[so]);
+          umma_commit(&b_empty[sb]);
+          umma_commit(&a_empty[sa]);
           if (kin == KCHUNK - 1 || kb == nkb - 1) {
             umma_commit(&acc_full[a]);
             ++acc_cnt;
@@ -309,16 +317,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     for (uint32_t tile = blockIdx.x; ok && tile < num_tiles; tile += gridDim.x) {
       for (uint32_t kb = 0; kb < nkb; ++kb, ++cnt) {
         const uint32_t su = cnt % SU, ru = cnt / SU;
-        const uint32_t so = cnt % SO, ro = cnt / SO;
+        const uint32_t sa = cnt % SA, rra = cnt / SA;
         if (!mbar_wait_abortable(&u8_full[su], ru & 1u, abort_flag, args.status,
                                  ZP_DEV_TIMEOUT_GEMM) ||
-            (ro > 0 && !mbar_wait_abortable(&op_empty[so], (ro - 1) & 1u, abort_flag,
-                                            args.status, ZP_DEV_TIMEOUT_GEMM))) {
+            (rra > 0 && !mbar_wait_abortable(&a_empty[sa], (rra - 1) & 1u, abort_flag,
+                                             args.status, ZP_DEV_TIMEOUT_GEMM))) {
           ok = false;
           break;
         }
         const uint8_t* src = u8_ring + su * U8_STAGE;
-        uint8_t* dst = op_ring + so * OP_STAGE;
+        uint8_t* dst = a_ring + sa * A16_BYTES;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
           const uint32_t idx = ct + 128u * i;
@@ -336,7 +344,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0) {
-          mbar_arrive(&a_ready[so]);
+          mbar_arrive(&a_ready[sa]);
           mbar_arrive(&u8_empty[su]);
         }
       }

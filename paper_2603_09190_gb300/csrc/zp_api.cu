@@ -624,8 +624,9 @@ extern "C" int zp_compress_products(zp_db* db, const uint32_t* dCKO, uint32_t B,
     if (!db->hint_ready) return zp_set_error(ZP_ESTATE, "zp_compress_products: no hint (call zp_gen_hint)");
     if (db->stale) return zp_set_error(ZP_ESTATE, "zp_compress_products: %u hint rows stale", db->stale);
     ZP_CUDA(cudaSetDevice(db->ctx->device));
+    // only a single query's products share the GPU with an answer
     return zp_launch_compress_products(db, dCKO, B, static_cast<cudaStream_t>(stream),
-                                       db->ctx->overlap_sms);
+                                       B == 1 ? db->ctx->overlap_sms : 0u);
   } catch (const std::bad_alloc&) {
     return zp_set_error(ZP_ENOMEM, "zp_compress_products: host allocation failed");
   }
