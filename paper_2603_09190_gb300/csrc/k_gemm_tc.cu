@@ -194,30 +194,34 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       // L2 prefetch runs PF K blocks ahead of the loads, so that the loads that fill
       // the byte ring hit L2 instead of waiting for HBM.
       constexpr uint32_t PF = 16;
-      for (uint32_t f = 0; f < PF; ++f) {
-        const uint32_t t = blockIdx.x + (f / nkb) * gridDim.x;
-        if (t < num_tiles)
-          tma_prefetch_l2_2d(&tmA, (int32_t)((f % nkb) * BK), (int32_t)((t / args.num_n_tiles) * BM));
-      }
+      // prefetch cursor: (tile, K block) PF blocks ahead of the load cursor
+      uint32_t pf_tile = blockIdx.x, pf_kb = 0;
+      auto pf_step = [&]() {
+        if (pf_tile < num_tiles)
+          tma_prefetch_l2_2d(&tmA, (int32_t)(pf_kb * BK), (int32_t)((pf_tile / args.num_n_tiles) * BM));
+        if (++pf_kb == nkb) {
+          pf_kb = 0;
+          pf_tile += gridDim.x;
+        }
+      };
+      for (uint32_t f = 0; f < PF; ++f) pf_step();
+      uint32_t su = 0, pu = 0;
       for (uint32_t tile = blockIdx.x; ok && tile < num_tiles; tile += gridDim.x) {
         const uint32_t mt = tile / args.num_n_tiles;
         for (uint32_t kb = 0; kb < nkb; ++kb, ++cnt) {
-          {
-            const uint32_t f = cnt + PF;
-            const uint32_t t = blockIdx.x + (f / nkb) * gridDim.x;
-            if (t < num_tiles)
-              tma_prefetch_l2_2d(&tmA, (int32_t)((f % nkb) * BK),
-                                 (int32_t)((t / args.num_n_tiles) * BM));
-          }
-          const uint32_t su = cnt % SU, ru = cnt / SU;
-          if (ru > 0 && !mbar_wait_abortable(&u8_empty[su], (ru - 1) & 1u, abort_flag,
-                                             args.status, ZP_DEV_TIMEOUT_GEMM)) {
+          pf_step();
+          if (cnt >= (uint32_t)SU && !mbar_wait_abortable(&u8_empty[su], pu ^ 1u, abort_flag,
+                                                          args.status, ZP_DEV_TIMEOUT_GEMM)) {
             ok = false;
             break;
           }
           mbar_arrive_expect_tx(&u8_full[su], U8_STAGE);
           tma_load_2d(u8_ring + su * U8_STAGE, &tmA, (int32_t)(kb * BK), (int32_t)(mt * BM),
                       &u8_full[su]);
+          if (++su == SU) {
+            su = 0;
+            pu ^= 1u;
+          }
         }
       }
       // Stay until the copies issued last have landed (bounded, ignores the abort flag).
@@ -261,45 +265,54 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
+      // Kept lean: one thread feeds the tensor core, on an SMSP shared with busy warps.
       const uint32_t idesc = idesc_f16_f32(BM, N);
-      uint32_t cnt = 0, acc_cnt = 0;
+      const uint64_t adesc0 = sdesc_k_sw128(smem_u32(a_ring));
+      const uint64_t bdesc0 = sdesc_k_sw128(smem_u32(b_ring));
+      uint32_t sb = 0, pb = 0, sa = 0, pa = 0, acc_cnt = 0;
       bool ok = true;
       for (uint32_t tile = blockIdx.x; ok && tile < num_tiles; tile += gridDim.x) {
-        uint32_t a = 0;
-        for (uint32_t kb = 0; kb < nkb; ++kb, ++cnt) {
-          const uint32_t kin = kb % KCHUNK;
+        uint32_t d = tmem_base, kin = 0;
+        for (uint32_t kb = 0; kb < nkb; ++kb) {
           if (kin == 0) {
-            a = acc_cnt & 1u;
-            const uint32_t ra = acc_cnt >> 1;
+            const uint32_t a = acc_cnt & 1u, ra = acc_cnt >> 1;
             if (ra > 0 && !mbar_wait_abortable(&acc_empty[a], (ra - 1) & 1u, abort_flag,
                                                args.status, ZP_DEV_TIMEOUT_GEMM)) {
               ok = false;
               break;
             }
             tc_fence_after();
+            d = tmem_base + a * 256u;
           }
-          const uint32_t sb = cnt % SB, rb = cnt / SB;
-          const uint32_t sa = cnt % SA, rra = cnt / SA;
-          if (!mbar_wait_abortable(&b_full[sb], rb & 1u, abort_flag, args.status,
+          if (!mbar_wait_abortable(&b_full[sb], pb, abort_flag, args.status,
                                    ZP_DEV_TIMEOUT_GEMM) ||
-              !mbar_wait_abortable(&a_ready[sa], rra & 1u, abort_flag, args.status,
+              !mbar_wait_abortable(&a_ready[sa], pa, abort_flag, args.status,
                                    ZP_DEV_TIMEOUT_GEMM)) {
             ok = false;
             break;
           }
           tc_fence_after();
-          const uint32_t abase = smem_u32(a_ring + sa * A16_BYTES);
-          const uint32_t bbase = smem_u32(b_ring + sb * B_MAX_BYTES);
-          const uint64_t ad = sdesc_k_sw128(abase), bd = sdesc_k_sw128(bbase);
-#pragma unroll
-          for (uint32_t kk = 0; kk < BK / 16; ++kk)
-            umma_f16(tmem_base + a * 256u, ad + 2u * kk, bd + 2u * kk, idesc,
-                     (kin > 0 || kk > 0) ? 1u : 0u);
+          // start-address field += stage offset >> 4 (stays below 2^14: shared memory < 256 KiB)
+          const uint64_t ad = adesc0 + (uint64_t)(sa * (A16_BYTES >> 4));
+          const uint64_t bd = bdesc0 + (uint64_t)(sb * (B_MAX_BYTES >> 4));
+          umma_f16(d, ad, bd, idesc, kin);
+          umma_f16(d, ad + 2u, bd + 2u, idesc, 1u);
+          umma_f16(d, ad + 4u, bd + 4u, idesc, 1u);
+          umma_f16(d, ad + 6u, bd + 6u, idesc, 1u);
           umma_commit(&b_empty[sb]);
           umma_commit(&a_empty[sa]);
-          if (kin == KCHUNK - 1 || kb == nkb - 1) {
-            umma_commit(&acc_full[a]);
+          if (++kin == KCHUNK || kb == nkb - 1) {
+            umma_commit(&acc_full[acc_cnt & 1u]);
             ++acc_cnt;
+            kin = 0;
+          }
+          if (++sb == SB) {
+            sb = 0;
+            pb ^= 1u;
+          }
+          if (++sa == SA) {
+            sa = 0;
+            pa ^= 1u;
           }
         }
       }
