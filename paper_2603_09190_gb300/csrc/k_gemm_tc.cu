@@ -51,7 +51,7 @@ constexpr int BM = 128;
 constexpr int BK = 64;
 constexpr int A16_BYTES = BM * BK * 2;       // 16 KiB
 constexpr int B_MAX_BYTES = 256 * BK * 2;    // 32 KiB
-constexpr int U8_STAGE = BM * BK;            // 8 KiB
+constexpr int U8_STAGE = BM * 2 * BK;        // 16 KiB: two K blocks of A bytes per copy (128-byte rows)
 constexpr int KCHUNK = 16;                   // K blocks per exact fp32 accumulation
 constexpr int NTHREADS = 384;
 constexpr int STG_PITCH = 67;                // words per staged row (odd: no bank conflicts)
@@ -63,9 +63,9 @@ enum { MODE_ANS = 0, MODE_HINT = 1, MODE_CMP = 2 };
 // HBM, L2-prefetched) and A as fp16 (written by the converters just before the MMA).
 template <int MODE>
 struct Cfg {
-  static constexpr int SB = (MODE == MODE_CMP) ? 4 : 5;
+  static constexpr int SB = (MODE == MODE_CMP) ? 3 : 4;
   static constexpr int SA = 2;
-  static constexpr int SU = (MODE == MODE_CMP) ? 3 : 4;
+  static constexpr int SU = 3;  // stages of two K blocks
   static constexpr int STG = (MODE == MODE_CMP) ? STG_BYTES : 0;
   static constexpr int SMEM = SB * B_MAX_BYTES + SA * A16_BYTES + SU * U8_STAGE + STG + 1024 + 512;
 };
@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                                              ~static_cast<uintptr_t>(1023));
   uint8_t* b_ring = smem;                                    // SB x 32 KiB (1024-aligned)
   uint8_t* a_ring = b_ring + SB * B_MAX_BYTES;               // SA x 16 KiB (1024-aligned)
-  uint8_t* u8_ring = a_ring + SA * A16_BYTES;                // SU x 8 KiB
+  uint8_t* u8_ring = a_ring + SA * A16_BYTES;                // SU x 16 KiB (1024-aligned)
   uint32_t* stg = reinterpret_cast<uint32_t*>(u8_ring + SU * U8_STAGE);
   uint64_t* bars = reinterpret_cast<uint64_t*>(u8_ring + SU * U8_STAGE + C::STG);
   uint64_t* u8_full = bars;
@@ -194,21 +194,22 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       // L2 prefetch runs PF K blocks ahead of the loads, so that the loads that fill
       // the byte ring hit L2 instead of waiting for HBM.
       constexpr uint32_t PF = 16;
-      // prefetch cursor: (tile, K block) PF blocks ahead of the load cursor
-      uint32_t pf_tile = blockIdx.x, pf_kb = 0;
+      // prefetch cursor: (tile, pair of K blocks) PF pairs ahead of the load cursor
+      const uint32_t npairs = (nkb + 1) / 2;
+      uint32_t pf_tile = blockIdx.x, pf_p = 0;
       auto pf_step = [&]() {
         if (pf_tile < num_tiles)
-          tma_prefetch_l2_2d(&tmA, (int32_t)(pf_kb * BK), (int32_t)((pf_tile / args.num_n_tiles) * BM));
-        if (++pf_kb == nkb) {
-          pf_kb = 0;
+          tma_prefetch_l2_2d(&tmA, (int32_t)(pf_p * 2 * BK), (int32_t)((pf_tile / args.num_n_tiles) * BM));
+        if (++pf_p == npairs) {
+          pf_p = 0;
           pf_tile += gridDim.x;
         }
       };
-      for (uint32_t f = 0; f < PF; ++f) pf_step();
+      for (uint32_t f = 0; f < PF / 2; ++f) pf_step();
       uint32_t su = 0, pu = 0;
       for (uint32_t tile = blockIdx.x; ok && tile < num_tiles; tile += gridDim.x) {
         const uint32_t mt = tile / args.num_n_tiles;
-        for (uint32_t kb = 0; kb < nkb; ++kb, ++cnt) {
+        for (uint32_t p = 0; p < npairs; ++p, ++cnt) {
           pf_step();
           if (cnt >= (uint32_t)SU && !mbar_wait_abortable(&u8_empty[su], pu ^ 1u, abort_flag,
                                                           args.status, ZP_DEV_TIMEOUT_GEMM)) {
@@ -216,7 +217,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             break;
           }
           mbar_arrive_expect_tx(&u8_full[su], U8_STAGE);
-          tma_load_2d(u8_ring + su * U8_STAGE, &tmA, (int32_t)(kb * BK), (int32_t)(mt * BM),
+          tma_load_2d(u8_ring + su * U8_STAGE, &tmA, (int32_t)(p * 2 * BK), (int32_t)(mt * BM),
                       &u8_full[su]);
           if (++su == SU) {
             su = 0;
@@ -325,14 +326,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   } else if (warp >= 8) {
     // ------------------------------------------------------------ converters
     const uint32_t ct = threadIdx.x - 256;  // 0..127
-    uint32_t cnt = 0;
+    uint32_t cnt = 0, su = 0, pu = 0;
     bool ok = true;
     for (uint32_t tile = blockIdx.x; ok && tile < num_tiles; tile += gridDim.x) {
       for (uint32_t kb = 0; kb < nkb; ++kb, ++cnt) {
-        const uint32_t su = cnt % SU, ru = cnt / SU;
+        const uint32_t h = kb & 1u;  // which K block of the 128-byte byte rows
         const uint32_t sa = cnt % SA, rra = cnt / SA;
-        if (!mbar_wait_abortable(&u8_full[su], ru & 1u, abort_flag, args.status,
-                                 ZP_DEV_TIMEOUT_GEMM) ||
+        if ((h == 0 && !mbar_wait_abortable(&u8_full[su], pu, abort_flag, args.status,
+                                            ZP_DEV_TIMEOUT_GEMM)) ||
             (rra > 0 && !mbar_wait_abortable(&a_empty[sa], (rra - 1) & 1u, abort_flag,
                                              args.status, ZP_DEV_TIMEOUT_GEMM))) {
           ok = false;
@@ -344,7 +345,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         for (int i = 0; i < 4; ++i) {
           const uint32_t idx = ct + 128u * i;
           const uint32_t row = idx >> 2, ch = idx & 3u;
-          const uint4 v = *reinterpret_cast<const uint4*>(src + row * 64 + ch * 16);
+          // byte tile: 128-byte rows, 16-byte chunk c stored at chunk c ^ (row % 8)
+          const uint4 v = *reinterpret_cast<const uint4*>(
+              src + row * 128 + (((4 * h + ch) ^ (row & 7u)) << 4));
           uint4 o0, o1;
           bytes_to_centred_f16(v.x, o0.x, o0.y);
           bytes_to_centred_f16(v.y, o0.z, o0.w);
@@ -356,9 +359,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
         fence_proxy_async_smem();
         __syncwarp();
+        const bool last_of_pair = h == 1 || kb == nkb - 1;
         if (lane == 0) {
           mbar_arrive(&a_ready[sa]);
-          mbar_arrive(&u8_empty[su]);
+          if (last_of_pair) mbar_arrive(&u8_empty[su]);
+        }
+        if (last_of_pair && ++su == SU) {
+          su = 0;
+          pu ^= 1u;
         }
       }
     }

@@ -296,8 +296,8 @@ extern "C" int zp_setup_db(zp_ctx* c, const uint8_t* dD, uint32_t R, uint32_t C,
       rc = zp_encode_tmap_2d(&db->tmap_gemv128, CU_TENSOR_MAP_DATA_TYPE_UINT8, dD, C, R, ld, 256, 128,
                              CU_TENSOR_MAP_SWIZZLE_NONE);
     if (!rc)
-      rc = zp_encode_tmap_2d(&db->tmap_gemm, CU_TENSOR_MAP_DATA_TYPE_UINT8, dD, C, R, ld, 64, 128,
-                             CU_TENSOR_MAP_SWIZZLE_NONE);
+      rc = zp_encode_tmap_2d(&db->tmap_gemm, CU_TENSOR_MAP_DATA_TYPE_UINT8, dD, C, R, ld, 128, 128,
+                             CU_TENSOR_MAP_SWIZZLE_128B);
     if (!rc) rc = zp_launch_rowsum(db, nullptr, 0, 0);
     if (!rc) {
       e = cudaDeviceSynchronize();
@@ -391,7 +391,7 @@ static int alloc_hint_state(zp_db* db) {
     e = cudaMemset(db->d_hpl_rowsum, 0, (size_t)4 * db->Rp * 4);
     if (e != cudaSuccess) return zp_cuda_check(e, "cudaMemset(plane sums)");
     int rc = zp_encode_tmap_2d(&db->tmap_hpl, CU_TENSOR_MAP_DATA_TYPE_UINT8, db->d_hpl, n,
-                               (uint64_t)4 * db->Rp, db->hpl_ld, 64, 128, CU_TENSOR_MAP_SWIZZLE_NONE);
+                               (uint64_t)4 * db->Rp, db->hpl_ld, 128, 128, CU_TENSOR_MAP_SWIZZLE_128B);
     if (rc) return rc;
   }
   return ZP_OK;
@@ -446,8 +446,8 @@ extern "C" int zp_gen_hint(zp_db* db, const uint32_t* dA, uint32_t* dH, const ui
     if (rc) return rc;
     if (tc) {
       CUtensorMap tmG;
-      rc = zp_encode_tmap_2d(&tmG, CU_TENSOR_MAP_DATA_TYPE_UINT8, dG, db->C, nrows, ldc, 64, 128,
-                             CU_TENSOR_MAP_SWIZZLE_NONE);
+      rc = zp_encode_tmap_2d(&tmG, CU_TENSOR_MAP_DATA_TYPE_UINT8, dG, db->C, nrows, ldc, 128, 128,
+                             CU_TENSOR_MAP_SWIZZLE_128B);
       if (!rc) rc = zp_launch_rowsum_buf(c, dG, ldc, nrows, db->C, dGsum, st);
       if (!rc) rc = zp_launch_answer_tc(db, tmG, nrows, dA, n, true, dHc, n, true, dGsum, st);
     } else {
