@@ -49,6 +49,9 @@ WORKLOADS = {
                 "1 GiB database 32768x32768, 64 queries of 64 clients, n=1024, 2048-bit moduli"),
 }
 KEY_BITS = 2048
+# ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of k_gemv<16, 6> (the GEMV
+# beside the compression products), 1 GiB workload, mean of two captured launches
+GEMV_TRAFFIC = {("1gib", True): 1075651584}
 L = KEY_BITS // 32
 
 
@@ -351,8 +354,11 @@ def run_ours(args, world, rank, local):
     # algorithmic bytes of one zp_answer (B = 1: query-plane prep + GEMV): D, q, ans
     alg_bytes = R * C + 4 * C * B + 4 * R * B
     achieved = alg_bytes / (ans_avg * 1e-3) / 1e9
+    # DRAM bytes (read + write) of one launch of the GEMV in this configuration, from one
+    # ncu capture of this workload (profiles/k_gemv_1gib_traffic.md); None elsewhere
+    traffic = GEMV_TRAFFIC.get((args.workload, overlap))
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-            "frac": achieved / hbm_peak, "traffic": None,
+            "frac": achieved / hbm_peak, "traffic": traffic,
             "kernel": "zp_answer (k_qplanes + k_gemv)" if B == 1 else "zp_answer (batched)",
             "peak_kind": peak_kind}
     cb = cpu_baseline(R, C, n, B) if world == 1 and not args.no_cpu else None
