@@ -388,21 +388,130 @@ def run_ours(args, world, rank, local):
     return 0
 
 
+def run_serve(args, world, rank, local):
+    """Serving workload: three resident databases, Poisson arrivals from many clients,
+    row updates with idle-time hint regeneration; continuous batching (serve.Server)."""
+    import threading
+    import torch
+    import paper_2603_09190_gb300 as zp
+    from paper_2603_09190_gb300 import build as zb
+    from paper_2603_09190_gb300.serve import Request, Server, ZipBackend
+    import synth
+
+    if rank == 0:
+        zb.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n = 1024
+    ctx = zp.Context(local, n=n, key_bits=KEY_BITS)
+    be = ZipBackend(ctx, max_batch=args.serve_batch)
+    shapes = {"db256m": (16384, 16384), "db1g": (32768, 32768), "db4g": (65536, 65536)}
+    if args.serve_small:
+        shapes = {"db256m": (4096, 4096), "db1g": (8192, 8192), "db4g": (16384, 16384)}
+    for i, (name, (R, C)) in enumerate(shapes.items()):
+        ld = zp.db_pitch(C)
+        D = synth.device_database(R, C, 10 + i, dev, ld=ld)
+        A = synth.device_uniform_u32((C, n), 20 + i, dev)
+        db = zp.Database(ctx, D, R, C, ld)
+        db.gen_hint(A)
+        be.add_database(name, db, A)
+    nclients = args.serve_clients
+    moduli = [synth.random_odd_modulus(KEY_BITS, 3000 + k) for k in range(nclients)]
+    for k, m in enumerate(moduli):
+        be.add_client(k, m)
+    g = synth.rng(77)
+    qpool = {name: [g.integers(0, 2**32, size=C, dtype=np.uint64).astype(np.uint32) for _ in range(4)]
+             for name, (R, C) in shapes.items()}
+    kpool = [synth.ints_to_limbs(synth.uniform_below(moduli[k % nclients], n, 4000 + k), L)
+             for k in range(8)]
+    free = torch.cuda.mem_get_info(dev)[0]
+    budget = int(free * 0.9) + sum(be.db_bytes(nm) for nm in shapes)
+    results = []
+    for rate in args.serve_rates:
+        srv = Server(be, hbm_budget=budget, max_batch=args.serve_batch)
+        for name, (R, C) in shapes.items():
+            srv.add_database(name, R, C)
+        stop = threading.Event()
+        names = list(shapes)
+
+        def arrivals():
+            rg = np.random.Generator(np.random.PCG64(int(rate)))
+            t_next = time.perf_counter()
+            rid = 0
+            upd_next = time.perf_counter() + 0.1
+            while not stop.is_set():
+                now = time.perf_counter()
+                if now >= upd_next:          # 1% of the rows per second, in 100 ms chunks
+                    upd_next += 0.1
+                    for name, (R, C) in shapes.items():
+                        k = max(1, R // 1000)
+                        rows = rg.choice(R, size=k, replace=False).astype(np.uint32)
+                        new = torch.randint(0, 256, (k, C), dtype=torch.uint8, device=dev)
+                        srv.update_rows(name, rows, new)
+                if now < t_next:
+                    time.sleep(min(t_next - now, 0.001))
+                    continue
+                name = names[int(rg.integers(0, 3))]
+                cid = int(rg.integers(0, nclients))
+                srv.submit(Request(rid, name, cid, qpool[name][rid % 4], kpool[cid % 8], t_next))
+                rid += 1
+                t_next += rg.exponential(1.0 / rate)
+
+        th = threading.Thread(target=arrivals, daemon=True)
+        t0 = time.perf_counter()
+        th.start()
+        while time.perf_counter() - t0 < args.serve_seconds:
+            if srv.step() == 0:
+                time.sleep(0.0001)
+        stop.set()
+        th.join()
+        srv.run_until_idle(timeout=120)
+        t1 = time.perf_counter()
+        rep = srv.report(t0, t1)
+        rep["offered_qps"] = rate
+        results.append(rep)
+    status = ctx.device_status()
+    if rank == 0:
+        best = max(results, key=lambda r: r["db_gb_s"])
+        line = {"metric": METRIC, "value": best["db_gb_s"], "unit": "GB/s", "n_gpus": world,
+                "steps": len(results), "warmup": 0, "ms_per_step": None,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+                "data": "synthetic",
+                "config": {"workload": "serving: resident databases %s, Poisson arrivals, %d "
+                                       "clients with their own 2048-bit moduli, 1%% rows/s "
+                                       "updated with idle-time hint regeneration, %d s per rate"
+                                       % (",".join("%s %dx%d" % (k, *v) for k, v in shapes.items()),
+                                          nclients, args.serve_seconds),
+                           "max_batch": args.serve_batch},
+                "rates": results, "device_status": status}
+        print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="1gib", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="1gib", choices=sorted(WORKLOADS) + ["serve"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--serve-rates", type=float, nargs="*", default=[50, 200, 1000, 2000])
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--serve-clients", type=int, default=1000)
+    ap.add_argument("--serve-batch", type=int, default=64)
+    ap.add_argument("--serve-small", action="store_true", help="smaller databases (smoke)")
     ap.add_argument("--overlap", type=int, default=None,
                     help="SMs for the compression products beside a single-query answer "
                          "(default: the library's)")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
+        if args.workload == "serve":
+            args.workload = "1gib"
         return run_reference(args, world, rank)
+    if args.workload == "serve":
+        return run_serve(args, world, rank, local)
     return run_ours(args, world, rank, local)
 
 
