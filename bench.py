@@ -47,6 +47,11 @@ WORKLOADS = {
              "1 MiB database 1024x1024, 1 query, n=1024, 2048-bit modulus"),
     "batch64": (32768, 32768, 1024, 64,
                 "1 GiB database 32768x32768, 64 queries of 64 clients, n=1024, 2048-bit moduli"),
+    "8gib": (65536, 131072, 1024, 1,
+             "8 GiB database 65536x131072, 1 query, n=1024, 2048-bit modulus"),
+    "8gib_b8": (65536, 131072, 1024, 8, "8 GiB database 65536x131072, 8 queries"),
+    "8gib_b32": (65536, 131072, 1024, 32, "8 GiB database 65536x131072, 32 queries"),
+    "8gib_b128": (65536, 131072, 1024, 128, "8 GiB database 65536x131072, 128 queries"),
 }
 KEY_BITS = 2048
 # ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of k_gemv<16, 6> (the GEMV
@@ -149,6 +154,14 @@ def dist_max(x: float, world: int) -> float:
     return float(t.item())
 
 
+def aggregate(ms_total_local: float, steps: int, bytes_per_step_per_rank: int, world: int):
+    """Whole-job throughput over the ranks: every rank runs its own replica; the job's time is
+    the slowest rank's, and the value counts the bytes of all ranks (GB/s)."""
+    ms_total = dist_max(ms_total_local, world)
+    ms_step = ms_total / steps
+    return ms_step, bytes_per_step_per_rank * world / (ms_step * 1e-3) / 1e9
+
+
 def dist_barrier(world: int):
     if world > 1:
         import torch.distributed as dist
@@ -237,7 +250,14 @@ def run_ours(args, world, rank, local):
     D = synth.device_database(R, C, 1 + rank, dev, ld=ld)
     A = synth.device_uniform_u32((C, n), 2 + rank, dev)
     db = zp.Database(ctx, D, R, C, ld)
+    db.gen_hint(A)                                   # warm-up (allocations, attributes)
+    torch.cuda.synchronize()
+    h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    h0.record()
     db.gen_hint(A)
+    h1.record()
+    torch.cuda.synchronize()
+    hint_ms = h0.elapsed_time(h1)
     del A
     moduli = [synth.random_odd_modulus(KEY_BITS, 1000 + b) for b in range(B)]
     clients = [ctx.register_client(m) for m in moduli]
@@ -304,15 +324,12 @@ def run_ours(args, world, rank, local):
     dist_barrier(world)
     launches = ctx.kernel_launches() - launches0
     sampler.window(tw0, tw1)
-    ms_total = start.elapsed_time(end)
-    ms_total = dist_max(ms_total, world)
-    ms_step = ms_total / args.steps
+    ms_step, value = aggregate(start.elapsed_time(end), args.steps, R * C * B, world)
     ans_ms = [e[0].elapsed_time(e[1]) for e in evs]
     cmp_ms = [e[1].elapsed_time(e[2]) for e in evs]
     prod_ms = [e[3].elapsed_time(e[4]) for e in evs] if overlap else []
     step_ms = [(e[3] if overlap else e[0]).elapsed_time(e[2]) for e in evs]
     db_bytes = R * C * B
-    value = db_bytes * world / (ms_step * 1e-3) / 1e9
 
     # ---- the composed step equals the library's zp_respond, bit for bit
     T_step = T.clone()
@@ -377,6 +394,8 @@ def run_ours(args, world, rank, local):
                           "step_p50": float(np.percentile(step_ms, 50)),
                           "step_p99": float(np.percentile(step_ms, 99))},
             "gib_s": value * 1e9 / 2**30,
+            "hint_ms": hint_ms,
+            "hint_tflops_fp16": 2.0 * R * C * 4 * n / (hint_ms * 1e-3) / 1e12,
             "roofline": roof,
             "e2e": {"value": db_bytes * world / e2e_s / 1e9, "unit": "GB/s",
                     "h2d_bytes_per_step": 4 * B * C + 4 * B * n * L,
