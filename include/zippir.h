@@ -200,9 +200,10 @@ int zp_update_rows(zp_db* db, const uint32_t* hRows, uint32_t k, const uint8_t* 
 int zp_stale_rows(const zp_db* db, uint32_t* count);
 
 /* Selects kernel variants for this context (tuning and cross-checking):
- *   "answer_path":   0 auto (GEMV for one query, tensor cores otherwise and for the
- *                    hint), 1 CUDA-core dp4a kernels for every batch and the hint,
- *                    2 tensor cores also for a single query;
+ *   "answer_path":   0 auto (one pass of the dp4a GEMV for one to four queries,
+ *                    tensor cores for larger batches and the hint), 1 CUDA-core dp4a
+ *                    tiled kernels for every batch and the hint, 2 tensor cores also
+ *                    for one to four queries;
  *   "compress_path": 0 auto (tensor cores when n <= 1024), 1 CUDA-core products,
  *                    2 tensor cores (ZP_EUNSUPPORTED at call time if n > 1024);
  *   "overlap_sms":   the number of SMs on which the compression products of a single

@@ -64,8 +64,8 @@ enum { MODE_ANS = 0, MODE_HINT = 1, MODE_CMP = 2 };
 template <int MODE>
 struct Cfg {
   static constexpr int SB = (MODE == MODE_CMP) ? 3 : 4;
-  static constexpr int SA = 2;
-  static constexpr int SU = 3;  // stages of two K blocks
+  static constexpr int SA = SB;  // the A and B stages of a K block are filled and freed together
+  static constexpr int SU = 2;   // stages of two K blocks
   static constexpr int STG = (MODE == MODE_CMP) ? STG_BYTES : 0;
   static constexpr int SMEM = SB * B_MAX_BYTES + SA * A16_BYTES + SU * U8_STAGE + STG + 1024 + 512;
 };
@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       mbar_init(&u8_empty[s], 4);
     }
     for (int s = 0; s < SB; ++s) {
-      mbar_init(&b_full[s], 1);
+      mbar_init(&b_full[s], 5);     // B bytes (TMA) + the four converter warps
       mbar_init(&b_empty[s], 1);
     }
     for (int s = 0; s < SA; ++s) {
@@ -286,8 +286,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             d = tmem_base + a * 256u;
           }
           if (!mbar_wait_abortable(&b_full[sb], pb, abort_flag, args.status,
-                                   ZP_DEV_TIMEOUT_GEMM) ||
-              !mbar_wait_abortable(&a_ready[sa], pa, abort_flag, args.status,
                                    ZP_DEV_TIMEOUT_GEMM)) {
             ok = false;
             break;
@@ -301,7 +299,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           umma_f16(d, ad + 4u, bd + 4u, idesc, 1u);
           umma_f16(d, ad + 6u, bd + 6u, idesc, 1u);
           umma_commit(&b_empty[sb]);
-          umma_commit(&a_empty[sa]);
           if (++kin == KCHUNK || kb == nkb - 1) {
             umma_commit(&acc_full[acc_cnt & 1u]);
             ++acc_cnt;
@@ -334,7 +331,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const uint32_t sa = cnt % SA, rra = cnt / SA;
         if ((h == 0 && !mbar_wait_abortable(&u8_full[su], pu, abort_flag, args.status,
                                             ZP_DEV_TIMEOUT_GEMM)) ||
-            (rra > 0 && !mbar_wait_abortable(&a_empty[sa], (rra - 1) & 1u, abort_flag,
+            (rra > 0 && !mbar_wait_abortable(&b_empty[sa], (rra - 1) & 1u, abort_flag,
                                              args.status, ZP_DEV_TIMEOUT_GEMM))) {
           ok = false;
           break;
@@ -344,7 +341,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
           const uint32_t idx = ct + 128u * i;
-          const uint32_t row = idx >> 2, ch = idx & 3u;
+          const uint32_t row = (idx & 7u) | ((idx >> 5) << 3), ch = (idx >> 3) & 3u;
           // byte tile: 128-byte rows, 16-byte chunk c stored at chunk c ^ (row % 8)
           const uint4 v = *reinterpret_cast<const uint4*>(
               src + row * 128 + (((4 * h + ch) ^ (row & 7u)) << 4));
@@ -361,7 +358,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         __syncwarp();
         const bool last_of_pair = h == 1 || kb == nkb - 1;
         if (lane == 0) {
-          mbar_arrive(&a_ready[sa]);
+          mbar_arrive(&b_full[sa]);
           if (last_of_pair) mbar_arrive(&u8_empty[su]);
         }
         if (last_of_pair && ++su == SU) {

@@ -503,9 +503,11 @@ extern "C" int zp_answer(zp_db* db, const uint32_t* dQ, uint32_t B, uint32_t* dA
   ZP_CUDA(cudaSetDevice(db->ctx->device));
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   zp_ctx* c = db->ctx;
-  if (B == 1 && c->answer_path != ZP_PATH_SIMT && c->answer_path != ZP_PATH_TC)
-    return zp_launch_gemv(db, dQ, dAns, st,
-                          c->overlap_sms ? (uint32_t)c->num_sms - c->overlap_sms : 0u);
+  // One to four queries: one pass of the dp4a GEMV over D (HBM- or dp4a-bound, ahead of
+  // the tensor cores for such batches); more: the tensor-core GEMM.
+  if (B <= 4 && c->answer_path != ZP_PATH_SIMT && c->answer_path != ZP_PATH_TC)
+    return zp_launch_gemv(db, dQ, B, dAns, st,
+                          B == 1 && c->overlap_sms ? (uint32_t)c->num_sms - c->overlap_sms : 0u);
   if (c->answer_path == ZP_PATH_SIMT)
     return zp_launch_answer_simt(db, dQ, B, db->C, dAns, db->R, 1, db->dD, db->R, db->ld, st);
   return zp_launch_answer_tc(db, db->tmap_gemm, db->R, dQ, B, false, dAns, db->R, false,
@@ -678,7 +680,7 @@ extern "C" int zp_respond(zp_db* db, zp_client* const* clients, const uint32_t* 
     ZP_CUDA(cudaStreamWaitEvent(db->side, db->ev_fork, 0));
     rc = zp_launch_compress_products(db, dCKO, B, db->side, c->overlap_sms);
     if (rc) return rc;
-    rc = zp_launch_gemv(db, dQ, dAns, st, (uint32_t)c->num_sms - c->overlap_sms);
+    rc = zp_launch_gemv(db, dQ, 1u, dAns, st, (uint32_t)c->num_sms - c->overlap_sms);
     if (rc) return rc;
     ZP_CUDA(cudaEventRecord(db->ev_join, db->side));
     ZP_CUDA(cudaStreamWaitEvent(st, db->ev_join, 0));

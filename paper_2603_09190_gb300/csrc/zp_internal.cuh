@@ -117,7 +117,8 @@ int zp_launch_answer_tc(zp_db* db, const CUtensorMap& tmD, uint32_t Rrows, const
 int zp_launch_vmul_tc(zp_db* db, const uint32_t* dCKO, uint32_t B, uint32_t* V4, cudaStream_t st,
                       uint32_t max_ctas);
 int zp_launch_hint_planes_rowsum(zp_db* db, const uint32_t* rows, uint32_t nrows, cudaStream_t st);
-int zp_launch_gemv(zp_db* db, const uint32_t* dq, uint32_t* dans, cudaStream_t st,
+// B in 1..4 queries (dq: B x C, dans: B x R); max_ctas limits the single-query grid.
+int zp_launch_gemv(zp_db* db, const uint32_t* dq, uint32_t B, uint32_t* dans, cudaStream_t st,
                    uint32_t max_ctas);
 int zp_launch_answer_simt(zp_db* db, const uint32_t* dQ, uint32_t B, uint32_t ldq,
                           uint32_t* dOut, uint64_t out_stride_b, uint64_t out_stride_r,

@@ -77,11 +77,53 @@ def test_gemv_closed_forms(zp, ctx):
     db2.close()
 
 
+@pytest.mark.parametrize("R,C,B", [(1, 1, 2), (7, 300, 3), (64, 256, 4), (65, 257, 2),
+                                   (333, 9999, 3), (2049, 700, 4), (130, 4096, 4)])
+def test_multi_query_gemv_parity(zp, ctx, R, C, B):
+    """Two to four queries share one pass of the dp4a GEMV over D (ragged row blocks and
+    column tiles, stream-K splits across CTAs)."""
+    D = synth.database(R, C, 11 * B + R)
+    Q = synth.uniform_queries(B, C, 13 * B + C)
+    dD, ld = to_dev_db(zp, D)
+    db = zp.Database(ctx, dD, R, C, ld)
+    got = u32_host(db.answer(u32_dev(Q)))
+    assert np.array_equal(got, lwe.matmat_mod_q(D, Q.T).T)
+    db.close()
+
+
+def test_multi_query_gemv_closed_form_and_tc(zp):
+    """All-255 database against all-ones queries gives -255 C mod 2^32 in every entry; the
+    tensor-core path forced for the same batch agrees on random data."""
+    R, C = 300, 70000
+    D = np.full((R, C), 255, dtype=np.uint8)
+    Q = np.full((4, C), 0xFFFFFFFF, dtype=np.uint32)
+    Q[1] = 1
+    c = zp.Context(0, n=64)
+    dD, ld = to_dev_db(zp, D)
+    db = zp.Database(c, dD, R, C, ld)
+    got = u32_host(db.answer(u32_dev(Q)))
+    assert np.all(got[[0, 2, 3]] == np.uint32((-255 * C) % 2**32))
+    assert np.all(got[1] == np.uint32(255 * C))
+    db.close()
+    D2 = synth.database(R, 3000, 17)
+    Q2 = synth.uniform_queries(3, 3000, 18)
+    dD2, ld2 = to_dev_db(zp, D2)
+    db2 = zp.Database(c, dD2, R, 3000, ld2)
+    a_gemv = u32_host(db2.answer(u32_dev(Q2)))
+    c.set_option("answer_path", "tc")
+    a_tc = u32_host(db2.answer(u32_dev(Q2)))
+    assert np.array_equal(a_gemv, a_tc)
+    assert np.array_equal(a_gemv, lwe.matmat_mod_q(D2, Q2.T).T)
+    db2.close()
+    c.close()
+
+
 @pytest.mark.parametrize("R,C,B", [(64, 64, 2), (100, 333, 5), (1024, 1024, 8), (257, 2000, 33),
                                    (1000, 4097, 17), (130, 1030, 64), (300, 3000, 65),
                                    (129, 700, 100)])
 def test_batched_answer_parity(zp, ctx, R, C, B):
-    """Batched answers on the tensor cores (byte planes, centred fp16, chunked exact sums)."""
+    """Batched answers (two queries: dp4a GEMV; five and more: tensor cores with byte planes,
+    centred fp16, chunked exact sums)."""
     D = synth.database(R, C, B)
     Q = synth.uniform_queries(B, C, B + 1)
     dD, ld = to_dev_db(zp, D)
