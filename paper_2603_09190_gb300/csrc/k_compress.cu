@@ -155,13 +155,18 @@ __device__ __forceinline__ bool warp_geq(const uint32_t (&a)[WPL], const uint32_
   return (GT >> top) & 1u;
 }
 
-// Column sums of the product a (na words) x b (nb words) for output words [0, nw):
-// col[w] = sum_{i+j=w} a[i] b[j] as three 32-bit words (exact: < 2^96). Lanes take
-// output words in a strided pattern, which balances the triangular column lengths.
+// Column sums of the product a (na words) x b (nb words) for output words [w_lo, nw):
+// col[w] = sum_{i+j=w} a[i] b[j] as three 32-bit words (exact: < 2^96); columns below
+// w_lo are set to zero. Lanes take output words in a strided pattern, which balances the
+// triangular column lengths.
 __device__ __forceinline__ void warp_mul_cols(const uint32_t* a, int na, const uint32_t* b, int nb,
-                                              uint32_t (*col)[3], int nw) {
+                                              uint32_t (*col)[3], int nw, int w_lo = 0) {
   for (int w = (int)lane_id(); w < nw; w += 32) {
     uint32_t c0 = 0, c1 = 0, c2 = 0;
+    if (w < w_lo) {
+      col[w][0] = col[w][1] = col[w][2] = 0u;
+      continue;
+    }
     const int i0 = w - (nb - 1) > 0 ? w - (nb - 1) : 0;
     const int i1 = w < na - 1 ? w : na - 1;
     for (int i = i0; i <= i1; ++i) mac96(c0, c1, c2, a[i], b[w - i]);
@@ -191,6 +196,7 @@ __device__ __forceinline__ void warp_cols_to_words(const uint32_t (*col)[3], int
 
 struct PackBarrett {
   uint32_t X[ZP_XW];        // the packed sum before reduction (< 2^4064)
+  uint32_t ans[64];         // the ell (< 64) answers of the packed row
   uint32_t col[160][3];     // product columns
   uint32_t q1[ZP_MAX_L + 1];
   uint32_t q3[ZP_MAX_L + 1];
@@ -232,6 +238,7 @@ __global__ void __launch_bounds__(PACK_WARPS * 32)
     S.mu[x] = cl[b].mu[x];
   }
   const uint32_t* ansb = ans + (uint64_t)b * R + row0;
+  for (uint32_t j = lane; j < nrows; j += 32) S.ans[j] = __ldg(ansb + j);
   __syncwarp();
 
   // ---- Horner: X <- X gamma + W_j (j = ell-1 .. 0), gamma = g1 2^32 + g2 2^64,
@@ -254,7 +261,7 @@ __global__ void __launch_bounds__(PACK_WARPS * 32)
       const uint32_t x = lane * 4 + t;
       if (x < VW) v[t] += Wj[x];
     }
-    if (lane == 0) v[0] += __ldg(ansb + j);
+    if (lane == 0) v[0] += S.ans[j];
     uint64_t c = 0;
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
@@ -278,7 +285,11 @@ __global__ void __launch_bounds__(PACK_WARPS * 32)
   //      r = (X mod b^(L+1)) - (q3 m mod b^(L+1)), then r -= m while r >= m.
   for (int x = lane; x < L + 1; x += 32) S.q1[x] = S.X[L - 1 + x];
   __syncwarp();
-  warp_mul_cols(S.q1, L + 1, S.mu, L + 1, S.col, 2 * L + 1);
+  // Only the columns from L - 1 up are summed (Handbook of Applied Cryptography, Note
+  // 14.44): the dropped lower part is below L b^L, so the quotient estimate below is at
+  // most one short of floor(q1 mu / b^(L+1)), r stays below 4m, and the correction loop's
+  // three subtractions still end with r < m.
+  warp_mul_cols(S.q1, L + 1, S.mu, L + 1, S.col, 2 * L + 1, L - 1);
   __syncwarp();
   {
     uint32_t w[5];  // words 0..159 of q1 * mu; q3 = words L+1 .. 2L+1
