@@ -196,6 +196,30 @@ int zp_respond_host(zp_db* db, zp_client* const* clients, const uint32_t* hQ,
 int zp_update_rows(zp_db* db, const uint32_t* hRows, uint32_t k, const uint8_t* dNewRows,
                    void* stream);
 
+/* Per-client hint (Algorithm "ZipPIR", Setup; Sec. 4.3 "Lowering offline communication
+ * costs", k = PaillierMatMul(H', ck_r)), offline:
+ *   k[r'] = prod_i ck_r[i]^{H'[r', i]} mod m^2,  H'[r', i] = sum_j gamma^j Hneg[r' ell + j, i]
+ * (Hneg = -D.A mod 2^32, rows past R zero). The client decrypts k to H'.pt_r, the term
+ * t leaves out. dCkr: n x 2L u32 (ck_r[i] < m^2, 2L little-endian limbs), 16-byte
+ * aligned. dK: d1' x 2L u32 output, 16-byte aligned. hPackedRows: NULL for every packed
+ * row, else a HOST array of nrows packed-row indices < d1' (the rows to recompute after
+ * zp_update_rows and zp_gen_hint of their answer rows; other rows of dK are untouched),
+ * read before the call returns. Needs the global hint and no stale rows. Work: about n
+ * (popcount of a 32-bit exponent) Montgomery products mod m^2 per answer row plus
+ * ell x 75 per packed row. Asynchronous on `stream`.
+ * Errors: ZP_EINVAL, ZP_ESTATE (no hint or stale rows), ZP_ENOMEM, ZP_ECUDA. */
+int zp_client_hint(zp_db* db, const zp_client* cl, const uint32_t* dCkr, uint32_t* dK,
+                   const uint32_t* hPackedRows, uint32_t nrows, void* stream);
+
+/* Combined response (Sec. 4.3, last extension): out[b][r'] = k[b][r'] (1 + t[b][r'] m_b)
+ * mod m_b^2, the homomorphic sum of the hint and t (encrypted with randomness 1), so that
+ * Dec(out) = Dec(k) + t mod m: one ciphertext per packed row instead of (k, t).
+ * dK: B x d1' x 2L u32 (k of query b's client, each < m_b^2); dT: B x d1' x L u32 (from
+ * zp_compress); dOut: B x d1' x 2L u32 output. All 16-byte aligned. clients: B client
+ * handles. Asynchronous on `stream`. Errors: ZP_EINVAL, ZP_ENOMEM, ZP_ECUDA. */
+int zp_combine(zp_db* db, zp_client* const* clients, const uint32_t* dK, const uint32_t* dT,
+               uint32_t B, uint32_t* dOut, void* stream);
+
 /* Number of hint rows marked stale by zp_update_rows and not yet regenerated. */
 int zp_stale_rows(const zp_db* db, uint32_t* count);
 

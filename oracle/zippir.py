@@ -187,6 +187,13 @@ def paillier_matmul_rows(client: Client, Hneg: np.ndarray, packed_rows) -> list[
     return out
 
 
+def combine(pk: paillier.PublicKey, k: list[int], t: list[int]) -> list[int]:
+    """Combined response k (+) t (Sec. 4.3, last extension): the homomorphic sum of the
+    hint ciphertext k[r'] and t[r'] encrypted with randomness 1, one ciphertext per packed
+    row, so that Dec(k (+) t) = Dec(k) + t mod m."""
+    return [paillier.add(pk, kk, paillier.encrypt(pk, tt, 1)) for kk, tt in zip(k, t)]
+
+
 def dec_k_shortcut(client: Client, Hneg: np.ndarray, packed_rows) -> list[int]:
     """Dec(k[r']) through the homomorphic identity Dec(k[r']) = H'[r', :] . pt_r mod m.
 

@@ -30,7 +30,7 @@ EXPORTS = [
     "zp_db_destroy", "zp_gen_hint", "zp_answer", "zp_register_client", "zp_client_destroy",
     "zp_compress", "zp_respond", "zp_respond_host", "zp_update_rows", "zp_stale_rows",
     "zp_device_status", "zp_kernel_launches", "zp_set_option", "zp_answer_noalloc",
-    "zp_compress_products", "zp_compress_finish", "zp_get_option",
+    "zp_compress_products", "zp_compress_finish", "zp_get_option", "zp_client_hint", "zp_combine",
 ]
 
 
@@ -82,6 +82,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "zp_compress_products": (i32, [vp, vp, u32, vp]),
         "zp_compress_finish": (i32, [vp, vp, vp, u32, vp, vp]),
         "zp_get_option": (i32, [vp, ctypes.c_char_p, ctypes.POINTER(ctypes.c_int64)]),
+        "zp_client_hint": (i32, [vp, vp, vp, vp, vp, u32, vp]),
+        "zp_combine": (i32, [vp, vp, vp, vp, u32, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -230,6 +232,20 @@ def zp_respond_host(db: int, clients, hQ: np.ndarray, hCKO: np.ndarray, B: int, 
     _check(load_library().zp_respond_host(
         db, ctypes.cast(_client_array(clients), ctypes.c_void_p), hQ.ctypes.data, hCKO.ctypes.data,
         B, hT.ctypes.data, None if hAns is None else hAns.ctypes.data, stream))
+
+
+def zp_client_hint(db: int, client, dCkr: int, dK: int, packed_rows, stream: int | None):
+    h = client.handle if isinstance(client, Client) else client
+    if packed_rows is None:
+        _check(load_library().zp_client_hint(db, h, dCkr, dK, None, 0, stream))
+    else:
+        r = np.ascontiguousarray(packed_rows, dtype=np.uint32)
+        _check(load_library().zp_client_hint(db, h, dCkr, dK, r.ctypes.data, len(r), stream))
+
+
+def zp_combine(db: int, clients, dK: int, dT: int, B: int, dOut: int, stream: int | None):
+    _check(load_library().zp_combine(db, ctypes.cast(_client_array(clients), ctypes.c_void_p),
+                                     dK, dT, B, dOut, stream))
 
 
 def zp_update_rows(db: int, hRows: np.ndarray, dNew: int, stream: int | None):
@@ -390,6 +406,28 @@ class Database:
             hT = np.empty((B, self.d1p, self.L), dtype=np.uint32)
         zp_respond_host(self.handle, clients, hQ, hCKO, B, hT, hAns, _stream(stream))
         return hT
+
+    def client_hint(self, client, CKR, out=None, packed_rows=None, stream=None):
+        """Per-client hint k (d1' x 2L words) from ck_r (n x 2L words)."""
+        import torch
+        _need(CKR, "i32", self.ctx.n * 2 * self.L, "ckr")
+        if out is None:
+            out = torch.zeros((self.d1p, 2 * self.L), dtype=torch.int32, device=CKR.device)
+        _need(out, "i32", self.d1p * 2 * self.L, "k")
+        zp_client_hint(self.handle, client, _ptr(CKR), _ptr(out), packed_rows, _stream(stream))
+        return out
+
+    def combine(self, clients, K, T, out=None, stream=None):
+        """Combined response k (+) t (B x d1' x 2L words)."""
+        import torch
+        B = len(clients)
+        _need(K, "i32", B * self.d1p * 2 * self.L, "k")
+        _need(T, "i32", B * self.d1p * self.L, "T")
+        if out is None:
+            out = torch.empty((B, self.d1p, 2 * self.L), dtype=torch.int32, device=T.device)
+        _need(out, "i32", B * self.d1p * 2 * self.L, "out")
+        zp_combine(self.handle, clients, _ptr(K), _ptr(T), B, _ptr(out), _stream(stream))
+        return out
 
     def update_rows(self, rows, new_rows, stream=None):
         _need(new_rows, "u8", len(rows) * self.C, "new_rows")

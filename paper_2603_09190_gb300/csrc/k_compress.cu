@@ -19,6 +19,7 @@
 //    96-bit accumulators and carries are resolved across the warp with a
 //    generate/propagate ballot (one integer addition over the 32 lane flags).
 #include "zp_internal.cuh"
+#include "zp_warpint.cuh"
 
 namespace {
 
@@ -66,93 +67,6 @@ __global__ void __launch_bounds__(256)
       carry = s >> 32;
     }
   }
-}
-
-// ------------------------------------------------------------------ warp big integers
-// A big integer of WPL*32 words is held with words [WPL*lane, WPL*lane + WPL) in lane.
-
-// Adds per-word 64-bit column values v (each < 2^62) into normalized 32-bit words w.
-template <int WPL>
-__device__ __forceinline__ void warp_normalize(const uint64_t (&v)[WPL], uint32_t (&w)[WPL]) {
-  const uint32_t lane = lane_id();
-  uint64_t c = 0;
-#pragma unroll
-  for (int t = 0; t < WPL; ++t) {
-    const uint64_t s = v[t] + c;
-    w[t] = (uint32_t)s;
-    c = s >> 32;
-  }
-  uint64_t cin = __shfl_up_sync(0xffffffffu, c, 1);
-  if (lane == 0) cin = 0;
-  uint32_t cc;
-  {
-    const uint64_t s = (uint64_t)w[0] + cin;
-    w[0] = (uint32_t)s;
-    cc = (uint32_t)(s >> 32);
-  }
-#pragma unroll
-  for (int t = 1; t < WPL; ++t) {
-    const uint64_t s = (uint64_t)w[t] + cc;
-    w[t] = (uint32_t)s;
-    cc = (uint32_t)(s >> 32);
-  }
-  uint32_t all = 0xFFFFFFFFu;
-#pragma unroll
-  for (int t = 0; t < WPL; ++t) all &= w[t];
-  const uint32_t G = __ballot_sync(0xffffffffu, cc != 0);
-  const uint32_t P = __ballot_sync(0xffffffffu, all == 0xFFFFFFFFu);
-  const uint32_t K = (uint32_t)((uint64_t)G + (uint64_t)(G | P)) ^ P;  // carry into each lane
-  if ((K >> lane) & 1u) {
-    uint32_t c1 = 1;
-#pragma unroll
-    for (int t = 0; t < WPL; ++t) {
-      const uint64_t s = (uint64_t)w[t] + c1;
-      w[t] = (uint32_t)s;
-      c1 = (uint32_t)(s >> 32);
-    }
-  }
-}
-
-// a -= b over the warp (mod 2^(32*32*WPL)).
-template <int WPL>
-__device__ __forceinline__ void warp_sub(uint32_t (&a)[WPL], const uint32_t (&b)[WPL]) {
-  const uint32_t lane = lane_id();
-  uint32_t br = 0;
-#pragma unroll
-  for (int t = 0; t < WPL; ++t) {
-    const uint64_t s = (uint64_t)a[t] - b[t] - br;
-    a[t] = (uint32_t)s;
-    br = (uint32_t)(s >> 63);
-  }
-  uint32_t any = 0;
-#pragma unroll
-  for (int t = 0; t < WPL; ++t) any |= a[t];
-  const uint32_t G = __ballot_sync(0xffffffffu, br != 0);
-  const uint32_t P = __ballot_sync(0xffffffffu, any == 0);
-  const uint32_t K = (uint32_t)((uint64_t)G + (uint64_t)(G | P)) ^ P;  // borrow into each lane
-  if ((K >> lane) & 1u) {
-    uint32_t b1 = 1;
-#pragma unroll
-    for (int t = 0; t < WPL; ++t) {
-      const uint64_t s = (uint64_t)a[t] - b1;
-      a[t] = (uint32_t)s;
-      b1 = (uint32_t)(s >> 63);
-    }
-  }
-}
-
-// a >= b over the warp.
-template <int WPL>
-__device__ __forceinline__ bool warp_geq(const uint32_t (&a)[WPL], const uint32_t (&b)[WPL]) {
-  int cmp = 0;
-#pragma unroll
-  for (int t = WPL - 1; t >= 0; --t)
-    if (cmp == 0 && a[t] != b[t]) cmp = a[t] > b[t] ? 1 : -1;
-  const uint32_t GT = __ballot_sync(0xffffffffu, cmp > 0);
-  const uint32_t LT = __ballot_sync(0xffffffffu, cmp < 0);
-  if ((GT | LT) == 0) return true;
-  const int top = 31 - __clz(GT | LT);
-  return (GT >> top) & 1u;
 }
 
 // Column sums of the product a (na words) x b (nb words) for output words [w_lo, nw):

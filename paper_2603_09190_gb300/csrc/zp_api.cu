@@ -349,7 +349,7 @@ extern "C" int zp_db_destroy(zp_db* db) {
   }
   zp_scratch* all[] = {&db->s_qplanes, &db->s_v,   &db->s_q,   &db->s_cko,  &db->s_ans,
                        &db->s_t,       &db->s_clients, &db->s_misc, &db->s_tcq, &db->s_hq,
-                       &db->s_hcko};
+                       &db->s_hcko, &db->s_ptab, &db->s_krows, &db->s_m2consts};
   for (zp_scratch* s : all) scratch_free(s);
   delete db;
   return ZP_OK;
@@ -554,23 +554,79 @@ extern "C" int zp_register_client(zp_ctx* c, const uint32_t* hM, uint32_t L, zp_
         if (i / 32 < (int64_t)(L + 1)) mu[i / 32] |= 1u << (i % 32);
       }
     }
+    // Montgomery constants mod m^2 (R = 2^(64 L)): m^2, R mod m^2, R^2 mod m^2 and
+    // -(m^2)^{-1} mod 2^32 (Newton's iteration x <- x (2 - a x) doubles the correct bits)
+    const uint32_t L2 = 2 * L;
+    std::vector<uint32_t> m2(L2, 0);
+    for (uint32_t i = 0; i < L; ++i) {
+      uint64_t carry = 0;
+      for (uint32_t j = 0; j < L; ++j) {
+        const uint64_t s = (uint64_t)m[i] * m[j] + m2[i + j] + carry;
+        m2[i + j] = (uint32_t)s;
+        carry = s >> 32;
+      }
+      m2[i + L] = (uint32_t)carry;
+    }
+    uint32_t inv = m2[0];
+    for (int it = 0; it < 5; ++it) inv *= 2u - m2[0] * inv;
+    const uint32_t m2inv = 0u - inv;
+    // 2^k mod m^2 by doubling with a conditional subtraction (values stay below m^2)
+    auto pow2_mod = [&](uint32_t k) {
+      std::vector<uint32_t> r(L2 + 1, 0);
+      r[0] = 1;
+      for (uint32_t it = 0; it < k; ++it) {
+        uint32_t carry = 0;
+        for (uint32_t w = 0; w <= L2; ++w) {
+          const uint32_t nc = r[w] >> 31;
+          r[w] = (r[w] << 1) | carry;
+          carry = nc;
+        }
+        bool ge = true;
+        for (int64_t w = L2; w >= 0; --w) {
+          const uint32_t mw = w < (int64_t)L2 ? m2[w] : 0u;
+          if (r[w] != mw) {
+            ge = r[w] > mw;
+            break;
+          }
+        }
+        if (ge) {
+          uint64_t br = 0;
+          for (uint32_t w = 0; w <= L2; ++w) {
+            const uint64_t s = (uint64_t)r[w] - (w < L2 ? m2[w] : 0u) - br;
+            r[w] = (uint32_t)s;
+            br = (s >> 63) & 1u;
+          }
+        }
+      }
+      r.resize(L2);
+      return r;
+    };
+    const std::vector<uint32_t> r1 = pow2_mod(32 * L2), r2 = pow2_mod(64 * L2);
     ZP_CUDA(cudaSetDevice(c->device));
     zp_client* cl = new zp_client();
     cl->ctx = c;
     cl->device = c->device;
     cl->L = L;
-    cl->d_m = nullptr;
-    cl->d_mu = nullptr;
-    if (cudaMalloc(&cl->d_m, L * 4) != cudaSuccess || cudaMalloc(&cl->d_mu, (L + 1) * 4) != cudaSuccess) {
-      if (cl->d_m) cudaFree(cl->d_m);
+    cl->d_m = cl->d_mu = cl->d_m2 = cl->d_r1 = cl->d_r2 = nullptr;
+    cl->m2inv = m2inv;
+    auto free_all = [cl]() {
+      for (uint32_t* p : {cl->d_m, cl->d_mu, cl->d_m2, cl->d_r1, cl->d_r2})
+        if (p) cudaFree(p);
+    };
+    if (cudaMalloc(&cl->d_m, L * 4) != cudaSuccess || cudaMalloc(&cl->d_mu, (L + 1) * 4) != cudaSuccess ||
+        cudaMalloc(&cl->d_m2, L2 * 4) != cudaSuccess || cudaMalloc(&cl->d_r1, L2 * 4) != cudaSuccess ||
+        cudaMalloc(&cl->d_r2, L2 * 4) != cudaSuccess) {
+      free_all();
       delete cl;
       return zp_set_error(ZP_ENOMEM, "zp_register_client: cudaMalloc");
     }
     cudaError_t e = cudaMemcpy(cl->d_m, m.data(), L * 4, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(cl->d_mu, mu.data(), (L + 1) * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(cl->d_m2, m2.data(), L2 * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(cl->d_r1, r1.data(), L2 * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(cl->d_r2, r2.data(), L2 * 4, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
-      cudaFree(cl->d_m);
-      cudaFree(cl->d_mu);
+      free_all();
       delete cl;
       return zp_cuda_check(e, "zp_register_client: copy constants");
     }
@@ -585,8 +641,8 @@ extern "C" int zp_client_destroy(zp_client* cl) {
   if (!cl) return ZP_OK;
   cudaSetDevice(cl->device);
   cudaDeviceSynchronize();
-  if (cl->d_m) cudaFree(cl->d_m);
-  if (cl->d_mu) cudaFree(cl->d_mu);
+  for (uint32_t* p : {cl->d_m, cl->d_mu, cl->d_m2, cl->d_r1, cl->d_r2})
+    if (p) cudaFree(p);
   delete cl;
   return ZP_OK;
 }
@@ -687,6 +743,54 @@ extern "C" int zp_respond(zp_db* db, zp_client* const* clients, const uint32_t* 
     return zp_launch_compress_finish(db, clients, dAns, B, dT, st);
   } catch (const std::bad_alloc&) {
     return zp_set_error(ZP_ENOMEM, "zp_respond: host allocation failed");
+  }
+}
+
+extern "C" int zp_client_hint(zp_db* db, const zp_client* cl, const uint32_t* dCkr, uint32_t* dK,
+                              const uint32_t* hPackedRows, uint32_t nrows, void* stream) {
+  try {
+    if (!db || !cl || !dCkr || !dK) return zp_set_error(ZP_EINVAL, "zp_client_hint: null argument");
+    if (cl->ctx != db->ctx) return zp_set_error(ZP_EINVAL, "zp_client_hint: client from another context");
+    if (!db->hint_ready) return zp_set_error(ZP_ESTATE, "zp_client_hint: no hint (call zp_gen_hint)");
+    if (db->stale) return zp_set_error(ZP_ESTATE, "zp_client_hint: %u hint rows stale after updates", db->stale);
+    if ((reinterpret_cast<uintptr_t>(dCkr) | reinterpret_cast<uintptr_t>(dK)) & 15u)
+      return zp_set_error(ZP_EINVAL, "zp_client_hint: dCkr and dK must be 16-byte aligned");
+    ZP_CUDA(cudaSetDevice(db->ctx->device));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const uint32_t* dRows = nullptr;
+    uint32_t np = db->d1p;
+    if (hPackedRows) {
+      if (nrows == 0) return ZP_OK;
+      for (uint32_t j = 0; j < nrows; ++j)
+        if (hPackedRows[j] >= db->d1p)
+          return zp_set_error(ZP_EINVAL, "zp_client_hint: packed row %u >= d1'=%u", hPackedRows[j], db->d1p);
+      int rc = zp_scratch_reserve(&db->s_misc, (size_t)nrows * 4);
+      if (rc) return rc;
+      ZP_CUDA(cudaMemcpyAsync(db->s_misc.p, hPackedRows, (size_t)nrows * 4, cudaMemcpyHostToDevice, st));
+      dRows = static_cast<const uint32_t*>(db->s_misc.p);
+      np = nrows;
+    }
+    return zp_launch_client_hint(db, cl, dCkr, dK, dRows, np, st);
+  } catch (const std::bad_alloc&) {
+    return zp_set_error(ZP_ENOMEM, "zp_client_hint: host allocation failed");
+  }
+}
+
+extern "C" int zp_combine(zp_db* db, zp_client* const* clients, const uint32_t* dK, const uint32_t* dT,
+                          uint32_t B, uint32_t* dOut, void* stream) {
+  try {
+    if (!db || !clients || !dK || !dT || !dOut) return zp_set_error(ZP_EINVAL, "zp_combine: null argument");
+    if (B < 1 || B > 4096) return zp_set_error(ZP_EINVAL, "zp_combine: B=%u out of [1, 4096]", B);
+    for (uint32_t b = 0; b < B; ++b) {
+      if (!clients[b]) return zp_set_error(ZP_EINVAL, "zp_combine: clients[%u] is null", b);
+      if (clients[b]->ctx != db->ctx) return zp_set_error(ZP_EINVAL, "zp_combine: client %u from another context", b);
+    }
+    if ((reinterpret_cast<uintptr_t>(dK) | reinterpret_cast<uintptr_t>(dT) | reinterpret_cast<uintptr_t>(dOut)) & 15u)
+      return zp_set_error(ZP_EINVAL, "zp_combine: dK, dT and dOut must be 16-byte aligned");
+    ZP_CUDA(cudaSetDevice(db->ctx->device));
+    return zp_launch_combine(db, clients, dK, dT, B, dOut, static_cast<cudaStream_t>(stream));
+  } catch (const std::bad_alloc&) {
+    return zp_set_error(ZP_ENOMEM, "zp_combine: host allocation failed");
   }
 }
 

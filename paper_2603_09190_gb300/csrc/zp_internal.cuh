@@ -48,6 +48,11 @@ struct zp_client {
   uint32_t L;
   uint32_t* d_m;   // L limbs
   uint32_t* d_mu;  // L+1 limbs: floor(2^(64 L) / m)  (Barrett constant)
+  // Montgomery arithmetic mod m^2 (R = 2^(64 L)): per-client hint k, combined response
+  uint32_t* d_m2;  // 2L limbs: m^2
+  uint32_t* d_r1;  // 2L limbs: R mod m^2
+  uint32_t* d_r2;  // 2L limbs: R^2 mod m^2
+  uint32_t m2inv;  // -(m^2)^{-1} mod 2^32
 };
 
 struct zp_scratch {
@@ -82,6 +87,7 @@ struct zp_db {
   cudaEvent_t ev_fork, ev_join;
   // scratch, grown on demand (never shrunk before zp_db_destroy)
   zp_scratch s_qplanes, s_v, s_q, s_cko, s_ans, s_t, s_clients, s_misc, s_tcq, s_hq, s_hcko;
+  zp_scratch s_ptab, s_krows, s_m2consts;  // per-client hint and combined response
 };
 
 // error reporting (thread-local message)
@@ -117,6 +123,12 @@ int zp_launch_answer_tc(zp_db* db, const CUtensorMap& tmD, uint32_t Rrows, const
 int zp_launch_vmul_tc(zp_db* db, const uint32_t* dCKO, uint32_t B, uint32_t* V4, cudaStream_t st,
                       uint32_t max_ctas);
 int zp_launch_hint_planes_rowsum(zp_db* db, const uint32_t* rows, uint32_t nrows, cudaStream_t st);
+// per-client hint k of the listed packed rows (dRows device, NULL = all d1'), and the
+// combined response k (+) t (k_paillier.cu)
+int zp_launch_client_hint(zp_db* db, const zp_client* cl, const uint32_t* dCkr, uint32_t* dK,
+                          const uint32_t* dRows, uint32_t nprows, cudaStream_t st);
+int zp_launch_combine(zp_db* db, zp_client* const* clients, const uint32_t* dK, const uint32_t* dT,
+                      uint32_t B, uint32_t* dOut, cudaStream_t st);
 // B in 1..4 queries (dq: B x C, dans: B x R); max_ctas limits the single-query grid.
 int zp_launch_gemv(zp_db* db, const uint32_t* dq, uint32_t B, uint32_t* dans, cudaStream_t st,
                    uint32_t max_ctas);

@@ -143,6 +143,26 @@ def test_e2e_real_hint(seed, secret):
     assert np.array_equal(rec, D[:, i0])
 
 
+@pytest.mark.parametrize("seed,secret", [(1, "uniform"), (3, "binary")])
+def test_e2e_combined_response(seed, secret):
+    """k (+) t (Sec. 4.3): one decryption per packed row gives mu = Dec(k) + t mod m directly,
+    and Extract on those mu returns column i0; the ciphertext equals k (1 + t m) mod m^2."""
+    R, C, n = 60, 48, 8
+    P, D, A, Hn, cl = _instance(R, C, n, secret, seed, True)
+    i0 = (5 * seed + 3) % C
+    qy = zippir.query(cl, A, i0, seed + 300)
+    ans, t = zippir.response(D, qy.qu, Hn, qy.cko, cl.pk.m, P)
+    rows = range(P.d1p(R))
+    k = zippir.paillier_matmul_rows(cl, Hn, rows)
+    kt = zippir.combine(cl.pk, k, t)
+    m, m2 = cl.pk.m, cl.pk.m2
+    assert kt == [kk * (1 + tt * m) % m2 for kk, tt in zip(k, t)]
+    mus = [paillier.decrypt(cl.sk, c) for c in kt]
+    assert mus == [(paillier.decrypt(cl.sk, kk) + tt) % m for kk, tt in zip(k, t)]
+    rec = zippir.extract(cl, [0] * len(mus), mus, R)
+    assert np.array_equal(rec, D[:, i0])
+
+
 def _proof_identity(P, cl, Hn, qy, ans, t, rows):
     """(t + H' pt_r) mod m == b' + H' sk exactly, and b' + H' sk < m (App. D)."""
     m = cl.pk.m
