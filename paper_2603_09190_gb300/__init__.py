@@ -302,9 +302,10 @@ class Context:
         return zp_kernel_launches(self.handle)
 
     def set_option(self, name: str, value):
-        """Kernel-variant selection: name in {"answer_path", "compress_path"},
-        value in {"auto", "simt", "tc"} (or 0/1/2)."""
-        v = {"auto": 0, "simt": 1, "tc": 2}.get(value, value)
+        """Kernel-variant selection: name in {"answer_path", "compress_path"}, value in
+        {"auto", "simt", "tc"} (compress_path also "rns"), or "overlap_sms" / "rns_min_batch"
+        with an integer."""
+        v = {"auto": 0, "simt": 1, "tc": 2, "rns": 3}.get(value, value)
         zp_set_option(self.handle, name, v)
 
     def close(self):

@@ -123,21 +123,39 @@ constexpr int PACK_WARPS = 4;
 struct ClientPtrs {
   const uint32_t* m;
   const uint32_t* mu;
+  const uint32_t* mkm;  // RNS: M_k mod m (ZP_RNS_K x L), then m - (M mod m)
 };
+
+// x mod p for x < 2^64 (Barrett with mu = floor((2^64 - 1) / p); one correction).
+__device__ __forceinline__ uint32_t mod_p(uint64_t x, uint32_t p, uint64_t mu) {
+  const uint64_t q = __umul64hi(x, mu);
+  const uint64_t r = x - q * p;
+  return (uint32_t)(r >= p ? r - p : r);
+}
 
 // grid (ceil(d1p / PACK_WARPS), B), block PACK_WARPS warps, dynamic shared memory
 // PACK_WARPS x (PackBarrett + ell x VW words). Requires L == ZP_MAX_L.
 // V: [b][Rp][VW] words, the exact products V[row] = H[row,:] . cko[b].
+//
+// RNS (the products are residues X[b][r'][k] = H'[r', :] . cko mod p_k): V is absent, the
+// Horner runs over the answers only (b'), and H'.cko is rebuilt by the Chinese remainder
+// theorem modulo m: with y_k = X_k (M/p_k)^{-1} mod p_k, H'.cko = sum_k y_k M/p_k - alpha M,
+// alpha = floor(sum_k y_k / p_k) exactly (H'.cko < M 2^-26, so the double-precision sum
+// plus 2^-30 floors to alpha), and
+//   b' + H'.cko = b' + sum_k y_k (M/p_k mod m) + alpha (m - (M mod m))   (mod m),
+// whose right side (< 2^2083) is summed into X's lazy registers before the reduction.
+template <bool RNS>
 __global__ void __launch_bounds__(PACK_WARPS * 32)
     k_pack_reduce(const uint32_t* __restrict__ ans, const uint32_t* __restrict__ V, uint32_t R,
                   uint32_t Rp, uint32_t ell, uint32_t d1p, uint32_t g1, uint32_t g2,
-                  const ClientPtrs* __restrict__ cl, uint32_t* __restrict__ T) {
+                  const ClientPtrs* __restrict__ cl, uint32_t* __restrict__ T,
+                  const zp_rns_dev* __restrict__ rns) {
   extern __shared__ __align__(16) uint32_t pack_smem[];
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t b = blockIdx.y;
   const uint32_t rp = blockIdx.x * PACK_WARPS + warp;
   if (rp >= d1p) return;
-  const uint32_t per_warp = (uint32_t)(sizeof(PackBarrett) / 4) + ell * VW;
+  const uint32_t per_warp = (uint32_t)(sizeof(PackBarrett) / 4) + (RNS ? 0u : ell * VW);
   PackBarrett& S = *reinterpret_cast<PackBarrett*>(pack_smem + warp * per_warp);
   uint32_t* Vs = pack_smem + warp * per_warp + sizeof(PackBarrett) / 4;  // ell x VW
   constexpr int L = ZP_MAX_L;
@@ -146,7 +164,8 @@ __global__ void __launch_bounds__(PACK_WARPS * 32)
   const uint32_t row0 = rp * ell;
   const uint32_t nrows = R - row0 < ell ? R - row0 : ell;
   const uint32_t* src = V + ((uint64_t)b * Rp + row0) * VW;
-  for (uint32_t idx = lane; idx < nrows * VW; idx += 32) Vs[idx] = __ldg(src + idx);
+  if (!RNS)
+    for (uint32_t idx = lane; idx < nrows * VW; idx += 32) Vs[idx] = __ldg(src + idx);
   for (int x = lane; x < L + 1; x += 32) {
     S.m[x] = x < L ? cl[b].m[x] : 0u;
     S.mu[x] = cl[b].mu[x];
@@ -170,10 +189,12 @@ __global__ void __launch_bounds__(PACK_WARPS * 32)
     v[1] = (uint64_t)g1 * xv[0] + (uint64_t)g2 * xm1;
     v[2] = (uint64_t)g1 * xv[1] + (uint64_t)g2 * xv[0];
     v[3] = (uint64_t)g1 * xv[2] + (uint64_t)g2 * xv[1];
+    if (!RNS) {
 #pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      const uint32_t x = lane * 4 + t;
-      if (x < VW) v[t] += Wj[x];
+      for (int t = 0; t < 4; ++t) {
+        const uint32_t x = lane * 4 + t;
+        if (x < VW) v[t] += Wj[x];
+      }
     }
     if (lane == 0) v[0] += S.ans[j];
     uint64_t c = 0;
@@ -185,6 +206,67 @@ __global__ void __launch_bounds__(PACK_WARPS * 32)
     }
     const uint64_t cin = __shfl_up_sync(0xffffffffu, c, 1);
     if (lane) xv[0] += cin;
+  }
+  if (RNS) {
+    // y_k for k = lane + 32 q, and alpha from the warp sum of y_k / p_k
+    constexpr int QK = (ZP_RNS_K + 31) / 32;
+    uint32_t y[QK];
+    double f = 0.0;
+    const uint32_t* Xr = V + ((uint64_t)b * d1p + rp) * ZP_RNS_K;
+#pragma unroll
+    for (int q = 0; q < QK; ++q) {
+      const uint32_t k = lane + 32u * q;
+      y[q] = 0u;
+      if (k < ZP_RNS_K) {
+        y[q] = mod_p((uint64_t)__ldg(Xr + k) * rns->inv[k], rns->p[k], rns->mu[k]);
+        f += (double)y[q] * rns->dinv[k];
+      }
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
+    const uint32_t alpha = (uint32_t)floor(f + 0x1p-30);
+    // sum_k y_k (M_k mod m) + alpha (m - M mod m) into words lane*4 .. lane*4+3 (< 64):
+    // low halves to the word, high halves to the next (the top one to the next lane)
+    const uint32_t* mk = cl[b].mkm;
+    uint64_t hi3 = 0;
+#pragma unroll
+    for (int q = 0; q < QK; ++q) {
+      for (uint32_t kk = 0; kk < 32; ++kk) {
+        const uint32_t k = 32u * q + kk;
+        if (k >= ZP_RNS_K) break;
+        const uint32_t yk = __shfl_sync(0xffffffffu, y[q], kk);
+        if (lane < ZP_MAX_L / 4) {
+          const uint32_t* row = mk + (uint64_t)k * ZP_MAX_L + lane * 4;
+          uint64_t ph[4];
+#pragma unroll
+          for (int t = 0; t < 4; ++t) {
+            const uint64_t pr = (uint64_t)yk * __ldg(row + t);
+            xv[t] += (uint32_t)pr;
+            ph[t] = pr >> 32;
+          }
+          xv[1] += ph[0];
+          xv[2] += ph[1];
+          xv[3] += ph[2];
+          hi3 += ph[3];
+        }
+      }
+    }
+    if (lane < ZP_MAX_L / 4) {  // alpha (m - (M mod m)), stored after the ZP_RNS_K rows
+      const uint32_t* row = mk + (uint64_t)ZP_RNS_K * ZP_MAX_L + lane * 4;
+      uint64_t ph[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const uint64_t pr = (uint64_t)alpha * __ldg(row + t);
+        xv[t] += (uint32_t)pr;
+        ph[t] = pr >> 32;
+      }
+      xv[1] += ph[0];
+      xv[2] += ph[1];
+      xv[3] += ph[2];
+      hi3 += ph[3];
+    }
+    const uint64_t hin = __shfl_up_sync(0xffffffffu, hi3, 1);
+    if (lane > 0) xv[0] += hin;
   }
   // final carry resolution, then X to shared memory
   {
@@ -249,8 +331,22 @@ int zp_launch_compress_products(zp_db* db, const uint32_t* dCKO, uint32_t B, cud
                                 uint32_t max_ctas) {
   zp_ctx* ctx = db->ctx;
   const uint32_t R = db->R, n = ctx->P.n;
-  if (ctx->compress_path == ZP_PATH_TC && n > 1024)
+  if ((ctx->compress_path == ZP_PATH_TC || ctx->compress_path == ZP_PATH_RNS) && n > 1024)
     return zp_set_error(ZP_EUNSUPPORTED, "tensor-core compression needs n <= 1024");
+  // large batches: residues of H'.cko modulo the RNS primes (the packed hint is read once
+  // per batch and there are ell times fewer rows); otherwise exact per-row products V
+  const bool rns = n <= 1024 && (ctx->compress_path == ZP_PATH_RNS ||
+                                 (ctx->compress_path == ZP_PATH_AUTO && ctx->rns_min_batch &&
+                                  B >= ctx->rns_min_batch));
+  if (rns) {
+    int rc = zp_ensure_rns(db, st);
+    if (!rc) rc = zp_scratch_reserve(&db->s_v, (size_t)B * db->d1p * ZP_RNS_K * sizeof(uint32_t));
+    if (!rc) rc = zp_launch_rns_products(db, dCKO, B, static_cast<uint32_t*>(db->s_v.p), st);
+    if (rc) return rc;
+    db->v_batch = B;
+    db->v_rns = true;
+    return ZP_OK;
+  }
   const bool tc = ctx->compress_path != ZP_PATH_SIMT && n <= 1024;
   int rc = zp_scratch_reserve(&db->s_v, (size_t)B * db->Rp * VW * sizeof(uint32_t));
   if (rc) return rc;
@@ -266,6 +362,7 @@ int zp_launch_compress_products(zp_db* db, const uint32_t* dCKO, uint32_t B, cud
     ZP_CUDA(cudaGetLastError());
   }
   db->v_batch = B;
+  db->v_rns = false;
   return ZP_OK;
 }
 
@@ -280,16 +377,18 @@ int zp_launch_compress_finish(zp_db* db, zp_client* const* clients, const uint32
   if (rc) return rc;
   ClientPtrs* dcl = static_cast<ClientPtrs*>(db->s_clients.p);
   // upload the per-query client constants only when the list changed
-  bool same = db->cl_cache.size() == 2 * (size_t)B;
+  bool same = db->cl_cache.size() == 3 * (size_t)B;
   for (uint32_t b = 0; same && b < B; ++b)
-    same = db->cl_cache[2 * b] == clients[b]->d_m && db->cl_cache[2 * b + 1] == clients[b]->d_mu;
+    same = db->cl_cache[3 * b] == clients[b]->d_m && db->cl_cache[3 * b + 1] == clients[b]->d_mu &&
+           db->cl_cache[3 * b + 2] == clients[b]->d_mkm;
   if (!same) {
     std::vector<ClientPtrs> h(B);
-    db->cl_cache.resize(2 * (size_t)B);
+    db->cl_cache.resize(3 * (size_t)B);
     for (uint32_t b = 0; b < B; ++b) {
-      h[b] = ClientPtrs{clients[b]->d_m, clients[b]->d_mu};
-      db->cl_cache[2 * b] = clients[b]->d_m;
-      db->cl_cache[2 * b + 1] = clients[b]->d_mu;
+      h[b] = ClientPtrs{clients[b]->d_m, clients[b]->d_mu, clients[b]->d_mkm};
+      db->cl_cache[3 * b] = clients[b]->d_m;
+      db->cl_cache[3 * b + 1] = clients[b]->d_mu;
+      db->cl_cache[3 * b + 2] = clients[b]->d_mkm;
     }
     // pageable source: the copy is staged before cudaMemcpyAsync returns
     cudaError_t e = cudaMemcpyAsync(dcl, h.data(), B * sizeof(ClientPtrs), cudaMemcpyHostToDevice, st);
@@ -298,18 +397,26 @@ int zp_launch_compress_finish(zp_db* db, zp_client* const* clients, const uint32
       return zp_cuda_check(e, "cudaMemcpyAsync(clients)");
     }
   }
-  const size_t smem = (size_t)PACK_WARPS * (sizeof(PackBarrett) + (size_t)ctx->ell * VW * 4);
   static bool attr = false;
   if (!attr) {
-    ZP_CUDA(cudaFuncSetAttribute(k_pack_reduce, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    ZP_CUDA(cudaFuncSetAttribute(k_pack_reduce<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)(PACK_WARPS * (sizeof(PackBarrett) + 64 * VW * 4))));
     attr = true;
   }
   dim3 grid((db->d1p + PACK_WARPS - 1) / PACK_WARPS, B);
   zp_clear_pending_error();
   ctx->launches++;
-  k_pack_reduce<<<grid, PACK_WARPS * 32, smem, st>>>(dAns, V, db->R, db->Rp, ctx->ell, db->d1p,
-                                                     ctx->gamma_w[1], ctx->gamma_w[2], dcl, dT);
+  if (db->v_rns) {
+    const size_t smem = (size_t)PACK_WARPS * sizeof(PackBarrett);
+    k_pack_reduce<true><<<grid, PACK_WARPS * 32, smem, st>>>(dAns, V, db->R, db->Rp, ctx->ell,
+                                                             db->d1p, ctx->gamma_w[1],
+                                                             ctx->gamma_w[2], dcl, dT, ctx->d_rns);
+  } else {
+    const size_t smem = (size_t)PACK_WARPS * (sizeof(PackBarrett) + (size_t)ctx->ell * VW * 4);
+    k_pack_reduce<false><<<grid, PACK_WARPS * 32, smem, st>>>(dAns, V, db->R, db->Rp, ctx->ell,
+                                                              db->d1p, ctx->gamma_w[1],
+                                                              ctx->gamma_w[2], dcl, dT, nullptr);
+  }
   ZP_CUDA(cudaGetLastError());
   return ZP_OK;
 }

@@ -57,16 +57,16 @@ constexpr int NTHREADS = 384;
 constexpr int STG_PITCH = 67;                // words per staged row (odd: no bank conflicts)
 constexpr int STG_BYTES = 4 * 32 * STG_PITCH * 4;
 
-enum { MODE_ANS = 0, MODE_HINT = 1, MODE_CMP = 2 };
+enum { MODE_ANS = 0, MODE_HINT = 1, MODE_CMP = 2, MODE_RNS = 3 };
 
 // Three rings: B (fp16, from L2: deep, it is the largest operand), A as bytes (from
 // HBM, L2-prefetched) and A as fp16 (written by the converters just before the MMA).
 template <int MODE>
 struct Cfg {
-  static constexpr int SB = (MODE == MODE_CMP) ? 3 : 4;
+  static constexpr int SB = (MODE == MODE_CMP || MODE == MODE_RNS) ? 3 : 4;
   static constexpr int SA = SB;  // the A and B stages of a K block are filled and freed together
   static constexpr int SU = 2;   // stages of two K blocks
-  static constexpr int STG = (MODE == MODE_CMP) ? STG_BYTES : 0;
+  static constexpr int STG = (MODE == MODE_CMP || MODE == MODE_RNS) ? STG_BYTES : 0;
   static constexpr int SMEM = SB * B_MAX_BYTES + SA * A16_BYTES + SU * U8_STAGE + STG + 1024 + 512;
 };
 
@@ -80,7 +80,18 @@ struct GemmArgs {
   uint64_t out_ld;            // ANS: R; HINT: n
   uint32_t Rp;                // CMP: plane stride (rows) of the output
   uint32_t* status;
+  // MODE_RNS: the M tiles of prime k are k * mt_per_prime ..; its B rows start at
+  // k * num_n_tiles * N; out[(b d1p + r') ZP_RNS_K + k]
+  uint32_t mt_per_prime, d1p;
+  const zp_rns_dev* rns;
 };
+
+// x mod p for x < 2^64, p < 2^32, mu = floor((2^64 - 1) / p) (Barrett; one correction).
+__device__ __forceinline__ uint32_t mod_p(uint64_t x, uint32_t p, uint64_t mu) {
+  const uint64_t q = __umul64hi(x, mu);
+  const uint64_t r = x - q * p;
+  return (uint32_t)(r >= p ? r - p : r);
+}
 
 __device__ __forceinline__ uint32_t cvt_rn(uint32_t fbits) {
   return (uint32_t)__float2int_rn(__uint_as_float(fbits));
@@ -242,6 +253,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       bool ok = true;
       for (uint32_t tile = blockIdx.x; ok && tile < num_tiles; tile += gridDim.x) {
         const uint32_t nt = tile % args.num_n_tiles;
+        // B rows of this tile (RNS: the block of the tile's prime)
+        const uint32_t brow0 = nt * N + (MODE == MODE_RNS ? (tile / args.num_n_tiles) /
+                                                                args.mt_per_prime *
+                                                                args.num_n_tiles * N
+                                                          : 0u);
         for (uint32_t kb = 0; kb < nkb; ++kb, ++cnt) {
           const uint32_t sb = cnt % SB, rb = cnt / SB;
           if (rb > 0 && !mbar_wait_abortable(&b_empty[sb], (rb - 1) & 1u, abort_flag,
@@ -250,7 +266,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             break;
           }
           mbar_arrive_expect_tx(&b_full[sb], N * BK * 2);
-          tma_load_2d(b_ring + sb * B_MAX_BYTES, &tmB, (int32_t)(kb * BK), (int32_t)(nt * N),
+          tma_load_2d(b_ring + sb * B_MAX_BYTES, &tmB, (int32_t)(kb * BK), (int32_t)brow0,
                       &b_full[sb]);
         }
       }
@@ -376,7 +392,62 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const uint32_t nchunks = (nkb + KCHUNK - 1) / KCHUNK;
     for (uint32_t tile = blockIdx.x; ok && tile < num_tiles; tile += gridDim.x) {
       const uint32_t nt = tile % args.num_n_tiles, mt = tile / args.num_n_tiles;
-      if constexpr (MODE == MODE_CMP) {
+      if constexpr (MODE == MODE_RNS) {
+        // single chunk (n <= 1024). Row (plane e, packed row 32 g + lane) of prime k: the
+        // exact byte-product sums of the 4 BT columns (c, bl) are folded into residues
+        // sum_c 2^(8c) S_c mod p per query bl, then the four planes e are combined with
+        // 2^(8e) mod p through shared memory.
+        const uint32_t a = acc_cnt & 1u, ra = acc_cnt >> 1;
+        if (!bar_and_128(warp_wait(&acc_full[a], ra & 1u, abort_flag, args.status))) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t k = mt / args.mt_per_prime, g = mt % args.mt_per_prime;
+        const uint32_t p = args.rns->p[k];
+        const uint64_t mu = args.rns->mu[k];
+        uint32_t p8[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) p8[c] = args.rns->pow8[k][c];
+        const uint32_t corr_row = 128u * __ldg(args.rowsumA + mt * BM + e * 32 + lane) -
+                                  16384u * args.Kp;
+        const uint32_t* cs = args.colsum + ((uint64_t)k * args.num_n_tiles + nt) * (4 * BT);
+        uint32_t res[BT];
+#pragma unroll
+        for (int bl = 0; bl < BT; ++bl) res[bl] = 0u;
+#pragma unroll
+        for (int g32 = 0; g32 < (4 * BT) / 32; ++g32) {
+          uint32_t r[32];
+          tmem_ld32(tmem_base + lane_addr + a * 256u + 32u * g32, r);
+          tmem_wait_ld();
+#pragma unroll
+          for (int q = 0; q < 32; ++q) {
+            const int col = 32 * g32 + q, c = col / BT, bl = col % BT;
+            // the exact sum of byte products (< 2^26) after undoing the centring
+            const uint32_t v = cvt_rn(r[q]) + corr_row + 128u * __ldg(cs + col);
+            res[bl] = mod_p((uint64_t)res[bl] + (uint64_t)v * p8[c], p, mu);
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&acc_empty[a]);
+        ++acc_cnt;
+        constexpr int PITCH = BT + 1;  // odd: conflict-free
+#pragma unroll
+        for (int bl = 0; bl < BT; ++bl) stg[(e * 32 + lane) * PITCH + bl] = res[bl];
+        asm volatile("bar.sync 1, 128;" ::: "memory");
+        const uint32_t tid = e * 32 + lane;
+        for (uint32_t idx = tid; idx < 32u * BT; idx += 128) {
+          const uint32_t t = idx / BT, bl = idx % BT;
+          uint64_t x = 0;
+#pragma unroll
+          for (int pl = 0; pl < 4; ++pl) x += (uint64_t)stg[(pl * 32 + t) * PITCH + bl] * p8[pl];
+          const uint32_t rp = g * 32 + t, b = nt * BT + bl;
+          if (rp < args.d1p && b < args.Bvalid)
+            args.out[((uint64_t)b * args.d1p + rp) * ZP_RNS_K + k] = mod_p(x, p, mu);
+        }
+        asm volatile("bar.sync 1, 128;" ::: "memory");
+      } else if constexpr (MODE == MODE_CMP) {
         // single chunk (n <= 1024): byte-column sums -> 67-word integer
         const uint32_t a = acc_cnt & 1u, ra = acc_cnt >> 1;
         // the four epilogue warps agree on the verdict before their named barriers
@@ -631,7 +702,7 @@ __global__ void k_prep_cko(const uint32_t* __restrict__ cko, uint32_t n, uint32_
   if (s) atomicAdd(&colsum[(uint64_t)b * 256 + beta], s);
 }
 
-bool g_attr[3][3] = {{false}};
+bool g_attr[4][3] = {{false}};
 
 template <int MODE, int BT>
 int launch_gemm(zp_ctx* ctx, const CUtensorMap& tmA, const CUtensorMap& tmB, const GemmArgs& ga,
@@ -748,4 +819,111 @@ int zp_launch_vmul_tc(zp_db* db, const uint32_t* dCKO, uint32_t B, uint32_t* V4,
   ga.Rp = db->Rp;
   ga.status = ctx->d_status;
   return launch_gemm<MODE_CMP, 64>(ctx, db->tmap_hpl, tmB, ga, st, max_ctas);
+}
+
+// ---------------------------------------------------------------------------------
+// RNS compression products (Sec. 5.2): X[b][r'][k] = H'[r', :] . cko[b] mod p_k for the
+// ZP_RNS_K primes, as one grouped tensor-core product: for prime k, the byte planes of
+// H' mod p_k (A, built by zp_launch_rns_planes) times the byte planes of cko mod p_k (B).
+namespace {
+
+constexpr int RG = 16;  // primes per pass of the residue loop
+
+// B operand: row (k nnt + nt) 4 BT + c BT + bl = byte c of (cko[b][i] mod p_k), b = nt BT + bl,
+// centred fp16, columns i < Kp (zero bytes past n and for b >= B); colsum[row] = byte sum.
+// grid (Kp / 128, nnt BT), one thread per column.
+__global__ void __launch_bounds__(128) k_prep_cko_rns(const uint32_t* __restrict__ cko, uint32_t B,
+                                                      uint32_t n, uint32_t Kp, uint32_t BT,
+                                                      uint32_t nnt, const zp_rns_dev* __restrict__ rns,
+                                                      __half* __restrict__ Bc,
+                                                      uint32_t* __restrict__ colsum) {
+  __shared__ uint32_t sw[ZP_RNS_K][ZP_MAX_L + 1];
+  for (uint32_t x = threadIdx.x; x < ZP_RNS_K * ZP_MAX_L; x += blockDim.x)
+    sw[x / ZP_MAX_L][x % ZP_MAX_L] = rns->w32[x / ZP_MAX_L][x % ZP_MAX_L];
+  __syncthreads();
+  const uint32_t i = blockIdx.x * 128 + threadIdx.x;  // < Kp (Kp is a multiple of 128)
+  const uint32_t b = blockIdx.y;
+  const uint32_t nt = b / BT, bl = b % BT, N = 4 * BT;
+  const uint32_t lane = threadIdx.x & 31;
+  uint32_t w[ZP_MAX_L];
+  const bool live = i < n && b < B;
+#pragma unroll
+  for (int x = 0; x < ZP_MAX_L; ++x) w[x] = live ? __ldg(cko + ((uint64_t)b * n + i) * ZP_MAX_L + x) : 0u;
+  for (uint32_t k0 = 0; k0 < ZP_RNS_K; k0 += RG) {
+    uint64_t acc[RG];
+#pragma unroll
+    for (int kk = 0; kk < RG; ++kk) acc[kk] = 0;
+#pragma unroll
+    for (int x = 0; x < ZP_MAX_L; ++x) {
+#pragma unroll
+      for (int kk = 0; kk < RG; ++kk)
+        if (k0 + kk < ZP_RNS_K) acc[kk] += (uint64_t)w[x] * sw[k0 + kk][x];  // < 2^59
+      if ((x & 15) == 15) {
+#pragma unroll
+        for (int kk = 0; kk < RG; ++kk)
+          if (k0 + kk < ZP_RNS_K) acc[kk] = mod_p(acc[kk], rns->p[k0 + kk], rns->mu[k0 + kk]);
+      }
+    }
+#pragma unroll
+    for (int kk = 0; kk < RG; ++kk) {
+      const uint32_t k = k0 + kk;
+      if (k >= ZP_RNS_K) break;
+      const uint32_t v = mod_p(acc[kk], rns->p[k], rns->mu[k]);
+      const uint64_t row0 = ((uint64_t)k * nnt + nt) * N + bl;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const uint32_t byte = (v >> (8 * c)) & 0xFFu;
+        Bc[(row0 + (uint64_t)c * BT) * Kp + i] = __int2half_rn((int)byte - 128);
+        uint32_t s = byte;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0 && s) atomicAdd(&colsum[row0 + (uint64_t)c * BT], s);
+      }
+    }
+  }
+}
+
+}  // namespace
+
+int zp_launch_rns_products(zp_db* db, const uint32_t* dCKO, uint32_t B, uint32_t* X, cudaStream_t st) {
+  zp_ctx* ctx = db->ctx;
+  const uint32_t n = ctx->P.n;
+  const uint32_t Kp = (n + 127) / 128 * 128;
+  const uint32_t BT = pick_bt(B), N = 4 * BT, nnt = (B + BT - 1) / BT;
+  const uint64_t brows = (uint64_t)ZP_RNS_K * nnt * N;
+  const size_t bc_bytes = (size_t)brows * Kp * 2;
+  const size_t cs_bytes = (size_t)brows * 4;
+  int rc = zp_scratch_reserve(&db->s_cko, bc_bytes + cs_bytes + 256);
+  if (rc) return rc;
+  __half* Bc = static_cast<__half*>(db->s_cko.p);
+  uint32_t* colsum = reinterpret_cast<uint32_t*>(static_cast<uint8_t*>(db->s_cko.p) + bc_bytes);
+  ZP_CUDA(cudaMemsetAsync(colsum, 0, cs_bytes, st));
+  zp_clear_pending_error();
+  ctx->launches++;
+  k_prep_cko_rns<<<dim3(Kp / 128, nnt * BT), 128, 0, st>>>(dCKO, B, n, Kp, BT, nnt, ctx->d_rns, Bc,
+                                                          colsum);
+  ZP_CUDA(cudaGetLastError());
+  CUtensorMap tmB;
+  rc = zp_encode_tmap_2d(&tmB, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, Bc, Kp, brows, (uint64_t)Kp * 2, 64,
+                         N, CU_TENSOR_MAP_SWIZZLE_128B);
+  if (rc) return rc;
+  GemmArgs ga{};
+  ga.num_m_tiles = ZP_RNS_K * (db->Rq / 32);
+  ga.num_n_tiles = nnt;
+  ga.N = N;
+  ga.nkb = Kp / BK;
+  ga.Kp = Kp;
+  ga.Mvalid = db->d1p;
+  ga.Bvalid = B;
+  ga.rowsumA = db->d_rns_rowsum;
+  ga.colsum = colsum;
+  ga.out = X;
+  ga.out_ld = 0;
+  ga.status = ctx->d_status;
+  ga.mt_per_prime = db->Rq / 32;
+  ga.d1p = db->d1p;
+  ga.rns = ctx->d_rns;
+  if (BT == 16) return launch_gemm<MODE_RNS, 16>(ctx, db->tmap_rns, tmB, ga, st);
+  if (BT == 32) return launch_gemm<MODE_RNS, 32>(ctx, db->tmap_rns, tmB, ga, st);
+  return launch_gemm<MODE_RNS, 64>(ctx, db->tmap_rns, tmB, ga, st);
 }

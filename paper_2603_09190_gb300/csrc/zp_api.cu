@@ -1,6 +1,7 @@
 // zp_api.cu -- host side of the C ABI declared in include/zippir.h: argument
 // validation, handle lifetime, per-client constants, scratch management and the
 // dispatch to the kernels of the online Response (Algorithm "ZipPIR").
+#include <algorithm>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -119,6 +120,126 @@ static uint32_t big_bits(const std::vector<uint32_t>& a) {
   return 0;
 }
 
+// schoolbook product of little-endian word vectors
+static std::vector<uint32_t> big_mul(const std::vector<uint32_t>& a, const std::vector<uint32_t>& b) {
+  std::vector<uint32_t> r(a.size() + b.size(), 0);
+  for (size_t i = 0; i < a.size(); ++i) {
+    uint64_t carry = 0;
+    for (size_t j = 0; j < b.size(); ++j) {
+      const uint64_t t = (uint64_t)a[i] * b[j] + r[i + j] + carry;
+      r[i + j] = (uint32_t)t;
+      carry = t >> 32;
+    }
+    r[i + b.size()] = (uint32_t)carry;
+  }
+  return r;
+}
+
+// x mod m for x < b^(2L) by Barrett's reduction (HAC Alg. 14.42) with mu = floor(b^(2L) / m),
+// b = 2^32 (the host twin of the reduction in k_compress.cu)
+static std::vector<uint32_t> big_barrett(std::vector<uint32_t> x, const std::vector<uint32_t>& m,
+                                         const std::vector<uint32_t>& mu) {
+  const size_t L = m.size();
+  x.resize(2 * L, 0);
+  std::vector<uint32_t> q1(x.begin() + (L - 1), x.end());               // L+1 words
+  std::vector<uint32_t> q2 = big_mul(q1, mu);
+  std::vector<uint32_t> q3(q2.begin() + (L + 1), q2.begin() + (2 * L + 2));
+  std::vector<uint32_t> r2 = big_mul(q3, m);
+  std::vector<uint32_t> r(L + 1);
+  uint64_t br = 0;
+  for (size_t w = 0; w <= L; ++w) {  // r = x - q3 m mod b^(L+1)
+    const uint64_t t = (uint64_t)x[w] - r2[w] - br;
+    r[w] = (uint32_t)t;
+    br = (t >> 63) & 1u;
+  }
+  for (;;) {  // at most twice
+    bool ge = r[L] != 0;
+    if (!ge) {
+      ge = true;
+      for (size_t w = L; w-- > 0;)
+        if (r[w] != m[w]) {
+          ge = r[w] > m[w];
+          break;
+        }
+    }
+    if (!ge) break;
+    br = 0;
+    for (size_t w = 0; w <= L; ++w) {
+      const uint64_t t = (uint64_t)r[w] - (w < L ? m[w] : 0u) - br;
+      r[w] = (uint32_t)t;
+      br = (t >> 63) & 1u;
+    }
+  }
+  r.resize(L);
+  return r;
+}
+
+static uint64_t pow_mod_u64(uint64_t a, uint64_t e, uint64_t p) {
+  uint64_t r = 1;
+  a %= p;
+  while (e) {
+    if (e & 1) r = (uint64_t)((unsigned __int128)r * a % p);
+    a = (uint64_t)((unsigned __int128)a * a % p);
+    e >>= 1;
+  }
+  return r;
+}
+
+static bool is_prime_u32(uint32_t x) {  // deterministic Miller-Rabin for 32-bit integers
+  if (x < 2) return false;
+  for (uint32_t q : {2u, 3u, 5u, 7u, 11u, 13u})
+    if (x % q == 0) return x == q;
+  uint32_t d = x - 1, sh = 0;
+  while (!(d & 1)) {
+    d >>= 1;
+    ++sh;
+  }
+  for (uint32_t a : {2u, 7u, 61u}) {
+    uint64_t y = pow_mod_u64(a, d, x);
+    if (y == 1 || y == x - 1) continue;
+    bool comp = true;
+    for (uint32_t i = 1; i < sh && comp; ++i) {
+      y = y * y % x;
+      if (y == x - 1) comp = false;
+    }
+    if (comp) return false;
+  }
+  return true;
+}
+
+// RNS constants of a context: the ZP_RNS_K largest primes below 2^27 and the tables of
+// zp_rns_dev (host copy).
+static void rns_setup(zp_ctx* c, zp_rns_dev& h) {
+  std::vector<uint32_t>& P = c->rns_p;
+  P.clear();
+  for (uint32_t x = (1u << 27) - 1; P.size() < ZP_RNS_K; x -= 2)
+    if (is_prime_u32(x)) P.push_back(x);
+  memset(&h, 0, sizeof(h));
+  for (int k = 0; k < ZP_RNS_K; ++k) {
+    const uint64_t p = P[k];
+    h.p[k] = (uint32_t)p;
+    uint64_t mk = 1;  // M / p mod p
+    for (int j = 0; j < ZP_RNS_K; ++j)
+      if (j != k) mk = mk * (P[j] % p) % p;
+    h.inv[k] = (uint32_t)pow_mod_u64(mk, p - 2, p);
+    h.mu[k] = ~0ull / p;
+    h.dinv[k] = 1.0 / (double)p;
+    uint64_t w = 1;
+    for (int i = 0; i < ZP_MAX_L; ++i) {
+      h.w32[k][i] = (uint32_t)w;
+      w = (w << 32) % p;
+    }
+    const uint64_t g = ((uint64_t)c->gamma_w[0] + ((uint64_t)c->gamma_w[1] << 32) % p +
+                        (uint64_t)((((unsigned __int128)c->gamma_w[2]) << 64) % p)) % p;
+    uint64_t gj = 1;
+    for (int j = 0; j < 64; ++j) {
+      h.gj[k][j] = (uint32_t)gj;
+      gj = gj * g % p;
+    }
+    for (int a = 0; a < 4; ++a) h.pow8[k][a] = (uint32_t)((1ull << (8 * a)) % p);
+  }
+}
+
 // ------------------------------------------------------------------ context
 extern "C" int zp_version(void) { return ZP_VERSION_NUM; }
 
@@ -183,6 +304,21 @@ extern "C" int zp_init(int device, const zp_params* P, zp_ctx** out) {
     c->launches = 0;
     c->answer_path = ZP_PATH_AUTO;
     c->compress_path = ZP_PATH_AUTO;
+    c->rns_min_batch = 16;  // from 16 queries on, the RNS compression reads less and multiplies less
+    {
+      zp_rns_dev h;
+      rns_setup(c, h);
+      if (cudaMalloc(&c->d_rns, sizeof(zp_rns_dev)) != cudaSuccess) {
+        c->d_rns = nullptr;
+        delete c;
+        return zp_set_error(ZP_ENOMEM, "cudaMalloc(RNS constants)");
+      }
+      if (cudaMemcpy(c->d_rns, &h, sizeof(h), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaFree(c->d_rns);
+        delete c;
+        return zp_set_error(ZP_ECUDA, "copy of the RNS constants");
+      }
+    }
     // default SM split of zp_respond for one query: about 3/8 of the SMs run the
     // compression products beside the GEMV (56 of 152 on GB300)
     c->overlap_sms = c->num_sms >= 64 ? (uint32_t)(c->num_sms * 3 + 4) / 8 : 0u;
@@ -205,6 +341,7 @@ extern "C" int zp_ctx_destroy(zp_ctx* c) {
   if (!c) return ZP_OK;
   cudaSetDevice(c->device);
   if (c->d_status) cudaFree(c->d_status);
+  if (c->d_rns) cudaFree(c->d_rns);
   delete c;
   return ZP_OK;
 }
@@ -213,7 +350,7 @@ extern "C" int zp_set_option(zp_ctx* c, const char* name, int64_t value) {
   if (!c || !name) return zp_set_error(ZP_EINVAL, "zp_set_option: null argument");
   const std::string k(name);
   if (k == "answer_path" || k == "compress_path") {
-    if (value < ZP_PATH_AUTO || value > ZP_PATH_TC)
+    if (value < ZP_PATH_AUTO || value > (k == "compress_path" ? ZP_PATH_RNS : ZP_PATH_TC))
       return zp_set_error(ZP_EINVAL, "zp_set_option: %s=%lld out of range", name, (long long)value);
     (k == "answer_path" ? c->answer_path : c->compress_path) = (int)value;
     return ZP_OK;
@@ -225,6 +362,12 @@ extern "C" int zp_set_option(zp_ctx* c, const char* name, int64_t value) {
     c->overlap_sms = (uint32_t)value;
     return ZP_OK;
   }
+  if (k == "rns_min_batch") {
+    if (value < 0 || value > 4096)
+      return zp_set_error(ZP_EINVAL, "zp_set_option: rns_min_batch=%lld out of [0, 4096]", (long long)value);
+    c->rns_min_batch = (uint32_t)value;
+    return ZP_OK;
+  }
   return zp_set_error(ZP_EINVAL, "zp_set_option: unknown option '%s'", name);
 }
 
@@ -234,6 +377,7 @@ extern "C" int zp_get_option(const zp_ctx* c, const char* name, int64_t* value) 
   if (k == "answer_path") *value = c->answer_path;
   else if (k == "compress_path") *value = c->compress_path;
   else if (k == "overlap_sms") *value = c->overlap_sms;
+  else if (k == "rns_min_batch") *value = c->rns_min_batch;
   else return zp_set_error(ZP_EINVAL, "zp_get_option: unknown option '%s'", name);
   return ZP_OK;
 }
@@ -342,6 +486,8 @@ extern "C" int zp_db_destroy(zp_db* db) {
   if (db->d_hneg) cudaFree(db->d_hneg);
   if (db->d_hpl) cudaFree(db->d_hpl);
   if (db->d_hpl_rowsum) cudaFree(db->d_hpl_rowsum);
+  if (db->d_rns_hpl) cudaFree(db->d_rns_hpl);
+  if (db->d_rns_rowsum) cudaFree(db->d_rns_rowsum);
   if (db->side) {
     cudaStreamDestroy(db->side);
     cudaEventDestroy(db->ev_fork);
@@ -349,7 +495,7 @@ extern "C" int zp_db_destroy(zp_db* db) {
   }
   zp_scratch* all[] = {&db->s_qplanes, &db->s_v,   &db->s_q,   &db->s_cko,  &db->s_ans,
                        &db->s_t,       &db->s_clients, &db->s_misc, &db->s_tcq, &db->s_hq,
-                       &db->s_hcko, &db->s_ptab, &db->s_krows, &db->s_m2consts};
+                       &db->s_hcko, &db->s_ptab, &db->s_krows, &db->s_m2consts, &db->s_prows};
   for (zp_scratch* s : all) scratch_free(s);
   delete db;
   return ZP_OK;
@@ -366,6 +512,30 @@ static int stage_rows(zp_db* db, const uint32_t* hRows, uint32_t k, size_t extra
   *dRows = static_cast<uint32_t*>(db->s_misc.p);
   ZP_CUDA(cudaMemcpyAsync(*dRows, hRows, (size_t)k * 4, cudaMemcpyHostToDevice, st));
   return ZP_OK;
+}
+
+int zp_ensure_rns(zp_db* db, cudaStream_t st) {
+  if (db->d_rns_hpl) return ZP_OK;
+  const uint32_t n = db->ctx->P.n;
+  db->Rq = (db->d1p + 31) / 32 * 32;
+  const uint64_t rows = (uint64_t)ZP_RNS_K * 4 * db->Rq;
+  const size_t bytes = (size_t)rows * db->hpl_ld;
+  if (cudaMalloc(&db->d_rns_hpl, bytes) != cudaSuccess) {
+    db->d_rns_hpl = nullptr;
+    return zp_set_error(ZP_ENOMEM, "RNS planes of the hint: cudaMalloc(%zu bytes)", bytes);
+  }
+  if (cudaMalloc(&db->d_rns_rowsum, (size_t)rows * 4) != cudaSuccess) {
+    cudaFree(db->d_rns_hpl);
+    db->d_rns_hpl = nullptr;
+    db->d_rns_rowsum = nullptr;
+    return zp_set_error(ZP_ENOMEM, "RNS planes of the hint: cudaMalloc(row sums)");
+  }
+  ZP_CUDA(cudaMemsetAsync(db->d_rns_hpl, 0, bytes, st));
+  ZP_CUDA(cudaMemsetAsync(db->d_rns_rowsum, 0, (size_t)rows * 4, st));
+  int rc = zp_encode_tmap_2d(&db->tmap_rns, CU_TENSOR_MAP_DATA_TYPE_UINT8, db->d_rns_hpl, n, rows,
+                             db->hpl_ld, 128, 128, CU_TENSOR_MAP_SWIZZLE_128B);
+  if (rc) return rc;
+  return zp_launch_rns_planes(db, nullptr, db->d1p, st);
 }
 
 static int alloc_hint_state(zp_db* db) {
@@ -423,6 +593,7 @@ extern "C" int zp_gen_hint(zp_db* db, const uint32_t* dA, uint32_t* dH, const ui
               : zp_launch_answer_simt(db, dA, n, 0, outp, 1, n, db->dD, db->R, db->ld, st);
       if (!rc) rc = zp_launch_hint_post(db, outp, nullptr, db->R, dH, st);
       if (!rc) rc = zp_launch_hint_planes_rowsum(db, nullptr, 0, st);
+      if (!rc && db->d_rns_hpl) rc = zp_launch_rns_planes(db, nullptr, db->d1p, st);
       if (rc) return rc;
       db->hint_ready = true;
       stale.assign(db->R, 0);
@@ -455,6 +626,19 @@ extern "C" int zp_gen_hint(zp_db* db, const uint32_t* dA, uint32_t* dH, const ui
     }
     if (!rc) rc = zp_launch_hint_post(db, dHc, dRows, nrows, dH, st);
     if (!rc) rc = zp_launch_hint_planes_rowsum(db, dRows, nrows, st);
+    if (!rc && db->d_rns_hpl) {  // keep the RNS planes of H' in step: their packed rows
+      std::vector<uint32_t> pr(hRows, hRows + nrows);
+      for (uint32_t& r : pr) r /= c->ell;
+      std::sort(pr.begin(), pr.end());
+      pr.erase(std::unique(pr.begin(), pr.end()), pr.end());
+      rc = zp_scratch_reserve(&db->s_prows, pr.size() * 4);
+      if (!rc) {
+        // pageable source: the copy is staged before cudaMemcpyAsync returns
+        cudaError_t e = cudaMemcpyAsync(db->s_prows.p, pr.data(), pr.size() * 4, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return zp_cuda_check(e, "cudaMemcpyAsync(packed rows)");
+        rc = zp_launch_rns_planes(db, static_cast<const uint32_t*>(db->s_prows.p), (uint32_t)pr.size(), st);
+      }
+    }
     if (rc) return rc;
     for (uint32_t j = 0; j < nrows; ++j) {
       if (stale[hRows[j]]) {
@@ -602,20 +786,42 @@ extern "C" int zp_register_client(zp_ctx* c, const uint32_t* hM, uint32_t L, zp_
       return r;
     };
     const std::vector<uint32_t> r1 = pow2_mod(32 * L2), r2 = pow2_mod(64 * L2);
+    // CRT constants of the RNS compression: M/p_k mod m from prefix and suffix products of
+    // the primes (Barrett reductions with mu), then m - (M mod m)
+    std::vector<uint32_t> mkm((size_t)(ZP_RNS_K + 1) * L, 0);
+    {
+      const std::vector<uint32_t>& P = c->rns_p;
+      std::vector<std::vector<uint32_t>> pre(ZP_RNS_K + 1), suf(ZP_RNS_K + 1);
+      pre[0].assign(L, 0);
+      pre[0][0] = 1;
+      suf[ZP_RNS_K] = pre[0];
+      for (int k = 0; k < ZP_RNS_K; ++k) pre[k + 1] = big_barrett(big_mul(pre[k], {P[k]}), m, mu);
+      for (int k = ZP_RNS_K - 1; k >= 0; --k) suf[k] = big_barrett(big_mul(suf[k + 1], {P[k]}), m, mu);
+      for (int k = 0; k < ZP_RNS_K; ++k) {
+        const std::vector<uint32_t> v = big_barrett(big_mul(pre[k], suf[k + 1]), m, mu);
+        std::copy(v.begin(), v.end(), mkm.begin() + (size_t)k * L);
+      }
+      uint64_t br = 0;  // m - (M mod m), M mod m = pre[K] (nonzero: m has no 27-bit factor)
+      for (uint32_t w = 0; w < L; ++w) {
+        const uint64_t t = (uint64_t)m[w] - pre[ZP_RNS_K][w] - br;
+        mkm[(size_t)ZP_RNS_K * L + w] = (uint32_t)t;
+        br = (t >> 63) & 1u;
+      }
+    }
     ZP_CUDA(cudaSetDevice(c->device));
     zp_client* cl = new zp_client();
     cl->ctx = c;
     cl->device = c->device;
     cl->L = L;
-    cl->d_m = cl->d_mu = cl->d_m2 = cl->d_r1 = cl->d_r2 = nullptr;
+    cl->d_m = cl->d_mu = cl->d_m2 = cl->d_r1 = cl->d_r2 = cl->d_mkm = nullptr;
     cl->m2inv = m2inv;
     auto free_all = [cl]() {
-      for (uint32_t* p : {cl->d_m, cl->d_mu, cl->d_m2, cl->d_r1, cl->d_r2})
+      for (uint32_t* p : {cl->d_m, cl->d_mu, cl->d_m2, cl->d_r1, cl->d_r2, cl->d_mkm})
         if (p) cudaFree(p);
     };
     if (cudaMalloc(&cl->d_m, L * 4) != cudaSuccess || cudaMalloc(&cl->d_mu, (L + 1) * 4) != cudaSuccess ||
         cudaMalloc(&cl->d_m2, L2 * 4) != cudaSuccess || cudaMalloc(&cl->d_r1, L2 * 4) != cudaSuccess ||
-        cudaMalloc(&cl->d_r2, L2 * 4) != cudaSuccess) {
+        cudaMalloc(&cl->d_r2, L2 * 4) != cudaSuccess || cudaMalloc(&cl->d_mkm, mkm.size() * 4) != cudaSuccess) {
       free_all();
       delete cl;
       return zp_set_error(ZP_ENOMEM, "zp_register_client: cudaMalloc");
@@ -625,6 +831,7 @@ extern "C" int zp_register_client(zp_ctx* c, const uint32_t* hM, uint32_t L, zp_
     if (e == cudaSuccess) e = cudaMemcpy(cl->d_m2, m2.data(), L2 * 4, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(cl->d_r1, r1.data(), L2 * 4, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(cl->d_r2, r2.data(), L2 * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(cl->d_mkm, mkm.data(), mkm.size() * 4, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
       free_all();
       delete cl;
@@ -641,7 +848,7 @@ extern "C" int zp_client_destroy(zp_client* cl) {
   if (!cl) return ZP_OK;
   cudaSetDevice(cl->device);
   cudaDeviceSynchronize();
-  for (uint32_t* p : {cl->d_m, cl->d_mu, cl->d_m2, cl->d_r1, cl->d_r2})
+  for (uint32_t* p : {cl->d_m, cl->d_mu, cl->d_m2, cl->d_r1, cl->d_r2, cl->d_mkm})
     if (p) cudaFree(p);
   delete cl;
   return ZP_OK;

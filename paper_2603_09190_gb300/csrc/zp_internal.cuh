@@ -26,6 +26,20 @@
 #define ZP_PATH_AUTO 0
 #define ZP_PATH_SIMT 1
 #define ZP_PATH_TC 2
+#define ZP_PATH_RNS 3  // compression only: residue number system on the tensor cores
+
+// Residue number system of the batched compression: ZP_RNS_K primes just below 2^27 whose
+// product (4131 bits) exceeds every H'.ck_o (< n 2^4095 <= 2^4105) by a margin of 2^26.
+#define ZP_RNS_K 153
+struct zp_rns_dev {             // device copy, one per context
+  uint32_t p[ZP_RNS_K];         // the primes
+  uint32_t inv[ZP_RNS_K];       // (M / p)^{-1} mod p, M = prod p
+  uint64_t mu[ZP_RNS_K];        // floor((2^64 - 1) / p) (Barrett reduction of 64-bit values)
+  double dinv[ZP_RNS_K];        // 1 / p
+  uint32_t w32[ZP_RNS_K][ZP_MAX_L];  // 2^(32 w) mod p
+  uint32_t gj[ZP_RNS_K][64];    // gamma^j mod p, j < ell
+  uint32_t pow8[ZP_RNS_K][4];   // 2^(8 a) mod p
+};
 
 struct zp_ctx {
   int device;
@@ -37,6 +51,9 @@ struct zp_ctx {
   uint32_t ell;        // slots per packed row
   uint32_t L;          // limbs per element of Z_m
   uint32_t gamma_w[3]; // packing scale gamma, little-endian 32-bit words (gamma < 2^96)
+  uint32_t rns_min_batch;  // batches of at least this many queries compress in RNS (0: never)
+  zp_rns_dev* d_rns;   // RNS constants (device)
+  std::vector<uint32_t> rns_p;  // the primes (host)
   int num_sms;
   uint32_t* d_status;  // device status word (ZP_DEV_* flags)
   uint64_t launches;   // kernels launched by this context
@@ -53,6 +70,8 @@ struct zp_client {
   uint32_t* d_r1;  // 2L limbs: R mod m^2
   uint32_t* d_r2;  // 2L limbs: R^2 mod m^2
   uint32_t m2inv;  // -(m^2)^{-1} mod 2^32
+  // CRT of the RNS compression: M_k mod m (ZP_RNS_K x L limbs), then m - (M mod m) (L limbs)
+  uint32_t* d_mkm;
 };
 
 struct zp_scratch {
@@ -82,12 +101,20 @@ struct zp_db {
   uint32_t stale;          // rows updated since the last hint generation
   std::vector<uint8_t> stale_v;  // per-row stale flags (host)
   uint32_t v_batch;        // queries whose products are in s_v (0: none)
+  bool v_rns;              // s_v holds RNS residues (else exact row products V)
+  // H' modulo the RNS primes as byte planes (lazily built for the first RNS batch):
+  // row k 4 Rq + 128 g + 32 a + t = byte a of H'[32 g + t, :] mod p_k, Rq = d1' rounded up to 32
+  uint8_t* d_rns_hpl;
+  uint32_t* d_rns_rowsum;  // byte sums of its rows
+  uint32_t Rq;
+  CUtensorMap tmap_rns;    // box 64 x 128
   std::vector<const uint32_t*> cl_cache;  // client constants last uploaded to s_clients
   cudaStream_t side;       // internal stream of zp_respond's overlap (lazily created)
   cudaEvent_t ev_fork, ev_join;
   // scratch, grown on demand (never shrunk before zp_db_destroy)
   zp_scratch s_qplanes, s_v, s_q, s_cko, s_ans, s_t, s_clients, s_misc, s_tcq, s_hq, s_hcko;
   zp_scratch s_ptab, s_krows, s_m2consts;  // per-client hint and combined response
+  zp_scratch s_prows;                      // packed rows whose RNS planes are rebuilt
 };
 
 // error reporting (thread-local message)
@@ -129,6 +156,13 @@ int zp_launch_client_hint(zp_db* db, const zp_client* cl, const uint32_t* dCkr, 
                           const uint32_t* dRows, uint32_t nprows, cudaStream_t st);
 int zp_launch_combine(zp_db* db, zp_client* const* clients, const uint32_t* dK, const uint32_t* dT,
                       uint32_t B, uint32_t* dOut, cudaStream_t st);
+// RNS compression (k_rns.cu, k_gemm_tc.cu): the residue planes of H' for the listed packed
+// rows (dRows device, NULL = all), the B operand of ck_o residues, and the residue product
+// X[b][r'][k] = H'[r', :] . cko[b] mod p_k
+int zp_launch_rns_planes(zp_db* db, const uint32_t* dRows, uint32_t nprows, cudaStream_t st);
+// allocates and builds the RNS planes of H' on first use (zp_api.cu)
+int zp_ensure_rns(zp_db* db, cudaStream_t st);
+int zp_launch_rns_products(zp_db* db, const uint32_t* dCKO, uint32_t B, uint32_t* X, cudaStream_t st);
 // B in 1..4 queries (dq: B x C, dans: B x R); max_ctas limits the single-query grid.
 int zp_launch_gemv(zp_db* db, const uint32_t* dq, uint32_t B, uint32_t* dans, cudaStream_t st,
                    uint32_t max_ctas);
