@@ -227,46 +227,37 @@ __global__ void __launch_bounds__(PACK_WARPS * 32)
     const uint32_t alpha = (uint32_t)floor(f + 0x1p-30);
     // sum_k y_k (M_k mod m) + alpha (m - M mod m) into words lane*4 .. lane*4+3 (< 64):
     // low halves to the word, high halves to the next (the top one to the next lane)
+    // The two half-warps take alternate k (the row after the ZP_RNS_K rows of M_k mod m is
+    // m - (M mod m), weighted by alpha); lane l of a half holds words 4 (l % 16) .. + 3.
     const uint32_t* mk = cl[b].mkm;
-    uint64_t hi3 = 0;
+    const uint32_t hl = lane & 15u, half = lane >> 4;
+    uint64_t cv[4] = {0, 0, 0, 0}, hi3 = 0;
+    for (uint32_t k = half; k <= ZP_RNS_K; k += 2) {
+      const uint32_t q = k >> 5;
+      uint32_t yq = y[0];
 #pragma unroll
-    for (int q = 0; q < QK; ++q) {
-      for (uint32_t kk = 0; kk < 32; ++kk) {
-        const uint32_t k = 32u * q + kk;
-        if (k >= ZP_RNS_K) break;
-        const uint32_t yk = __shfl_sync(0xffffffffu, y[q], kk);
-        if (lane < ZP_MAX_L / 4) {
-          const uint32_t* row = mk + (uint64_t)k * ZP_MAX_L + lane * 4;
-          uint64_t ph[4];
-#pragma unroll
-          for (int t = 0; t < 4; ++t) {
-            const uint64_t pr = (uint64_t)yk * __ldg(row + t);
-            xv[t] += (uint32_t)pr;
-            ph[t] = pr >> 32;
-          }
-          xv[1] += ph[0];
-          xv[2] += ph[1];
-          xv[3] += ph[2];
-          hi3 += ph[3];
-        }
-      }
+      for (int qq = 1; qq < QK; ++qq)
+        if (q == (uint32_t)qq) yq = y[qq];
+      const uint32_t ys = __shfl_sync(0xffffffffu, yq, k & 31);
+      const uint32_t yk = k < ZP_RNS_K ? ys : alpha;
+      const uint4 mw = __ldg(reinterpret_cast<const uint4*>(mk + (uint64_t)k * ZP_MAX_L + hl * 4));
+      const uint64_t p0 = (uint64_t)yk * mw.x, p1 = (uint64_t)yk * mw.y;
+      const uint64_t p2 = (uint64_t)yk * mw.z, p3 = (uint64_t)yk * mw.w;
+      cv[0] += (uint32_t)p0;
+      cv[1] += (uint32_t)p1 + (p0 >> 32);
+      cv[2] += (uint32_t)p2 + (p1 >> 32);
+      cv[3] += (uint32_t)p3 + (p2 >> 32);
+      hi3 += p3 >> 32;
     }
-    if (lane < ZP_MAX_L / 4) {  // alpha (m - (M mod m)), stored after the ZP_RNS_K rows
-      const uint32_t* row = mk + (uint64_t)ZP_RNS_K * ZP_MAX_L + lane * 4;
-      uint64_t ph[4];
 #pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        const uint64_t pr = (uint64_t)alpha * __ldg(row + t);
-        xv[t] += (uint32_t)pr;
-        ph[t] = pr >> 32;
-      }
-      xv[1] += ph[0];
-      xv[2] += ph[1];
-      xv[3] += ph[2];
-      hi3 += ph[3];
+    for (int t = 0; t < 4; ++t) cv[t] += __shfl_down_sync(0xffffffffu, cv[t], 16);
+    hi3 += __shfl_down_sync(0xffffffffu, hi3, 16);
+    if (lane < 16) {
+#pragma unroll
+      for (int t = 0; t < 4; ++t) xv[t] += cv[t];
     }
-    const uint64_t hin = __shfl_up_sync(0xffffffffu, hi3, 1);
-    if (lane > 0) xv[0] += hin;
+    const uint64_t hin = __shfl_up_sync(0xffffffffu, hi3, 1);  // into the next lane's word 0
+    if (lane >= 1 && lane <= 16) xv[0] += hin;
   }
   // final carry resolution, then X to shared memory
   {
@@ -281,11 +272,22 @@ __global__ void __launch_bounds__(PACK_WARPS * 32)
   //      r = (X mod b^(L+1)) - (q3 m mod b^(L+1)), then r -= m while r >= m.
   for (int x = lane; x < L + 1; x += 32) S.q1[x] = S.X[L - 1 + x];
   __syncwarp();
+  // significant words of an (L+1)-word integer in shared memory (q1 and q3 are short when X
+  // is far below b^(2L), as the RNS sums are: < 2^2083)
+  auto sig_words = [&](const uint32_t* a) {
+    int top = -1;
+    for (int x = lane; x < L + 1; x += 32)
+      if (a[x]) top = x;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) top = max(top, __shfl_xor_sync(0xffffffffu, top, o));
+    return top + 1 > 1 ? top + 1 : 1;
+  };
+  const int n1 = sig_words(S.q1);
   // Only the columns from L - 1 up are summed (Handbook of Applied Cryptography, Note
   // 14.44): the dropped lower part is below L b^L, so the quotient estimate below is at
   // most one short of floor(q1 mu / b^(L+1)), r stays below 4m, and the correction loop's
   // three subtractions still end with r < m.
-  warp_mul_cols(S.q1, L + 1, S.mu, L + 1, S.col, 2 * L + 1, L - 1);
+  warp_mul_cols(S.q1, n1, S.mu, L + 1, S.col, 2 * L + 1, L - 1);
   __syncwarp();
   {
     uint32_t w[5];  // words 0..159 of q1 * mu; q3 = words L+1 .. 2L+1
@@ -298,7 +300,7 @@ __global__ void __launch_bounds__(PACK_WARPS * 32)
     }
   }
   __syncwarp();
-  warp_mul_cols(S.q3, L + 1, S.m, L, S.col, L + 1);
+  warp_mul_cols(S.q3, sig_words(S.q3), S.m, L, S.col, L + 1);
   __syncwarp();
   uint32_t r[3], r2[3], mm[3];
   warp_cols_to_words<3>(S.col, L + 1, r2);
@@ -335,9 +337,10 @@ int zp_launch_compress_products(zp_db* db, const uint32_t* dCKO, uint32_t B, cud
     return zp_set_error(ZP_EUNSUPPORTED, "tensor-core compression needs n <= 1024");
   // large batches: residues of H'.cko modulo the RNS primes (the packed hint is read once
   // per batch and there are ell times fewer rows); otherwise exact per-row products V
-  const bool rns = n <= 1024 && (ctx->compress_path == ZP_PATH_RNS ||
-                                 (ctx->compress_path == ZP_PATH_AUTO && ctx->rns_min_batch &&
-                                  B >= ctx->rns_min_batch));
+  const bool rns = n <= 1024 && (reinterpret_cast<uintptr_t>(dCKO) & 15u) == 0 &&
+                   (ctx->compress_path == ZP_PATH_RNS ||
+                    (ctx->compress_path == ZP_PATH_AUTO && ctx->rns_min_batch &&
+                     B >= ctx->rns_min_batch));
   if (rns) {
     int rc = zp_ensure_rns(db, st);
     if (!rc) rc = zp_scratch_reserve(&db->s_v, (size_t)B * db->d1p * ZP_RNS_K * sizeof(uint32_t));

@@ -831,54 +831,63 @@ constexpr int RG = 16;  // primes per pass of the residue loop
 
 // B operand: row (k nnt + nt) 4 BT + c BT + bl = byte c of (cko[b][i] mod p_k), b = nt BT + bl,
 // centred fp16, columns i < Kp (zero bytes past n and for b >= B); colsum[row] = byte sum.
-// grid (Kp / 128, nnt BT), one thread per column.
+// grid (Kp / 128, nnt BT, ceil(ZP_RNS_K / RG)), one thread per (column, query, RG primes).
 __global__ void __launch_bounds__(128) k_prep_cko_rns(const uint32_t* __restrict__ cko, uint32_t B,
                                                       uint32_t n, uint32_t Kp, uint32_t BT,
                                                       uint32_t nnt, const zp_rns_dev* __restrict__ rns,
                                                       __half* __restrict__ Bc,
                                                       uint32_t* __restrict__ colsum) {
-  __shared__ uint32_t sw[ZP_RNS_K][ZP_MAX_L + 1];
-  for (uint32_t x = threadIdx.x; x < ZP_RNS_K * ZP_MAX_L; x += blockDim.x)
-    sw[x / ZP_MAX_L][x % ZP_MAX_L] = rns->w32[x / ZP_MAX_L][x % ZP_MAX_L];
+  __shared__ uint32_t sw[RG][ZP_MAX_L];
+  __shared__ uint32_t sp[RG];
+  __shared__ uint64_t smu[RG];
+  const uint32_t k0 = blockIdx.z * RG;
+  for (uint32_t x = threadIdx.x; x < RG * ZP_MAX_L; x += blockDim.x) {
+    const uint32_t kk = x / ZP_MAX_L, w = x % ZP_MAX_L;
+    sw[kk][w] = k0 + kk < ZP_RNS_K ? rns->w32[k0 + kk][w] : 0u;
+  }
+  for (uint32_t kk = threadIdx.x; kk < (uint32_t)RG; kk += blockDim.x) {
+    sp[kk] = k0 + kk < ZP_RNS_K ? rns->p[k0 + kk] : 1u;
+    smu[kk] = k0 + kk < ZP_RNS_K ? rns->mu[k0 + kk] : 0ull;
+  }
   __syncthreads();
   const uint32_t i = blockIdx.x * 128 + threadIdx.x;  // < Kp (Kp is a multiple of 128)
   const uint32_t b = blockIdx.y;
   const uint32_t nt = b / BT, bl = b % BT, N = 4 * BT;
   const uint32_t lane = threadIdx.x & 31;
-  uint32_t w[ZP_MAX_L];
   const bool live = i < n && b < B;
+  const uint32_t* src = cko + ((uint64_t)b * n + i) * ZP_MAX_L;
+  uint64_t acc[RG];
 #pragma unroll
-  for (int x = 0; x < ZP_MAX_L; ++x) w[x] = live ? __ldg(cko + ((uint64_t)b * n + i) * ZP_MAX_L + x) : 0u;
-  for (uint32_t k0 = 0; k0 < ZP_RNS_K; k0 += RG) {
-    uint64_t acc[RG];
+  for (int kk = 0; kk < RG; ++kk) acc[kk] = 0;
 #pragma unroll
-    for (int kk = 0; kk < RG; ++kk) acc[kk] = 0;
+  for (int x4 = 0; x4 < ZP_MAX_L / 4; ++x4) {
+    const uint4 v = live ? __ldg(reinterpret_cast<const uint4*>(src) + x4) : make_uint4(0, 0, 0, 0);
+    const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-    for (int x = 0; x < ZP_MAX_L; ++x) {
+    for (int u = 0; u < 4; ++u) {
+      const int x = 4 * x4 + u;
 #pragma unroll
-      for (int kk = 0; kk < RG; ++kk)
-        if (k0 + kk < ZP_RNS_K) acc[kk] += (uint64_t)w[x] * sw[k0 + kk][x];  // < 2^59
+      for (int kk = 0; kk < RG; ++kk) acc[kk] += (uint64_t)wv[u] * sw[kk][x];  // < 2^59
       if ((x & 15) == 15) {
 #pragma unroll
-        for (int kk = 0; kk < RG; ++kk)
-          if (k0 + kk < ZP_RNS_K) acc[kk] = mod_p(acc[kk], rns->p[k0 + kk], rns->mu[k0 + kk]);
+        for (int kk = 0; kk < RG; ++kk) acc[kk] = mod_p(acc[kk], sp[kk], smu[kk]);
       }
     }
+  }
 #pragma unroll
-    for (int kk = 0; kk < RG; ++kk) {
-      const uint32_t k = k0 + kk;
-      if (k >= ZP_RNS_K) break;
-      const uint32_t v = mod_p(acc[kk], rns->p[k], rns->mu[k]);
-      const uint64_t row0 = ((uint64_t)k * nnt + nt) * N + bl;
+  for (int kk = 0; kk < RG; ++kk) {
+    const uint32_t k = k0 + kk;
+    if (k >= ZP_RNS_K) break;
+    const uint32_t v = mod_p(acc[kk], sp[kk], smu[kk]);
+    const uint64_t row0 = ((uint64_t)k * nnt + nt) * N + bl;
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const uint32_t byte = (v >> (8 * c)) & 0xFFu;
-        Bc[(row0 + (uint64_t)c * BT) * Kp + i] = __int2half_rn((int)byte - 128);
-        uint32_t s = byte;
+    for (int c = 0; c < 4; ++c) {
+      const uint32_t byte = (v >> (8 * c)) & 0xFFu;
+      Bc[(row0 + (uint64_t)c * BT) * Kp + i] = __int2half_rn((int)byte - 128);
+      uint32_t s = byte;
 #pragma unroll
-        for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0 && s) atomicAdd(&colsum[row0 + (uint64_t)c * BT], s);
-      }
+      for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0 && s) atomicAdd(&colsum[row0 + (uint64_t)c * BT], s);
     }
   }
 }
@@ -900,8 +909,8 @@ int zp_launch_rns_products(zp_db* db, const uint32_t* dCKO, uint32_t B, uint32_t
   ZP_CUDA(cudaMemsetAsync(colsum, 0, cs_bytes, st));
   zp_clear_pending_error();
   ctx->launches++;
-  k_prep_cko_rns<<<dim3(Kp / 128, nnt * BT), 128, 0, st>>>(dCKO, B, n, Kp, BT, nnt, ctx->d_rns, Bc,
-                                                          colsum);
+  k_prep_cko_rns<<<dim3(Kp / 128, nnt * BT, (ZP_RNS_K + RG - 1) / RG), 128, 0, st>>>(
+      dCKO, B, n, Kp, BT, nnt, ctx->d_rns, Bc, colsum);
   ZP_CUDA(cudaGetLastError());
   CUtensorMap tmB;
   rc = zp_encode_tmap_2d(&tmB, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, Bc, Kp, brows, (uint64_t)Kp * 2, 64,
