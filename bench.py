@@ -507,13 +507,83 @@ def run_serve(args, world, rank, local):
     return 0
 
 
+def run_client_hint(args, world, rank, local):
+    """Offline per-client hint k = PaillierMatMul(H', ck_r) for one client over a 1 GiB
+    database (n = 1024), and the online combined response k (+) t for 1 and 64 queries."""
+    import torch
+    import paper_2603_09190_gb300 as zp
+    from paper_2603_09190_gb300 import build as zb
+    import synth
+
+    if rank == 0:
+        zb.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    R = C = 32768
+    n = 1024
+    ctx = zp.Context(local, n=n, key_bits=KEY_BITS)
+    ld = zp.db_pitch(C)
+    D = synth.device_database(R, C, 1, dev, ld=ld)
+    A = synth.device_uniform_u32((C, n), 2, dev)
+    db = zp.Database(ctx, D, R, C, ld)
+    db.gen_hint(A)
+    del A
+    m = synth.random_odd_modulus(KEY_BITS, 3)
+    cl = ctx.register_client(m)
+    g = synth.rng(9)
+    m2 = m * m
+    ckr = [int.from_bytes(g.bytes(2 * KEY_BITS // 8 + 16), "little") % m2 for _ in range(n)]
+    CKR = torch.from_numpy(synth.ints_to_limbs(ckr, 2 * L).view(np.int32)).to(dev)
+    K = torch.zeros((db.d1p, 2 * L), dtype=torch.int32, device=dev)
+    db.client_hint(cl, CKR, out=K, packed_rows=[0])          # warm-up: one packed row
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches0 = ctx.kernel_launches()
+    e0.record()
+    db.client_hint(cl, CKR, out=K)
+    e1.record()
+    torch.cuda.synchronize()
+    k_ms = e0.elapsed_time(e1)
+    comb = {}
+    for B in (1, 64):
+        T = synth.device_uniform_u32((B, db.d1p, L), 7, dev)
+        KB = K[None].expand(B, -1, -1).contiguous()
+        cls = [cl] * B
+        for _ in range(max(args.warmup, 3)):
+            db.combine(cls, KB, T)
+        torch.cuda.synchronize()
+        steps = max(args.steps // 100, 10)
+        e0.record()
+        for _ in range(steps):
+            db.combine(cls, KB, T)
+        e1.record()
+        torch.cuda.synchronize()
+        comb[B] = e0.elapsed_time(e1) / steps
+    status = ctx.device_status()
+    if rank == 0:
+        line = {"metric": METRIC, "value": R * C / (k_ms * 1e-3) / 1e9, "unit": "GB/s",
+                "n_gpus": world, "steps": 1, "warmup": 1, "ms_per_step": k_ms,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+                "data": "synthetic",
+                "config": {"workload": "per-client hint k = PaillierMatMul(H', ck_r) over a 1 GiB "
+                                       "database 32768x32768, n=1024, 2048-bit modulus (offline; "
+                                       "value = database bytes covered per second)",
+                           "R": R, "C": C, "n": n, "d1p": db.d1p},
+                "client_hint_s": k_ms / 1e3,
+                "combine_ms": {"B1": comb[1], "B64": comb[64]},
+                "gpu_launches": ctx.kernel_launches() - launches0,
+                "device_status": status}
+        print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="1gib", choices=sorted(WORKLOADS) + ["serve"])
+    ap.add_argument("--workload", default="1gib", choices=sorted(WORKLOADS) + ["serve", "client_hint"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--serve-rates", type=float, nargs="*", default=[50, 200, 1000, 2000])
     ap.add_argument("--serve-seconds", type=float, default=10.0)
@@ -526,11 +596,13 @@ def main():
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
-        if args.workload == "serve":
+        if args.workload in ("serve", "client_hint"):
             args.workload = "1gib"
         return run_reference(args, world, rank)
     if args.workload == "serve":
         return run_serve(args, world, rank, local)
+    if args.workload == "client_hint":
+        return run_client_hint(args, world, rank, local)
     return run_ours(args, world, rank, local)
 
 

@@ -228,8 +228,16 @@ int zp_stale_rows(const zp_db* db, uint32_t* count);
  *                    tensor cores for larger batches and the hint), 1 CUDA-core dp4a
  *                    tiled kernels for every batch and the hint, 2 tensor cores also
  *                    for one to four queries;
- *   "compress_path": 0 auto (tensor cores when n <= 1024), 1 CUDA-core products,
- *                    2 tensor cores (ZP_EUNSUPPORTED at call time if n > 1024);
+ *   "compress_path": 0 auto (tensor cores when n <= 1024: byte planes of H for small
+ *                    batches, residues modulo 153 primes below 2^27 from "rns_min_batch"
+ *                    queries on), 1 CUDA-core products, 2 tensor-core byte planes, 3 RNS
+ *                    (2 and 3: ZP_EUNSUPPORTED at call time if n > 1024). The RNS path
+ *                    (Sec. 5.2: H'.ck_o modulo word-size primes, one reduction mod m at the
+ *                    end by the Chinese remainder theorem) builds H' modulo the primes on
+ *                    its first use for a database (about 0.75 GB per GiB of database at
+ *                    n = 1024, milliseconds of GPU time) and keeps it in step with
+ *                    zp_gen_hint; it needs a 16-byte aligned dCKO (else byte planes run);
+ *   "rns_min_batch": smallest batch compressed in RNS under "auto" (default 8; 0 never);
  *   "overlap_sms":   the number of SMs on which the compression products of a single
  *                    query run while the answer uses the other SMs (zp_respond,
  *                    zp_compress_products, single-query zp_answer); 0 = no overlap.

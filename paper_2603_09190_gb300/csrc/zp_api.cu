@@ -304,7 +304,8 @@ extern "C" int zp_init(int device, const zp_params* P, zp_ctx** out) {
     c->launches = 0;
     c->answer_path = ZP_PATH_AUTO;
     c->compress_path = ZP_PATH_AUTO;
-    c->rns_min_batch = 16;  // from 16 queries on, the RNS compression reads less and multiplies less
+    // from 8 queries on the RNS compression is faster (measured at 1 and 8 GiB, n = 1024)
+    c->rns_min_batch = 8;
     {
       zp_rns_dev h;
       rns_setup(c, h);

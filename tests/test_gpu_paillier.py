@@ -124,10 +124,28 @@ def test_combine_batch_of_clients(zp):
 
 
 def test_client_hint_full_size_row(zp):
-    """n = 1024 (the paper's LWE dimension), 2048-bit key: one packed row against the oracle."""
+    """n = 1024 (the paper's LWE dimension), 2048-bit key: one packed row against the oracle.
+    ck_r is drawn uniformly from Z_{m^2} without the client's decryptions (k does not use
+    them), which keeps the oracle's side to the n modular exponentiations of that row."""
     R, C, n = 54, 64, 1024
-    P, D, A, Hn, cl, ctx, db, gcl, ckr, dD = _setup(zp, R, C, n, "uniform", 31)
-    k = db.client_hint(gcl, ckr)
+    P = Params(n=n, key_bits=2048, secret="uniform")
+    D = synth.database(R, C, 31)
+    A = synth.seed_matrix(C, n, 31)
+    Hn = lwe.hint_neg(D, A)
+    cl0 = zippir.setup(P, 131, sample_ck_r=False)
+    m2 = cl0.pk.m2
+    g = np.random.default_rng(31)
+    ck_r = [int.from_bytes(g.bytes(528), "little") % m2 for _ in range(n)]
+    cl = zippir.Client(P, cl0.pk, cl0.sk, ck_r, [])
+    ctx = zp.Context(0, n=n, key_bits=2048, secret="uniform")
+    ld = zp.db_pitch(C)
+    buf = np.zeros((R, ld), dtype=np.uint8)
+    buf[:, :C] = D
+    dD = torch.from_numpy(buf).cuda()
+    db = zp.Database(ctx, dD, R, C, ld)
+    db.gen_hint(u32_dev(A))
+    gcl = ctx.register_client(cl.pk.m)
+    k = db.client_hint(gcl, u32_dev(synth.ints_to_limbs(ck_r, 2 * ctx.L)))
     got = synth.limbs_to_ints(u32_host(k))
     assert got[1] == zippir.paillier_matmul_rows(cl, Hn, [1])[0]
 

@@ -83,7 +83,7 @@ def test_rns_edge_values(zp):
 
 
 def test_rns_auto_threshold_equals_tc_and_updates(zp):
-    """Automatic choice: 20 queries (>= rns_min_batch 16) take the RNS path and agree with
+    """Automatic choice: 20 queries (>= rns_min_batch, default 8) take the RNS path and agree with
     the tensor-core byte-plane path bit for bit; after row updates and hint regeneration
     the RNS planes of the touched packed rows follow and t matches the oracle."""
     R, C, n, B = 150, 64, 32, 20
