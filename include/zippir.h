@@ -211,6 +211,14 @@ int zp_update_rows(zp_db* db, const uint32_t* hRows, uint32_t k, const uint8_t* 
 int zp_client_hint(zp_db* db, const zp_client* cl, const uint32_t* dCkr, uint32_t* dK,
                    const uint32_t* hPackedRows, uint32_t nrows, void* stream);
 
+/* Builds now the residues of H' modulo the RNS primes that the compression of large
+ * batches uses (see "compress_path"), which the first such batch would otherwise build:
+ * a serving loop calls it at setup so that no request waits for it. About 0.75 GB of
+ * device memory per GiB of database at n = 1024. Asynchronous on `stream`.
+ * Errors: ZP_EINVAL, ZP_ESTATE (no hint or stale rows), ZP_EUNSUPPORTED (n > 1024),
+ * ZP_ENOMEM, ZP_ECUDA. */
+int zp_db_prepare_rns(zp_db* db, void* stream);
+
 /* Combined response (Sec. 4.3, last extension): out[b][r'] = k[b][r'] (1 + t[b][r'] m_b)
  * mod m_b^2, the homomorphic sum of the hint and t (encrypted with randomness 1), so that
  * Dec(out) = Dec(k) + t mod m: one ciphertext per packed row instead of (k, t).

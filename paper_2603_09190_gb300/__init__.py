@@ -31,6 +31,7 @@ EXPORTS = [
     "zp_compress", "zp_respond", "zp_respond_host", "zp_update_rows", "zp_stale_rows",
     "zp_device_status", "zp_kernel_launches", "zp_set_option", "zp_answer_noalloc",
     "zp_compress_products", "zp_compress_finish", "zp_get_option", "zp_client_hint", "zp_combine",
+    "zp_db_prepare_rns",
 ]
 
 
@@ -84,6 +85,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "zp_get_option": (i32, [vp, ctypes.c_char_p, ctypes.POINTER(ctypes.c_int64)]),
         "zp_client_hint": (i32, [vp, vp, vp, vp, vp, u32, vp]),
         "zp_combine": (i32, [vp, vp, vp, vp, u32, vp, vp]),
+        "zp_db_prepare_rns": (i32, [vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -429,6 +431,10 @@ class Database:
         _need(out, "i32", B * self.d1p * 2 * self.L, "out")
         zp_combine(self.handle, clients, _ptr(K), _ptr(T), B, _ptr(out), _stream(stream))
         return out
+
+    def prepare_rns(self, stream=None):
+        """Builds the RNS residue planes of H' now (else on the first large batch)."""
+        _check(load_library().zp_db_prepare_rns(self.handle, _stream(stream)))
 
     def update_rows(self, rows, new_rows, stream=None):
         _need(new_rows, "u8", len(rows) * self.C, "new_rows")

@@ -984,6 +984,15 @@ extern "C" int zp_client_hint(zp_db* db, const zp_client* cl, const uint32_t* dC
   }
 }
 
+extern "C" int zp_db_prepare_rns(zp_db* db, void* stream) {
+  if (!db) return zp_set_error(ZP_EINVAL, "zp_db_prepare_rns: null argument");
+  if (!db->hint_ready) return zp_set_error(ZP_ESTATE, "zp_db_prepare_rns: no hint (call zp_gen_hint)");
+  if (db->stale) return zp_set_error(ZP_ESTATE, "zp_db_prepare_rns: %u hint rows stale after updates", db->stale);
+  if (db->ctx->P.n > 1024) return zp_set_error(ZP_EUNSUPPORTED, "zp_db_prepare_rns: needs n <= 1024");
+  ZP_CUDA(cudaSetDevice(db->ctx->device));
+  return zp_ensure_rns(db, static_cast<cudaStream_t>(stream));
+}
+
 extern "C" int zp_combine(zp_db* db, zp_client* const* clients, const uint32_t* dK, const uint32_t* dT,
                           uint32_t B, uint32_t* dOut, void* stream) {
   try {

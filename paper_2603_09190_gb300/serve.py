@@ -190,6 +190,8 @@ class ZipBackend:
         torch = self.torch
         Bm, C, R, L, n = self.max_batch, db.C, db.R, db.L, self.ctx.n
         dev = db.D.device
+        if Bm >= 8 and n <= 1024:
+            db.prepare_rns()  # large batches compress in RNS: build its tables now, not mid-run
         self.d[name] = {
             "db": db, "A": A, "stream": torch.cuda.Stream(dev),
             "hQ": torch.empty((Bm, C), dtype=torch.int32, pin_memory=True),
@@ -207,7 +209,9 @@ class ZipBackend:
         db = x["db"]
         n = self.ctx.n
         Rp = (db.R + 31) // 32 * 32
-        return db.R * db.ld + db.R * n * 8 + 4 * Rp * math.ceil(n / 16) * 16 + \
+        Rq = (db.d1p + 31) // 32 * 32
+        rns = 153 * 4 * Rq * (math.ceil(n / 16) * 16 + 4) if self.max_batch >= 8 and n <= 1024 else 0
+        return db.R * db.ld + db.R * n * 8 + 4 * Rp * math.ceil(n / 16) * 16 + rns + \
             sum(t.numel() * t.element_size() for k, t in x.items() if k in ("Q", "K", "T", "ans"))
 
     def batch_bytes(self, name, B):

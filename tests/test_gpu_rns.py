@@ -115,3 +115,26 @@ def test_rns_auto_threshold_equals_tc_and_updates(zp):
             for b in (0, 7, 19):
                 assert synth.limbs_to_ints(T2[b]) == zippir.compress_rows(ans[b], Hn2, ckos[b], ms[b], P)
     assert np.array_equal(outs[0], outs[1])
+
+
+def test_prepare_rns(zp):
+    """zp_db_prepare_rns builds the residue planes up front (the serving loop's setup); it
+    needs the hint first, and the batch that follows gives the oracle's t."""
+    R, C, n, B = 70, 32, 16, 9
+    P = Params(n=n, key_bits=2048)
+    c = zp.Context(0, n=n)
+    D = synth.database(R, C, 44)
+    A = synth.seed_matrix(C, n, 45)
+    Hn = lwe.hint_neg(D, A)
+    db, dD = _db(zp, c, D)
+    with pytest.raises(zp.ZipPIRError):
+        db.prepare_rns()
+    db.gen_hint(u32_dev(A))
+    db.prepare_rns()
+    m = synth.random_odd_modulus(2048, 46)
+    cl = c.register_client(m)
+    ckos = [synth.uniform_below(m, n, 47 + b) for b in range(B)]
+    ans = synth.uniform_queries(B, R, 48)
+    T = u32_host(db.compress([cl] * B, u32_dev(ans), u32_dev(np.stack([synth.ints_to_limbs(x, 64) for x in ckos]))))
+    for b in (0, B - 1):
+        assert synth.limbs_to_ints(T[b]) == zippir.compress_rows(ans[b], Hn, ckos[b], m, P)
