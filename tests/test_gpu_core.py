@@ -78,10 +78,13 @@ def test_gemv_closed_forms(zp, ctx):
 
 
 @pytest.mark.parametrize("R,C,B", [(1, 1, 2), (7, 300, 3), (64, 256, 4), (65, 257, 2),
-                                   (333, 9999, 3), (2049, 700, 4), (130, 4096, 4)])
+                                   (333, 9999, 3), (2049, 700, 4), (130, 4096, 4), (1, 1, 5),
+                                   (31, 300, 6), (33, 257, 7), (333, 9999, 8), (2049, 700, 5),
+                                   (4096, 4096, 8)])
 def test_multi_query_gemv_parity(zp, ctx, R, C, B):
     """Two to four queries share one pass of the dp4a GEMV over D (ragged row blocks and
-    column tiles, stream-K splits across CTAs)."""
+    column tiles, stream-K splits across CTAs); five to eight, at the boundary, take the
+    tensor cores."""
     D = synth.database(R, C, 11 * B + R)
     Q = synth.uniform_queries(B, C, 13 * B + C)
     dD, ld = to_dev_db(zp, D)
@@ -92,18 +95,24 @@ def test_multi_query_gemv_parity(zp, ctx, R, C, B):
 
 
 def test_multi_query_gemv_closed_form_and_tc(zp):
-    """All-255 database against all-ones queries gives -255 C mod 2^32 in every entry; the
-    tensor-core path forced for the same batch agrees on random data."""
+    """All-255 database against all-ones queries gives -255 C mod 2^32 in every entry (4
+    queries on the GEMV, 8 on the tensor cores); the tensor-core path forced for the same
+    batch agrees on random data."""
     R, C = 300, 70000
     D = np.full((R, C), 255, dtype=np.uint8)
     Q = np.full((4, C), 0xFFFFFFFF, dtype=np.uint32)
     Q[1] = 1
+    Q8 = np.full((8, C), 0xFFFFFFFF, dtype=np.uint32)
+    Q8[5] = 1
     c = zp.Context(0, n=64)
     dD, ld = to_dev_db(zp, D)
     db = zp.Database(c, dD, R, C, ld)
     got = u32_host(db.answer(u32_dev(Q)))
     assert np.all(got[[0, 2, 3]] == np.uint32((-255 * C) % 2**32))
     assert np.all(got[1] == np.uint32(255 * C))
+    got8 = u32_host(db.answer(u32_dev(Q8)))
+    assert np.all(got8[[0, 1, 2, 3, 4, 6, 7]] == np.uint32((-255 * C) % 2**32))
+    assert np.all(got8[5] == np.uint32(255 * C))
     db.close()
     D2 = synth.database(R, 3000, 17)
     Q2 = synth.uniform_queries(3, 3000, 18)
