@@ -263,6 +263,14 @@ int zp_kernel_launches(const zp_ctx* ctx, uint64_t* count);
  * cleared by the read. */
 int zp_device_status(zp_ctx* ctx, uint32_t* code);
 
+/* Failure-detection self-test: launches one kernel whose mbarrier wait nothing
+ * satisfies, bounded by `cycles` SM clock cycles (at most 2^32, about 2 s). When the wait
+ * gives up, the kernel sets bit 0x4 (a timeout outside the answer and product kernels) of
+ * the status word and returns: the path every bounded wait of the library takes, so that
+ * a wait that cannot complete costs its limit and an error code, never a hung or faulted
+ * device. The context stays usable. Asynchronous on `stream`. Errors: ZP_EINVAL, ZP_ECUDA. */
+int zp_selftest_wait(zp_ctx* ctx, uint64_t cycles, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

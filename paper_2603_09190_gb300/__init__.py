@@ -31,7 +31,7 @@ EXPORTS = [
     "zp_compress", "zp_respond", "zp_respond_host", "zp_update_rows", "zp_stale_rows",
     "zp_device_status", "zp_kernel_launches", "zp_set_option", "zp_answer_noalloc",
     "zp_compress_products", "zp_compress_finish", "zp_get_option", "zp_client_hint", "zp_combine",
-    "zp_db_prepare_rns",
+    "zp_db_prepare_rns", "zp_selftest_wait",
 ]
 
 
@@ -86,6 +86,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "zp_client_hint": (i32, [vp, vp, vp, vp, vp, u32, vp]),
         "zp_combine": (i32, [vp, vp, vp, vp, u32, vp, vp]),
         "zp_db_prepare_rns": (i32, [vp, vp]),
+        "zp_selftest_wait": (i32, [vp, u64, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -299,6 +300,10 @@ class Context:
 
     def device_status(self) -> int:
         return zp_device_status(self.handle)
+
+    def selftest_wait(self, cycles: int, stream=None):
+        """Runs a bounded wait that nothing satisfies (the failure path of every wait)."""
+        _check(load_library().zp_selftest_wait(self.handle, int(cycles), _stream(stream)))
 
     def kernel_launches(self) -> int:
         return zp_kernel_launches(self.handle)

@@ -240,3 +240,33 @@ int zp_launch_copy_rows(const uint8_t* src, uint64_t lds, uint8_t* dst, uint64_t
   ZP_CUDA(cudaGetLastError());
   return ZP_OK;
 }
+
+// ---------------------------------------------------------------------------------
+// Failure-detection self-test: one mbarrier wait that nothing satisfies, bounded by
+// `cycles` SM clock cycles. It gives up the way every bounded wait of the library does:
+// a bit in the context's status word, then return (no trap, no fault).
+namespace {
+__global__ void k_selftest_wait(unsigned long long cycles, uint32_t* status) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && !mbar_wait_until(&bar, 0, clock64() + cycles))
+    atomicOr(status, ZP_DEV_TIMEOUT_MISC);
+  __syncthreads();
+}
+}  // namespace
+
+extern "C" int zp_selftest_wait(zp_ctx* c, uint64_t cycles, void* stream) {
+  if (!c) return zp_set_error(ZP_EINVAL, "zp_selftest_wait: null argument");
+  if (cycles > (1ull << 32))
+    return zp_set_error(ZP_EINVAL, "zp_selftest_wait: cycles=%llu above 2^32", (unsigned long long)cycles);
+  ZP_CUDA(cudaSetDevice(c->device));
+  zp_clear_pending_error();
+  c->launches++;
+  k_selftest_wait<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>(cycles, c->d_status);
+  ZP_CUDA(cudaGetLastError());
+  return ZP_OK;
+}
