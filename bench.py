@@ -272,6 +272,8 @@ def run_ours(args, world, rank, local):
     side = torch.cuda.Stream(dev)
     sp = stream.cuda_stream
     handles = [c.handle for c in clients]
+    # thresholds and SM split measured on this database (zp_autotune)
+    tuned = None if args.no_autotune else db.autotune()
     if args.overlap is not None:
         ctx.set_option("overlap_sms", args.overlap)
     overlap = B == 1 and zp.zp_get_overlap(ctx) > 0
@@ -341,6 +343,64 @@ def run_ours(args, world, rank, local):
     if not (torch.equal(T2, T_step) and torch.equal(ans2, ans)):
         raise RuntimeError("composed step and zp_respond disagree")
 
+    # ---- latency of one Response (zp_respond), warm and with L2 flushed before each call
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    lat = {"warm": [], "cold": []}
+    e_a, e_b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for kind in ("warm", "cold"):
+        for _ in range(50):
+            if kind == "cold":
+                flush.fill_(1)
+            e_a.record(stream)
+            zp.zp_respond(db.handle, handles, Q.data_ptr(), CKO.data_ptr(), B, ans2.data_ptr(),
+                          T2.data_ptr(), sp)
+            e_b.record(stream)
+            torch.cuda.synchronize()
+            lat[kind].append(e_a.elapsed_time(e_b) * 1e3)
+    latency_us = {k: {"p50": float(np.percentile(v, 50)), "p99": float(np.percentile(v, 99))}
+                  for k, v in lat.items()}
+    del flush
+
+    # ---- the Response captured once in a CUDA graph and replayed (inputs in place)
+    graph = None
+    try:
+        g = torch.cuda.CUDAGraph()
+        gs = torch.cuda.Stream(dev)
+        gs.wait_stream(stream)
+        with torch.cuda.stream(gs):
+            zp.zp_respond(db.handle, handles, Q.data_ptr(), CKO.data_ptr(), B, ans2.data_ptr(),
+                          T2.data_ptr(), gs.cuda_stream)      # sizes scratch before capture
+        gs.synchronize()
+        with torch.cuda.graph(g, stream=gs):
+            zp.zp_respond(db.handle, handles, Q.data_ptr(), CKO.data_ptr(), B, ans2.data_ptr(),
+                          T2.data_ptr(), torch.cuda.current_stream().cuda_stream)
+        T2.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        same = bool(torch.equal(T2, T_step))
+        reps = max(10, min(args.steps, 500))
+        e_a.record(stream)
+        for _ in range(reps):
+            g.replay()
+        e_b.record(stream)
+        torch.cuda.synchronize()
+        graph = {"ms_per_step": e_a.elapsed_time(e_b) / reps, "identical": same}
+    except Exception as ex:  # noqa: BLE001 - reported in the line, not fatal
+        graph = {"error": str(ex)[:200]}
+
+    # ---- batched answers against B single-query GEMV passes on the same database
+    single = None
+    if B > 1:
+        q1 = torch.empty((1, R), dtype=torch.int32, device=dev)
+        for _ in range(3):
+            zp.zp_answer(db.handle, Q.data_ptr(), 1, q1.data_ptr(), sp)
+        e_a.record(stream)
+        for b in range(B):
+            zp.zp_answer(db.handle, Q[b].data_ptr(), 1, q1.data_ptr(), sp)
+        e_b.record(stream)
+        torch.cuda.synchronize()
+        single = e_a.elapsed_time(e_b)
+
     # ---- e2e through the host-buffer entry point
     hQ = torch.empty((B, C), dtype=torch.int32, pin_memory=True)
     hQ.copy_(Q.cpu())
@@ -394,6 +454,12 @@ def run_ours(args, world, rank, local):
                           "step_p50": float(np.percentile(step_ms, 50)),
                           "step_p99": float(np.percentile(step_ms, 99))},
             "gib_s": value * 1e9 / 2**30,
+            "latency_us": latency_us,
+            "graph": graph,
+            "autotuned": tuned,
+            "batched_vs_single_gemv": None if single is None else
+                {"single_query_gemv_x_B_ms": single, "batched_answers_ms": ans_avg,
+                 "speedup": single / ans_avg},
             "hint_ms": hint_ms,
             "hint_tflops_fp16": 2.0 * R * C * 4 * n / (hint_ms * 1e-3) / 1e12,
             "roofline": roof,
@@ -585,6 +651,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="1gib", choices=sorted(WORKLOADS) + ["serve", "client_hint"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the library's default thresholds and SM split")
     ap.add_argument("--serve-rates", type=float, nargs="*", default=[50, 200, 1000, 2000])
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--serve-clients", type=int, default=1000)

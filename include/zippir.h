@@ -211,6 +211,17 @@ int zp_update_rows(zp_db* db, const uint32_t* hRows, uint32_t k, const uint8_t* 
 int zp_client_hint(zp_db* db, const zp_client* cl, const uint32_t* dCkr, uint32_t* dK,
                    const uint32_t* hPackedRows, uint32_t nrows, void* stream);
 
+/* Autotuner: measures on `db` (zero-filled test buffers it allocates and frees; the
+ * kernels' time does not depend on the values) the one-pass GEMV against the tensor-core
+ * GEMM for 2..4 queries, the byte-plane against the RNS compression for 2..16 queries
+ * (when the hint is ready, n <= 1024 and "compress_path" is auto; this builds the RNS
+ * tables), and the SM split of the single-query zp_respond (0 and 24%..52% of the SMs),
+ * and sets the context options "gemv_max_batch", "rns_min_batch" and "overlap_sms" to the
+ * fastest choices. chosen (may be NULL): receives those three values. Synchronous on
+ * `stream`; tens of milliseconds at 1 GiB. Errors: ZP_EINVAL, ZP_ENOMEM, ZP_ECUDA (the
+ * options are left as they were). */
+int zp_autotune(zp_db* db, void* stream, int64_t* chosen);
+
 /* Builds now the residues of H' modulo the RNS primes that the compression of large
  * batches uses (see "compress_path"), which the first such batch would otherwise build:
  * a serving loop calls it at setup so that no request waits for it. About 0.75 GB of
@@ -246,6 +257,8 @@ int zp_stale_rows(const zp_db* db, uint32_t* count);
  *                    n = 1024, milliseconds of GPU time) and keeps it in step with
  *                    zp_gen_hint; it needs a 16-byte aligned dCKO (else byte planes run);
  *   "rns_min_batch": smallest batch compressed in RNS under "auto" (default 8; 0 never);
+ *   "gemv_max_batch": largest batch (1..4) answered by one GEMV pass under "auto"
+ *                    (default 4; zp_autotune measures both);
  *   "overlap_sms":   the number of SMs on which the compression products of a single
  *                    query run while the answer uses the other SMs (zp_respond,
  *                    zp_compress_products, single-query zp_answer); 0 = no overlap.

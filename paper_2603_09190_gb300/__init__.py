@@ -31,7 +31,7 @@ EXPORTS = [
     "zp_compress", "zp_respond", "zp_respond_host", "zp_update_rows", "zp_stale_rows",
     "zp_device_status", "zp_kernel_launches", "zp_set_option", "zp_answer_noalloc",
     "zp_compress_products", "zp_compress_finish", "zp_get_option", "zp_client_hint", "zp_combine",
-    "zp_db_prepare_rns", "zp_selftest_wait",
+    "zp_db_prepare_rns", "zp_selftest_wait", "zp_autotune",
 ]
 
 
@@ -87,6 +87,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "zp_combine": (i32, [vp, vp, vp, vp, u32, vp, vp]),
         "zp_db_prepare_rns": (i32, [vp, vp]),
         "zp_selftest_wait": (i32, [vp, u64, vp]),
+        "zp_autotune": (i32, [vp, vp, ctypes.POINTER(ctypes.c_int64)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -272,6 +273,14 @@ def zp_set_option(ctx: int, name: str, value: int):
     _check(load_library().zp_set_option(ctx, name.encode(), int(value)))
 
 
+def zp_get_option_value(ctx, name: str) -> int:
+    """An option of a context (Context or handle), by name."""
+    h = ctx.handle if isinstance(ctx, Context) else ctx
+    v = ctypes.c_int64()
+    _check(load_library().zp_get_option(h, name.encode(), ctypes.byref(v)))
+    return v.value
+
+
 def zp_get_overlap(ctx) -> int:
     """Current "overlap_sms" option of a context (Context or handle)."""
     h = ctx.handle if isinstance(ctx, Context) else ctx
@@ -436,6 +445,12 @@ class Database:
         _need(out, "i32", B * self.d1p * 2 * self.L, "out")
         zp_combine(self.handle, clients, _ptr(K), _ptr(T), B, _ptr(out), _stream(stream))
         return out
+
+    def autotune(self, stream=None) -> dict:
+        """Measures and sets the context's batch thresholds and SM split (zp_autotune)."""
+        out = (ctypes.c_int64 * 3)()
+        _check(load_library().zp_autotune(self.handle, _stream(stream), out))
+        return {"gemv_max_batch": out[0], "rns_min_batch": out[1], "overlap_sms": out[2]}
 
     def prepare_rns(self, stream=None):
         """Builds the RNS residue planes of H' now (else on the first large batch)."""

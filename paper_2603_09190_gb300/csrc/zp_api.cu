@@ -306,6 +306,7 @@ extern "C" int zp_init(int device, const zp_params* P, zp_ctx** out) {
     c->compress_path = ZP_PATH_AUTO;
     // from 8 queries on the RNS compression is faster (measured at 1 and 8 GiB, n = 1024)
     c->rns_min_batch = 8;
+    c->gemv_max_batch = 4;  // one dp4a pass beats the tensor cores up to 4 queries (1 GiB)
     {
       zp_rns_dev h;
       rns_setup(c, h);
@@ -363,6 +364,12 @@ extern "C" int zp_set_option(zp_ctx* c, const char* name, int64_t value) {
     c->overlap_sms = (uint32_t)value;
     return ZP_OK;
   }
+  if (k == "gemv_max_batch") {
+    if (value < 1 || value > 4)
+      return zp_set_error(ZP_EINVAL, "zp_set_option: gemv_max_batch=%lld out of [1, 4]", (long long)value);
+    c->gemv_max_batch = (uint32_t)value;
+    return ZP_OK;
+  }
   if (k == "rns_min_batch") {
     if (value < 0 || value > 4096)
       return zp_set_error(ZP_EINVAL, "zp_set_option: rns_min_batch=%lld out of [0, 4096]", (long long)value);
@@ -379,6 +386,7 @@ extern "C" int zp_get_option(const zp_ctx* c, const char* name, int64_t* value) 
   else if (k == "compress_path") *value = c->compress_path;
   else if (k == "overlap_sms") *value = c->overlap_sms;
   else if (k == "rns_min_batch") *value = c->rns_min_batch;
+  else if (k == "gemv_max_batch") *value = c->gemv_max_batch;
   else return zp_set_error(ZP_EINVAL, "zp_get_option: unknown option '%s'", name);
   return ZP_OK;
 }
@@ -690,7 +698,7 @@ extern "C" int zp_answer(zp_db* db, const uint32_t* dQ, uint32_t B, uint32_t* dA
   zp_ctx* c = db->ctx;
   // One to four queries: one pass of the dp4a GEMV over D (HBM- or dp4a-bound, ahead of
   // the tensor cores for such batches); more: the tensor-core GEMM.
-  if (B <= 4 && c->answer_path != ZP_PATH_SIMT && c->answer_path != ZP_PATH_TC)
+  if (B <= c->gemv_max_batch && c->answer_path != ZP_PATH_SIMT && c->answer_path != ZP_PATH_TC)
     return zp_launch_gemv(db, dQ, B, dAns, st,
                           B == 1 && c->overlap_sms ? (uint32_t)c->num_sms - c->overlap_sms : 0u);
   if (c->answer_path == ZP_PATH_SIMT)
@@ -981,6 +989,129 @@ extern "C" int zp_client_hint(zp_db* db, const zp_client* cl, const uint32_t* dC
     return zp_launch_client_hint(db, cl, dCkr, dK, dRows, np, st);
   } catch (const std::bad_alloc&) {
     return zp_set_error(ZP_ENOMEM, "zp_client_hint: host allocation failed");
+  }
+}
+
+// ------------------------------------------------------------------ autotuner
+// Measures on `db` (zero-filled test inputs: the kernels' time does not depend on the
+// values) and sets the context's batch thresholds and the SM split to the fastest choices.
+extern "C" int zp_autotune(zp_db* db, void* stream, int64_t* chosen) {
+  try {
+    if (!db) return zp_set_error(ZP_EINVAL, "zp_autotune: null argument");
+    zp_ctx* c = db->ctx;
+    ZP_CUDA(cudaSetDevice(c->device));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const uint32_t BQ = 16, n = c->P.n, L = c->L;
+    const int saved_answer = c->answer_path, saved_compress = c->compress_path;
+    const uint32_t saved_overlap = c->overlap_sms, saved_gemv = c->gemv_max_batch,
+                   saved_rns = c->rns_min_batch;
+    uint32_t *dQ = nullptr, *dAns = nullptr, *dCKO = nullptr, *dT = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    zp_client* cl = nullptr;
+    auto cleanup = [&]() {
+      for (uint32_t* p : {dQ, dAns, dCKO, dT})
+        if (p) cudaFree(p);
+      if (e0) cudaEventDestroy(e0);
+      if (e1) cudaEventDestroy(e1);
+      if (cl) zp_client_destroy(cl);
+      c->answer_path = saved_answer;
+      c->compress_path = saved_compress;
+    };
+    auto fail = [&](int rc) {
+      cleanup();
+      c->overlap_sms = saved_overlap;
+      c->gemv_max_batch = saved_gemv;
+      c->rns_min_batch = saved_rns;
+      return rc;
+    };
+    if (cudaMalloc(&dQ, (size_t)BQ * db->C * 4) != cudaSuccess ||
+        cudaMalloc(&dAns, (size_t)BQ * db->R * 4) != cudaSuccess ||
+        cudaMalloc(&dCKO, (size_t)BQ * n * L * 4) != cudaSuccess ||
+        cudaMalloc(&dT, (size_t)BQ * db->d1p * L * 4) != cudaSuccess)
+      return fail(zp_set_error(ZP_ENOMEM, "zp_autotune: test buffers"));
+    if (cudaMemsetAsync(dQ, 0, (size_t)BQ * db->C * 4, st) != cudaSuccess ||
+        cudaMemsetAsync(dCKO, 0, (size_t)BQ * n * L * 4, st) != cudaSuccess ||
+        cudaMemsetAsync(dAns, 0, (size_t)BQ * db->R * 4, st) != cudaSuccess ||
+        cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+      return fail(zp_set_error(ZP_ECUDA, "zp_autotune: setup"));
+    // mean of 5 runs after one warm-up; a failing run aborts the tuning
+    int err = ZP_OK;
+    auto time_ms = [&](auto&& fn) {
+      float ms = 0.f;
+      if (err) return 1e30f;
+      if ((err = fn())) return 1e30f;
+      cudaEventRecord(e0, st);
+      for (int i = 0; i < 5 && !err; ++i) err = fn();
+      cudaEventRecord(e1, st);
+      cudaEventSynchronize(e1);
+      cudaEventElapsedTime(&ms, e0, e1);
+      return err ? 1e30f : ms / 5.f;
+    };
+    // (1) answers: one dp4a pass against the tensor cores, 2..4 queries
+    uint32_t gemv_max = 1;
+    for (uint32_t B = 2; B <= 4; ++B) {
+      c->answer_path = ZP_PATH_AUTO;
+      c->gemv_max_batch = 4;
+      const float g = time_ms([&] { return zp_answer(db, dQ, B, dAns, stream); });
+      c->answer_path = ZP_PATH_TC;
+      const float t = time_ms([&] { return zp_answer(db, dQ, B, dAns, stream); });
+      if (err) return fail(err);
+      if (g > t) break;
+      gemv_max = B;
+    }
+    c->answer_path = saved_answer;
+    c->gemv_max_batch = gemv_max;
+    // (2) compression: byte planes against RNS (needs the hint and n <= 1024)
+    uint32_t rns_min = c->rns_min_batch;
+    if (db->hint_ready && !db->stale && n <= 1024 && saved_compress == ZP_PATH_AUTO) {
+      std::vector<uint32_t> m(L, 0);  // a fixed odd modulus of key_bits bits
+      m[0] = 1;
+      m[L - 1] = 0xC0000000u;
+      int rc = zp_register_client(c, m.data(), L, &cl);
+      if (rc) return fail(rc);
+      std::vector<zp_client*> cls(BQ, cl);
+      rns_min = 0;
+      for (uint32_t B : {2u, 4u, 6u, 8u, 12u, 16u}) {
+        c->compress_path = ZP_PATH_TC;
+        const float bp = time_ms([&] { return zp_compress(db, cls.data(), dAns, dCKO, B, dT, stream); });
+        c->compress_path = ZP_PATH_RNS;
+        const float rn = time_ms([&] { return zp_compress(db, cls.data(), dAns, dCKO, B, dT, stream); });
+        if (err) return fail(err);
+        if (rn < bp) {
+          rns_min = B;
+          break;
+        }
+      }
+      c->compress_path = saved_compress;
+    }
+    c->rns_min_batch = rns_min;
+    // (3) the SM split of the single-query Response
+    if (cl && c->num_sms >= 64) {
+      float best = 1e30f;
+      uint32_t best_ov = 0;
+      for (uint32_t frac = 0; frac <= 8; ++frac) {  // 0 and 24% .. 52% of the SMs
+        const uint32_t ov = frac == 0 ? 0u : (uint32_t)(c->num_sms * (20 + 4 * frac) / 100);
+        c->overlap_sms = ov;
+        const float r = time_ms([&] {
+          return zp_respond(db, &cl, dQ, dCKO, 1, dAns, dT, stream);
+        });
+        if (err) return fail(err);
+        if (r < best) {
+          best = r;
+          best_ov = ov;
+        }
+      }
+      c->overlap_sms = best_ov;
+    }
+    cleanup();
+    if (chosen) {
+      chosen[0] = c->gemv_max_batch;
+      chosen[1] = c->rns_min_batch;
+      chosen[2] = c->overlap_sms;
+    }
+    return ZP_OK;
+  } catch (const std::bad_alloc&) {
+    return zp_set_error(ZP_ENOMEM, "zp_autotune: host allocation failed");
   }
 }
 

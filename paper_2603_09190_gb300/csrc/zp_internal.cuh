@@ -52,6 +52,7 @@ struct zp_ctx {
   uint32_t L;          // limbs per element of Z_m
   uint32_t gamma_w[3]; // packing scale gamma, little-endian 32-bit words (gamma < 2^96)
   uint32_t rns_min_batch;  // batches of at least this many queries compress in RNS (0: never)
+  uint32_t gemv_max_batch; // batches of at most this many queries (<= 4) answer by the GEMV
   zp_rns_dev* d_rns;   // RNS constants (device)
   std::vector<uint32_t> rns_p;  // the primes (host)
   int num_sms;
