@@ -400,7 +400,8 @@ int zp_launch_compress_finish(zp_db* db, zp_client* const* clients, const uint32
       return zp_cuda_check(e, "cudaMemcpyAsync(clients)");
     }
   }
-  static bool attr = false;
+  static bool attr_dev[64] = {false};  // the attribute is per device
+  bool& attr = attr_dev[ctx->device & 63];
   if (!attr) {
     ZP_CUDA(cudaFuncSetAttribute(k_pack_reduce<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)(PACK_WARPS * (sizeof(PackBarrett) + 64 * VW * 4))));

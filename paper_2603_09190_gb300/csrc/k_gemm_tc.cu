@@ -702,16 +702,16 @@ __global__ void k_prep_cko(const uint32_t* __restrict__ cko, uint32_t n, uint32_
   if (s) atomicAdd(&colsum[(uint64_t)b * 256 + beta], s);
 }
 
-bool g_attr[4][3] = {{false}};
+bool g_attr[64][4][3] = {};  // per device, mode and tile width
 
 template <int MODE, int BT>
 int launch_gemm(zp_ctx* ctx, const CUtensorMap& tmA, const CUtensorMap& tmB, const GemmArgs& ga,
                 cudaStream_t st, uint32_t max_ctas = 0) {
   constexpr int bi = BT == 16 ? 0 : (BT == 32 ? 1 : 2);
-  if (!g_attr[MODE][bi]) {
+  if (!g_attr[ctx->device & 63][MODE][bi]) {
     ZP_CUDA(cudaFuncSetAttribute(k_gemm_tc<MODE, BT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  Cfg<MODE>::SMEM));
-    g_attr[MODE][bi] = true;
+    g_attr[ctx->device & 63][MODE][bi] = true;
   }
   uint32_t tiles = ga.num_m_tiles * ga.num_n_tiles;
   uint32_t grid = tiles < (uint32_t)ctx->num_sms ? tiles : (uint32_t)ctx->num_sms;
