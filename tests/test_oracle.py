@@ -221,3 +221,21 @@ def test_sizes():
     d1p = P.d1p(32768)
     assert d1p * 2048 // 8 == 1214 * 256
     assert 2 * d1p * 2048 // 8 == 621568
+
+
+def test_chacha20_keystream_matches_library():
+    """The oracle's ChaCha20 (RFC 8439 block function) against the `cryptography` package's
+    ChaCha20 keystream, for several keys, nonces and block counters and a ragged length."""
+    ciphers = pytest.importorskip("cryptography.hazmat.primitives.ciphers")
+    from oracle import chacha20
+    g = np.random.default_rng(8439)
+    for trial in range(4):
+        key = g.bytes(32)
+        nonce = g.bytes(12)
+        ctr = int(g.integers(0, 2**31))
+        nwords = 16 * trial + 7
+        enc = ciphers.Cipher(ciphers.algorithms.ChaCha20(key, ctr.to_bytes(4, "little") + nonce),
+                             mode=None).encryptor()
+        ks = enc.update(b"\0" * (4 * nwords))
+        want = [int.from_bytes(ks[4 * i:4 * i + 4], "little") for i in range(nwords)]
+        assert chacha20.keystream_words(key, nonce, ctr, nwords) == want
