@@ -276,6 +276,25 @@ int zp_kernel_launches(const zp_ctx* ctx, uint64_t* count);
  * cleared by the read. */
 int zp_device_status(zp_ctx* ctx, uint32_t* code);
 
+/* ChaCha20 keystream (RFC 8439 block function) on the GPU: dOut[0 .. nwords) receives the
+ * little-endian 32-bit words of blocks counter0, counter0 + 1, ... for the 32-byte key hKey
+ * and the 12-byte nonce hNonce (both HOST, read before the call returns). The PRG that
+ * expands the public matrix A (Sec. 2.1.1) and ck_r (Sec. 4.3) from short seeds, for
+ * servers that keep only the seed; the paper names no PRG, ChaCha20 is this library's
+ * choice. Runs on the current device. Asynchronous on `stream`.
+ * Errors: ZP_EINVAL (null argument, 32-bit block counter would wrap), ZP_ECUDA. */
+int zp_prg_chacha20(const uint8_t* hKey, const uint8_t* hNonce, uint32_t counter0,
+                    uint32_t* dOut, uint64_t nwords, void* stream);
+
+/* Batched modular exponentiation mod m^2 of a client (Montgomery products, one warp per
+ * base): dOut[i] = dBase[i]^e mod m^2 for i < count, e = the expWords (1..128) little-endian
+ * words of the HOST array hExp. dBase, dOut: count x 2L u32, 16-byte aligned, each base
+ * < m^2. The core of Paillier's decryption (e = lambda: Dec(c) = ((c^lambda mod m^2) - 1)/m
+ * * mu mod m) and of its encryption's randomness factor (e = m), for client-side load
+ * generation. Asynchronous on `stream`. Errors: ZP_EINVAL, ZP_ECUDA. */
+int zp_client_powm(const zp_client* cl, const uint32_t* dBase, const uint32_t* hExp,
+                   uint32_t expWords, uint32_t* dOut, uint32_t count, void* stream);
+
 /* Failure-detection self-test: launches one kernel whose mbarrier wait nothing
  * satisfies, bounded by `cycles` SM clock cycles (at most 2^32, about 2 s). When the wait
  * gives up, the kernel sets bit 0x4 (a timeout outside the answer and product kernels) of

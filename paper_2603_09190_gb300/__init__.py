@@ -31,7 +31,7 @@ EXPORTS = [
     "zp_compress", "zp_respond", "zp_respond_host", "zp_update_rows", "zp_stale_rows",
     "zp_device_status", "zp_kernel_launches", "zp_set_option", "zp_answer_noalloc",
     "zp_compress_products", "zp_compress_finish", "zp_get_option", "zp_client_hint", "zp_combine",
-    "zp_db_prepare_rns", "zp_selftest_wait", "zp_autotune",
+    "zp_db_prepare_rns", "zp_selftest_wait", "zp_autotune", "zp_prg_chacha20", "zp_client_powm",
 ]
 
 
@@ -88,6 +88,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "zp_db_prepare_rns": (i32, [vp, vp]),
         "zp_selftest_wait": (i32, [vp, u64, vp]),
         "zp_autotune": (i32, [vp, vp, ctypes.POINTER(ctypes.c_int64)]),
+        "zp_prg_chacha20": (i32, [vp, vp, u32, vp, u64, vp]),
+        "zp_client_powm": (i32, [vp, vp, vp, u32, vp, u32, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -252,6 +254,18 @@ def zp_combine(db: int, clients, dK: int, dT: int, B: int, dOut: int, stream: in
                                      dK, dT, B, dOut, stream))
 
 
+def prg_chacha20(key: bytes, nonce: bytes, counter0: int, out, stream=None):
+    """Fills the int32 CUDA tensor `out` with ChaCha20 keystream words (zp_prg_chacha20)."""
+    if len(key) != 32 or len(nonce) != 12:
+        raise ValueError("ChaCha20 takes a 32-byte key and a 12-byte nonce")
+    _need(out, "i32", None, "out")
+    kb = ctypes.create_string_buffer(bytes(key), 32)
+    nb = ctypes.create_string_buffer(bytes(nonce), 12)
+    _check(load_library().zp_prg_chacha20(kb, nb, int(counter0), _ptr(out), out.numel(),
+                                          _stream(stream)))
+    return out
+
+
 def zp_update_rows(db: int, hRows: np.ndarray, dNew: int, stream: int | None):
     r = np.ascontiguousarray(hRows, dtype=np.uint32)
     _check(load_library().zp_update_rows(db, r.ctypes.data, len(r), dNew, stream))
@@ -342,6 +356,19 @@ class Client:
     def __init__(self, ctx: Context, m: int):
         self.ctx, self.m = ctx, int(m)
         self.handle = zp_register_client(ctx.handle, self.m, ctx.L)
+
+    def powm(self, bases, exponent: int, out=None, stream=None):
+        """bases^exponent mod m^2 for a CUDA int32 tensor of (count, 2L) limbs (zp_client_powm)."""
+        import torch
+        count = bases.shape[0]
+        _need(bases, "i32", count * 2 * self.ctx.L, "bases")
+        if out is None:
+            out = torch.empty_like(bases)
+        ew = max(1, (int(exponent).bit_length() + 31) // 32)
+        e = np.array([(int(exponent) >> (32 * i)) & 0xFFFFFFFF for i in range(ew)], dtype=np.uint32)
+        _check(load_library().zp_client_powm(self.handle, _ptr(bases), e.ctypes.data, ew, _ptr(out),
+                                             count, _stream(stream)))
+        return out
 
     def close(self):
         if self.handle:

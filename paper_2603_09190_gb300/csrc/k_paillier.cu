@@ -265,6 +265,40 @@ __global__ void __launch_bounds__(128) k_combine(const uint32_t* __restrict__ k,
   store_lane_words(out + (uint64_t)idx * MW, kv);
 }
 
+// out[i] = base[i]^e mod m^2 for a shared exponent of ew words (left-to-right binary):
+// the core of Paillier's decryption (e = lambda) and of its randomness factor (e = m). One
+// warp per base.
+struct PowExp {
+  uint32_t w[128];
+};
+__global__ void __launch_bounds__(128) k_powm(const uint32_t* __restrict__ base, PowExp e,
+                                              uint32_t ew, uint32_t count, M2Consts c,
+                                              uint32_t* __restrict__ out) {
+  const uint32_t idx = blockIdx.x * 4 + (threadIdx.x >> 5);
+  if (idx >= count) return;
+  const ModM2 M = load_mod(c);
+  int top = -1;  // highest set bit of e (warp-uniform)
+  for (int w = (int)ew - 1; w >= 0 && top < 0; --w)
+    if (e.w[w]) top = 32 * w + 31 - __clz(e.w[w]);
+  uint32_t x[MWPL], y[MWPL], r2[MWPL];
+  load_lane_words(base + (uint64_t)idx * MW, x);
+  load_lane_words(c.r2, r2);
+  mont_mul(M, x, r2, x);  // to Montgomery form
+  if (top < 0) {
+    load_lane_words(c.r1, y);  // e = 0: the Montgomery form of 1
+  } else {
+#pragma unroll
+    for (int k = 0; k < MWPL; ++k) y[k] = x[k];
+    for (int bit = top - 1; bit >= 0; --bit) {
+      mont_mul(M, y, y, y);
+      if ((e.w[bit >> 5] >> (bit & 31)) & 1u) mont_mul(M, y, x, y);
+    }
+  }
+  uint32_t one[MWPL] = {lane_id() == 0 ? 1u : 0u, 0u, 0u, 0u};
+  mont_mul(M, y, one, y);
+  store_lane_words(out + (uint64_t)idx * MW, y);
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------------
@@ -318,6 +352,26 @@ int zp_launch_combine(zp_db* db, zp_client* const* clients, const uint32_t* dK, 
   ctx->launches++;
   k_combine<<<(unsigned)((warps + 3) / 4), 128, 0, st>>>(
       dK, dT, B, db->d1p, static_cast<const M2Consts*>(db->s_m2consts.p), dOut);
+  ZP_CUDA(cudaGetLastError());
+  return ZP_OK;
+}
+
+extern "C" int zp_client_powm(const zp_client* cl, const uint32_t* dBase, const uint32_t* hExp,
+                              uint32_t expWords, uint32_t* dOut, uint32_t count, void* stream) {
+  if (!cl || !hExp || ((!dBase || !dOut) && count))
+    return zp_set_error(ZP_EINVAL, "zp_client_powm: null argument");
+  if (expWords == 0 || expWords > 128)
+    return zp_set_error(ZP_EINVAL, "zp_client_powm: expWords=%u out of [1, 128]", expWords);
+  if ((reinterpret_cast<uintptr_t>(dBase) | reinterpret_cast<uintptr_t>(dOut)) & 15u)
+    return zp_set_error(ZP_EINVAL, "zp_client_powm: dBase and dOut must be 16-byte aligned");
+  if (count == 0) return ZP_OK;
+  ZP_CUDA(cudaSetDevice(cl->device));
+  PowExp e{};
+  for (uint32_t i = 0; i < expWords; ++i) e.w[i] = hExp[i];
+  zp_clear_pending_error();
+  cl->ctx->launches++;
+  k_powm<<<(count + 3) / 4, 128, 0, static_cast<cudaStream_t>(stream)>>>(dBase, e, expWords, count,
+                                                                          client_consts(cl), dOut);
   ZP_CUDA(cudaGetLastError());
   return ZP_OK;
 }
