@@ -2,8 +2,8 @@
 infrastructure only.
 
 The paper expands the public matrix A and the clients' random ck_r from short seeds with
-"a cryptographically secure PRG" (Sec. 2.1.1, Sec. 4.3) without naming one; ChaCha20 is
-the reading taken. Plain Python integers, one block at a time.
+a secure PRG that it does not name (Sec. 2.1.1, Sec. 4.3); ChaCha20 is the reading
+taken. Plain Python integers, one block at a time.
 """
 from __future__ import annotations
 

@@ -34,8 +34,38 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from . import lwe, paillier
+from . import chacha20, lwe, paillier
 from .params import Params, Q
+
+# Nonces (domain tags) of the ChaCha20 expansions: the ASCII tag, zero-padded to 12 bytes.
+NONCE_A = b"A" + bytes(11)
+NONCE_CKR = b"ckr" + bytes(9)
+
+
+def expand_matrix(key: bytes, rows: int, cols: int, nonce: bytes = NONCE_A) -> np.ndarray:
+    """The public matrix A (rows x cols u32) from a 32-byte seed: entry (r, c) is keystream
+    word r cols + c (block counter from 0). A is uniform in Z_q^{rows x cols} with q = 2^32,
+    so the words are used as they are (Sec. 2.1.1)."""
+    w = chacha20.keystream_words(key, nonce, 0, rows * cols)
+    return np.array(w, dtype=np.uint32).reshape(rows, cols)
+
+
+def expand_ck_r(key: bytes, pk: paillier.PublicKey, key_bits: int, count: int,
+                nonce: bytes = NONCE_CKR, counter0: int = 0) -> list[int]:
+    """ck_r from a 32-byte seed (Sec. 4.3, offline communication): element i is the
+    integer of 2 key_bits + 128 bits in keystream words [W i, W (i + 1)), W = (2 key_bits +
+    128) / 32, little-endian, reduced mod m^2, so that its distance from uniform on
+    Z_{m^2} is below 2^-128."""
+    W = (2 * key_bits + 128) // 32
+    w = chacha20.keystream_words(key, nonce, counter0, W * count)
+    m2 = pk.m2
+    out = []
+    for i in range(count):
+        v = 0
+        for x in reversed(w[W * i:W * (i + 1)]):
+            v = (v << 32) | x
+        out.append(v % m2)
+    return out
 
 
 # ----------------------------------------------------------------------------- packing

@@ -239,3 +239,28 @@ def test_chacha20_keystream_matches_library():
         ks = enc.update(b"\0" * (4 * nwords))
         want = [int.from_bytes(ks[4 * i:4 * i + 4], "little") for i in range(nwords)]
         assert chacha20.keystream_words(key, nonce, ctr, nwords) == want
+
+
+def test_seed_expansions_match_library():
+    """A and ck_r expanded from seeds: the oracle's words against the `cryptography`
+    package's ChaCha20 byte stream, read independently (little-endian words; 528-byte
+    integers reduced mod m^2)."""
+    ciphers = pytest.importorskip("cryptography.hazmat.primitives.ciphers")
+    from oracle import paillier, zippir
+    key = bytes(range(7, 39))
+
+    def stream(nonce, nbytes, ctr=0):
+        enc = ciphers.Cipher(ciphers.algorithms.ChaCha20(key, ctr.to_bytes(4, "little") + nonce),
+                             mode=None).encryptor()
+        return enc.update(b"\0" * nbytes)
+
+    A = zippir.expand_matrix(key, 5, 7)
+    ks = stream(zippir.NONCE_A, 4 * 35)
+    assert A.dtype == np.uint32 and A.shape == (5, 7)
+    assert A[3, 4] == int.from_bytes(ks[4 * 25:4 * 26], "little")
+    assert A.tobytes() == ks  # row-major little-endian words
+    pk, _ = paillier.keygen(512, 3)
+    ck = zippir.expand_ck_r(key, pk, 512, 6, counter0=5)
+    ks = stream(zippir.NONCE_CKR, 6 * 144, ctr=5)
+    assert ck == [int.from_bytes(ks[144 * i:144 * (i + 1)], "little") % pk.m2 for i in range(6)]
+    assert all(0 <= c < pk.m2 for c in ck)
