@@ -295,6 +295,24 @@ int zp_prg_chacha20(const uint8_t* hKey, const uint8_t* hNonce, uint32_t counter
 int zp_client_powm(const zp_client* cl, const uint32_t* dBase, const uint32_t* hExp,
                    uint32_t expWords, uint32_t* dOut, uint32_t count, void* stream);
 
+/* ck_r expanded from a seed on the GPU: dOut[i] (2L u32, i < count, 16-byte aligned)
+ * = the keystream words [(2L+4) i, (2L+4)(i+1)) of zp_prg_chacha20(hKey, hNonce,
+ * counter0), read as a little-endian integer of 2 key_bits + 128 bits, mod m^2 of the
+ * client: statistically uniform in Z_{m^2} (Sec. 4.3: the client expands ck_r from a
+ * short seed so that only the seed is sent offline). Asynchronous on `stream`.
+ * Errors: ZP_EINVAL (null, misaligned, 32-bit block counter would wrap), ZP_ECUDA. */
+int zp_client_expand_ckr(const zp_client* cl, const uint8_t* hKey, const uint8_t* hNonce,
+                         uint32_t counter0, uint32_t* dOut, uint32_t count, void* stream);
+
+/* Batched Paillier decryption (g = m + 1) on the GPU: dOut[i] (L u32) = Dec(dC[i]) =
+ * ((dC[i]^(lambda mu) mod m^2) - 1) / m for i < count; dC is count x 2L u32, each in
+ * Z*_{m^2}; hLam, hMu: the client's secret lambda and mu = lambda^{-1} mod m (HOST, L
+ * words each, read before the call returns). The client-side decryptions of the protocol
+ * (pt_r = Dec(ck_r) at setup, Dec(k) at extraction). dC, dOut 16-byte aligned.
+ * Asynchronous on `stream`. Errors: ZP_EINVAL, ZP_ENOMEM, ZP_ECUDA. */
+int zp_client_decrypt(const zp_client* cl, const uint32_t* hLam, const uint32_t* hMu,
+                      const uint32_t* dC, uint32_t* dOut, uint32_t count, void* stream);
+
 /* Failure-detection self-test: launches one kernel whose mbarrier wait nothing
  * satisfies, bounded by `cycles` SM clock cycles (at most 2^32, about 2 s). When the wait
  * gives up, the kernel sets bit 0x4 (a timeout outside the answer and product kernels) of

@@ -32,6 +32,7 @@ EXPORTS = [
     "zp_device_status", "zp_kernel_launches", "zp_set_option", "zp_answer_noalloc",
     "zp_compress_products", "zp_compress_finish", "zp_get_option", "zp_client_hint", "zp_combine",
     "zp_db_prepare_rns", "zp_selftest_wait", "zp_autotune", "zp_prg_chacha20", "zp_client_powm",
+    "zp_client_expand_ckr", "zp_client_decrypt",
 ]
 
 
@@ -90,6 +91,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "zp_autotune": (i32, [vp, vp, ctypes.POINTER(ctypes.c_int64)]),
         "zp_prg_chacha20": (i32, [vp, vp, u32, vp, u64, vp]),
         "zp_client_powm": (i32, [vp, vp, vp, u32, vp, u32, vp]),
+        "zp_client_expand_ckr": (i32, [vp, vp, vp, u32, vp, u32, vp]),
+        "zp_client_decrypt": (i32, [vp, vp, vp, vp, vp, u32, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -368,6 +371,38 @@ class Client:
         e = np.array([(int(exponent) >> (32 * i)) & 0xFFFFFFFF for i in range(ew)], dtype=np.uint32)
         _check(load_library().zp_client_powm(self.handle, _ptr(bases), e.ctypes.data, ew, _ptr(out),
                                              count, _stream(stream)))
+        return out
+
+    def expand_ckr(self, key: bytes, count: int, nonce: bytes = b"ckr" + bytes(9), counter0: int = 0,
+                   out=None, stream=None):
+        """ck_r[i] for i < count from a 32-byte seed (zp_client_expand_ckr): (count, 2L) int32."""
+        import torch
+        if len(key) != 32 or len(nonce) != 12:
+            raise ValueError("ChaCha20 takes a 32-byte key and a 12-byte nonce")
+        if out is None:
+            out = torch.empty((count, 2 * self.ctx.L), dtype=torch.int32,
+                              device=torch.device("cuda", self.ctx.device))
+        _need(out, "i32", count * 2 * self.ctx.L, "out")
+        kb = ctypes.create_string_buffer(bytes(key), 32)
+        nb = ctypes.create_string_buffer(bytes(nonce), 12)
+        _check(load_library().zp_client_expand_ckr(self.handle, kb, nb, int(counter0), _ptr(out), count,
+                                                   _stream(stream)))
+        return out
+
+    def decrypt(self, cts, lam: int, mu: int, out=None, stream=None):
+        """Paillier decryption of a CUDA int32 tensor of (count, 2L) limbs (zp_client_decrypt):
+        (count, L) int32."""
+        import torch
+        count = cts.shape[0]
+        L = self.ctx.L
+        _need(cts, "i32", count * 2 * L, "cts")
+        if out is None:
+            out = torch.empty((count, L), dtype=torch.int32, device=cts.device)
+        _need(out, "i32", count * L, "out")
+        words = lambda v: np.array([(int(v) >> (32 * i)) & 0xFFFFFFFF for i in range(L)], dtype=np.uint32)
+        hl, hm = words(lam), words(mu)
+        _check(load_library().zp_client_decrypt(self.handle, hl.ctypes.data, hm.ctypes.data, _ptr(cts),
+                                                _ptr(out), count, _stream(stream)))
         return out
 
     def close(self):

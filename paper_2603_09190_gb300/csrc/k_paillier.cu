@@ -22,6 +22,7 @@
 // (a_i, u, the shifted word). One normalisation and one conditional subtraction of m^2 at
 // the end give the result below m^2.
 #include "zp_internal.cuh"
+#include "zp_chacha.cuh"
 #include "zp_warpint.cuh"
 
 namespace {
@@ -265,38 +266,144 @@ __global__ void __launch_bounds__(128) k_combine(const uint32_t* __restrict__ k,
   store_lane_words(out + (uint64_t)idx * MW, kv);
 }
 
-// out[i] = base[i]^e mod m^2 for a shared exponent of ew words (left-to-right binary):
-// the core of Paillier's decryption (e = lambda) and of its randomness factor (e = m). One
-// warp per base.
+// An exponent of up to 128 words, passed by value.
 struct PowExp {
   uint32_t w[128];
 };
+
+// y = x^e (both in Montgomery form) by left-to-right binary exponentiation; e = 0 gives
+// the Montgomery form of 1.
+__device__ __forceinline__ void mont_powm(const ModM2& M, const M2Consts& c, const uint32_t (&x)[MWPL],
+                                          const PowExp& e, uint32_t ew, uint32_t (&y)[MWPL]) {
+  int top = -1;  // highest set bit of e (warp-uniform)
+  for (int w = (int)ew - 1; w >= 0 && top < 0; --w)
+    if (e.w[w]) top = 32 * w + 31 - __clz(e.w[w]);
+  if (top < 0) {
+    load_lane_words(c.r1, y);
+    return;
+  }
+#pragma unroll
+  for (int k = 0; k < MWPL; ++k) y[k] = x[k];
+  for (int bit = top - 1; bit >= 0; --bit) {
+    mont_mul(M, y, y, y);
+    if ((e.w[bit >> 5] >> (bit & 31)) & 1u) mont_mul(M, y, x, y);
+  }
+}
+
+// out[i] = base[i]^e mod m^2 for a shared exponent of ew words: the core of Paillier's
+// decryption and of its randomness factor r^m. One warp per base.
 __global__ void __launch_bounds__(128) k_powm(const uint32_t* __restrict__ base, PowExp e,
                                               uint32_t ew, uint32_t count, M2Consts c,
                                               uint32_t* __restrict__ out) {
   const uint32_t idx = blockIdx.x * 4 + (threadIdx.x >> 5);
   if (idx >= count) return;
   const ModM2 M = load_mod(c);
-  int top = -1;  // highest set bit of e (warp-uniform)
-  for (int w = (int)ew - 1; w >= 0 && top < 0; --w)
-    if (e.w[w]) top = 32 * w + 31 - __clz(e.w[w]);
   uint32_t x[MWPL], y[MWPL], r2[MWPL];
   load_lane_words(base + (uint64_t)idx * MW, x);
   load_lane_words(c.r2, r2);
   mont_mul(M, x, r2, x);  // to Montgomery form
-  if (top < 0) {
-    load_lane_words(c.r1, y);  // e = 0: the Montgomery form of 1
-  } else {
-#pragma unroll
-    for (int k = 0; k < MWPL; ++k) y[k] = x[k];
-    for (int bit = top - 1; bit >= 0; --bit) {
-      mont_mul(M, y, y, y);
-      if ((e.w[bit >> 5] >> (bit & 31)) & 1u) mont_mul(M, y, x, y);
-    }
-  }
+  mont_powm(M, c, x, e, ew, y);
   uint32_t one[MWPL] = {lane_id() == 0 ? 1u : 0u, 0u, 0u, 0u};
   mont_mul(M, y, one, y);
   store_lane_words(out + (uint64_t)idx * MW, y);
+}
+
+// Paillier decryption (g = m + 1): with e = lambda mu, v = c^e mod m^2 = 1 + m Dec(c) (c^lambda
+// = 1 + m lambda Dec(c) mod m^2 and lambda mu = 1 mod m), and Dec(c) = (v - 1) / m, an exact
+// division computed as the low L words of (v - 1) m^{-1} mod 2^(32 L) (m is odd and the
+// quotient is below m < 2^(32 L)). One warp per ciphertext; out is count x L words.
+struct MinvArg {
+  uint32_t w[ZP_MAX_L];  // m^{-1} mod 2^(32 L)
+};
+__global__ void __launch_bounds__(128) k_decrypt(const uint32_t* __restrict__ cts, PowExp e,
+                                                 uint32_t ew, MinvArg minv, uint32_t count,
+                                                 M2Consts c, uint32_t* __restrict__ out) {
+  __shared__ uint32_t sv[4][ZP_MAX_L];
+  const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
+  const uint32_t idx = blockIdx.x * 4 + warp;
+  if (idx >= count) return;
+  const ModM2 M = load_mod(c);
+  uint32_t x[MWPL], y[MWPL], r2[MWPL];
+  load_lane_words(cts + (uint64_t)idx * MW, x);
+  load_lane_words(c.r2, r2);
+  mont_mul(M, x, r2, x);
+  mont_powm(M, c, x, e, ew, y);
+  uint32_t one[MWPL] = {lane == 0 ? 1u : 0u, 0u, 0u, 0u};
+  mont_mul(M, y, one, y);  // v
+  warp_sub<MWPL>(y, one);  // v - 1
+  if (lane < ZP_MAX_L / MWPL) {
+#pragma unroll
+    for (int k = 0; k < MWPL; ++k) sv[warp][lane * MWPL + k] = y[k];
+  }
+  __syncwarp();
+  // word xw of the product: sum_{i + j = xw} v_i minv_j; the high halves carry into word xw + 1
+  uint64_t acc[MWPL] = {0, 0, 0, 0}, hi[MWPL] = {0, 0, 0, 0};
+#pragma unroll
+  for (int kk = 0; kk < MWPL; ++kk) {
+    const int xw = (int)lane * MWPL + kk;
+    if (xw < ZP_MAX_L)
+      for (int i = 0; i <= xw; ++i) {
+        const uint64_t p = (uint64_t)sv[warp][i] * minv.w[xw - i];
+        acc[kk] += (uint32_t)p;
+        hi[kk] += p >> 32;
+      }
+  }
+  acc[1] += hi[0];
+  acc[2] += hi[1];
+  acc[3] += hi[2];
+  const uint64_t sp_in = __shfl_up_sync(0xffffffffu, hi[3], 1);
+  if (lane > 0) acc[0] += sp_in;
+  uint32_t q[MWPL];
+  warp_normalize<MWPL>(acc, q);  // words >= L are discarded (mod 2^(32 L))
+  if (lane < ZP_MAX_L / MWPL)
+    *reinterpret_cast<uint4*>(out + (uint64_t)idx * ZP_MAX_L + MWPL * lane) = make_uint4(q[0], q[1], q[2], q[3]);
+}
+
+// ck_r[i] = (the 2L + 4 keystream words [(2L + 4) i, (2L + 4)(i + 1)) of ChaCha20, read as a
+// little-endian integer) mod m^2: a value of 2 key_bits + 128 bits whose residue is
+// statistically uniform in Z_{m^2}. One warp per element: lanes 0..8 make the (at most 9)
+// blocks that cover the element's words, then x = x_lo + 2^(64 L) x_hi is reduced as
+// (x_lo + (x_hi R mod m^2)) mod m^2, x_hi R mod m^2 = MontMul(x_hi, R^2).
+constexpr int CKR_W = 2 * ZP_MAX_L + 4;
+__global__ void __launch_bounds__(128) k_expand_ckr(ChachaKey key, uint32_t counter0,
+                                                    uint32_t count, M2Consts c,
+                                                    uint32_t* __restrict__ out) {
+  __shared__ uint32_t ks[4][9 * 16];
+  const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
+  const uint32_t idx = blockIdx.x * 4 + warp;
+  if (idx >= count) return;
+  const uint64_t w0 = (uint64_t)idx * CKR_W;
+  const uint32_t o = (uint32_t)(w0 & 15u);
+  if (lane < 9) {
+    uint32_t b[16];
+    chacha20_block(key, counter0 + (uint32_t)(w0 >> 4) + lane, b);
+#pragma unroll
+    for (int t = 0; t < 16; ++t) ks[warp][16 * lane + t] = b[t];
+  }
+  __syncwarp();
+  uint32_t xl[MWPL], xh[MWPL] = {0, 0, 0, 0}, r2[MWPL];
+#pragma unroll
+  for (int k = 0; k < MWPL; ++k) xl[k] = ks[warp][o + MWPL * lane + k];
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) xh[k] = ks[warp][o + MW + k];
+  }
+  const ModM2 M = load_mod(c);
+  load_lane_words(c.r2, r2);
+  mont_mul(M, xh, r2, xh);  // x_hi R mod m^2
+  uint64_t acc[MWPL];
+#pragma unroll
+  for (int k = 0; k < MWPL; ++k) acc[k] = (uint64_t)xl[k] + xh[k];
+  uint32_t w[MWPL];
+  uint32_t top = warp_normalize_top<MWPL>(acc, w);
+  // the sum is below 2^(64 L) + m^2 <= 5 m^2 (m^2 >= 2^(64 L - 2)): at most four subtractions
+  for (int it = 0; it < 5; ++it) {
+    const bool ge = warp_geq<MWPL>(w, M.n);
+    if (!top && !ge) break;
+    warp_sub<MWPL>(w, M.n);
+    top = top && ge;
+  }
+  store_lane_words(out + (uint64_t)idx * MW, w);
 }
 
 }  // namespace
@@ -372,6 +479,39 @@ extern "C" int zp_client_powm(const zp_client* cl, const uint32_t* dBase, const 
   cl->ctx->launches++;
   k_powm<<<(count + 3) / 4, 128, 0, static_cast<cudaStream_t>(stream)>>>(dBase, e, expWords, count,
                                                                           client_consts(cl), dOut);
+  ZP_CUDA(cudaGetLastError());
+  return ZP_OK;
+}
+
+int zp_launch_decrypt(const zp_client* cl, const uint32_t* e, uint32_t ew, const uint32_t* minv,
+                      const uint32_t* dC, uint32_t* dOut, uint32_t count, cudaStream_t st) {
+  PowExp pe{};
+  for (uint32_t i = 0; i < ew; ++i) pe.w[i] = e[i];
+  MinvArg mi;
+  for (int i = 0; i < ZP_MAX_L; ++i) mi.w[i] = minv[i];
+  zp_clear_pending_error();
+  cl->ctx->launches++;
+  k_decrypt<<<(count + 3) / 4, 128, 0, st>>>(dC, pe, ew, mi, count, client_consts(cl), dOut);
+  ZP_CUDA(cudaGetLastError());
+  return ZP_OK;
+}
+
+extern "C" int zp_client_expand_ckr(const zp_client* cl, const uint8_t* hKey, const uint8_t* hNonce,
+                                    uint32_t counter0, uint32_t* dOut, uint32_t count, void* stream) {
+  if (!cl || !hKey || !hNonce || (!dOut && count))
+    return zp_set_error(ZP_EINVAL, "zp_client_expand_ckr: null argument");
+  if (reinterpret_cast<uintptr_t>(dOut) & 15u)
+    return zp_set_error(ZP_EINVAL, "zp_client_expand_ckr: dOut must be 16-byte aligned");
+  if (count == 0) return ZP_OK;
+  const uint64_t last_block = ((uint64_t)count * CKR_W - 1) / 16 + 1;  // lanes may make one more
+  if ((uint64_t)counter0 + last_block > 0xFFFFFFFFull)
+    return zp_set_error(ZP_EINVAL, "zp_client_expand_ckr: the 32-bit block counter would wrap");
+  ZP_CUDA(cudaSetDevice(cl->device));
+  const ChachaKey k = chacha_key_from_bytes(hKey, hNonce);
+  zp_clear_pending_error();
+  cl->ctx->launches++;
+  k_expand_ckr<<<(count + 3) / 4, 128, 0, static_cast<cudaStream_t>(stream)>>>(k, counter0, count,
+                                                                               client_consts(cl), dOut);
   ZP_CUDA(cudaGetLastError());
   return ZP_OK;
 }

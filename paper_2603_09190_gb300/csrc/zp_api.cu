@@ -824,6 +824,7 @@ extern "C" int zp_register_client(zp_ctx* c, const uint32_t* hM, uint32_t L, zp_
     cl->L = L;
     cl->d_m = cl->d_mu = cl->d_m2 = cl->d_r1 = cl->d_r2 = cl->d_mkm = nullptr;
     cl->m2inv = m2inv;
+    cl->h_m = m;
     auto free_all = [cl]() {
       for (uint32_t* p : {cl->d_m, cl->d_mu, cl->d_m2, cl->d_r1, cl->d_r2, cl->d_mkm})
         if (p) cudaFree(p);
@@ -1122,6 +1123,45 @@ extern "C" int zp_db_prepare_rns(zp_db* db, void* stream) {
   if (db->ctx->P.n > 1024) return zp_set_error(ZP_EUNSUPPORTED, "zp_db_prepare_rns: needs n <= 1024");
   ZP_CUDA(cudaSetDevice(db->ctx->device));
   return zp_ensure_rns(db, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int zp_client_decrypt(const zp_client* cl, const uint32_t* hLam, const uint32_t* hMu,
+                                 const uint32_t* dC, uint32_t* dOut, uint32_t count, void* stream) {
+  try {
+    if (!cl || !hLam || !hMu || ((!dC || !dOut) && count))
+      return zp_set_error(ZP_EINVAL, "zp_client_decrypt: null argument");
+    if ((reinterpret_cast<uintptr_t>(dC) | reinterpret_cast<uintptr_t>(dOut)) & 15u)
+      return zp_set_error(ZP_EINVAL, "zp_client_decrypt: dC and dOut must be 16-byte aligned");
+    if (count == 0) return ZP_OK;
+    const uint32_t L = cl->L;
+    const std::vector<uint32_t>& m = cl->h_m;
+    // e = lambda mu (< m^2: 2L words)
+    std::vector<uint32_t> e = big_mul(std::vector<uint32_t>(hLam, hLam + L),
+                                      std::vector<uint32_t>(hMu, hMu + L));
+    while (e.size() > 1 && e.back() == 0) e.pop_back();
+    // m^{-1} mod 2^(32 L) by Newton's iteration x <- x (2 - m x), from the inverse mod 2^32
+    std::vector<uint32_t> x(L, 0);
+    uint32_t inv = m[0];
+    for (int it = 0; it < 5; ++it) inv *= 2u - m[0] * inv;
+    x[0] = inv;
+    for (uint32_t prec = 32; prec < 32 * L; prec *= 2) {
+      std::vector<uint32_t> t = big_mul(m, x);
+      t.resize(L);
+      uint64_t br = 0;  // t = 2 - t mod 2^(32 L)
+      for (uint32_t w = 0; w < L; ++w) {
+        const uint64_t s = (uint64_t)(w == 0 ? 2u : 0u) - t[w] - br;
+        t[w] = (uint32_t)s;
+        br = (s >> 63) & 1u;
+      }
+      x = big_mul(x, t);
+      x.resize(L);
+    }
+    ZP_CUDA(cudaSetDevice(cl->device));
+    return zp_launch_decrypt(cl, e.data(), (uint32_t)e.size(), x.data(), dC, dOut, count,
+                             static_cast<cudaStream_t>(stream));
+  } catch (const std::bad_alloc&) {
+    return zp_set_error(ZP_ENOMEM, "zp_client_decrypt: host allocation");
+  }
 }
 
 extern "C" int zp_combine(zp_db* db, zp_client* const* clients, const uint32_t* dK, const uint32_t* dT,

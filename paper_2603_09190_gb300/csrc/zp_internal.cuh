@@ -64,6 +64,7 @@ struct zp_client {
   zp_ctx* ctx;
   int device;
   uint32_t L;
+  std::vector<uint32_t> h_m;  // L limbs (host copy)
   uint32_t* d_m;   // L limbs
   uint32_t* d_mu;  // L+1 limbs: floor(2^(64 L) / m)  (Barrett constant)
   // Montgomery arithmetic mod m^2 (R = 2^(64 L)): per-client hint k, combined response
@@ -157,6 +158,10 @@ int zp_launch_client_hint(zp_db* db, const zp_client* cl, const uint32_t* dCkr, 
                           const uint32_t* dRows, uint32_t nprows, cudaStream_t st);
 int zp_launch_combine(zp_db* db, zp_client* const* clients, const uint32_t* dK, const uint32_t* dT,
                       uint32_t B, uint32_t* dOut, cudaStream_t st);
+// Paillier decryption of count ciphertexts with the exponent e = lambda mu (ew words) and
+// minv = m^{-1} mod 2^(32 L) (L words), both host arrays (k_paillier.cu)
+int zp_launch_decrypt(const zp_client* cl, const uint32_t* e, uint32_t ew, const uint32_t* minv,
+                      const uint32_t* dC, uint32_t* dOut, uint32_t count, cudaStream_t st);
 // RNS compression (k_rns.cu, k_gemm_tc.cu): the residue planes of H' for the listed packed
 // rows (dRows device, NULL = all), the B operand of ck_o residues, and the residue product
 // X[b][r'][k] = H'[r', :] . cko[b] mod p_k

@@ -98,3 +98,94 @@ def test_powm_invalid_arguments(zp):
         gcl.powm(b, 1 << (32 * 128))  # 129 exponent words
     with pytest.raises(zp.ZipPIRError):
         gcl.powm(torch.empty(2 * 2 * ctx.L + 1, dtype=torch.int32, device="cuda")[1:].view(2, -1), 5)
+
+
+@pytest.mark.parametrize("count,counter0", [(1, 0), (5, 3), (64, 1000)])
+def test_expand_ckr_parity(zp, count, counter0):
+    """ck_r from a seed: consecutive elements start at every word offset within a block
+    (132 i mod 16 in {0, 4, 8, 12})."""
+    cl, ctx, gcl = _client(zp, 600 + count)
+    key = bytes(range(count, count + 32))
+    got = synth.limbs_to_ints(gcl.expand_ckr(key, count, counter0=counter0).cpu().numpy().view(np.uint32))
+    assert got == zippir.expand_ck_r(key, cl.pk, 2048, count, counter0=counter0)
+
+
+def test_expand_ckr_small_modulus_needs_four_subtractions(zp):
+    """m = 2^2047 + 1 (odd, 2048 bits, m^2 just above 2^4094): the reduction of a value
+    below 2^4096 + m^2 takes up to four subtractions of m^2; powm under the same m."""
+    from oracle import paillier as pl
+    m = (1 << 2047) + 1
+    ctx = zp.Context(0, n=8, key_bits=2048)
+    gcl = ctx.register_client(m)
+    key = bytes(32)
+    got = synth.limbs_to_ints(gcl.expand_ckr(key, 40).cpu().numpy().view(np.uint32))
+    assert got == zippir.expand_ck_r(key, pl.PublicKey(m), 2048, 40)
+    b = got[:8]
+    out = synth.limbs_to_ints(gcl.powm(_dev(b, ctx.L), 65537).cpu().numpy().view(np.uint32))
+    assert out == [pow(x, 65537, m * m) for x in b]
+
+
+def test_expand_ckr_rejects_counter_wrap(zp):
+    cl, ctx, gcl = _client(zp, 3)
+    with pytest.raises(zp.ZipPIRError):
+        gcl.expand_ckr(bytes(32), 16, counter0=2**32 - 100)  # needs 132 blocks
+
+
+def test_decrypt_parity(zp):
+    """Dec on the GPU equals the oracle's for random plaintexts, 0, 1 and m - 1, and for
+    the client's ck_r (pt_r = Dec(ck_r))."""
+    P = Params(n=8, key_bits=2048, secret="uniform")
+    cl = zippir.setup(P, 900, sample_ck_r=True)
+    ctx = zp.Context(0, n=8, key_bits=2048)
+    gcl = ctx.register_client(cl.pk.m)
+    m = cl.pk.m
+    g = np.random.default_rng(900)
+    xs = [0, 1, m - 1] + [int.from_bytes(g.bytes(256), "little") % m for _ in range(9)]
+    cs = [paillier.encrypt(cl.pk, x, int.from_bytes(g.bytes(256), "little") % (m - 2) + 2) for x in xs]
+    got = synth.limbs_to_ints(gcl.decrypt(_dev(cs, ctx.L), cl.sk.lam, cl.sk.mu).cpu().numpy().view(np.uint32))
+    assert got == xs
+    pt = synth.limbs_to_ints(gcl.decrypt(_dev(cl.ck_r, ctx.L), cl.sk.lam, cl.sk.mu).cpu().numpy().view(np.uint32))
+    assert pt == cl.pt_r
+
+
+def test_seeded_client_end_to_end(zp):
+    """The whole client side from seeds on the GPU: A from its seed feeds the hint, ck_r
+    from its seed feeds k, Dec(k) on the GPU equals H' pt_r mod m (the homomorphic
+    identity of the hint), with pt_r = Dec(ck_r) also from the GPU; all against the oracle."""
+    from oracle import lwe
+    R, C, n = 60, 48, 8
+    P = Params(n=n, key_bits=2048, secret="uniform")
+    D = synth.database(R, C, 5)
+    keyA, keyC = bytes(range(32)), bytes(range(32, 64))
+    A = zippir.expand_matrix(keyA, C, n)
+    cl0 = zippir.setup(P, 55, sample_ck_r=False)
+    ctx = zp.Context(0, n=n, key_bits=2048)
+    gcl = ctx.register_client(cl0.pk.m)
+    dA = torch.empty((C, n), dtype=torch.int32, device="cuda")
+    zp.prg_chacha20(keyA, zippir.NONCE_A, 0, dA)
+    assert np.array_equal(dA.cpu().numpy().view(np.uint32), A)
+    ld = zp.db_pitch(C)
+    buf = np.zeros((R, ld), dtype=np.uint8)
+    buf[:, :C] = D
+    dD = torch.from_numpy(buf).cuda()
+    db = zp.Database(ctx, dD, R, C, ld)
+    db.gen_hint(dA)
+    ckr = gcl.expand_ckr(keyC, n)
+    ck_r = zippir.expand_ck_r(keyC, cl0.pk, 2048, n)
+    pt_r = synth.limbs_to_ints(gcl.decrypt(ckr, cl0.sk.lam, cl0.sk.mu).cpu().numpy().view(np.uint32))
+    assert pt_r == [paillier.decrypt(cl0.sk, c) for c in ck_r]
+    k = db.client_hint(gcl, ckr)
+    deck = synth.limbs_to_ints(gcl.decrypt(k, cl0.sk.lam, cl0.sk.mu).cpu().numpy().view(np.uint32))
+    cl = zippir.Client(P, cl0.pk, cl0.sk, ck_r, pt_r)
+    Hn = lwe.hint_neg(D, A)
+    assert deck == zippir.dec_k_shortcut(cl, Hn, range(db.d1p))
+
+
+def test_decrypt_invalid_arguments(zp):
+    cl, ctx, gcl = _client(zp, 10)
+    c = _dev([5, 6], ctx.L)
+    with pytest.raises(zp.ZipPIRError):
+        gcl.decrypt(torch.empty(2 * 2 * ctx.L + 1, dtype=torch.int32, device="cuda")[1:].view(2, -1),
+                    cl.sk.lam, cl.sk.mu)
+    out = gcl.decrypt(c[:0], cl.sk.lam, cl.sk.mu)  # count 0: nothing to do
+    assert out.shape[0] == 0
