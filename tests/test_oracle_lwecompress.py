@@ -1,0 +1,154 @@
+"""Pins of the LWE/RLWE compression oracle (Sec. 3, App. B, packed-key appendix) against
+what the paper's theorems fix: a compressed ciphertext decrypts to the LWE (or RLWE
+coefficient) decryption of what it compressed, the batched form to every slot, the
+packed key to the same message; the fast form equals the plain one; the negacyclic
+product equals a polynomial product folded by X^N = -1 computed by numpy."""
+import numpy as np
+import pytest
+
+from oracle import lwecompress as lc
+from oracle import paillier
+
+Q64 = 1 << 64
+Q27 = 134217689  # a prime below 2^27 (checked below)
+
+
+@pytest.fixture(scope="module")
+def keys():
+    return paillier.keygen(512, 77)
+
+
+def _cts(s, q, p, count, g):
+    mus = [int(g.integers(0, p)) for _ in range(count)]
+    return mus, [lc.lwe_encrypt(s, mu, q, p, g) for mu in mus]
+
+
+def test_q27_is_prime():
+    sympy = pytest.importorskip("sympy")
+    assert sympy.isprime(Q27) and Q27 < 2 ** 27
+
+
+@pytest.mark.parametrize("n,q,p,binary", [(16, Q64, 16, False), (24, 1 << 11, 4, False),
+                                          (12, Q27, 8, True), (20, Q64, 2, True)])
+def test_lwe_compress_correct(keys, n, q, p, binary):
+    """Theorem "Correctness" (Sec. 3.1): Dec(x) = b + sum_i ((q - a_i) mod q) s_i < q + n q^2
+    exactly, its residue mod q is the LWE phase, and the modified decryption gives the
+    message."""
+    pk, sk = keys
+    g = np.random.default_rng(n)
+    s = lc.lwe_keygen(n, q, binary, g)
+    ck = lc.compression_key(pk, s, g)
+    mus, cts = _cts(s, q, p, 3, g)
+    for mu, (a, b) in zip(mus, cts):
+        x = lc.lwe_compress(pk, ck, a, b, q)
+        dec = paillier.decrypt(sk, x)
+        assert dec == b + sum(((q - ai) % q) * si for ai, si in zip(a, s))
+        assert dec < lc.gamma_of(q, n, binary)
+        assert dec % q == lc.lwe_phase(s, a, b, q)
+        assert lc.modified_lwe_decrypt(sk, x, q, p) == lc.lwe_decrypt(s, a, b, q, p) == mu
+
+
+def test_fast_equals_plain_compress(keys):
+    """Algorithm "Batch compression ... using precomputed powers": the expanded key gives
+    the same ciphertext, bit for bit; a = 0 (exponent 0) included."""
+    pk, sk = keys
+    g = np.random.default_rng(5)
+    n, q = 10, Q64
+    s = lc.lwe_keygen(n, q, False, g)
+    ck = lc.compression_key(pk, s, g)
+    eck = lc.expand_compression_key(pk, ck, 64)
+    assert eck[5][3] == pow(ck[3], 32, pk.m2)
+    _, cts = _cts(s, q, 16, 2, g)
+    cts.append(([0] * n, 7))
+    for a, b in cts:
+        assert lc.fast_lwe_compress(pk, eck, a, b, q) == lc.lwe_compress(pk, ck, a, b, q)
+
+
+@pytest.mark.parametrize("binary", [False, True])
+def test_batched_compress_correct(keys, binary):
+    """Theorem "Correctness" (Sec. 3.3): with gamma^ell < m every slot decrypts; ell is the
+    largest such count."""
+    pk, sk = keys
+    g = np.random.default_rng(9 + binary)
+    n, q, p = 16, 1 << 32, 16
+    gamma = lc.gamma_of(q, n, binary)
+    ell = lc.max_slots(pk.m, gamma)
+    assert gamma ** ell < pk.m <= gamma ** (ell + 1)
+    s = lc.lwe_keygen(n, q, binary, g)
+    ck = lc.compression_key(pk, s, g)
+    mus, cts = _cts(s, q, p, ell, g)
+    x = lc.batched_lwe_compress(pk, ck, cts, q, gamma)
+    assert lc.modified_batched_decrypt(sk, x, q, p, gamma, ell) == mus
+
+
+def test_negacyclic_product_matches_numpy():
+    g = np.random.default_rng(1)
+    N, q = 16, Q27
+    A = [int(v) for v in g.integers(0, q, size=N)]
+    S = [int(v) for v in g.integers(0, q, size=N)]
+    full = np.convolve(np.array(A, dtype=object), np.array(S, dtype=object))
+    folded = [(full[k] - (full[k + N] if k + N < len(full) else 0)) % q for k in range(N)]
+    assert lc.negacyclic_mul(A, S, q) == folded
+    # X^(N-1) * X = X^N = -1
+    e1 = [0] * N
+    e1[1] = 1
+    top = [0] * N
+    top[N - 1] = 1
+    assert lc.negacyclic_mul(top, e1, q) == [q - 1] + [0] * (N - 1)
+
+
+@pytest.mark.parametrize("q,binary", [(Q27, False), (Q64, True)])
+def test_rlwe_coefficient_compress_correct(keys, q, binary):
+    """Theorem "Correctness" (App. B): the compressed coefficient k decrypts to coefficient
+    k of the RLWE decryption (first, middle and last coefficient)."""
+    pk, sk = keys
+    g = np.random.default_rng(3)
+    N, p = 16, 8
+    S = lc.lwe_keygen(N, q, binary, g)
+    ck = lc.compression_key(pk, S, g)
+    mu = [int(v) for v in g.integers(0, p, size=N)]
+    A, B = lc.rlwe_encrypt(S, mu, q, p, g)
+    assert lc.rlwe_decrypt(S, A, B, q, p) == mu
+    for k in (0, 5, N - 1):
+        x = lc.rlwe_compress_coefficient(pk, ck, A, B, k, q)
+        assert lc.modified_lwe_decrypt(sk, x, q, p) == mu[k]
+
+
+@pytest.mark.parametrize("binary", [False, True])
+def test_packed_key_correct(keys, binary):
+    """Packed compression keys: unpacking and compressing, then the packed-key decryption,
+    gives the message; t is the largest count with delta^(2t) <= m, and a ragged last
+    packed ciphertext (n not a multiple of t) works."""
+    pk, sk = keys
+    g = np.random.default_rng(21 + binary)
+    q, p = 1 << 16, 16
+    n = 7
+    delta = lc.gamma_of(q, n, binary)
+    t = lc.packed_slots(pk.m, delta)
+    assert t >= 2 and delta ** (2 * t) <= pk.m < delta ** (2 * t + 2)
+    s = lc.lwe_keygen(n, q, binary, g)
+    pck = lc.generate_packed_key(pk, s, delta, t, g)
+    assert len(pck) == -(-n // t)
+    ck = lc.unpack_compression_key(pk, pck, delta, t, n)
+    mus, cts = _cts(s, q, p, 3, g)
+    for mu, (a, b) in zip(mus, cts):
+        x = lc.lwe_compress(pk, ck, a, b, q)
+        assert lc.modified_lwe_decrypt_packed(sk, x, q, p, delta, t) == mu
+
+
+def test_planted_sign_mistake_fails(keys):
+    """Compressing with a[i] instead of (q - a[i]) mod q gives b + <a, s>, which does not
+    decrypt (the pins above would catch the dropped negation)."""
+    pk, sk = keys
+    g = np.random.default_rng(30)
+    n, q, p = 16, Q64, 16
+    s = lc.lwe_keygen(n, q, False, g)
+    ck = lc.compression_key(pk, s, g)
+    mus, cts = _cts(s, q, p, 6, g)
+    wrong = 0
+    for mu, (a, b) in zip(mus, cts):
+        x = lc.trivial(pk, b)
+        for ai, c in zip(a, ck):
+            x = paillier.add(pk, x, paillier.smul(pk, ai, c))
+        wrong += lc.modified_lwe_decrypt(sk, x, q, p) != mu
+    assert wrong >= 4
