@@ -63,6 +63,7 @@ typedef struct zp_params {
 typedef struct zp_ctx zp_ctx;       /* one device, one parameter set */
 typedef struct zp_db zp_db;         /* one resident database and its hint */
 typedef struct zp_client zp_client; /* one client's public Paillier modulus and constants */
+typedef struct zp_lc zp_lc;         /* standalone LWE compression: a Paillier modulus and an expanded key */
 
 /* Library ABI version (major*10000 + minor*100 + patch). */
 int zp_version(void);
@@ -320,6 +321,61 @@ int zp_client_decrypt(const zp_client* cl, const uint32_t* hLam, const uint32_t*
  * a wait that cannot complete costs its limit and an error code, never a hung or faulted
  * device. The context stays usable. Asynchronous on `stream`. Errors: ZP_EINVAL, ZP_ECUDA. */
 int zp_selftest_wait(zp_ctx* ctx, uint64_t cycles, void* stream);
+
+/* ---- Standalone compression of LWE ciphertexts and RLWE coefficients (Sec. 3, App. B) ----
+ *
+ * A Paillier modulus m (g = m + 1) of 2048 or 3072 bits and a compression key
+ * ck[i] = Enc(s[i]) (i < n) of an LWE (or RLWE) secret s. LWECompress of ct = (a, b)
+ * (Algorithm "LWE compression") is
+ *     x = (1 + b m) prod_i ck[i]^{(q - a[i]) mod q}  mod m^2,
+ * so that Dec(x) = b + sum_i ((q - a[i]) mod q) s[i] < q + n q^2 and Dec(x) mod q is the LWE
+ * phase b - <a, s> mod q; batched compression (Algorithm "Batch Compression") of ell
+ * ciphertexts is x = prod_j x_j^{gamma^j} (gamma = q + n q^2, or q + n q for binary s, and
+ * gamma^ell < m). Integers mod q are u64 (q <= 2^64; q = 0 stands for 2^64), each below q;
+ * Paillier ciphertexts are 2L u32 little-endian words (L = key_bits / 32), 16-byte aligned.
+ * Deterministic: the result is bit-identical to the definition. */
+
+/* m: HOST, key_bits / 32 words, odd, exactly key_bits bits (2048 or 3072). Runs on `device`.
+ * Errors: ZP_EINVAL, ZP_EUNSUPPORTED (other key sizes), ZP_ENOMEM, ZP_ECUDA. */
+int zp_lc_create(int device, uint32_t key_bits, const uint32_t* hM, zp_lc** out);
+int zp_lc_destroy(zp_lc* lc);
+
+/* Expanded key (Algorithm "Batch compression ... using precomputed powers"): from dCk (n x 2L
+ * u32, each < m^2, device) the library keeps eck[i][k] = ck[i]^{2^k} mod m^2 for k < T (n T
+ * 2L words of device memory, owned by lc). T must cover the exponents used: bits(q - 1)
+ * for one ciphertext at a time, bits((q - 1) sum_{j < ell} gamma^j) (<= key_bits) for the
+ * folded batched form. dCk may be freed once the call's stream work is done.
+ * Errors: ZP_EINVAL (n = 0 or > 2^20, T = 0 or > key_bits, misaligned), ZP_ENOMEM, ZP_ECUDA. */
+int zp_lc_set_key(zp_lc* lc, const uint32_t* dCk, uint32_t n, uint32_t T, void* stream);
+
+/* Packed compression keys (appendix "LWECompress Using Packed Compression Keys"): from
+ * ceil(n / t) packed ciphertexts dPck, dCk[i t + j] = dPck[i]^{delta^(t-1-j)} mod m^2 for
+ * i t + j < n (by repeated exponentiation by delta). delta: HOST, deltaWords (1..8) words,
+ * at least 2. dCk: n x 2L u32. Errors: ZP_EINVAL, ZP_ECUDA. */
+int zp_lc_unpack_key(zp_lc* lc, const uint32_t* dPck, uint32_t n, uint32_t t,
+                     const uint32_t* hDelta, uint32_t deltaWords, uint32_t* dCk, void* stream);
+
+/* Compression of count ciphertexts: dA count x n u64 (row j = a of ciphertext j), dB count
+ * u64, both device. ell = 1: dX[j] = LWECompress(ck, ct_j) (count x 2L u32). ell > 1: the
+ * ciphertexts in groups of ell consecutive ones (the last group may be shorter), dX[g] =
+ * prod_{j < ell_g} x_{g ell + j}^{gamma^j} (ceil(count / ell) x 2L u32); gamma: HOST,
+ * gammaWords (1..8) words, > q - 1. mode: 0 auto, 1 Horner (per-ciphertext products, then
+ * X <- X^gamma x_j per group), 2 folded (one exponent sum_j gamma^j e_j per base and group;
+ * needs T >= its bits); both give the same bits. Requires (q - 1) sum_{j<ell} gamma^j < m.
+ * Asynchronous on `stream` (scratch held by lc). Errors: ZP_EINVAL, ZP_ESTATE (no key),
+ * ZP_ENOMEM, ZP_ECUDA. */
+int zp_lc_compress(zp_lc* lc, const uint64_t* dA, const uint64_t* dB, uint32_t count, uint64_t q,
+                   uint32_t ell, const uint32_t* hGamma, uint32_t gammaWords, int mode, uint32_t* dX,
+                   void* stream);
+
+/* Sample extraction of RLWE coefficients (App. B, Algorithm "Compressing Extracted RLWE
+ * Coefficient"): for the RLWE ciphertext (A, B) over Z_q[X]/(X^N + 1) (dA, dB: N u64,
+ * device) and coefficient indices hK[c] < N (HOST, count <= 65535), the LWE ciphertext
+ * dAout[c] (N u64), dBout[c] = B[k] with a'[i] = A[k - i] (i <= k) and (q - A[N + k - i]) mod q
+ * (i > k), whose compression by zp_lc_compress is RLWECompressCoefficient(ck, C, k).
+ * Errors: ZP_EINVAL (k >= N, count too large), ZP_ENOMEM, ZP_ECUDA. */
+int zp_lc_rlwe_extract(zp_lc* lc, const uint64_t* dA, const uint64_t* dB, uint32_t N, uint64_t q,
+                       const uint32_t* hK, uint32_t count, uint64_t* dAout, uint64_t* dBout, void* stream);
 
 #ifdef __cplusplus
 }

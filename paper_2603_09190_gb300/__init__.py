@@ -33,6 +33,8 @@ EXPORTS = [
     "zp_compress_products", "zp_compress_finish", "zp_get_option", "zp_client_hint", "zp_combine",
     "zp_db_prepare_rns", "zp_selftest_wait", "zp_autotune", "zp_prg_chacha20", "zp_client_powm",
     "zp_client_expand_ckr", "zp_client_decrypt",
+    "zp_lc_create", "zp_lc_destroy", "zp_lc_set_key", "zp_lc_unpack_key", "zp_lc_compress",
+    "zp_lc_rlwe_extract",
 ]
 
 
@@ -93,6 +95,12 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "zp_client_powm": (i32, [vp, vp, vp, u32, vp, u32, vp]),
         "zp_client_expand_ckr": (i32, [vp, vp, vp, u32, vp, u32, vp]),
         "zp_client_decrypt": (i32, [vp, vp, vp, vp, vp, u32, vp]),
+        "zp_lc_create": (i32, [ctypes.c_int, u32, vp, ctypes.POINTER(vp)]),
+        "zp_lc_destroy": (i32, [vp]),
+        "zp_lc_set_key": (i32, [vp, vp, u32, u32, vp]),
+        "zp_lc_unpack_key": (i32, [vp, vp, u32, u32, vp, u32, vp, vp]),
+        "zp_lc_compress": (i32, [vp, vp, vp, u32, u64, u32, vp, u32, ctypes.c_int, vp, vp]),
+        "zp_lc_rlwe_extract": (i32, [vp, vp, vp, u32, u64, vp, u32, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -133,7 +141,7 @@ def _stream(stream) -> int | None:
 
 def _need(t, dtype_name: str, numel: int | None = None, what: str = "tensor"):
     import torch
-    dt = {"u8": torch.uint8, "i32": torch.int32}[dtype_name]
+    dt = {"u8": torch.uint8, "i32": torch.int32, "i64": torch.int64}[dtype_name]
     if not isinstance(t, torch.Tensor):
         raise TypeError("%s must be a torch tensor" % what)
     if t.dtype != dt:
@@ -528,6 +536,91 @@ class Database:
     def close(self):
         if self.handle:
             zp_db_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _words(v: int, nw: int | None = None) -> np.ndarray:
+    v = int(v)
+    if nw is None:
+        nw = max(1, (v.bit_length() + 31) // 32)
+    return np.array([(v >> (32 * i)) & 0xFFFFFFFF for i in range(nw)], dtype=np.uint32)
+
+
+class LweCompressor:
+    """Standalone compression of LWE ciphertexts / RLWE coefficients into Paillier
+    ciphertexts of one modulus m (zp_lc_*). Integers mod q travel as int64 CUDA tensors
+    (their u64 bits); Paillier ciphertexts as int32 tensors of 2L limbs."""
+
+    _MODES = {"auto": 0, "horner": 1, "folded": 2}
+
+    def __init__(self, device: int, key_bits: int, m: int):
+        self.device, self.key_bits, self.m = device, key_bits, int(m)
+        self.L = key_bits // 32
+        self.n = 0
+        lib = load_library()
+        h = ctypes.c_void_p()
+        mw = _words(self.m, self.L)
+        _check(lib.zp_lc_create(device, key_bits, mw.ctypes.data, ctypes.byref(h)))
+        self.handle = h.value
+
+    def set_key(self, ck, T: int, stream=None):
+        """Expanded key from ck (n, 2L) for exponents of up to T bits."""
+        n = ck.shape[0]
+        _need(ck, "i32", n * 2 * self.L, "ck")
+        _check(load_library().zp_lc_set_key(self.handle, _ptr(ck), n, int(T), _stream(stream)))
+        self.n = n
+
+    def unpack_key(self, pck, n: int, t: int, delta: int, out=None, stream=None):
+        import torch
+        npk = -(-n // t)
+        _need(pck, "i32", npk * 2 * self.L, "pck")
+        if out is None:
+            out = torch.empty((n, 2 * self.L), dtype=torch.int32, device=pck.device)
+        _need(out, "i32", n * 2 * self.L, "out")
+        d = _words(delta)
+        _check(load_library().zp_lc_unpack_key(self.handle, _ptr(pck), n, t, d.ctypes.data, len(d),
+                                               _ptr(out), _stream(stream)))
+        return out
+
+    def compress(self, A, B, q: int, ell: int = 1, gamma: int | None = None, mode: str = "auto",
+                 out=None, stream=None):
+        """A (count, n), B (count,) int64 tensors -> (ceil(count / ell), 2L) int32 tensor."""
+        import torch
+        count = B.shape[0]
+        _need(A, "i64", count * self.n, "A")
+        _need(B, "i64", count, "B")
+        G = -(-count // ell)
+        if out is None:
+            out = torch.empty((G, 2 * self.L), dtype=torch.int32, device=B.device)
+        _need(out, "i32", G * 2 * self.L, "out")
+        g = _words(gamma if gamma is not None else 1)
+        _check(load_library().zp_lc_compress(self.handle, _ptr(A), _ptr(B), count, int(q) % (1 << 64),
+                                             ell, g.ctypes.data, len(g), self._MODES[mode], _ptr(out),
+                                             _stream(stream)))
+        return out
+
+    def rlwe_extract(self, A, B, q: int, ks, stream=None):
+        """LWE ciphertexts of RLWE coefficients ks: ((len(ks), N), (len(ks),)) int64 tensors."""
+        import torch
+        N = A.shape[0]
+        _need(A, "i64", N, "A")
+        _need(B, "i64", N, "B")
+        k = np.ascontiguousarray(ks, dtype=np.uint32)
+        Ao = torch.empty((len(k), N), dtype=torch.int64, device=A.device)
+        Bo = torch.empty((len(k),), dtype=torch.int64, device=A.device)
+        _check(load_library().zp_lc_rlwe_extract(self.handle, _ptr(A), _ptr(B), N, int(q) % (1 << 64),
+                                                 k.ctypes.data, len(k), _ptr(Ao), _ptr(Bo), _stream(stream)))
+        return Ao, Bo
+
+    def close(self):
+        if self.handle:
+            load_library().zp_lc_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

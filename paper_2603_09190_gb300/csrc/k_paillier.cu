@@ -13,89 +13,18 @@
 //    homomorphic addition of t encrypted with randomness 1, so that Dec(k (+) t) =
 //    Dec(k) + t mod m.
 //
-// All products mod m^2 are Montgomery products (Montgomery, Math. Comp. 1985) with
-// R = 2^(64 L): the coarsely integrated operand scanning form (CIOS; Koc, Acar, Kaliski,
-// IEEE Micro 1996), one warp per product, 4 words per lane. Each of the 2L steps adds
-// a_i b and u m^2 (u = t_0 (-m^2)^{-1} mod 2^32, which zeroes word 0) and shifts the sum
-// down one word; the word sums stay lazily unnormalised in 64-bit lane accumulators
-// (each stays below 2^42), so a step needs no carry chain across lanes: three shuffles
-// (a_i, u, the shifted word). One normalisation and one conditional subtraction of m^2 at
-// the end give the result below m^2.
+// All products mod m^2 are the Montgomery products of zp_mont.cuh with R = 2^(64 L), one
+// warp per product, 4 words per lane.
 #include "zp_internal.cuh"
 #include "zp_chacha.cuh"
-#include "zp_warpint.cuh"
+#include "zp_mont.cuh"
 
 namespace {
 
 constexpr int MW = 2 * ZP_MAX_L;  // words of m^2
 constexpr int MWPL = MW / 32;     // words per lane
 
-struct ModM2 {
-  uint32_t n[MWPL];  // this lane's words of m^2
-  uint32_t ninv;     // -(m^2)^{-1} mod 2^32
-};
-
-__device__ __forceinline__ void load_lane_words(const uint32_t* __restrict__ src, uint32_t (&w)[MWPL]) {
-  const uint4 v = *reinterpret_cast<const uint4*>(src + MWPL * lane_id());
-  w[0] = v.x;
-  w[1] = v.y;
-  w[2] = v.z;
-  w[3] = v.w;
-}
-
-__device__ __forceinline__ void store_lane_words(uint32_t* __restrict__ dst, const uint32_t (&w)[MWPL]) {
-  *reinterpret_cast<uint4*>(dst + MWPL * lane_id()) = make_uint4(w[0], w[1], w[2], w[3]);
-}
-
-// r = a b 2^(-64 L) mod m^2, for a, b < m^2 (r may alias a or b).
-__device__ __forceinline__ void mont_mul(const ModM2& M, const uint32_t (&a)[MWPL],
-                                      const uint32_t (&b)[MWPL], uint32_t (&r)[MWPL]) {
-  const uint32_t lane = lane_id();
-  uint64_t acc[MWPL] = {0, 0, 0, 0};
-#pragma unroll 1
-  for (int src = 0; src < 32; ++src) {
-#pragma unroll
-    for (int s = 0; s < MWPL; ++s) {
-      const uint32_t ai = __shfl_sync(0xffffffffu, a[s], src);  // word 4 src + s of a
-      uint32_t ph[MWPL];
-#pragma unroll
-      for (int k = 0; k < MWPL; ++k) {
-        const uint64_t p = (uint64_t)ai * b[k];
-        acc[k] += (uint32_t)p;
-        ph[k] = (uint32_t)(p >> 32);
-      }
-      acc[1] += ph[0];
-      acc[2] += ph[1];
-      acc[3] += ph[2];
-      // u makes word 0 vanish mod 2^32 (word 0 lives in lane 0)
-      const uint32_t u = __shfl_sync(0xffffffffu, (uint32_t)acc[0] * M.ninv, 0);
-      uint32_t qh[MWPL];
-#pragma unroll
-      for (int k = 0; k < MWPL; ++k) {
-        const uint64_t q = (uint64_t)u * M.n[k];
-        acc[k] += (uint32_t)q;
-        qh[k] = (uint32_t)(q >> 32);
-      }
-      acc[1] += qh[0];
-      acc[2] += qh[1];
-      acc[3] += qh[2];
-      // divide by 2^32: every word moves down one place; word 0 keeps only its carry
-      const uint64_t from_next = __shfl_down_sync(0xffffffffu, acc[0], 1);
-      const uint64_t c0 = lane == 0 ? (acc[0] >> 32) : 0ull;
-      acc[0] = acc[1] + c0;
-      acc[1] = acc[2];
-      acc[2] = acc[3];
-      // the high halves of the top words belong to the next lane's word 0, which is now
-      // this lane's word 3
-      acc[3] = (lane == 31 ? 0ull : from_next) + ph[3] + qh[3];
-    }
-  }
-  uint32_t w[MWPL];
-  const uint32_t top = warp_normalize_top<MWPL>(acc, w);  // the sum is below 2 m^2 < 2^(64L+1)
-  if (top != 0 || warp_geq<MWPL>(w, M.n)) warp_sub<MWPL>(w, M.n);
-#pragma unroll
-  for (int k = 0; k < MWPL; ++k) r[k] = w[k];
-}
+using ModM2 = ModN<MWPL>;
 
 // x <- x^gamma (Montgomery form), gamma = g[0] + g[1] 2^32 + g[2] 2^64 > 0.
 __device__ void mont_pow_gamma(const ModM2& M, uint32_t (&x)[MWPL], uint32_t g0, uint32_t g1,
