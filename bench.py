@@ -643,13 +643,115 @@ def run_client_hint(args, world, rank, local):
     return 0
 
 
+# Single-compression parameter sets of the evaluation (Sec. 5.1, table of single LWE
+# ciphertext / RLWE coefficient compression): (kind, n or N, log2 q, the paper's time in ms
+# on its CPU with a 3072-bit Paillier modulus -- context, not a target).
+LC_SETS = [("lwe", 630, 64, 9.7), ("lwe", 742, 64, 11.0), ("lwe", 870, 64, 12.9), ("lwe", 1305, 11, 16.6),
+           ("rlwe", 1024, 27, 7.2), ("rlwe", 2048, 54, 23.8), ("rlwe", 4096, 36, 33.8), ("rlwe", 8192, 43, 83.3)]
+
+
+def run_lwe_compress(args, world, rank, local):
+    """Standalone compression with a 3072-bit Paillier modulus: one ciphertext (latency) and
+    256 ciphertexts (throughput) for every single-compression parameter set, RLWE
+    coefficients after sample extraction, and batched compression of (630, 2^64)."""
+    import torch
+    import paper_2603_09190_gb300 as zp
+    from paper_2603_09190_gb300 import build as zb
+    import synth
+
+    if rank == 0:
+        zb.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    bits = 3072
+    m = synth.random_odd_modulus(bits, 11)
+    comp = zp.LweCompressor(local, bits, m)
+    g = synth.rng(12)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, reps):
+        for _ in range(max(args.warmup, 3)):
+            fn()
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    def u64(shape, lq):
+        x = g.integers(0, 2 ** 63, size=shape, dtype=np.uint64) * np.uint64(2) + \
+            g.integers(0, 2, size=shape, dtype=np.uint64)
+        if lq < 64:
+            x &= np.uint64((1 << lq) - 1)
+        return torch.from_numpy(x.view(np.int64)).to(dev)
+
+    def ck_of(n):  # uniform below 2^(64 L - 32) < m^2
+        v = g.integers(0, 2 ** 32, size=(n, 2 * bits // 32), dtype=np.uint64).astype(np.uint32)
+        v[:, -1] = 0
+        return torch.from_numpy(v.view(np.int32)).to(dev)
+
+    steps = max(args.steps // 200, 5)
+    sets = []
+    for kind, n, lq, paper_ms in LC_SETS:
+        q = 1 << lq
+        comp.set_key(ck_of(n), lq)
+        if kind == "lwe":
+            A1, B1 = u64((1, n), lq), u64((1,), lq)
+            single = timed(lambda: comp.compress(A1, B1, q), steps)
+        else:
+            Ap, Bp = u64((n,), lq), u64((n,), lq)
+            single = timed(lambda: comp.compress(*comp.rlwe_extract(Ap, Bp, q, [n // 2]), q), steps)
+        A, B = u64((256, n), lq), u64((256,), lq)
+        many = timed(lambda: comp.compress(A, B, q), 2)
+        sets.append({"kind": kind, "n": n, "log2q": lq, "single_ms": single, "paper_single_ms": paper_ms,
+                     "ct_per_s_256": 256 / many * 1e3})
+    # batched (630, 2^64): gamma = q + n q^2, ell = largest with gamma^ell < m
+    n, q = 630, 1 << 64
+    gamma = q + n * q * q
+    ell = 0
+    while gamma ** (ell + 1) < m:
+        ell += 1
+    T = ((q - 1) * sum(gamma ** j for j in range(ell))).bit_length()
+    comp.set_key(ck_of(n), T)
+    batched = {}
+    for groups in (1, 16):
+        A, B = u64((groups * ell, n), 64), u64((groups * ell,), 64)
+        ms = timed(lambda: comp.compress(A, B, q, ell=ell, gamma=gamma), 1)
+        batched["groups%d" % groups] = {"cts": groups * ell, "ms": ms, "ct_per_s": groups * ell / ms * 1e3}
+    cpu = None
+    if not args.no_cpu:
+        from oracle import lwecompress as olc
+        from oracle import paillier as opl
+        pk = opl.PublicKey(m)
+        ck = [int.from_bytes(g.bytes(760), "little") for _ in range(630)]
+        a = [int.from_bytes(g.bytes(8), "little") for _ in range(630)]
+        t0 = time.perf_counter()
+        olc.lwe_compress(pk, ck, a, 12345, 1 << 64)
+        cpu = {"value": (time.perf_counter() - t0) * 1e3, "unit": "ms", "cores": 1, "kind": "oracle",
+               "sample": "one (630, 2^64) ciphertext, Python integers"}
+    if rank == 0:
+        head = sets[0]
+        line = {"metric": "single LWE ciphertext compression latency, (n, q) = (630, 2^64), 3072-bit Paillier",
+                "value": head["single_ms"], "unit": "ms", "n_gpus": world, "steps": steps,
+                "warmup": max(args.warmup, 3), "ms_per_step": head["single_ms"], "higher_is_better": False,
+                "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+                "config": {"workload": "standalone compression: single-compression parameter sets and batched "
+                                       "(630, 2^64), 3072-bit modulus, inputs resident in HBM",
+                           "key_bits": bits, "ell": ell, "T_folded": T},
+                "sets": sets, "batched_630_64": batched, "cpu_baseline": cpu}
+        print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="1gib", choices=sorted(WORKLOADS) + ["serve", "client_hint"])
+    ap.add_argument("--workload", default="1gib", choices=sorted(WORKLOADS) + ["serve", "client_hint", "lwe_compress"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the library's default thresholds and SM split")
@@ -664,13 +766,15 @@ def main():
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
-        if args.workload in ("serve", "client_hint"):
+        if args.workload in ("serve", "client_hint", "lwe_compress"):
             args.workload = "1gib"
         return run_reference(args, world, rank)
     if args.workload == "serve":
         return run_serve(args, world, rank, local)
     if args.workload == "client_hint":
         return run_client_hint(args, world, rank, local)
+    if args.workload == "lwe_compress":
+        return run_lwe_compress(args, world, rank, local)
     return run_ours(args, world, rank, local)
 
 

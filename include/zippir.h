@@ -53,11 +53,22 @@ enum zp_secret {
   ZP_SECRET_BINARY = 1   /* LWE secret in {0,1}:     packing scale gamma = q + n q   (Sec. 3.3.3) */
 };
 
+enum zp_scale {
+  ZP_SCALE_PROVEN = 0, /* gamma = the slot bound above (the batched correctness theorem) */
+  ZP_SCALE_OVERLAP = 1 /* gamma = q^2 (uniform) or q (binary): neighbouring slots overlap,
+                          which the modified decryption tolerates while the noise stays below
+                          Delta / 4 (Sec. 3.3.3, "Better compression with a smaller scale") */
+};
+
 typedef struct zp_params {
   uint32_t n;        /* LWE dimension (1 <= n <= 4096) */
   uint32_t key_bits; /* bits of every client's Paillier modulus m; 2048 in this build */
   uint32_t secret;   /* enum zp_secret */
   uint32_t p_bits;   /* log2 of the plaintext modulus p; must be 8 (one byte per entry) */
+  uint32_t scale;    /* enum zp_scale. Slots per packed row: ell = the largest count with
+                        (bound - 1) sum_{j<ell} gamma^j < 2^(key_bits - 1), bound = q + n q^2
+                        (uniform) or q + n q (binary): 27 / 48 proven, 31 / 63 overlap at
+                        2048 bits and n = 1024 */
 } zp_params;
 
 typedef struct zp_ctx zp_ctx;       /* one device, one parameter set */

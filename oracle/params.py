@@ -11,6 +11,14 @@ formula with the smaller, overlap scale): ell is the largest integer with
 gamma^ell < 2^(key_bits - 1). Every key of ``key_bits`` bits has
 m >= 2^(key_bits - 1), so the theorem's m > gamma^ell holds for all clients with
 keys of that size and the packed hint is the same for all of them.
+
+Overlap scale (Sec. 3.3.3, "Better compression with a smaller scale"; its proof is
+not in the paper): gamma = q^2 (uniform secret) or q (binary), so that neighbouring
+slots overlap; the slot values still lie below the proven bound gamma_p = q + n q^2
+(or q + n q). Reading: ell is the largest integer with
+(gamma_p - 1) sum_{j<ell} gamma^j < 2^(key_bits - 1), the largest packed value, which
+for gamma = gamma_p is the rule above. Recovery then needs the noise plus the spill of
+the slot below (at most about n) to stay under Delta / 2; checked by end-to-end recovery.
 """
 from __future__ import annotations
 
@@ -27,6 +35,7 @@ class Params:
     secret: str = "uniform"  # "uniform" (sk in Z_q^n) or "binary" (sk in {0,1}^n)
     p: int = 256             # plaintext modulus (database entries in Z_p)
     sigma: float = 6.4       # error standard deviation (Sec. 5.2)
+    scale: str = "proven"    # "proven" (gamma = slot bound) or "overlap" (Sec. 3.3.3)
 
     @property
     def q(self) -> int:
@@ -38,8 +47,9 @@ class Params:
         return (Q + self.p // 2) // self.p
 
     @property
-    def gamma(self) -> int:
-        # gamma = q + n q^2 (uniform secret, Sec. 3.3) or q + n q (binary, Sec. 3.3.3)
+    def slot_bound(self) -> int:
+        # every slot value is below q + n q^2 (uniform secret, Sec. 3.3) or q + n q (binary,
+        # Sec. 3.3.3)
         if self.secret == "uniform":
             return Q + self.n * Q * Q
         if self.secret == "binary":
@@ -47,13 +57,23 @@ class Params:
         raise ValueError("secret must be 'uniform' or 'binary'")
 
     @property
+    def gamma(self) -> int:
+        if self.scale == "proven":
+            return self.slot_bound
+        if self.scale == "overlap":
+            return Q * Q if self.secret == "uniform" else Q
+        raise ValueError("scale must be 'proven' or 'overlap'")
+
+    @property
     def ell(self) -> int:
-        # largest ell with gamma^ell < 2^(key_bits-1)  (batched correctness theorem, Sec. 3.3)
-        g = self.gamma
+        # largest ell whose largest packed value (slot_bound - 1) sum_{j<ell} gamma^j is
+        # below 2^(key_bits-1); for the proven scale: gamma^ell < 2^(key_bits-1) (batched
+        # correctness theorem, Sec. 3.3)
+        g, top = self.gamma, self.slot_bound - 1
         bound = 1 << (self.key_bits - 1)
-        ell, acc = 0, 1
-        while acc * g < bound:
-            acc *= g
+        ell, acc = 0, 0
+        while top * (acc + g ** ell) < bound:
+            acc += g ** ell
             ell += 1
         if ell == 0:
             raise ValueError("key too small for one slot")

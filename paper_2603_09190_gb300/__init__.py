@@ -46,7 +46,7 @@ class ZipPIRError(RuntimeError):
 
 class _Params(ctypes.Structure):
     _fields_ = [("n", ctypes.c_uint32), ("key_bits", ctypes.c_uint32),
-                ("secret", ctypes.c_uint32), ("p_bits", ctypes.c_uint32)]
+                ("secret", ctypes.c_uint32), ("p_bits", ctypes.c_uint32), ("scale", ctypes.c_uint32)]
 
 
 _lib = None
@@ -159,8 +159,12 @@ def zp_version() -> int:
     return load_library().zp_version()
 
 
-def zp_init(device: int, n: int, key_bits: int = 2048, secret: str = "uniform", p_bits: int = 8) -> int:
-    P = _Params(n, key_bits, SECRETS[secret], p_bits)
+SCALES = {"proven": 0, "overlap": 1}
+
+
+def zp_init(device: int, n: int, key_bits: int = 2048, secret: str = "uniform", p_bits: int = 8,
+            scale: str = "proven") -> int:
+    P = _Params(n, key_bits, SECRETS[secret], p_bits, SCALES[scale])
     out = ctypes.c_void_p()
     _check(load_library().zp_init(device, ctypes.byref(P), ctypes.byref(out)))
     return out.value
@@ -324,9 +328,10 @@ def zp_kernel_launches(ctx: int) -> int:
 class Context:
     """One device and one parameter set (n, key size, secret distribution)."""
 
-    def __init__(self, device: int = 0, n: int = 1024, key_bits: int = 2048, secret: str = "uniform"):
-        self.device, self.n, self.key_bits, self.secret = device, n, key_bits, secret
-        self.handle = zp_init(device, n, key_bits, secret)
+    def __init__(self, device: int = 0, n: int = 1024, key_bits: int = 2048, secret: str = "uniform",
+                 scale: str = "proven"):
+        self.device, self.n, self.key_bits, self.secret, self.scale = device, n, key_bits, secret, scale
+        self.handle = zp_init(device, n, key_bits, secret, scale=scale)
         self.L = key_bits // 32
 
     def register_client(self, m: int) -> "Client":

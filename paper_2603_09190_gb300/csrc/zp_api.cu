@@ -260,6 +260,8 @@ extern "C" int zp_init(int device, const zp_params* P, zp_ctx** out) {
     if (P->p_bits != 8) return zp_set_error(ZP_EINVAL, "zp_init: p_bits must be 8");
     if (P->secret != ZP_SECRET_UNIFORM && P->secret != ZP_SECRET_BINARY)
       return zp_set_error(ZP_EINVAL, "zp_init: bad secret kind %u", P->secret);
+    if (P->scale != ZP_SCALE_PROVEN && P->scale != ZP_SCALE_OVERLAP)
+      return zp_set_error(ZP_EINVAL, "zp_init: bad scale %u", P->scale);
     if (P->key_bits != 32 * ZP_MAX_L)
       return zp_set_error(ZP_EUNSUPPORTED, "zp_init: key_bits=%u (this build: %d)", P->key_bits,
                           32 * ZP_MAX_L);
@@ -268,29 +270,52 @@ extern "C" int zp_init(int device, const zp_params* P, zp_ctx** out) {
     c->device = device;
     c->P = *P;
     c->L = P->key_bits / 32;
-    // gamma = q + n q^2 (uniform secret) or q + n q (binary secret), q = 2^32
-    c->gamma_w[0] = 0;
-    if (P->secret == ZP_SECRET_UNIFORM) {
-      c->gamma_w[1] = 1;
-      c->gamma_w[2] = P->n;
-    } else {
-      c->gamma_w[1] = 1 + P->n;
-      c->gamma_w[2] = 0;
+    // slot bound q + n q^2 (uniform secret) or q + n q (binary secret), q = 2^32; gamma is
+    // the bound (proven scale) or q^2 / q (overlap scale)
+    uint32_t bound_w[3] = {0, 1, P->n};
+    if (P->secret == ZP_SECRET_BINARY) {
+      bound_w[1] = 1 + P->n;
+      bound_w[2] = 0;
     }
-    // ell = largest integer with gamma^ell < 2^(key_bits - 1)
+    if (P->scale == ZP_SCALE_PROVEN) {
+      for (int k = 0; k < 3; ++k) c->gamma_w[k] = bound_w[k];
+    } else {
+      c->gamma_w[0] = 0;
+      c->gamma_w[1] = P->secret == ZP_SECRET_UNIFORM ? 0u : 1u;
+      c->gamma_w[2] = P->secret == ZP_SECRET_UNIFORM ? 1u : 0u;
+    }
+    // ell = largest count with (bound - 1) sum_{j<ell} gamma^j < 2^(key_bits - 1): the largest
+    // packed value stays below every key of key_bits bits (for gamma = bound: gamma^ell <
+    // 2^(key_bits - 1))
     {
-      std::vector<uint32_t> acc(1, 1);
+      std::vector<uint32_t> bm1(bound_w, bound_w + 3);  // bound - 1 (bound >= 2^32)
+      for (int k = 0; k < 3; ++k) {
+        if (bm1[k]--) break;
+      }
+      std::vector<uint32_t> pw(1, 1), sum(1, 0);
       uint32_t ell = 0;
       for (;;) {
-        std::vector<uint32_t> nx = acc;
-        big_mul_small(nx, c->gamma_w, 3);
-        if (big_bits(nx) > P->key_bits - 1) break;  // nx >= 2^(key_bits-1)
-        acc.swap(nx);
+        std::vector<uint32_t> ns = sum;  // sum + gamma^ell
+        ns.resize(std::max(ns.size(), pw.size()) + 1, 0);
+        uint64_t cy = 0;
+        for (size_t w = 0; w < ns.size(); ++w) {
+          cy += (uint64_t)ns[w] + (w < pw.size() ? pw[w] : 0u);
+          ns[w] = (uint32_t)cy;
+          cy >>= 32;
+        }
+        std::vector<uint32_t> top = big_mul(ns, bm1);
+        if (big_bits(top) > P->key_bits - 1) break;  // top >= 2^(key_bits-1)
+        sum.swap(ns);
+        big_mul_small(pw, c->gamma_w, 3);
         ++ell;
       }
       if (ell == 0) {
         delete c;
         return zp_set_error(ZP_EINVAL, "zp_init: key too small for one slot");
+      }
+      if (ell > 64) {
+        delete c;
+        return zp_set_error(ZP_EUNSUPPORTED, "zp_init: %u slots per packed row (at most 64)", ell);
       }
       c->ell = ell;
     }

@@ -193,9 +193,11 @@ def test_hint_parity(zp, R, C, n, path):
     c.close()
 
 
-def _e2e(zp, R, C, n, secret, seed, B=1):
-    P = Params(n=n, key_bits=2048, secret=secret)
-    c = zp.Context(0, n=n, secret=secret)
+def _e2e(zp, R, C, n, secret, seed, B=1, scale="proven", path=None):
+    P = Params(n=n, key_bits=2048, secret=secret, scale=scale)
+    c = zp.Context(0, n=n, secret=secret, scale=scale)
+    if path:
+        c.set_option("compress_path", path)
     D = synth.database(R, C, seed)
     A = synth.seed_matrix(C, n, seed)
     Hn = lwe.hint_neg(D, A)
@@ -238,6 +240,18 @@ def test_e2e_tiny_config(zp):
     (500, 300, 128, "uniform", 5, 3), (49, 33, 1024, "binary", 6, 1)])
 def test_e2e_ragged(zp, R, C, n, secret, seed, B):
     _e2e(zp, R, C, n, secret, seed, B)
+
+
+@pytest.mark.parametrize("R,C,n,secret,seed,B,path", [
+    (1024, 1024, 1024, "uniform", 11, 1, None), (700, 256, 1024, "binary", 12, 2, None),
+    (300, 64, 64, "uniform", 13, 8, "rns"), (200, 96, 32, "binary", 14, 3, "simt")])
+def test_e2e_overlap_scale(zp, R, C, n, secret, seed, B, path):
+    """Overlap scale (Sec. 3.3.3): gamma = q^2 (uniform) or q (binary), 31 / 63 slots per
+    packed row at n = 1024; t bit-identical to the oracle on the tensor-core, RNS and
+    CUDA-core paths, and the record is recovered."""
+    if n == 1024:
+        assert Params(n=n, secret=secret, scale="overlap").ell == (31 if secret == "uniform" else 63)
+    _e2e(zp, R, C, n, secret, seed, B, scale="overlap", path=path)
 
 
 def test_compress_edge_values(zp):

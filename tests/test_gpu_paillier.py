@@ -28,13 +28,13 @@ def u32_host(t):
     return t.cpu().numpy().view(np.uint32)
 
 
-def _setup(zp, R, C, n, secret, seed):
-    P = Params(n=n, key_bits=2048, secret=secret)
+def _setup(zp, R, C, n, secret, seed, scale="proven"):
+    P = Params(n=n, key_bits=2048, secret=secret, scale=scale)
     D = synth.database(R, C, seed)
     A = synth.seed_matrix(C, n, seed)
     Hn = lwe.hint_neg(D, A)
     cl = zippir.setup(P, seed + 100, sample_ck_r=True)
-    ctx = zp.Context(0, n=n, key_bits=2048, secret=secret)
+    ctx = zp.Context(0, n=n, key_bits=2048, secret=secret, scale=scale)
     ld = zp.db_pitch(C)
     buf = np.zeros((R, ld), dtype=np.uint8)
     buf[:, :C] = D
@@ -46,12 +46,14 @@ def _setup(zp, R, C, n, secret, seed):
     return P, D, A, Hn, cl, ctx, db, gcl, ckr, dD
 
 
-@pytest.mark.parametrize("R,C,n,secret,seed", [(60, 48, 8, "uniform", 1), (200, 64, 16, "uniform", 2),
-                                               (100, 40, 12, "binary", 3)])
-def test_client_hint_parity(zp, R, C, n, secret, seed):
+@pytest.mark.parametrize("R,C,n,secret,seed,scale", [
+    (60, 48, 8, "uniform", 1, "proven"), (200, 64, 16, "uniform", 2, "proven"),
+    (100, 40, 12, "binary", 3, "proven"), (100, 40, 8, "uniform", 4, "overlap"),
+    (140, 40, 8, "binary", 5, "overlap")])
+def test_client_hint_parity(zp, R, C, n, secret, seed, scale):
     """k on the GPU equals prod_i ck_r[i]^{H'[r', i]} mod m^2 for every packed row,
-    including the ragged last one."""
-    P, D, A, Hn, cl, ctx, db, gcl, ckr, dD = _setup(zp, R, C, n, secret, seed)
+    including the ragged last one (proven and overlap scales)."""
+    P, D, A, Hn, cl, ctx, db, gcl, ckr, dD = _setup(zp, R, C, n, secret, seed, scale)
     k = db.client_hint(gcl, ckr)
     got = synth.limbs_to_ints(u32_host(k))
     want = zippir.paillier_matmul_rows(cl, Hn, range(db.d1p))

@@ -74,6 +74,62 @@ def test_slots_worst_case(secret, bits):
     assert zippir.unpack(top, P) == [slot_max] * P.ell
 
 
+@pytest.mark.parametrize("secret,scale,ell", [("uniform", "proven", 27), ("binary", "proven", 48),
+                                               ("uniform", "overlap", 31), ("binary", "overlap", 63)])
+def test_slot_counts(secret, scale, ell):
+    """Slots per packed row at n = 1024, 2048 bits: ell slots of the largest slot value
+    (b + H sk < q + n q^2, or q + n q) fit below 2^2047 at the scale's gamma; one more slot
+    of the bound does not (the overlap scale's slots overlap: gamma < bound)."""
+    P = Params(n=1024, key_bits=2048, secret=secret, scale=scale)
+    assert P.ell == ell
+    smax = 1 if secret == "binary" else Q - 1
+    slot_max = (Q - 1) + P.n * (Q - 1) * smax
+    bound = Q + P.n * Q * (Q if secret == "uniform" else 1)
+    assert slot_max < bound
+    assert P.gamma == (bound if scale == "proven" else (Q * Q if secret == "uniform" else Q))
+    assert sum(slot_max * P.gamma ** j for j in range(ell)) < 2 ** 2047
+    assert sum((bound - 1) * P.gamma ** j for j in range(ell + 1)) >= 2 ** 2047
+
+
+@pytest.mark.parametrize("seed,secret", [(4, "uniform"), (5, "binary")])
+def test_e2e_overlap_scale(seed, secret):
+    """Overlap scale (Sec. 3.3.3): with the real hint k, Extract still returns column i0;
+    the slots overlap (gamma below the slot bound), so this is checked by recovery (the
+    paper defers its proof)."""
+    R, C, n = 130, 48, 8
+    P = Params(n=n, key_bits=2048, secret=secret, scale="overlap")
+    assert P.gamma < P.slot_bound
+    D = synth.database(R, C, seed)
+    A = synth.seed_matrix(C, n, seed)
+    Hn = lwe.hint_neg(D, A)
+    cl = zippir.setup(P, seed + 100, sample_ck_r=True)
+    i0 = (11 * seed) % C
+    qy = zippir.query(cl, A, i0, seed + 200)
+    ans, t = zippir.response(D, qy.qu, Hn, qy.cko, cl.pk.m, P)
+    rows = range(P.d1p(R))
+    k = zippir.paillier_matmul_rows(cl, Hn, rows)
+    dec_k = [paillier.decrypt(cl.sk, kk) for kk in k]
+    assert dec_k == zippir.dec_k_shortcut(cl, Hn, rows)
+    rec = zippir.extract(cl, dec_k, t, R)
+    assert np.array_equal(rec, D[:, i0])
+
+
+def test_e2e_overlap_tiny_config():
+    """1024 x 1024, n = 1024, uniform secret at the overlap scale (31 slots)."""
+    R = C = n = 1024
+    P = Params(n=n, key_bits=2048, secret="uniform", scale="overlap")
+    D = synth.database(R, C, 9)
+    A = synth.seed_matrix(C, n, 9)
+    Hn = lwe.hint_neg(D, A)
+    cl = zippir.setup(P, 109, sample_ck_r=False)
+    qy = zippir.query(cl, A, 77, 309)
+    ans, t = zippir.response(D, qy.qu, Hn, qy.cko, cl.pk.m, P)
+    assert len(t) == -(-R // 31)
+    rows = list(range(len(t)))
+    rec = zippir.extract(cl, zippir.dec_k_shortcut(cl, Hn, rows), t, R)
+    assert np.array_equal(rec, D[:, 77])
+
+
 def test_pack_unpack_roundtrip():
     P = Params(n=1024, key_bits=2048)
     g = synth.rng(5)
