@@ -80,11 +80,17 @@ def lwe_decrypt(s: list[int], a: list[int], b: int, q: int, p: int) -> int:
     return round_div(lwe_phase(s, a, b, q), delta_of(q, p)) % p
 
 
-def compression_key(pk: paillier.PublicKey, s: list[int], g: np.random.Generator) -> list[int]:
-    """ck[i] = Enc(s[i]) with fresh randomness."""
-    m = pk.m
-    return [paillier.encrypt(pk, si, int.from_bytes(g.bytes(pk.m.bit_length() // 8 + 8), "little") % (m - 2) + 2)
-            for si in s]
+def compression_key(pk: paillier.PublicKey, s: list[int], g: np.random.Generator,
+                    shared_randomness: bool = False) -> list[int]:
+    """ck[i] = Enc(s[i]) with fresh randomness; with ``shared_randomness`` every entry uses
+    the same r (valid ciphertexts that decrypt alike, one r^m instead of n: for tests of
+    large n only, not a secure key)."""
+    m, m2 = pk.m, pk.m2
+    draw = lambda: int.from_bytes(g.bytes(pk.m.bit_length() // 8 + 8), "little") % (m - 2) + 2
+    if shared_randomness:
+        rho = pow(draw(), m, m2)
+        return [(1 + (si % m) * m) * rho % m2 for si in s]
+    return [paillier.encrypt(pk, si, draw()) for si in s]
 
 
 def trivial(pk: paillier.PublicKey, x: int) -> int:

@@ -45,7 +45,7 @@ def _setup(zp, keys, bits, n, q, binary, seed, T):
     pk, sk = keys[bits]
     g = np.random.default_rng(seed)
     s = lc.lwe_keygen(n, q, binary, g)
-    ck = lc.compression_key(pk, s, g)
+    ck = lc.compression_key(pk, s, g, shared_randomness=bits == 3072 or n > 64)
     comp = zp.LweCompressor(0, bits, pk.m)
     comp.set_key(ct_dev(ck, bits // 32), T)
     return pk, sk, g, s, ck, comp

@@ -48,6 +48,16 @@ def test_lwe_compress_correct(keys, n, q, p, binary):
         assert lc.modified_lwe_decrypt(sk, x, q, p) == lc.lwe_decrypt(s, a, b, q, p) == mu
 
 
+def test_shared_randomness_key_decrypts(keys):
+    """The test-speed compression key (one r for every entry) decrypts to s."""
+    pk, sk = keys
+    g = np.random.default_rng(4)
+    s = lc.lwe_keygen(6, Q64, False, g)
+    ck = lc.compression_key(pk, s, g, shared_randomness=True)
+    assert [paillier.decrypt(sk, c) for c in ck] == s
+    assert len(set(ck)) == len(set(s))
+
+
 def test_fast_equals_plain_compress(keys):
     """Algorithm "Batch compression ... using precomputed powers": the expanded key gives
     the same ciphertext, bit for bit; a = 0 (exponent 0) included."""
