@@ -288,6 +288,14 @@ int zp_kernel_launches(const zp_ctx* ctx, uint64_t* count);
  * cleared by the read. */
 int zp_device_status(zp_ctx* ctx, uint32_t* code);
 
+/* Resident fp16 copy of the database for batched answers: allocates R x Kp fp16 (Kp = C
+ * rounded up to 128; twice the bytes of D) and fills it with D - 128 (centred, exact).
+ * From then on the tensor-core answers (batches above gemv_max_batch) read it as their A
+ * operand through TMA, with no byte-to-fp16 conversion in shared memory; zp_update_rows
+ * keeps it current. Option "answer_fp16" (zp_set_option, default 1) turns its use off (0)
+ * or on (1). Asynchronous on `stream`. Errors: ZP_EINVAL, ZP_ENOMEM, ZP_ECUDA. */
+int zp_db_prepare_fp16(zp_db* db, void* stream);
+
 /* ChaCha20 keystream (RFC 8439 block function) on the GPU: dOut[0 .. nwords) receives the
  * little-endian 32-bit words of blocks counter0, counter0 + 1, ... for the 32-byte key hKey
  * and the 12-byte nonce hNonce (both HOST, read before the call returns). The PRG that

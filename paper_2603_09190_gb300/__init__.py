@@ -32,7 +32,7 @@ EXPORTS = [
     "zp_device_status", "zp_kernel_launches", "zp_set_option", "zp_answer_noalloc",
     "zp_compress_products", "zp_compress_finish", "zp_get_option", "zp_client_hint", "zp_combine",
     "zp_db_prepare_rns", "zp_selftest_wait", "zp_autotune", "zp_prg_chacha20", "zp_client_powm",
-    "zp_client_expand_ckr", "zp_client_decrypt",
+    "zp_client_expand_ckr", "zp_client_decrypt", "zp_db_prepare_fp16",
     "zp_lc_create", "zp_lc_destroy", "zp_lc_set_key", "zp_lc_unpack_key", "zp_lc_compress",
     "zp_lc_rlwe_extract",
 ]
@@ -95,6 +95,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "zp_client_powm": (i32, [vp, vp, vp, u32, vp, u32, vp]),
         "zp_client_expand_ckr": (i32, [vp, vp, vp, u32, vp, u32, vp]),
         "zp_client_decrypt": (i32, [vp, vp, vp, vp, vp, u32, vp]),
+        "zp_db_prepare_fp16": (i32, [vp, vp]),
         "zp_lc_create": (i32, [ctypes.c_int, u32, vp, ctypes.POINTER(vp)]),
         "zp_lc_destroy": (i32, [vp]),
         "zp_lc_set_key": (i32, [vp, vp, u32, u32, vp]),
@@ -349,8 +350,8 @@ class Context:
 
     def set_option(self, name: str, value):
         """Kernel-variant selection: name in {"answer_path", "compress_path"}, value in
-        {"auto", "simt", "tc"} (compress_path also "rns"), or "overlap_sms" / "rns_min_batch"
-        with an integer."""
+        {"auto", "simt", "tc"} (compress_path also "rns"), or "overlap_sms" / "rns_min_batch" /
+        "gemv_max_batch" / "answer_fp16" with an integer."""
         v = {"auto": 0, "simt": 1, "tc": 2, "rns": 3}.get(value, value)
         zp_set_option(self.handle, name, v)
 
@@ -526,6 +527,10 @@ class Database:
         out = (ctypes.c_int64 * 3)()
         _check(load_library().zp_autotune(self.handle, _stream(stream), out))
         return {"gemv_max_batch": out[0], "rns_min_batch": out[1], "overlap_sms": out[2]}
+
+    def prepare_fp16(self, stream=None):
+        """Builds the resident fp16 copy of D (twice its bytes) that batched answers read."""
+        _check(load_library().zp_db_prepare_fp16(self.handle, _stream(stream)))
 
     def prepare_rns(self, stream=None):
         """Builds the RNS residue planes of H' now (else on the first large batch)."""

@@ -61,13 +61,22 @@ enum { MODE_ANS = 0, MODE_HINT = 1, MODE_CMP = 2, MODE_RNS = 3 };
 
 // Three rings: B (fp16, from L2: deep, it is the largest operand), A as bytes (from
 // HBM, L2-prefetched) and A as fp16 (written by the converters just before the MMA).
-template <int MODE>
+// A16: A is already centred fp16 in HBM (the resident fp16 copy of D), so TMA fills the
+// A ring directly: no byte ring, no converters, and the B stages are sized to the tile (N
+// rows). For N <= 128 a stage holds KPS = 2 K blocks (one wait and one commit per two K
+// blocks: measured 11-14 % faster); the 256-wide tile keeps four one-block stages (two
+// two-block stages were slower).
+template <int MODE, int BT = 64, bool A16 = false>
 struct Cfg {
-  static constexpr int SB = (MODE == MODE_CMP || MODE == MODE_RNS) ? 3 : 4;
+  static constexpr int KPS = (A16 && BT < 64) ? 2 : 1;                     // K blocks per stage
+  static constexpr int BST = A16 ? KPS * 4 * BT * BK * 2 : B_MAX_BYTES;   // B stage stride
+  static constexpr int AST = KPS * A16_BYTES;                              // A stage stride
+  static constexpr int SB = A16 ? (BT == 16 ? 4 : (BT == 32 ? 3 : 4))
+                                : ((MODE == MODE_CMP || MODE == MODE_RNS) ? 3 : 4);
   static constexpr int SA = SB;  // the A and B stages of a K block are filled and freed together
-  static constexpr int SU = 2;   // stages of two K blocks
+  static constexpr int SU = A16 ? 0 : 2;  // stages of two K blocks of A bytes
   static constexpr int STG = (MODE == MODE_CMP || MODE == MODE_RNS) ? STG_BYTES : 0;
-  static constexpr int SMEM = SB * B_MAX_BYTES + SA * A16_BYTES + SU * U8_STAGE + STG + 1024 + 512;
+  static constexpr int SMEM = SB * BST + SA * AST + SU * U8_STAGE + STG + 1024 + 512;
 };
 
 struct GemmArgs {
@@ -136,18 +145,19 @@ __device__ __forceinline__ bool bar_and_128(bool pred) {
   return r != 0;
 }
 
-template <int MODE, int BT>
+template <int MODE, int BT, bool A16 = false>
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
               const GemmArgs args) {
-  using C = Cfg<MODE>;
+  using C = Cfg<MODE, BT, A16>;
+  static_assert(!A16 || MODE == MODE_ANS, "fp16 A operand: batched answers only");
   constexpr int SB = C::SB, SA = C::SA, SU = C::SU;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~static_cast<uintptr_t>(1023));
   uint8_t* b_ring = smem;                                    // SB x 32 KiB (1024-aligned)
-  uint8_t* a_ring = b_ring + SB * B_MAX_BYTES;               // SA x 16 KiB (1024-aligned)
-  uint8_t* u8_ring = a_ring + SA * A16_BYTES;                // SU x 16 KiB (1024-aligned)
+  uint8_t* a_ring = b_ring + SB * C::BST;                   // SA x 16 KiB (1024-aligned)
+  uint8_t* u8_ring = a_ring + SA * C::AST;                  // SU x 16 KiB (1024-aligned)
   uint32_t* stg = reinterpret_cast<uint32_t*>(u8_ring + SU * U8_STAGE);
   uint64_t* bars = reinterpret_cast<uint64_t*>(u8_ring + SU * U8_STAGE + C::STG);
   uint64_t* u8_full = bars;
@@ -165,6 +175,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t num_tiles = args.num_m_tiles * args.num_n_tiles;
   const uint32_t N = args.N, nkb = args.nkb;
+  constexpr uint32_t KPS = C::KPS;
+  const uint32_t nks = nkb / KPS;  // stages per tile (nkb is a multiple of KPS)
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < SU; ++s) {
@@ -172,7 +184,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       mbar_init(&u8_empty[s], 4);
     }
     for (int s = 0; s < SB; ++s) {
-      mbar_init(&b_full[s], 5);     // B bytes (TMA) + the four converter warps
+      mbar_init(&b_full[s], A16 ? 2 : 5);  // B (TMA) + the four converter warps, or A and B (TMA)
       mbar_init(&b_empty[s], 1);
     }
     for (int s = 0; s < SA; ++s) {
@@ -196,7 +208,50 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   tc_fence_after();
   const uint32_t tmem_base = *tmem_holder;
 
-  if (warp == 0) {
+  if (A16 && warp == 0) {
+    // ------------------------------------------------------------ TMA producer of A (fp16)
+    if (lane == 0) {
+      prefetch_tmap(&tmA);
+      uint32_t cnt = 0;
+      bool ok = true;
+      constexpr uint32_t PF = 16;  // K blocks of L2 prefetch ahead of the loads
+      uint32_t pf_tile = blockIdx.x, pf_kb = 0;
+      auto pf_step = [&]() {
+        if (pf_tile < num_tiles)
+          tma_prefetch_l2_2d(&tmA, (int32_t)(pf_kb * BK), (int32_t)((pf_tile / args.num_n_tiles) * BM));
+        if (++pf_kb == nkb) {
+          pf_kb = 0;
+          pf_tile += gridDim.x;
+        }
+      };
+      for (uint32_t f = 0; f < PF; ++f) pf_step();
+      for (uint32_t tile = blockIdx.x; ok && tile < num_tiles; tile += gridDim.x) {
+        const uint32_t mt = tile / args.num_n_tiles;
+        for (uint32_t ks = 0; ks < nks; ++ks, ++cnt) {
+          const uint32_t sb = cnt % SB, rb = cnt / SB;
+          if (rb > 0 && !mbar_wait_abortable(&b_empty[sb], (rb - 1) & 1u, abort_flag,
+                                             args.status, ZP_DEV_TIMEOUT_GEMM)) {
+            ok = false;
+            break;
+          }
+          mbar_arrive_expect_tx(&b_full[sb], KPS * A16_BYTES);
+          for (uint32_t h = 0; h < KPS; ++h) {
+            pf_step();
+            tma_load_2d(a_ring + sb * C::AST + h * A16_BYTES, &tmA, (int32_t)((ks * KPS + h) * BK),
+                        (int32_t)(mt * BM), &b_full[sb]);
+          }
+        }
+      }
+      // Stay until the copies issued last have landed (bounded, ignores the abort flag).
+      const uint32_t f_o = cnt > (uint32_t)SB ? cnt - SB : 0;
+      const unsigned long long deadline = clock64() + ZP_WAIT_CYCLES;
+      for (uint32_t i = f_o; i < cnt; ++i)
+        if (!mbar_wait_until(&b_full[i % SB], (i / SB) & 1u, deadline)) {
+          atomicOr(args.status, ZP_DEV_TIMEOUT_GEMM);
+          break;
+        }
+    }
+  } else if (warp == 0) {
     // ------------------------------------------------------------ TMA producer of A (bytes)
     if (lane == 0) {
       prefetch_tmap(&tmA);
@@ -258,16 +313,17 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                                                                 args.mt_per_prime *
                                                                 args.num_n_tiles * N
                                                           : 0u);
-        for (uint32_t kb = 0; kb < nkb; ++kb, ++cnt) {
+        for (uint32_t ks = 0; ks < nks; ++ks, ++cnt) {
           const uint32_t sb = cnt % SB, rb = cnt / SB;
           if (rb > 0 && !mbar_wait_abortable(&b_empty[sb], (rb - 1) & 1u, abort_flag,
                                              args.status, ZP_DEV_TIMEOUT_GEMM)) {
             ok = false;
             break;
           }
-          mbar_arrive_expect_tx(&b_full[sb], N * BK * 2);
-          tma_load_2d(b_ring + sb * B_MAX_BYTES, &tmB, (int32_t)(kb * BK), (int32_t)brow0,
-                      &b_full[sb]);
+          mbar_arrive_expect_tx(&b_full[sb], KPS * N * BK * 2);
+          for (uint32_t h = 0; h < KPS; ++h)
+            tma_load_2d(b_ring + sb * C::BST + h * (N * BK * 2), &tmB, (int32_t)((ks * KPS + h) * BK),
+                        (int32_t)brow0, &b_full[sb]);
         }
       }
       // Stay until the copies issued last have landed (bounded, ignores the abort flag).
@@ -290,7 +346,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       bool ok = true;
       for (uint32_t tile = blockIdx.x; ok && tile < num_tiles; tile += gridDim.x) {
         uint32_t d = tmem_base, kin = 0;
-        for (uint32_t kb = 0; kb < nkb; ++kb) {
+        for (uint32_t ks = 0; ks < nks; ++ks) {
           if (kin == 0) {
             const uint32_t a = acc_cnt & 1u, ra = acc_cnt >> 1;
             if (ra > 0 && !mbar_wait_abortable(&acc_empty[a], (ra - 1) & 1u, abort_flag,
@@ -307,15 +363,20 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             break;
           }
           tc_fence_after();
-          // start-address field += stage offset >> 4 (stays below 2^14: shared memory < 256 KiB)
-          const uint64_t ad = adesc0 + (uint64_t)(sa * (A16_BYTES >> 4));
-          const uint64_t bd = bdesc0 + (uint64_t)(sb * (B_MAX_BYTES >> 4));
-          umma_f16(d, ad, bd, idesc, kin);
-          umma_f16(d, ad + 2u, bd + 2u, idesc, 1u);
-          umma_f16(d, ad + 4u, bd + 4u, idesc, 1u);
-          umma_f16(d, ad + 6u, bd + 6u, idesc, 1u);
+#pragma unroll
+          for (uint32_t h = 0; h < KPS; ++h) {
+            // start-address field += stage offset >> 4 (stays below 2^14: shared memory < 256 KiB)
+            const uint64_t ad = adesc0 + (uint64_t)((sa * C::AST + h * A16_BYTES) >> 4);
+            const uint64_t bd = bdesc0 + (uint64_t)((sb * C::BST + h * N * BK * 2) >> 4);
+            umma_f16(d, ad, bd, idesc, kin);
+            umma_f16(d, ad + 2u, bd + 2u, idesc, 1u);
+            umma_f16(d, ad + 4u, bd + 4u, idesc, 1u);
+            umma_f16(d, ad + 6u, bd + 6u, idesc, 1u);
+            ++kin;
+          }
           umma_commit(&b_empty[sb]);
-          if (++kin == KCHUNK || kb == nkb - 1) {
+          // KCHUNK is a multiple of KPS: a chunk ends with a stage
+          if (kin == KCHUNK || ks == nks - 1) {
             umma_commit(&acc_full[acc_cnt & 1u]);
             ++acc_cnt;
             kin = 0;
@@ -338,6 +399,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     __syncwarp();
   } else if (warp >= 8) {
     // ------------------------------------------------------------ converters
+    if constexpr (!A16) {
     const uint32_t ct = threadIdx.x - 256;  // 0..127
     uint32_t cnt = 0, su = 0, pu = 0;
     bool ok = true;
@@ -382,6 +444,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           pu ^= 1u;
         }
       }
+    }
     }
   } else if (warp >= 4) {
     // ------------------------------------------------------------ epilogue
@@ -702,23 +765,24 @@ __global__ void k_prep_cko(const uint32_t* __restrict__ cko, uint32_t n, uint32_
   if (s) atomicAdd(&colsum[(uint64_t)b * 256 + beta], s);
 }
 
-bool g_attr[64][4][3] = {};  // per device, mode and tile width
+bool g_attr[64][4][3][2] = {};  // per device, mode, tile width and A operand type
 
-template <int MODE, int BT>
+template <int MODE, int BT, bool A16 = false>
 int launch_gemm(zp_ctx* ctx, const CUtensorMap& tmA, const CUtensorMap& tmB, const GemmArgs& ga,
                 cudaStream_t st, uint32_t max_ctas = 0) {
   constexpr int bi = BT == 16 ? 0 : (BT == 32 ? 1 : 2);
-  if (!g_attr[ctx->device & 63][MODE][bi]) {
-    ZP_CUDA(cudaFuncSetAttribute(k_gemm_tc<MODE, BT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 Cfg<MODE>::SMEM));
-    g_attr[ctx->device & 63][MODE][bi] = true;
+  using C = Cfg<MODE, BT, A16>;
+  if (!g_attr[ctx->device & 63][MODE][bi][A16]) {
+    ZP_CUDA(cudaFuncSetAttribute(k_gemm_tc<MODE, BT, A16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 C::SMEM));
+    g_attr[ctx->device & 63][MODE][bi][A16] = true;
   }
   uint32_t tiles = ga.num_m_tiles * ga.num_n_tiles;
   uint32_t grid = tiles < (uint32_t)ctx->num_sms ? tiles : (uint32_t)ctx->num_sms;
   if (max_ctas && grid > max_ctas) grid = max_ctas;
   zp_clear_pending_error();
   ctx->launches++;
-  k_gemm_tc<MODE, BT><<<grid, NTHREADS, Cfg<MODE>::SMEM, st>>>(tmA, tmB, ga);
+  k_gemm_tc<MODE, BT, A16><<<grid, NTHREADS, C::SMEM, st>>>(tmA, tmB, ga);
   ZP_CUDA(cudaGetLastError());
   return ZP_OK;
 }
@@ -732,10 +796,11 @@ static uint32_t pick_bt(uint32_t B) { return B <= 16 ? 16u : (B <= 32 ? 32u : 64
 // Q(b, k) = dQ[b*C + k] (rows) or dQ[k*B + b] (cols). D given by its tensor map.
 int zp_launch_answer_tc(zp_db* db, const CUtensorMap& tmD, uint32_t Rrows, const uint32_t* dQ,
                         uint32_t B, bool q_cols, uint32_t* dOut, uint64_t out_ld, bool hint,
-                        const uint32_t* rowsum, cudaStream_t st) {
+                        const uint32_t* rowsum, cudaStream_t st, bool a16) {
   zp_ctx* ctx = db->ctx;
   const uint32_t C = db->C;
-  const uint32_t Kp = (C + 63) / 64 * 64;
+  // the fp16 A path takes two K blocks per stage: K padded to 128
+  const uint32_t Kp = a16 ? (C + 127) / 128 * 128 : (C + 63) / 64 * 64;
   const uint32_t BT = pick_bt(B);
   const uint32_t N = 4 * BT;
   const uint32_t nnt = (B + BT - 1) / BT;
@@ -778,9 +843,59 @@ int zp_launch_answer_tc(zp_db* db, const CUtensorMap& tmD, uint32_t Rrows, const
     if (BT == 32) return launch_gemm<MODE_HINT, 32>(ctx, tmD, tmB, ga, st);
     return launch_gemm<MODE_HINT, 64>(ctx, tmD, tmB, ga, st);
   }
+  if (a16) {
+    if (BT == 16) return launch_gemm<MODE_ANS, 16, true>(ctx, tmD, tmB, ga, st);
+    if (BT == 32) return launch_gemm<MODE_ANS, 32, true>(ctx, tmD, tmB, ga, st);
+    return launch_gemm<MODE_ANS, 64, true>(ctx, tmD, tmB, ga, st);
+  }
   if (BT == 16) return launch_gemm<MODE_ANS, 16>(ctx, tmD, tmB, ga, st);
   if (BT == 32) return launch_gemm<MODE_ANS, 32>(ctx, tmD, tmB, ga, st);
   return launch_gemm<MODE_ANS, 64>(ctx, tmD, tmB, ga, st);
+}
+
+// The resident fp16 copy of D for the tensor-core answers: row r, column k < Kp (C rounded
+// up to 128) holds D[r][k] - 128 (k < C) or -128 (the padding, the centred value of a zero
+// byte, as the byte path's out-of-range loads give). dRows lists the rows to write (NULL = all R).
+// grid (ceil(Kp / 2048), min(rows, 32768)), rows strided over grid.y; eight columns per thread.
+__global__ void k_d16_rows(const uint8_t* __restrict__ D, uint64_t ld, uint32_t C, uint32_t Kp,
+                           const uint32_t* __restrict__ dRows, uint32_t nrows,
+                           __half* __restrict__ D16) {
+  const uint32_t k0 = blockIdx.x * 2048 + threadIdx.x * 8;
+  if (k0 >= Kp) return;
+  for (uint32_t idx = blockIdx.y; idx < nrows; idx += gridDim.y) {
+  const uint32_t r = dRows ? dRows[idx] : idx;
+  const uint8_t* src = D + (uint64_t)r * ld;
+  uint32_t v[8];
+  if (k0 + 8 <= C) {
+    const uint2 w = *reinterpret_cast<const uint2*>(src + k0);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      v[j] = (w.x >> (8 * j)) & 0xFFu;
+      v[4 + j] = (w.y >> (8 * j)) & 0xFFu;
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = k0 + j < C ? src[k0 + j] : 0u;
+  }
+  uint32_t h[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const __half2 x = __halves2half2(__int2half_rn((int)v[2 * j] - 128), __int2half_rn((int)v[2 * j + 1] - 128));
+    h[j] = *reinterpret_cast<const uint32_t*>(&x);
+  }
+  *reinterpret_cast<uint4*>(D16 + (uint64_t)r * Kp + k0) = make_uint4(h[0], h[1], h[2], h[3]);
+  }
+}
+
+int zp_launch_d16_rows(zp_db* db, const uint32_t* dRows, uint32_t nrows, cudaStream_t st) {
+  if (nrows == 0) return ZP_OK;
+  const uint32_t Kp = (db->C + 127) / 128 * 128;
+  zp_clear_pending_error();
+  db->ctx->launches++;
+  dim3 grid((Kp + 2047) / 2048, nrows < 32768u ? nrows : 32768u);
+  k_d16_rows<<<grid, 256, 0, st>>>(db->dD, db->ld, db->C, Kp, dRows, nrows, static_cast<__half*>(db->d_D16));
+  ZP_CUDA(cudaGetLastError());
+  return ZP_OK;
 }
 
 // Compression products V4[b][a][r][67] = sum_i Hbyte_a[r][i] cko[b][i] (n <= 1024).

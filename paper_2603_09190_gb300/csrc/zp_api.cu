@@ -332,6 +332,7 @@ extern "C" int zp_init(int device, const zp_params* P, zp_ctx** out) {
     // from 8 queries on the RNS compression is faster (measured at 1 and 8 GiB, n = 1024)
     c->rns_min_batch = 8;
     c->gemv_max_batch = 4;  // one dp4a pass beats the tensor cores up to 4 queries (1 GiB)
+    c->answer_fp16 = 1;
     {
       zp_rns_dev h;
       rns_setup(c, h);
@@ -395,6 +396,12 @@ extern "C" int zp_set_option(zp_ctx* c, const char* name, int64_t value) {
     c->gemv_max_batch = (uint32_t)value;
     return ZP_OK;
   }
+  if (k == "answer_fp16") {
+    if (value < 0 || value > 1)
+      return zp_set_error(ZP_EINVAL, "zp_set_option: answer_fp16=%lld out of [0, 1]", (long long)value);
+    c->answer_fp16 = (uint32_t)value;
+    return ZP_OK;
+  }
   if (k == "rns_min_batch") {
     if (value < 0 || value > 4096)
       return zp_set_error(ZP_EINVAL, "zp_set_option: rns_min_batch=%lld out of [0, 4096]", (long long)value);
@@ -412,6 +419,7 @@ extern "C" int zp_get_option(const zp_ctx* c, const char* name, int64_t* value) 
   else if (k == "overlap_sms") *value = c->overlap_sms;
   else if (k == "rns_min_batch") *value = c->rns_min_batch;
   else if (k == "gemv_max_batch") *value = c->gemv_max_batch;
+  else if (k == "answer_fp16") *value = c->answer_fp16;
   else return zp_set_error(ZP_EINVAL, "zp_get_option: unknown option '%s'", name);
   return ZP_OK;
 }
@@ -522,6 +530,7 @@ extern "C" int zp_db_destroy(zp_db* db) {
   if (db->d_hpl_rowsum) cudaFree(db->d_hpl_rowsum);
   if (db->d_rns_hpl) cudaFree(db->d_rns_hpl);
   if (db->d_rns_rowsum) cudaFree(db->d_rns_rowsum);
+  if (db->d_D16) cudaFree(db->d_D16);
   if (db->side) {
     cudaStreamDestroy(db->side);
     cudaEventDestroy(db->ev_fork);
@@ -700,6 +709,7 @@ extern "C" int zp_update_rows(zp_db* db, const uint32_t* hRows, uint32_t k, cons
     db->ctx->launches++;
     rc = zp_launch_copy_rows(dNew, db->C, const_cast<uint8_t*>(db->dD), db->ld, db->C, dRows, k, 0, st);
     if (!rc) rc = zp_launch_rowsum(db, dRows, k, st);
+    if (!rc && db->d_D16) rc = zp_launch_d16_rows(db, dRows, k, st);
     if (rc) return rc;
     std::vector<uint8_t>& stale = stale_flags(db);
     for (uint32_t j = 0; j < k; ++j) {
@@ -728,8 +738,9 @@ extern "C" int zp_answer(zp_db* db, const uint32_t* dQ, uint32_t B, uint32_t* dA
                           B == 1 && c->overlap_sms ? (uint32_t)c->num_sms - c->overlap_sms : 0u);
   if (c->answer_path == ZP_PATH_SIMT)
     return zp_launch_answer_simt(db, dQ, B, db->C, dAns, db->R, 1, db->dD, db->R, db->ld, st);
-  return zp_launch_answer_tc(db, db->tmap_gemm, db->R, dQ, B, false, dAns, db->R, false,
-                             db->d_rowsum, st);
+  const bool a16 = db->d_D16 && c->answer_fp16;
+  return zp_launch_answer_tc(db, a16 ? db->tmap_d16 : db->tmap_gemm, db->R, dQ, B, false, dAns, db->R,
+                             false, db->d_rowsum, st, a16);
 }
 
 extern "C" int zp_register_client(zp_ctx* c, const uint32_t* hM, uint32_t L, zp_client** out) {
@@ -1139,6 +1150,27 @@ extern "C" int zp_autotune(zp_db* db, void* stream, int64_t* chosen) {
   } catch (const std::bad_alloc&) {
     return zp_set_error(ZP_ENOMEM, "zp_autotune: host allocation failed");
   }
+}
+
+extern "C" int zp_db_prepare_fp16(zp_db* db, void* stream) {
+  if (!db) return zp_set_error(ZP_EINVAL, "zp_db_prepare_fp16: null argument");
+  if (db->d_D16) return ZP_OK;
+  ZP_CUDA(cudaSetDevice(db->ctx->device));
+  const uint64_t Kp = (db->C + 127) / 128 * 128;  // two K blocks per stage of the fp16 path
+  const size_t bytes = (size_t)db->R * Kp * 2;
+  if (cudaMalloc(&db->d_D16, bytes) != cudaSuccess) {
+    db->d_D16 = nullptr;
+    zp_clear_pending_error();
+    return zp_set_error(ZP_ENOMEM, "zp_db_prepare_fp16: cudaMalloc(%zu bytes)", bytes);
+  }
+  int rc = zp_encode_tmap_2d(&db->tmap_d16, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, db->d_D16, Kp, db->R, Kp * 2,
+                             64, 128, CU_TENSOR_MAP_SWIZZLE_128B);
+  if (!rc) rc = zp_launch_d16_rows(db, nullptr, db->R, static_cast<cudaStream_t>(stream));
+  if (rc) {
+    cudaFree(db->d_D16);
+    db->d_D16 = nullptr;
+  }
+  return rc;
 }
 
 extern "C" int zp_db_prepare_rns(zp_db* db, void* stream) {

@@ -53,6 +53,7 @@ struct zp_ctx {
   uint32_t gamma_w[3]; // packing scale gamma, little-endian 32-bit words (gamma < 2^96)
   uint32_t rns_min_batch;  // batches of at least this many queries compress in RNS (0: never)
   uint32_t gemv_max_batch; // batches of at most this many queries (<= 4) answer by the GEMV
+  uint32_t answer_fp16;    // tensor-core answers read a database's fp16 copy when it has one
   zp_rns_dev* d_rns;   // RNS constants (device)
   std::vector<uint32_t> rns_p;  // the primes (host)
   int num_sms;
@@ -93,6 +94,10 @@ struct zp_db {
   CUtensorMap tmap_gemv;   // D as a 2-D u8 tensor, box 256 x 64 (GEMV on the whole GPU)
   CUtensorMap tmap_gemv128;  // box 256 x 128 (GEMV beside the compression products)
   CUtensorMap tmap_gemm;   // D as a 2-D u8 tensor, box 64 x 128 (tensor-core products)
+  // resident centred fp16 copy of D (R x Kp, Kp = C rounded up to 128; built on request):
+  // the A operand of the tensor-core answers without conversion in shared memory
+  void* d_D16;
+  CUtensorMap tmap_d16;    // box 64 x 128, 128-byte swizzle
   // hint in compression layout (library-owned)
   uint32_t* d_hneg;        // R x n u32: -D.A mod 2^32
   uint8_t* d_hpl;          // 4 Rp x lda bytes: row 128 g + 32 a + t = byte a of d_hneg row 32 g + t
@@ -148,7 +153,9 @@ int zp_launch_copy_rows(const uint8_t* src, uint64_t lds, uint8_t* dst, uint64_t
                         const uint32_t* rows, uint32_t cnt, int gather, cudaStream_t st);
 int zp_launch_answer_tc(zp_db* db, const CUtensorMap& tmD, uint32_t Rrows, const uint32_t* dQ,
                         uint32_t B, bool q_cols, uint32_t* dOut, uint64_t out_ld, bool hint,
-                        const uint32_t* rowsum, cudaStream_t st);
+                        const uint32_t* rowsum, cudaStream_t st, bool a16 = false);
+// the fp16 copy of the listed rows of D (dRows device, NULL = all R) (k_gemm_tc.cu)
+int zp_launch_d16_rows(zp_db* db, const uint32_t* dRows, uint32_t nrows, cudaStream_t st);
 int zp_launch_vmul_tc(zp_db* db, const uint32_t* dCKO, uint32_t B, uint32_t* V4, cudaStream_t st,
                       uint32_t max_ctas);
 int zp_launch_hint_planes_rowsum(zp_db* db, const uint32_t* rows, uint32_t nrows, cudaStream_t st);

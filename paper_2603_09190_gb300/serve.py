@@ -192,6 +192,8 @@ class ZipBackend:
         dev = db.D.device
         if Bm >= 8 and n <= 1024:
             db.prepare_rns()  # large batches compress in RNS: build its tables now, not mid-run
+        if Bm > 4:
+            db.prepare_fp16()  # batches of five and more answer from the fp16 copy of D
         self.d[name] = {
             "db": db, "A": A, "stream": torch.cuda.Stream(dev),
             "hQ": torch.empty((Bm, C), dtype=torch.int32, pin_memory=True),
@@ -211,7 +213,8 @@ class ZipBackend:
         Rp = (db.R + 31) // 32 * 32
         Rq = (db.d1p + 31) // 32 * 32
         rns = 153 * 4 * Rq * (math.ceil(n / 16) * 16 + 4) if self.max_batch >= 8 and n <= 1024 else 0
-        return db.R * db.ld + db.R * n * 8 + 4 * Rp * math.ceil(n / 16) * 16 + rns + \
+        d16 = 2 * db.R * ((db.C + 127) // 128 * 128) if self.max_batch > 4 else 0
+        return db.R * db.ld + db.R * n * 8 + 4 * Rp * math.ceil(n / 16) * 16 + rns + d16 + \
             sum(t.numel() * t.element_size() for k, t in x.items() if k in ("Q", "K", "T", "ans"))
 
     def batch_bytes(self, name, B):

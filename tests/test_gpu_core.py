@@ -142,9 +142,38 @@ def test_batched_answer_parity(zp, ctx, R, C, B):
     db.close()
 
 
+@pytest.mark.parametrize("R,C,B", [(100, 333, 5), (1024, 1024, 8), (257, 2000, 33), (1000, 4097, 17),
+                                   (130, 1030, 64), (300, 3000, 65), (129, 700, 100)])
+def test_batched_answer_fp16_copy(zp, ctx, R, C, B):
+    """The resident fp16 copy of D as the A operand (TMA straight into the tensor-core
+    pipeline, no converters): the same bits as the oracle, ragged R and C (its padding holds
+    the centred value of a zero byte), and after row updates the copy follows D."""
+    D = synth.database(R, C, B + 7)
+    Q = synth.uniform_queries(B, C, B + 8)
+    dD, ld = to_dev_db(zp, D)
+    db = zp.Database(ctx, dD, R, C, ld)
+    db.prepare_fp16()
+    got = u32_host(db.answer(u32_dev(Q)))
+    assert np.array_equal(got, lwe.matmat_mod_q(D, Q.T).T)
+    rows = np.array([0, R // 2, R - 1], dtype=np.uint32)
+    new = synth.database(len(rows), C, B + 9)
+    db.update_rows(rows, torch.from_numpy(new).cuda())
+    D2 = D.copy()
+    D2[rows] = new
+    got = u32_host(db.answer(u32_dev(Q)))
+    assert np.array_equal(got, lwe.matmat_mod_q(D2, Q.T).T)
+    ctx.set_option("answer_fp16", 0)  # the byte path on the same database agrees
+    try:
+        assert np.array_equal(u32_host(db.answer(u32_dev(Q))), got)
+    finally:
+        ctx.set_option("answer_fp16", 1)
+    db.close()
+
+
 @pytest.mark.parametrize("dval,qval", [(0, 0), (255, 0xFFFFFFFF), (0, 0xFFFFFFFF), (255, 0),
                                        ("alt", 0xFF00FF00)])
-def test_batched_answer_extremes(zp, ctx, dval, qval):
+@pytest.mark.parametrize("fp16", [False, True])
+def test_batched_answer_extremes(zp, ctx, dval, qval, fp16):
     """Centred products at their extremes: |A'B'| = 2^14 for every term, so each 1024-long
     chunk sum sits exactly at the fp32 exactness limit 2^24."""
     R, C, B = 256, 3072, 20
@@ -156,6 +185,8 @@ def test_batched_answer_extremes(zp, ctx, dval, qval):
     Q[1::2] = ~Q[1::2]
     dD, ld = to_dev_db(zp, D)
     db = zp.Database(ctx, dD, R, C, ld)
+    if fp16:
+        db.prepare_fp16()
     got = u32_host(db.answer(u32_dev(Q)))
     assert np.array_equal(got, lwe.matmat_mod_q(D, Q.T).T)
     db.close()
