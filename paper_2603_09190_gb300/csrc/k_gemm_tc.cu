@@ -66,17 +66,32 @@ enum { MODE_ANS = 0, MODE_HINT = 1, MODE_CMP = 2, MODE_RNS = 3 };
 // rows). For N <= 128 a stage holds KPS = 2 K blocks (one wait and one commit per two K
 // blocks: measured 11-14 % faster); the 256-wide tile keeps four one-block stages (two
 // two-block stages were slower).
+#ifndef ZP_ANS_SU
+#define ZP_ANS_SU 2
+#endif
+#ifndef ZP_ANS_SB
+#define ZP_ANS_SB 4
+#endif
+#ifndef ZP_ANS_FIT
+#define ZP_ANS_FIT 0
+#endif
 template <int MODE, int BT = 64, bool A16 = false>
 struct Cfg {
+  static constexpr bool ANS_BYTES = MODE == MODE_ANS && !A16;
   static constexpr int KPS = (A16 && BT < 64) ? 2 : 1;                     // K blocks per stage
-  static constexpr int BST = A16 ? KPS * 4 * BT * BK * 2 : B_MAX_BYTES;   // B stage stride
+  static constexpr int BST = A16 ? KPS * 4 * BT * BK * 2
+                                 : ((ANS_BYTES && ZP_ANS_FIT) ? 4 * BT * BK * 2 : B_MAX_BYTES);  // B stage stride
   static constexpr int AST = KPS * A16_BYTES;                              // A stage stride
   static constexpr int SB = A16 ? (BT == 16 ? 4 : (BT == 32 ? 3 : 4))
-                                : ((MODE == MODE_CMP || MODE == MODE_RNS) ? 3 : 4);
+                                : ((MODE == MODE_CMP || MODE == MODE_RNS) ? 3 : (ANS_BYTES ? ZP_ANS_SB : 4));
   static constexpr int SA = SB;  // the A and B stages of a K block are filled and freed together
-  static constexpr int SU = A16 ? 0 : 2;  // stages of two K blocks of A bytes
+  // stages of two K blocks of A bytes: the ring that hides the HBM latency
+  static constexpr int SU_FIT = (224 * 1024 - SB * BST - SA * AST) / U8_STAGE;
+  static constexpr int SU = A16 ? 0 : (ANS_BYTES ? (ZP_ANS_SU < SU_FIT ? ZP_ANS_SU : SU_FIT) : 2);
   static constexpr int STG = (MODE == MODE_CMP || MODE == MODE_RNS) ? STG_BYTES : 0;
   static constexpr int SMEM = SB * BST + SA * AST + SU * U8_STAGE + STG + 1024 + 512;
+  static_assert(SMEM <= 232448, "shared memory above the per-block limit");
+  static_assert(A16 || SU >= 1, "at least one byte stage");
 };
 
 struct GemmArgs {
