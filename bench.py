@@ -734,6 +734,15 @@ def run_lwe_compress(args, world, rank, local):
         olc.lwe_compress(pk, ck, a, 12345, 1 << 64)
         cpu = {"value": (time.perf_counter() - t0) * 1e3, "unit": "ms", "cores": 1, "kind": "oracle",
                "sample": "one (630, 2^64) ciphertext, Python integers"}
+    # roofline of the dominant kernel (k_lc_products): word multiply-accumulates of the
+    # Montgomery products, 2 (2L)^2 per product, about n * 32 + 2 products per (630, 2^64)
+    # ciphertext (the set bits of 64-bit exponents, the pairwise tree, the final factor),
+    # against 152 SMs x 64 IMAD.WIDE lanes x 2.07 GHz; integer ALU-bound (ncu: ALU pipe 64 %)
+    macs = sets[0]["ct_per_s_256"] * (630 * 32 + 2) * 2 * (2 * bits // 32) ** 2
+    alu_peak = 152 * 64 * 2.07e9
+    roof = {"bound": "alu", "achieved": macs, "peak": alu_peak, "unit": "word MAC/s",
+            "frac": macs / alu_peak, "traffic": None, "kernel": "k_lc_products (+ pairwise tree)",
+            "peak_kind": "derived: 152 SMs x 64 IMAD.WIDE lanes x 2.07 GHz"}
     if rank == 0:
         head = sets[0]
         line = {"metric": "single LWE ciphertext compression latency, (n, q) = (630, 2^64), 3072-bit Paillier",
@@ -743,7 +752,7 @@ def run_lwe_compress(args, world, rank, local):
                 "config": {"workload": "standalone compression: single-compression parameter sets and batched "
                                        "(630, 2^64), 3072-bit modulus, inputs resident in HBM",
                            "key_bits": bits, "ell": ell, "T_folded": T},
-                "sets": sets, "batched_630_64": batched, "cpu_baseline": cpu}
+                "sets": sets, "batched_630_64": batched, "roofline": roof, "cpu_baseline": cpu}
         print(json.dumps(line))
     return 0
 
