@@ -628,6 +628,28 @@ def run_client_hint(args, world, rank, local):
         e1.record()
         torch.cuda.synchronize()
         comb[B] = e0.elapsed_time(e1) / steps
+    # client-side pieces: ChaCha20 keystream (1 GiB), ck_r from a seed, modexp and decryption
+    def ev_time(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+    ks = torch.empty(1 << 28, dtype=torch.int32, device=dev)
+    ks_ms = ev_time(lambda: zp.prg_chacha20(bytes(32), bytes(12), 0, ks), 5)
+    del ks
+    ck16 = torch.empty((16384, 2 * L), dtype=torch.int32, device=dev)
+    exp_ms = ev_time(lambda: cl.expand_ckr(bytes(range(32)), 16384, out=ck16), 5)
+    lam = synth.random_odd_modulus(KEY_BITS, 5)   # 2048-bit exponents (timing: any value works)
+    ct4 = ck16[:4096].contiguous()
+    pw_ms = ev_time(lambda: cl.powm(ct4, lam), 2)
+    dec_ms = ev_time(lambda: cl.decrypt(ct4, lam, lam), 2)
+    client = {"chacha20_1gib_ms": ks_ms, "chacha20_gb_s": 2 ** 30 / (ks_ms * 1e-3) / 1e9,
+              "expand_ckr_16384_ms": exp_ms, "powm_2048bit_exp_per_s": 4096 / (pw_ms * 1e-3),
+              "decrypt_per_s": 4096 / (dec_ms * 1e-3)}
     status = ctx.device_status()
     if rank == 0:
         line = {"metric": METRIC, "value": R * C / (k_ms * 1e-3) / 1e9, "unit": "GB/s",
@@ -640,6 +662,7 @@ def run_client_hint(args, world, rank, local):
                            "R": R, "C": C, "n": n, "d1p": db.d1p},
                 "client_hint_s": k_ms / 1e3,
                 "combine_ms": {"B1": comb[1], "B64": comb[64]},
+                "client_side": client,
                 "gpu_launches": ctx.kernel_launches() - launches0,
                 "device_status": status}
         print(json.dumps(line))
