@@ -223,7 +223,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   tc_fence_after();
   const uint32_t tmem_base = *tmem_holder;
 
-  if (A16 && warp == 0) {
+  if (warp == 0) {
+    if constexpr (A16) {
     // ------------------------------------------------------------ TMA producer of A (fp16)
     if (lane == 0) {
       prefetch_tmap(&tmA);
@@ -266,7 +267,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           break;
         }
     }
-  } else if (warp == 0) {
+    } else {
     // ------------------------------------------------------------ TMA producer of A (bytes)
     if (lane == 0) {
       prefetch_tmap(&tmA);
@@ -314,6 +315,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           atomicOr(args.status, ZP_DEV_TIMEOUT_GEMM);
           break;
         }
+    }
     }
   } else if (warp == 2) {
     // ------------------------------------------------------------ TMA producer of B (fp16)
