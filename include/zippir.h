@@ -292,8 +292,11 @@ int zp_device_status(zp_ctx* ctx, uint32_t* code);
  * rounded up to 128; twice the bytes of D) and fills it with D - 128 (centred, exact).
  * From then on the tensor-core answers (batches above gemv_max_batch) read it as their A
  * operand through TMA, with no byte-to-fp16 conversion in shared memory; zp_update_rows
- * keeps it current. Option "answer_fp16" (zp_set_option, default 1) turns its use off (0)
- * or on (1). Asynchronous on `stream`. Errors: ZP_EINVAL, ZP_ENOMEM, ZP_ECUDA. */
+ * keeps it current. With it, the residue planes of H' used by the RNS compression (when
+ * built, by zp_db_prepare_rns or the first large batch) also get an fp16 copy (twice their
+ * bytes), kept current by hint regeneration. Option "answer_fp16" (zp_set_option, default
+ * 1) turns the use of both off (0) or on (1). Asynchronous on `stream`.
+ * Errors: ZP_EINVAL, ZP_ENOMEM, ZP_ECUDA. */
 int zp_db_prepare_fp16(zp_db* db, void* stream);
 
 /* ChaCha20 keystream (RFC 8439 block function) on the GPU: dOut[0 .. nwords) receives the

@@ -82,7 +82,8 @@ struct Cfg {
   static constexpr int BST = A16 ? KPS * 4 * BT * BK * 2
                                  : ((ANS_BYTES && ZP_ANS_FIT) ? 4 * BT * BK * 2 : B_MAX_BYTES);  // B stage stride
   static constexpr int AST = KPS * A16_BYTES;                              // A stage stride
-  static constexpr int SB = A16 ? (BT == 16 ? 4 : (BT == 32 ? 3 : 4))
+  static constexpr int SB = A16 ? (MODE == MODE_RNS ? (BT == 32 ? 2 : 3)  // the RNS epilogue stages rows
+                                                   : (BT == 16 ? 4 : (BT == 32 ? 3 : 4)))
                                 : ((MODE == MODE_CMP || MODE == MODE_RNS) ? 3 : (ANS_BYTES ? ZP_ANS_SB : 4));
   static constexpr int SA = SB;  // the A and B stages of a K block are filled and freed together
   // stages of two K blocks of A bytes: the ring that hides the HBM latency
@@ -165,7 +166,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
               const GemmArgs args) {
   using C = Cfg<MODE, BT, A16>;
-  static_assert(!A16 || MODE == MODE_ANS, "fp16 A operand: batched answers only");
+  static_assert(!A16 || MODE == MODE_ANS || MODE == MODE_RNS,
+                "fp16 A operand: batched answers and RNS compression products only");
   constexpr int SB = C::SB, SA = C::SA, SU = C::SU;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
@@ -1064,6 +1066,11 @@ int zp_launch_rns_products(zp_db* db, const uint32_t* dCKO, uint32_t B, uint32_t
   ga.mt_per_prime = db->Rq / 32;
   ga.d1p = db->d1p;
   ga.rns = ctx->d_rns;
+  if (db->d_rns16 && ctx->answer_fp16) {  // the resident fp16 copy of the residue planes
+    if (BT == 16) return launch_gemm<MODE_RNS, 16, true>(ctx, db->tmap_rns16, tmB, ga, st);
+    if (BT == 32) return launch_gemm<MODE_RNS, 32, true>(ctx, db->tmap_rns16, tmB, ga, st);
+    return launch_gemm<MODE_RNS, 64, true>(ctx, db->tmap_rns16, tmB, ga, st);
+  }
   if (BT == 16) return launch_gemm<MODE_RNS, 16>(ctx, db->tmap_rns, tmB, ga, st);
   if (BT == 32) return launch_gemm<MODE_RNS, 32>(ctx, db->tmap_rns, tmB, ga, st);
   return launch_gemm<MODE_RNS, 64>(ctx, db->tmap_rns, tmB, ga, st);

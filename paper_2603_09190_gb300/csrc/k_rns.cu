@@ -8,6 +8,8 @@
 // the layout of the tensor-core product: row k 4 Rq + 128 g + 32 a + t holds byte a of
 // H'[32 g + t, :] mod p_k. Built once per database (about a second per GiB of database at
 // n = 1024) and for the packed rows of updated rows after each hint regeneration.
+#include <cuda_fp16.h>
+
 #include "zp_internal.cuh"
 
 namespace {
@@ -90,7 +92,41 @@ __global__ void k_rns_rowsum(const uint8_t* __restrict__ planes, uint64_t ld, ui
   if (lane == 0) out[row] = s;
 }
 
+// Centred fp16 copy of the plane rows of the listed packed rows: row k 4 Rq + 128 g + 32 a
+// + t (rp = 32 g + t) for every prime k and plane a, columns < Kp (n rounded up to 128),
+// value byte - 128 (-128 in the padding). grid (ceil(Kp / 2048), nprows, ZP_RNS_K * 4).
+__global__ void k_rns16_rows(const uint8_t* __restrict__ planes, uint64_t ld, uint32_t n,
+                             uint32_t Kp, const uint32_t* __restrict__ prows, uint32_t Rq,
+                             __half* __restrict__ out) {
+  const uint32_t k0 = blockIdx.x * 2048 + threadIdx.x * 8;
+  if (k0 >= Kp) return;
+  const uint32_t rp = prows ? prows[blockIdx.y] : blockIdx.y;
+  const uint32_t k = blockIdx.z >> 2, a = blockIdx.z & 3u;
+  const uint64_t row = (uint64_t)k * 4 * Rq + 128ull * (rp >> 5) + 32 * a + (rp & 31u);
+  const uint8_t* src = planes + row * ld;
+  uint32_t h[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const uint32_t c0 = k0 + 2 * j, c1 = c0 + 1;
+    const int v0 = c0 < n ? (int)src[c0] : 0, v1 = c1 < n ? (int)src[c1] : 0;
+    const __half2 x = __halves2half2(__int2half_rn(v0 - 128), __int2half_rn(v1 - 128));
+    h[j] = *reinterpret_cast<const uint32_t*>(&x);
+  }
+  *reinterpret_cast<uint4*>(out + row * Kp + k0) = make_uint4(h[0], h[1], h[2], h[3]);
+}
+
 }  // namespace
+
+int zp_launch_rns16_rows(zp_db* db, const uint32_t* dRows, uint32_t nprows, cudaStream_t st) {
+  if (nprows == 0 || !db->d_rns16) return ZP_OK;
+  const uint32_t Kp = (db->ctx->P.n + 127) / 128 * 128;
+  zp_clear_pending_error();
+  db->ctx->launches++;
+  k_rns16_rows<<<dim3((Kp + 2047) / 2048, nprows, ZP_RNS_K * 4), 256, 0, st>>>(
+      db->d_rns_hpl, db->hpl_ld, db->ctx->P.n, Kp, dRows, db->Rq, static_cast<__half*>(db->d_rns16));
+  ZP_CUDA(cudaGetLastError());
+  return ZP_OK;
+}
 
 int zp_launch_rns_planes(zp_db* db, const uint32_t* dRows, uint32_t nprows, cudaStream_t st) {
   zp_ctx* ctx = db->ctx;
@@ -106,5 +142,5 @@ int zp_launch_rns_planes(zp_db* db, const uint32_t* dRows, uint32_t nprows, cuda
   k_rns_rowsum<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(
       db->d_rns_hpl, db->hpl_ld, n, dRows, nprows, db->Rq, db->d_rns_rowsum);
   ZP_CUDA(cudaGetLastError());
-  return ZP_OK;
+  return zp_launch_rns16_rows(db, dRows, nprows, st);  // keeps the fp16 copy current, if any
 }

@@ -531,6 +531,7 @@ extern "C" int zp_db_destroy(zp_db* db) {
   if (db->d_rns_hpl) cudaFree(db->d_rns_hpl);
   if (db->d_rns_rowsum) cudaFree(db->d_rns_rowsum);
   if (db->d_D16) cudaFree(db->d_D16);
+  if (db->d_rns16) cudaFree(db->d_rns16);
   if (db->side) {
     cudaStreamDestroy(db->side);
     cudaEventDestroy(db->ev_fork);
@@ -578,7 +579,28 @@ int zp_ensure_rns(zp_db* db, cudaStream_t st) {
   int rc = zp_encode_tmap_2d(&db->tmap_rns, CU_TENSOR_MAP_DATA_TYPE_UINT8, db->d_rns_hpl, n, rows,
                              db->hpl_ld, 128, 128, CU_TENSOR_MAP_SWIZZLE_128B);
   if (rc) return rc;
-  return zp_launch_rns_planes(db, nullptr, db->d1p, st);
+  rc = zp_launch_rns_planes(db, nullptr, db->d1p, st);
+  return rc ? rc : zp_ensure_rns16(db, st);
+}
+
+int zp_ensure_rns16(zp_db* db, cudaStream_t st) {
+  if (db->d_rns16 || !db->d_rns_hpl || !db->d_D16) return ZP_OK;
+  const uint64_t Kp = (db->ctx->P.n + 127) / 128 * 128;
+  const uint64_t rows = (uint64_t)ZP_RNS_K * 4 * db->Rq;
+  const size_t bytes = (size_t)rows * Kp * 2;
+  if (cudaMalloc(&db->d_rns16, bytes) != cudaSuccess) {
+    db->d_rns16 = nullptr;
+    zp_clear_pending_error();
+    return zp_set_error(ZP_ENOMEM, "fp16 RNS planes: cudaMalloc(%zu bytes)", bytes);
+  }
+  int rc = zp_encode_tmap_2d(&db->tmap_rns16, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, db->d_rns16, Kp, rows,
+                             Kp * 2, 64, 128, CU_TENSOR_MAP_SWIZZLE_128B);
+  if (!rc) rc = zp_launch_rns16_rows(db, nullptr, db->Rq, st);  // every row, the padding too
+  if (rc) {
+    cudaFree(db->d_rns16);
+    db->d_rns16 = nullptr;
+  }
+  return rc;
 }
 
 static int alloc_hint_state(zp_db* db) {
@@ -1169,8 +1191,9 @@ extern "C" int zp_db_prepare_fp16(zp_db* db, void* stream) {
   if (rc) {
     cudaFree(db->d_D16);
     db->d_D16 = nullptr;
+    return rc;
   }
-  return rc;
+  return zp_ensure_rns16(db, static_cast<cudaStream_t>(stream));  // if the RNS planes exist
 }
 
 extern "C" int zp_db_prepare_rns(zp_db* db, void* stream) {

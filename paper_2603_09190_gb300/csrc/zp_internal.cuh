@@ -115,6 +115,10 @@ struct zp_db {
   uint32_t* d_rns_rowsum;  // byte sums of its rows
   uint32_t Rq;
   CUtensorMap tmap_rns;    // box 64 x 128
+  // their centred fp16 copy (rows x Kp, Kp = n rounded up to 128), built when the database
+  // has its fp16 copy of D: the A operand of the RNS products without conversion
+  void* d_rns16;
+  CUtensorMap tmap_rns16;
   std::vector<const uint32_t*> cl_cache;  // client constants last uploaded to s_clients
   cudaStream_t side;       // internal stream of zp_respond's overlap (lazily created)
   cudaEvent_t ev_fork, ev_join;
@@ -175,6 +179,11 @@ int zp_launch_decrypt(const zp_client* cl, const uint32_t* e, uint32_t ew, const
 int zp_launch_rns_planes(zp_db* db, const uint32_t* dRows, uint32_t nprows, cudaStream_t st);
 // allocates and builds the RNS planes of H' on first use (zp_api.cu)
 int zp_ensure_rns(zp_db* db, cudaStream_t st);
+// the fp16 copy of the RNS plane rows of the listed packed rows (dRows device; NULL = packed
+// rows 0 .. nprows - 1, the padding rows up to Rq included) (k_rns.cu)
+int zp_launch_rns16_rows(zp_db* db, const uint32_t* dRows, uint32_t nprows, cudaStream_t st);
+// builds the fp16 copy of the RNS planes when the database has both (zp_api.cu)
+int zp_ensure_rns16(zp_db* db, cudaStream_t st);
 int zp_launch_rns_products(zp_db* db, const uint32_t* dCKO, uint32_t B, uint32_t* X, cudaStream_t st);
 // B in 1..4 queries (dq: B x C, dans: B x R); max_ctas limits the single-query grid.
 int zp_launch_gemv(zp_db* db, const uint32_t* dq, uint32_t B, uint32_t* dans, cudaStream_t st,

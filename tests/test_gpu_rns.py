@@ -39,10 +39,12 @@ def _db(zp, c, D):
 
 @pytest.mark.parametrize("R,C,n,B,secret", [(60, 32, 8, 1, "uniform"), (100, 48, 64, 3, "uniform"),
                                             (333, 64, 64, 17, "uniform"), (95, 40, 16, 5, "binary"),
-                                            (200, 64, 1000, 2, "uniform")])
-def test_rns_compress_parity(zp, R, C, n, B, secret):
+                                            (200, 64, 1000, 2, "uniform"), (700, 64, 1024, 40, "uniform")])
+@pytest.mark.parametrize("fp16", [False, True])
+def test_rns_compress_parity(zp, R, C, n, B, secret, fp16):
     """Forced RNS path: t equals the oracle's (b' + H'.cko) mod m for every query and packed
-    row, each query with its own client modulus, ragged last packed row."""
+    row, each query with its own client modulus, ragged last packed row; with the fp16 copy
+    of the residue planes (A operand through TMA) as well."""
     P = Params(n=n, key_bits=2048, secret=secret)
     c = zp.Context(0, n=n, secret=secret)
     c.set_option("compress_path", "rns")
@@ -51,6 +53,8 @@ def test_rns_compress_parity(zp, R, C, n, B, secret):
     Hn = lwe.hint_neg(D, A)
     db, dD = _db(zp, c, D)
     db.gen_hint(u32_dev(A))
+    if fp16:
+        db.prepare_fp16()  # the RNS planes are built by the first batch, their fp16 copy with them
     ms = [synth.random_odd_modulus(2048, 50 + b) for b in range(B)]
     cls = [c.register_client(m) for m in ms]
     ckos = [synth.uniform_below(ms[b], n, 60 + b) for b in range(B)]
@@ -62,7 +66,8 @@ def test_rns_compress_parity(zp, R, C, n, B, secret):
     assert c.device_status() == 0
 
 
-def test_rns_edge_values(zp):
+@pytest.mark.parametrize("fp16", [False, True])
+def test_rns_edge_values(zp, fp16):
     """cko at 0 and m - 1 and answers at 2^32 - 1 (the largest residue products and CRT sums)."""
     R, C, n = 60, 32, 64
     P = Params(n=n, key_bits=2048)
@@ -73,6 +78,9 @@ def test_rns_edge_values(zp):
     Hn = lwe.hint_neg(D, A)
     db, dD = _db(zp, c, D)
     db.gen_hint(u32_dev(A))
+    if fp16:
+        db.prepare_rns()
+        db.prepare_fp16()  # planes first, then the fp16 copies of D and of the planes
     pk, _ = paillier.keygen(2048, 77)
     m = pk.m
     cl = c.register_client(m)
@@ -101,6 +109,8 @@ def test_rns_auto_threshold_equals_tc_and_updates(zp):
         assert zp.zp_get_overlap(c) >= 0
         db, dD = _db(zp, c, D)
         db.gen_hint(u32_dev(A))
+        if path == "auto":
+            db.prepare_fp16()  # regeneration below must keep the fp16 residue planes current
         cls = [c.register_client(m) for m in ms]
         outs.append(u32_host(db.compress(cls, u32_dev(ans), ckod)))
         if path == "auto":
