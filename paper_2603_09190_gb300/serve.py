@@ -214,7 +214,7 @@ class ZipBackend:
         Rq = (db.d1p + 31) // 32 * 32
         rns = 153 * 4 * Rq * (math.ceil(n / 16) * 16 + 4) if self.max_batch >= 8 and n <= 1024 else 0
         d16 = 2 * db.R * ((db.C + 127) // 128 * 128) if self.max_batch > 4 else 0
-        if self.max_batch > 4 and self.max_batch >= 8 and n <= 1024:
+        if self.max_batch >= 8 and n <= 1024:
             d16 += 2 * 153 * 4 * Rq * ((n + 127) // 128 * 128)  # fp16 copy of the RNS planes
         return db.R * db.ld + db.R * n * 8 + 4 * Rp * math.ceil(n / 16) * 16 + rns + d16 + \
             sum(t.numel() * t.element_size() for k, t in x.items() if k in ("Q", "K", "T", "ans"))
