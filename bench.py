@@ -462,7 +462,7 @@ def run_ours(args, world, rank, local):
     alg_bytes = R * C + 4 * C * B + 4 * R * B
     achieved = alg_bytes / (ans_avg * 1e-3) / 1e9
     # DRAM bytes (read + write) of one launch of the GEMV in this configuration, from one
-    # ncu capture of this workload (profiles/k_gemv_1gib_traffic.md); None elsewhere
+    # ncu capture of this workload (mean of two launches); None elsewhere
     traffic = GEMV_TRAFFIC.get((args.workload, overlap))
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
             "frac": achieved / hbm_peak, "traffic": traffic,
