@@ -47,3 +47,32 @@ def test_version_and_host_validation(lib):
     assert lib.zp_init(0, ctypes.byref(P), ctypes.byref(out)) == zp.ZP_EINVAL
     assert lib.zp_answer(None, None, 1, None, None) == zp.ZP_EINVAL
     assert lib.zp_compress(None, None, None, None, 1, None, None) == zp.ZP_EINVAL
+
+
+def test_host_validation_of_the_newer_entry_points(lib):
+    """Argument checks of the scale option, the keystream, the standalone compression and
+    the client-side calls return before any device work (no GPU here)."""
+    import ctypes
+    import paper_2603_09190_gb300 as zp
+    out = ctypes.c_void_p()
+    P = zp._Params(1024, 2048, 0, 8, 2)  # scale 2 does not exist
+    assert lib.zp_init(0, ctypes.byref(P), ctypes.byref(out)) == zp.ZP_EINVAL
+    assert "scale" in zp.last_error()
+    key, nonce = ctypes.create_string_buffer(32), ctypes.create_string_buffer(12)
+    fake = ctypes.c_void_p(1 << 40)  # never dereferenced: the calls fail first
+    # 3 blocks from counter 2^32 - 2 would wrap the 32-bit block counter
+    assert lib.zp_prg_chacha20(key, nonce, 2**32 - 2, fake, 33, None) == zp.ZP_EINVAL
+    assert lib.zp_prg_chacha20(None, nonce, 0, fake, 16, None) == zp.ZP_EINVAL
+    assert lib.zp_prg_chacha20(key, nonce, 0, fake, 0, None) == zp.ZP_OK  # nothing to do
+    m = (1 << 2047) + 1
+    mw = (ctypes.c_uint32 * 96)(*[(m >> (32 * i)) & 0xFFFFFFFF for i in range(96)])
+    assert lib.zp_lc_create(0, 1024, mw, ctypes.byref(out)) == zp.ZP_EUNSUPPORTED
+    assert lib.zp_lc_create(0, 3072, mw, ctypes.byref(out)) == zp.ZP_EINVAL  # m has 2048 bits
+    even = (ctypes.c_uint32 * 64)(*([0] * 63 + [1 << 31]))
+    assert lib.zp_lc_create(0, 2048, even, ctypes.byref(out)) == zp.ZP_EINVAL
+    assert lib.zp_lc_compress(None, None, None, 1, 0, 1, None, 0, 0, None, None) == zp.ZP_EINVAL
+    assert lib.zp_lc_set_key(None, None, 8, 8, None) == zp.ZP_EINVAL
+    assert lib.zp_client_powm(None, None, None, 1, None, 1, None) == zp.ZP_EINVAL
+    assert lib.zp_client_decrypt(None, None, None, None, None, 1, None) == zp.ZP_EINVAL
+    assert lib.zp_client_expand_ckr(None, key, nonce, 0, None, 1, None) == zp.ZP_EINVAL
+    assert lib.zp_db_prepare_fp16(None, None) == zp.ZP_EINVAL
