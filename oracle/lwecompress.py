@@ -150,6 +150,16 @@ def modified_batched_decrypt(sk: paillier.SecretKey, x: int, q: int, p: int, gam
     return [round_div((mu // gamma ** j) % gamma % q, d) % p for j in range(ell)]
 
 
+def rescale(a: list[int], b: int, q: int, r: int) -> tuple[list[int], int]:
+    """Modulus switching before compression (Sec. 3.3, "Rescaling for Compression"): every
+    coefficient x of (a, b) becomes round(x r / q) mod r, ties up, i.e.
+    floor((x r + floor(q / 2)) / q) mod r. The ciphertext then lives modulo r < q; the
+    paper states (proof not in its text) that it still decrypts for binary keys when the
+    noise stays below Delta / 4."""
+    f = lambda x: ((x * r + q // 2) // q) % r
+    return [f(x) for x in a], f(b)
+
+
 # ----------------------------------------------------------------------------- RLWE
 def negacyclic_mul(A: list[int], S: list[int], q: int) -> list[int]:
     """A S in Z_q[X]/(X^N + 1): X^N = -1, so the term A[j] S[i] lands on X^(i + j) with sign

@@ -162,3 +162,35 @@ def test_planted_sign_mistake_fails(keys):
             x = paillier.add(pk, x, paillier.smul(pk, ai, c))
         wrong += lc.modified_lwe_decrypt(sk, x, q, p) != mu
     assert wrong >= 4
+
+
+@pytest.mark.parametrize("q,r", [(Q64, 1 << 20), (Q27, 1 << 11), (1 << 32, 12289)])
+def test_rescale_rounding(q, r):
+    """Rounding to nearest with ties up, against the doubled-numerator form
+    floor((2 x r + q) / (2 q)), and for q = 2^64, r = 2^20 against the shift form
+    (x + 2^43) >> 44; edge values 0, q - 1 and the neighbours of every tie."""
+    g = np.random.default_rng(r)
+    xs = [0, 1, q - 1, q // 2, q // 2 - 1] + [int.from_bytes(g.bytes(8), "little") % q for _ in range(200)]
+    ties = [(2 * k + 1) * q // (2 * r) for k in range(5)]
+    xs += ties + [t + 1 for t in ties] + [t - 1 for t in ties if t > 0]
+    a2, b2 = lc.rescale(xs, xs[7], q, r)
+    assert a2 == [((2 * x * r + q) // (2 * q)) % r for x in xs]
+    assert b2 == a2[7]
+    if (q, r) == (Q64, 1 << 20):
+        assert a2 == [((x + (1 << 43)) >> 44) % r for x in xs]
+
+
+def test_rescale_then_compress_decrypts(keys):
+    """Binary secret, small noise: (a, b) mod 2^64 rescaled to r = 2^20 still decrypts
+    (the rounding adds at most (n + 1) / 2 to the phase), and so does its compression
+    modulo r."""
+    pk, sk = keys
+    g = np.random.default_rng(12)
+    n, q, r, p = 64, Q64, 1 << 20, 16
+    s = lc.lwe_keygen(n, q, True, g)
+    ck = lc.compression_key(pk, s, g)
+    for mu in (0, 5, 15):
+        a, b = lc.lwe_encrypt(s, mu, q, p, g)
+        a2, b2 = lc.rescale(a, b, q, r)
+        assert lc.lwe_decrypt(s, a2, b2, r, p) == mu
+        assert lc.modified_lwe_decrypt(sk, lc.lwe_compress(pk, ck, a2, b2, r), r, p) == mu
