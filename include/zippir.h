@@ -390,6 +390,16 @@ int zp_lc_compress(zp_lc* lc, const uint64_t* dA, const uint64_t* dB, uint32_t c
                    uint32_t ell, const uint32_t* hGamma, uint32_t gammaWords, int mode, uint32_t* dX,
                    void* stream);
 
+/* Rescaling (modulus switching, Sec. 3.3 "Rescaling for Compression") of count LWE
+ * ciphertexts from q to r (2 <= r < q; q = 0 stands for 2^64): every coefficient x of dA
+ * (count x n u64) and dB (count u64) becomes round(x r / q) mod r, ties up
+ * (floor((x r + floor(q / 2)) / q) mod r), written to dAout / dBout (same shapes; may
+ * alias the inputs). Compressing the result with modulus r uses smaller exponents; the
+ * paper states that decryption survives for binary keys with noise below Delta / 4.
+ * Runs on the current device. Asynchronous on `stream`. Errors: ZP_EINVAL, ZP_ECUDA. */
+int zp_lc_rescale(const uint64_t* dA, const uint64_t* dB, uint32_t count, uint32_t n, uint64_t q,
+                  uint64_t r, uint64_t* dAout, uint64_t* dBout, void* stream);
+
 /* Sample extraction of RLWE coefficients (App. B, Algorithm "Compressing Extracted RLWE
  * Coefficient"): for the RLWE ciphertext (A, B) over Z_q[X]/(X^N + 1) (dA, dB: N u64,
  * device) and coefficient indices hK[c] < N (HOST, count <= 65535), the LWE ciphertext

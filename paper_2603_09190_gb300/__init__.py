@@ -34,7 +34,7 @@ EXPORTS = [
     "zp_db_prepare_rns", "zp_selftest_wait", "zp_autotune", "zp_prg_chacha20", "zp_client_powm",
     "zp_client_expand_ckr", "zp_client_decrypt", "zp_db_prepare_fp16",
     "zp_lc_create", "zp_lc_destroy", "zp_lc_set_key", "zp_lc_unpack_key", "zp_lc_compress",
-    "zp_lc_rlwe_extract",
+    "zp_lc_rlwe_extract", "zp_lc_rescale",
 ]
 
 
@@ -102,6 +102,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "zp_lc_unpack_key": (i32, [vp, vp, u32, u32, vp, u32, vp, vp]),
         "zp_lc_compress": (i32, [vp, vp, vp, u32, u64, u32, vp, u32, ctypes.c_int, vp, vp]),
         "zp_lc_rlwe_extract": (i32, [vp, vp, vp, u32, u64, vp, u32, vp, vp, vp]),
+        "zp_lc_rescale": (i32, [vp, vp, u32, u32, u64, u64, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -553,6 +554,20 @@ class Database:
             self.close()
         except Exception:
             pass
+
+
+def lc_rescale(A, B, q: int, r: int, stream=None):
+    """Modulus switching of LWE ciphertexts (zp_lc_rescale): int64 tensors A (count, n) and
+    B (count,) modulo q -> new tensors modulo r."""
+    import torch
+    count = B.shape[0]
+    n = A.shape[1] if A.dim() == 2 else 0
+    _need(A, "i64", count * n, "A")
+    _need(B, "i64", count, "B")
+    Ao, Bo = torch.empty_like(A), torch.empty_like(B)
+    _check(load_library().zp_lc_rescale(_ptr(A), _ptr(B), count, n, int(q) % (1 << 64), int(r) % (1 << 64),
+                                        _ptr(Ao), _ptr(Bo), _stream(stream)))
+    return Ao, Bo
 
 
 def _words(v: int, nw: int | None = None) -> np.ndarray:

@@ -330,6 +330,26 @@ __global__ void __launch_bounds__(256) k_lc_rlwe_extract(const uint64_t* __restr
   if (i == 0) Bout[c] = Bp[k];
 }
 
+// Modulus switching of LWE coefficients: x -> floor((x r + floor(q / 2)) / q) mod r (round
+// to nearest, ties up), q = 0 standing for 2^64. x r + floor(q / 2) < 2^128 for x < q <= 2^64
+// and r < q. One thread per coefficient (count x n of A, then the count of B).
+__global__ void __launch_bounds__(256) k_lc_rescale(const uint64_t* __restrict__ A,
+                                                    const uint64_t* __restrict__ B, uint64_t nA,
+                                                    uint64_t nB, uint64_t q, uint64_t r,
+                                                    uint64_t* __restrict__ Ao, uint64_t* __restrict__ Bo) {
+  const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nA + nB) return;
+  const uint64_t x = i < nA ? A[i] : B[i - nA];
+  const unsigned __int128 half = q == 0 ? ((unsigned __int128)1 << 63) : (unsigned __int128)(q / 2);
+  const unsigned __int128 num = (unsigned __int128)x * r + half;
+  const uint64_t quo = q == 0 ? (uint64_t)(num >> 64) : (uint64_t)(num / q);
+  const uint64_t v = quo % r;
+  if (i < nA)
+    Ao[i] = v;
+  else
+    Bo[i - nA] = v;
+}
+
 template <int WPL>
 LcConsts<WPL> lc_consts(const zp_lc* lc) {
   LcConsts<WPL> c;
@@ -621,6 +641,20 @@ extern "C" int zp_lc_rlwe_extract(zp_lc* lc, const uint64_t* dA, const uint64_t*
   zp_clear_pending_error();
   dim3 grid((N + 255) / 256, count);
   k_lc_rlwe_extract<<<grid, 256, 0, st>>>(dA, dB, N, q, dK, dAout, dBout);
+  ZP_CUDA(cudaGetLastError());
+  return ZP_OK;
+}
+
+extern "C" int zp_lc_rescale(const uint64_t* dA, const uint64_t* dB, uint32_t count, uint32_t n,
+                             uint64_t q, uint64_t r, uint64_t* dAout, uint64_t* dBout, void* stream) {
+  if (!dA || !dB || !dAout || !dBout) return zp_set_error(ZP_EINVAL, "zp_lc_rescale: null argument");
+  if (r < 2) return zp_set_error(ZP_EINVAL, "zp_lc_rescale: r must be at least 2");
+  if (q != 0 && r >= q) return zp_set_error(ZP_EINVAL, "zp_lc_rescale: r must be below q");
+  if (count == 0) return ZP_OK;
+  const uint64_t nA = (uint64_t)count * n, total = nA + count;
+  zp_clear_pending_error();
+  k_lc_rescale<<<(unsigned)((total + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+      dA, dB, nA, count, q, r, dAout, dBout);
   ZP_CUDA(cudaGetLastError());
   return ZP_OK;
 }

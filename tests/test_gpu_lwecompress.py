@@ -181,3 +181,35 @@ def test_invalid_arguments(zp, keys):
                       gamma=lc.gamma_of(Q27, 8, False))  # gamma^ell far above m
     with pytest.raises(zp.ZipPIRError):
         comp.rlwe_extract(u64_dev([1] * 8), u64_dev([2] * 8), Q27, [8])
+
+
+@pytest.mark.parametrize("q,r", [(Q64, 1 << 20), (Q27, 1 << 11), (1 << 32, 12289)])
+def test_rescale_parity(zp, q, r):
+    """Modulus switching on the GPU equals the oracle's rounding, edge values included."""
+    g = np.random.default_rng(r)
+    count, n = 6, 37
+    A = [[int.from_bytes(g.bytes(8), "little") % q for _ in range(n)] for _ in range(count)]
+    A[0][:5] = [0, 1, q - 1, q // 2, q // 2 - 1]
+    A[1][:3] = [(2 * k + 1) * q // (2 * r) for k in range(3)]  # ties
+    B = [int.from_bytes(g.bytes(8), "little") % q for _ in range(count)]
+    Ao, Bo = zp.lc_rescale(u64_dev(A), u64_dev(B), q, r)
+    got_a = [[int(v) for v in row] for row in Ao.cpu().numpy().view(np.uint64)]
+    got_b = [int(v) for v in Bo.cpu().numpy().view(np.uint64)]
+    for j in range(count):
+        wa, wb = lc.rescale(A[j], B[j], q, r)
+        assert got_a[j] == wa and got_b[j] == wb
+
+
+def test_rescale_then_compress_on_gpu(zp, keys):
+    """Binary secret, q = 2^64 rescaled to 2^20 on the GPU, then compressed modulo 2^20 on
+    the GPU: the oracle's ciphertext, and the messages decrypt."""
+    n, q, r, p = 32, Q64, 1 << 20, 16
+    pk, sk, g, s, ck, comp = _setup(zp, keys, 2048, n, q, True, 90, 20)
+    mus = [int(g.integers(0, p)) for _ in range(4)]
+    cts = [lc.lwe_encrypt(s, mu, q, p, g) for mu in mus]
+    Ao, Bo = zp.lc_rescale(u64_dev([a for a, _ in cts]), u64_dev([b for _, b in cts]), q, r)
+    X = ct_host(comp.compress(Ao, Bo, r))
+    for j, (a, b) in enumerate(cts):
+        a2, b2 = lc.rescale(a, b, q, r)
+        assert X[j] == lc.lwe_compress(pk, ck, a2, b2, r)
+        assert lc.modified_lwe_decrypt(sk, X[j], r, p) == mus[j]
