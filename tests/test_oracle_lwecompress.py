@@ -194,3 +194,25 @@ def test_rescale_then_compress_decrypts(keys):
         a2, b2 = lc.rescale(a, b, q, r)
         assert lc.lwe_decrypt(s, a2, b2, r, p) == mu
         assert lc.modified_lwe_decrypt(sk, lc.lwe_compress(pk, ck, a2, b2, r), r, p) == mu
+
+
+def test_sizes_match_the_papers_table():
+    """The printed sizes of the single-compression table (tests/golden/lwe_compress_sizes.txt):
+    a compressed ciphertext is one Paillier ciphertext, 2 log2 m bits = 768 bytes at 3072
+    bits (the library's 2L words); an uncompressed LWE ciphertext is (n + 1) log2 q bits and
+    an RLWE one (A from a seed) N log2 q bits; the reduction is 1 - compressed/uncompressed.
+    LWE rows agree to the printed precision; the RLWE sizes are printed 0.01 KB above
+    N log2 q / 8 bytes in three rows, so they get that much slack."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "lwe_compress_sizes.txt")
+    rows = [ln.split() for ln in open(path) if ln.strip() and not ln.startswith("#")]
+    assert len(rows) == 8
+    key_bits = 3072
+    for kind, n, lq, comp, kb, red in rows:
+        n, lq, comp, kb, red = int(n), int(lq), int(comp), float(kb), float(red)
+        assert comp == 2 * key_bits // 8 == 4 * (2 * key_bits // 32)
+        bits = (n + 1) * lq if kind == "lwe" else n * lq
+        size = bits / 8
+        slack = 0.006 if kind == "lwe" else 0.016
+        assert abs(size / 1000 - kb) < slack, (kind, n, lq)
+        assert abs(100 * (1 - comp / size) - red) < (0.011 if kind == "lwe" else 0.03), (kind, n, lq)
