@@ -1,5 +1,5 @@
-// k_paillier.cu -- Paillier arithmetic mod m^2 for the per-client hint and the combined
-// response.
+// k_paillier.cu -- Paillier arithmetic mod m^2 for the per-client hint, the combined
+// response and the client-side pieces (ck_r from a seed, exponentiation, decryption).
 //
 //  * the per-client hint (Algorithm "ZipPIR", Setup, and Sec. 4.3 "Lowering offline
 //    communication costs": k = PaillierMatMul(H', ck_r)):
@@ -12,6 +12,9 @@
 //  * the combined response (Sec. 4.3, last extension): k (+) t = k (1 + t m) mod m^2, the
 //    homomorphic addition of t encrypted with randomness 1, so that Dec(k (+) t) =
 //    Dec(k) + t mod m.
+//  * client side: ck_r expanded from a ChaCha20 seed and reduced mod m^2, x^e mod m^2 for
+//    a shared exponent, and decryption by one exponentiation to lambda mu followed by an
+//    exact division by m.
 //
 // All products mod m^2 are the Montgomery products of zp_mont.cuh with R = 2^(64 L), one
 // warp per product, 4 words per lane.
