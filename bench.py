@@ -173,7 +173,7 @@ def dist_barrier(world: int):
 
 
 # ----------------------------------------------------------------------------- CPU oracle baseline
-def cpu_baseline(R, C, n, B, target_s=12.0):
+def cpu_baseline(R, C, n, B, target_s=12.0, packed_rows=8):
     """Times the oracle's online Response (matvec mod 2^32 + compression with Python
     ints) on a bounded sample of rows of the same workload; returns GB/s of database
     bytes scanned, threads used and a description of the sample."""
@@ -183,7 +183,7 @@ def cpu_baseline(R, C, n, B, target_s=12.0):
 
     P = Params(n=n, key_bits=KEY_BITS)
     ell = P.ell
-    rows = min(R, ell * 8)          # whole packed rows
+    rows = min(R, ell * packed_rows)  # whole packed rows
     D = synth.database(rows, C, 101)
     q = synth.uniform_queries(1, C, 102)[0]
     # hint rows: uniform u32, statistically equal to -D.A for a uniform A (the hint
@@ -216,8 +216,11 @@ def run_reference(args, world, rank):
     R, C, n, B, desc = WORKLOADS[args.workload]
     vals = []
     cb = None
+    # each step is a bounded sample, sized so that all W + K steps take about 150 s
+    budget = min(3.0, max(0.02, 150.0 / (args.warmup + args.steps)))
+    packed = 8 if budget >= 0.5 else 1
     for i in range(args.warmup + args.steps):
-        r = cpu_baseline(R, C, n, B, target_s=3.0)
+        r = cpu_baseline(R, C, n, B, target_s=budget, packed_rows=packed)
         if i >= args.warmup:
             vals.append(r["value"])
             cb = r
