@@ -173,6 +173,9 @@ def dist_barrier(world: int):
 
 
 # ----------------------------------------------------------------------------- CPU oracle baseline
+_CPU_SAMPLES = {}
+
+
 def cpu_baseline(R, C, n, B, target_s=12.0, packed_rows=8):
     """Times the oracle's online Response (matvec mod 2^32 + compression with Python
     ints) on a bounded sample of rows of the same workload; returns GB/s of database
@@ -184,13 +187,16 @@ def cpu_baseline(R, C, n, B, target_s=12.0, packed_rows=8):
     P = Params(n=n, key_bits=KEY_BITS)
     ell = P.ell
     rows = min(R, ell * packed_rows)  # whole packed rows
-    D = synth.database(rows, C, 101)
-    q = synth.uniform_queries(1, C, 102)[0]
-    # hint rows: uniform u32, statistically equal to -D.A for a uniform A (the hint
-    # itself is offline work and not part of the timed online Response)
-    Hn = synth.rng(103).integers(0, 2**32, size=(rows, n), dtype=np.uint64).astype(np.uint32)
-    m = synth.random_odd_modulus(KEY_BITS, 104)
-    cko = synth.uniform_below(m, n, 105)
+    key = (rows, C, n)
+    if key not in _CPU_SAMPLES:  # the sample's inputs are built once (not timed)
+        D = synth.database(rows, C, 101)
+        q = synth.uniform_queries(1, C, 102)[0]
+        # hint rows: uniform u32, statistically equal to -D.A for a uniform A (the hint
+        # itself is offline work and not part of the timed online Response)
+        Hn = synth.rng(103).integers(0, 2**32, size=(rows, n), dtype=np.uint64).astype(np.uint32)
+        m = synth.random_odd_modulus(KEY_BITS, 104)
+        _CPU_SAMPLES[key] = (D, q, Hn, m, synth.uniform_below(m, n, 105))
+    D, q, Hn, m, cko = _CPU_SAMPLES[key]
     done_bytes, t_used, reps = 0, 0.0, 0
     t0 = time.perf_counter()
     while True:
