@@ -10,10 +10,13 @@ inputs resident in HBM, timed over K replays of one zp_respond captured in a CUD
 graph (inputs in place); the same step composed eagerly from its three calls gives
 the per-kernel stages and the roofline (reported as "eager"). e2e = the same metric
 through zp_respond_host with host buffers (query and offsets copied in, compressed
-answer copied out, each step).
+answer copied out, each step). The default line also carries "answer_alone" (the
+single-query answer on every SM, against the HBM roofline) and "batched": 64 queries of
+64 clients on the same database (graph-replayed zp_respond, its own e2e, and the answer
+GEMM against the tensor-core roofline).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload 1gib|tiny|256mib|batch64|8gib|8gib_b8|8gib_b32|8gib_b128|
+                  [--workload 1gib|tiny|256mib|batch64|256mib_b64|8gib|8gib_b8|8gib_b32|8gib_b128|
                               serve|client_hint|lwe_compress]
 
 --impl reference times the oracle (the plain CPU implementation) on a bounded
@@ -51,6 +54,8 @@ WORKLOADS = {
              "1 MiB database 1024x1024, 1 query, n=1024, 2048-bit modulus"),
     "batch64": (32768, 32768, 1024, 64,
                 "1 GiB database 32768x32768, 64 queries of 64 clients, n=1024, 2048-bit moduli"),
+    "256mib_b64": (16384, 16384, 1024, 64,
+                   "256 MiB database 16384x16384, 64 queries of 64 clients, n=1024, 2048-bit moduli"),
     "8gib": (65536, 131072, 1024, 1,
              "8 GiB database 65536x131072, 1 query, n=1024, 2048-bit modulus"),
     "8gib_b8": (65536, 131072, 1024, 8, "8 GiB database 65536x131072, 8 queries"),
@@ -64,13 +69,18 @@ GEMV_TRAFFIC = {("1gib", True): 1075723136}
 L = KEY_BITS // 32
 
 
+NOMINAL_HBM_GBS = 7900.0   # GB300 HBM3e, nominal (context beside the measured peak)
+
+
 def load_peaks():
+    """(HBM GB/s, bf16 TFLOP/s burst, kind): the driver's measured copy bandwidth and cuBLAS
+    bf16 rate on this machine's GPUs, else the fallback figures of an earlier GB300 measurement."""
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
         with open(p) as f:
             d = json.load(f)
-        return d.get("hbm_gbs"), "measured"
-    return 6800.0, "fallback"
+        return d.get("hbm_gbs"), d.get("bf16_tflops"), "measured"
+    return 6800.0, 1900.0, "fallback"
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -213,14 +223,43 @@ def cpu_baseline(R, C, n, B, target_s=12.0, packed_rows=8):
             "sample": "%d of %d rows (%d packed rows) x %d columns, 1 query, %d repetition(s), "
                       "%.2f s per repetition; numpy uint64 matvec + Python-int compression, "
                       "single thread" % (rows, R, rows // ell, C, reps, per_q),
-            "seconds": t_used}
+            "seconds": t_used, "reps": reps, "rows": rows}
+
+
+def cpu_matvec_all_cores(R, C, target_s=6.0):
+    """The oracle's answer (numpy uint64 matvec mod 2^32) over a sample of the database's
+    rows on every host core (row blocks in threads: numpy releases the GIL inside its
+    integer products); the compression's Python integers stay single-threaded, so this is
+    the answer alone. Returns GB/s of database bytes, the thread count and the sample."""
+    from concurrent.futures import ThreadPoolExecutor
+    import synth
+    from oracle import lwe
+
+    cores = max(1, len(os.sched_getaffinity(0)))
+    rows = min(R, 64 * cores)
+    D = synth.database(rows, C, 111)
+    q = synth.uniform_queries(1, C, 112)[0]
+    blocks = [(a, min(rows, a + 64)) for a in range(0, rows, 64)]
+    done, reps = 0, 0
+    with ThreadPoolExecutor(cores) as ex:
+        t0 = time.perf_counter()
+        while True:
+            list(ex.map(lambda ab: lwe.matvec_mod_q(D[ab[0]:ab[1]], q), blocks))
+            reps += 1
+            done += rows * C
+            dt = time.perf_counter() - t0
+            if dt >= target_s or reps >= 1000:
+                break
+    return {"value": done / dt / 1e9, "unit": "GB/s", "cores": cores, "kind": "oracle",
+            "sample": "answer only (numpy uint64 matvec mod 2^32), %d of %d rows x %d columns in "
+                      "blocks of 64 rows on %d threads, %d repetition(s)" % (rows, R, C, cores, reps)}
 
 
 def run_reference(args, world, rank):
     if rank != 0:
         return 0
     R, C, n, B, desc = WORKLOADS[args.workload]
-    vals = []
+    vals, secs = [], []
     cb = None
     # each step is a bounded sample, sized so that all W + K steps take about 150 s
     budget = min(3.0, max(0.02, 150.0 / (args.warmup + args.steps)))
@@ -229,11 +268,16 @@ def run_reference(args, world, rank):
         r = cpu_baseline(R, C, n, B, target_s=budget, packed_rows=packed)
         if i >= args.warmup:
             vals.append(r["value"])
+            secs.append(r["seconds"])
             cb = r
     v = statistics.mean(vals)
-    ms = R * C * B / (v * 1e9) * 1e3
+    # ms_per_step: the measured wall time of one step (one bounded sample); the time the
+    # oracle would take for the whole workload is an extrapolation, reported apart
+    ms = statistics.mean(secs) * 1e3
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "GB/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "step": "one bounded sample of the workload: %s" % cb["sample"],
+            "extrapolated_full_workload_ms": R * C * B / (v * 1e9) * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
             "data": "synthetic",
             "config": {"workload": desc, "R": R, "C": C, "n": n, "B": B, "key_bits": KEY_BITS},
@@ -437,6 +481,37 @@ def run_ours(args, world, rank, local):
         torch.cuda.synchronize()
         single = e_a.elapsed_time(e_b)
 
+    # ---- the single-query answer alone on the whole GPU (no compression products beside it)
+    answer_alone = None
+    if B == 1:
+        ov = zp.zp_get_overlap(ctx)
+        ctx.set_option("overlap_sms", 0)
+        try:
+            for _ in range(max(args.warmup, 3)):
+                zp.zp_answer(db.handle, Q.data_ptr(), 1, ans2.data_ptr(), sp)
+            reps = max(args.steps, 20)
+            e_a.record(stream)
+            for _ in range(reps):
+                zp.zp_answer(db.handle, Q.data_ptr(), 1, ans2.data_ptr(), sp)
+            e_b.record(stream)
+            torch.cuda.synchronize()
+        finally:
+            ctx.set_option("overlap_sms", ov)
+        if not torch.equal(ans2, ans):
+            raise RuntimeError("answer on the whole GPU differs from the step's")
+        a_ms = e_a.elapsed_time(e_b) / reps
+        hbm_peak, _, peak_kind = load_peaks()
+        gbs = (R * C + 4 * C + 4 * R) / (a_ms * 1e-3) / 1e9
+        answer_alone = {"ms": a_ms, "launches": reps, "achieved_gb_s": gbs, "peak": hbm_peak,
+                        "frac": gbs / hbm_peak, "frac_nominal": gbs / NOMINAL_HBM_GBS,
+                        "peak_kind": peak_kind,
+                        "kernel": "zp_answer alone (k_qplanes + k_gemv<8,12> on every SM)"}
+
+    # ---- the batched half of the metric: 64 queries of 64 clients on the same database
+    batched = None
+    if args.workload == "1gib" and not args.no_batched:
+        batched = measure_batched(args, zp, torch, ctx, db, dev, R, C, n, 64, stream, world)
+
     # ---- e2e through the host-buffer entry point
     hQ = torch.empty((B, C), dtype=torch.int32, pin_memory=True)
     hQ.copy_(Q.cpu())
@@ -469,7 +544,7 @@ def run_ours(args, world, rank, local):
         timing = "eager composed step (zp_compress_products, zp_answer, zp_compress_finish)"
     if rank != 0:
         return 0
-    hbm_peak, peak_kind = load_peaks()
+    hbm_peak, _, peak_kind = load_peaks()
     ans_avg = statistics.mean(ans_ms)
     # algorithmic bytes of one zp_answer (B = 1: query-plane prep + GEMV): D, q, ans
     alg_bytes = R * C + 4 * C * B + 4 * R * B
@@ -478,10 +553,14 @@ def run_ours(args, world, rank, local):
     # ncu capture of this workload (mean of two launches); None elsewhere
     traffic = GEMV_TRAFFIC.get((args.workload, overlap))
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-            "frac": achieved / hbm_peak, "traffic": traffic,
+            "frac": achieved / hbm_peak, "frac_nominal": achieved / NOMINAL_HBM_GBS,
+            "nominal_peak": NOMINAL_HBM_GBS, "traffic": traffic,
             "kernel": "zp_answer (k_qplanes + k_gemv)" if B == 1 else "zp_answer (batched)",
             "peak_kind": peak_kind}
-    cb = cpu_baseline(R, C, n, B) if world == 1 and not args.no_cpu else None
+    cb = None
+    if world == 1 and not args.no_cpu:
+        cb = cpu_baseline(R, C, n, B)
+        cb["all_cores"] = cpu_matvec_all_cores(R, C)
     line = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
@@ -514,9 +593,130 @@ def run_ours(args, world, rank, local):
                     "d2h_bytes_per_step": 4 * B * db.d1p * L, "ms_per_step": e2e_s * 1e3},
             "gpu_launches": launches,
             "clocks": clocks,
+            "answer_alone": answer_alone,
+            "batched": batched,
             "cpu_baseline": cb}
     print(json.dumps(line))
     return 0
+
+
+def measure_batched(args, zp, torch, ctx, db, dev, R, C, n, B, stream, world):
+    """B queries of B clients (their own 2048-bit moduli) on the resident database: the
+    answers from the fp16 copy of D on the tensor cores, the compression in the residue
+    number system. Headline: K replays of one zp_respond captured in a CUDA graph (inputs in
+    place), checked bit for bit against the eager call; the eager composed step (zp_answer,
+    then zp_compress) brackets the answer GEMM with CUDA events for its tensor roofline;
+    e2e through zp_respond_host (queries and offsets copied in, t copied out, every step)."""
+    import synth
+    sp = stream.cuda_stream
+    db.prepare_fp16()
+    moduli = [synth.random_odd_modulus(KEY_BITS, 5000 + b) for b in range(B)]
+    clients = [ctx.register_client(m) for m in moduli]
+    handles = [c.handle for c in clients]
+    Q = synth.device_uniform_u32((B, C), 41, dev)
+    cko_h = np.stack([synth.ints_to_limbs(synth.uniform_below(moduli[b], n, 6000 + b), L)
+                      for b in range(B)])
+    CKO = torch.from_numpy(cko_h.view(np.int32)).to(dev)
+    ans = torch.empty((B, R), dtype=torch.int32, device=dev)
+    T = torch.empty((B, db.d1p, L), dtype=torch.int32, device=dev)
+    K, W = args.steps, max(args.warmup, 3)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+
+    def step(ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        zp.zp_answer(db.handle, Q.data_ptr(), B, ans.data_ptr(), sp)
+        if ev is not None:
+            ev[1].record(stream)
+        zp.zp_compress(db.handle, handles, ans.data_ptr(), CKO.data_ptr(), B, T.data_ptr(), sp)
+        if ev is not None:
+            ev[2].record(stream)
+
+    for _ in range(W):
+        step()
+    torch.cuda.synchronize()
+    for k in range(K):
+        step(evs[k])
+    torch.cuda.synchronize()
+    ans_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in evs)
+    cmp_ms = statistics.mean(e[1].elapsed_time(e[2]) for e in evs)
+    eager_ms = evs[0][0].elapsed_time(evs[-1][2]) / K
+    T_ref, ans_ref = T.clone(), ans.clone()
+    # the Response captured in a CUDA graph, replayed K times
+    g = torch.cuda.CUDAGraph()
+    gs = torch.cuda.Stream(dev)
+    gs.wait_stream(stream)
+    with torch.cuda.stream(gs):
+        zp.zp_respond(db.handle, handles, Q.data_ptr(), CKO.data_ptr(), B, ans.data_ptr(),
+                      T.data_ptr(), gs.cuda_stream)
+    gs.synchronize()
+    with torch.cuda.graph(g, stream=gs):
+        zp.zp_respond(db.handle, handles, Q.data_ptr(), CKO.data_ptr(), B, ans.data_ptr(),
+                      T.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    T.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    if not (torch.equal(T, T_ref) and torch.equal(ans, ans_ref)):
+        raise RuntimeError("batched graph replay differs from the eager step")
+    for _ in range(W):
+        g.replay()
+    e_a, e_b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = ctx.kernel_launches()
+    zp.zp_respond(db.handle, handles, Q.data_ptr(), CKO.data_ptr(), B, ans.data_ptr(),
+                  T.data_ptr(), sp)
+    torch.cuda.synchronize()
+    per_resp = ctx.kernel_launches() - l0
+    dist_barrier(world)
+    torch.cuda.synchronize()
+    e_a.record(stream)
+    for _ in range(K):
+        g.replay()
+    e_b.record(stream)
+    torch.cuda.synchronize()
+    dist_barrier(world)
+    ms_step, value = aggregate(e_a.elapsed_time(e_b), K, R * C * B, world)
+    # e2e: host buffers (pinned), copies inside the timed region
+    hQ = torch.empty((B, C), dtype=torch.int32, pin_memory=True)
+    hQ.copy_(Q.cpu())
+    hC = torch.from_numpy(cko_h.view(np.int32)).pin_memory()
+    hT = torch.empty((B, db.d1p, L), dtype=torch.int32, pin_memory=True)
+    hQn, hCn, hTn = hQ.numpy().view(np.uint32), hC.numpy().view(np.uint32), hT.numpy().view(np.uint32)
+    for _ in range(2):
+        zp.zp_respond_host(db.handle, handles, hQn, hCn, B, hTn, None, sp)
+    if not torch.equal(hT, T_ref.cpu()):
+        raise RuntimeError("batched host-buffer Response differs from the device one")
+    e2e_steps = max(3, min(K, 100))
+    dist_barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        zp.zp_respond_host(db.handle, handles, hQn, hCn, B, hTn, None, sp)
+    torch.cuda.synchronize()
+    e2e_s = dist_max((time.perf_counter() - t0) / e2e_steps, world)
+    dist_barrier(world)
+    for c in clients:
+        c.close()
+    _, bf16_peak, peak_kind = load_peaks()
+    flops = 2.0 * R * C * 4 * B          # executed: 4 byte planes of every query (fp16 MMAs)
+    tfl = flops / (ans_ms * 1e-3) / 1e12
+    return {"workload": "1 GiB database 32768x32768, %d queries of %d clients (own 2048-bit "
+                        "moduli), n=1024: answers on the tensor cores from the fp16 copy of D, "
+                        "compression in the residue number system" % (B, B),
+            "B": B, "steps": K, "warmup": W, "ms_per_step": ms_step, "value": value, "unit": "GB/s",
+            "gib_s": value * 1e9 / 2**30,
+            "timing": "CUDA graph of zp_respond replayed K times (inputs in place)",
+            "gpu_launches": per_resp * K,
+            "eager": {"ms_per_step": eager_ms, "answer_ms": ans_ms, "compress_ms": cmp_ms},
+            "roofline": {"bound": "tensor", "achieved": tfl, "peak": bf16_peak, "unit": "TFLOP/s",
+                         "frac": tfl / bf16_peak, "traffic": None,
+                         "kernel": "zp_answer, B=%d (k_prep_q_rows + k_gemm_tc<ANS, 64, fp16 A>)" % B,
+                         "peak_kind": peak_kind + " bf16 burst (kind::f16 with fp16 operands runs at "
+                                                  "the bf16 rate)",
+                         "executed_flops": flops, "algorithmic_macs": R * C * B,
+                         "algorithmic_tmacs_s": R * C * B / (ans_ms * 1e-3) / 1e12},
+            "e2e": {"value": R * C * B * world / e2e_s / 1e9, "unit": "GB/s",
+                    "h2d_bytes_per_step": 4 * B * C + 4 * B * n * L,
+                    "d2h_bytes_per_step": 4 * B * db.d1p * L, "ms_per_step": e2e_s * 1e3}}
 
 
 def run_serve(args, world, rank, local):
@@ -833,6 +1033,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the library's default thresholds and SM split")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the 64-query measurement of the default workload")
     ap.add_argument("--serve-rates", type=float, nargs="*", default=[50, 200, 1000, 2000])
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--serve-clients", type=int, default=1000)

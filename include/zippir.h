@@ -27,6 +27,8 @@
  *    and clients may be destroyed before or after one another.
  *  - All arithmetic is exact integer arithmetic; results are bit-identical to the
  *    definitions cited at each call.
+ *  - Every entry point runs on its handle's device and gives the caller's current
+ *    device back before it returns.
  */
 #ifndef ZIPPIR_H
 #define ZIPPIR_H
@@ -129,10 +131,10 @@ int zp_answer(zp_db* db, const uint32_t* dQ, uint32_t B, uint32_t* dAns, void* s
 /* Single-query answer that allocates no device memory (the paper has no
  * counterpart; it serves callers of this library that cannot allocate). Same result
  * as zp_answer with B = 1: ans[r] = sum_c D[r][c] * q[c] mod 2^32, dQ: C u32, dAns:
- * R u32 (device). Some callers may not call cudaMalloc at all: code recorded into a
- * CUDA graph, latency-critical serving threads that must never block on the device
- * allocator (cudaMalloc can synchronise the device), and hosts whose memory manager
- * owns every byte of HBM. zp_answer grows library scratch on demand; this entry
+ * R u32 (device). Some callers may not call cudaMalloc at all: latency-critical serving
+ * threads that must never block on the device allocator (cudaMalloc can synchronise the
+ * device), and plug-ins running inside a host whose memory manager owns every byte of HBM
+ * and hands out none. zp_answer grows library scratch on demand; this entry
  * point instead keeps its scratch (the query byte planes) in a 1 MiB array compiled
  * into the library, which every GPU that loads the library holds until the process
  * exits. Limit: C <= 262144 columns (ZP_EINVAL above it, before any work). The first
@@ -140,7 +142,8 @@ int zp_answer(zp_db* db, const uint32_t* dQ, uint32_t B, uint32_t* dAns, void* s
  * that first call before any stream capture. All calls on a device share the array,
  * so calls that overlap on the GPU (different streams, no ordering) race and give
  * wrong answers; calls ordered on one stream are safe, and each call rewrites every
- * plane it reads and zeroes dAns itself. Asynchronous on `stream`.
+ * plane it reads and zeroes dAns itself. Asynchronous on `stream`. Like every entry point,
+ * it leaves the caller's current device as it found it.
  * Errors: ZP_EINVAL, ZP_ECUDA. */
 int zp_answer_noalloc(zp_db* db, const uint32_t* dQ, uint32_t* dAns, void* stream);
 

@@ -18,6 +18,8 @@
 //    Big integers live in shared memory; products are summed per output column in
 //    96-bit accumulators and carries are resolved across the warp with a
 //    generate/propagate ballot (one integer addition over the 32 lane flags).
+#include <atomic>
+
 #include "zp_internal.cuh"
 #include "zp_warpint.cuh"
 
@@ -400,8 +402,9 @@ int zp_launch_compress_finish(zp_db* db, zp_client* const* clients, const uint32
       return zp_cuda_check(e, "cudaMemcpyAsync(clients)");
     }
   }
-  static bool attr_dev[64] = {false};  // the attribute is per device
-  bool& attr = attr_dev[ctx->device & 63];
+  // the attribute is per device; two host threads may both set it, which is harmless
+  static std::atomic<bool> attr_dev[64];
+  std::atomic<bool>& attr = attr_dev[ctx->device & 63];
   if (!attr) {
     ZP_CUDA(cudaFuncSetAttribute(k_pack_reduce<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)(PACK_WARPS * (sizeof(PackBarrett) + 64 * VW * 4))));

@@ -43,6 +43,8 @@
 // a bit in the context's status word, and every role then leaves its loop.
 #include <cuda_fp16.h>
 
+#include <atomic>
+
 #include "zp_internal.cuh"
 
 namespace {
@@ -784,7 +786,9 @@ __global__ void k_prep_cko(const uint32_t* __restrict__ cko, uint32_t n, uint32_
   if (s) atomicAdd(&colsum[(uint64_t)b * 256 + beta], s);
 }
 
-bool g_attr[64][4][3][2] = {};  // per device, mode, tile width and A operand type
+// per device, mode, tile width and A operand type: the kernel attribute is set (atomic flags:
+// two host threads may both set an attribute, which is harmless)
+std::atomic<bool> g_attr[64][4][3][2];
 
 template <int MODE, int BT, bool A16 = false>
 int launch_gemm(zp_ctx* ctx, const CUtensorMap& tmA, const CUtensorMap& tmB, const GemmArgs& ga,

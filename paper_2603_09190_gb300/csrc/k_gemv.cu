@@ -13,6 +13,7 @@
 // four queries is answered in the same single pass over D (BQ query plane sets per tile):
 // the pass is HBM-bound for two queries and bound by dp4a issue beyond (about 19 T dp4a/s
 // on the whole GPU), still well ahead of the tensor-core path for such small batches.
+#include <atomic>
 #include <cstdio>
 #include <mutex>
 
@@ -191,7 +192,9 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1)
   if (ok) flush(cur_rb);
 }
 
-bool g_attr_done[64] = {false};
+// per device: the kernel attributes are set (atomic flags: two host threads may both set
+// them, which is harmless)
+std::atomic<bool> g_attr_done[64];
 
 }  // namespace
 
@@ -209,7 +212,7 @@ int launch_gemv_multi(zp_db* db, const uint32_t* qp, uint32_t* dans, uint32_t nc
   zp_ctx* ctx = db->ctx;
   constexpr int S = MultiStages<BQ>::value;
   using G = GemvCfg<8, S, BQ>;
-  static bool attr_done[64] = {false};
+  static std::atomic<bool> attr_done[64];
   if (!attr_done[ctx->device & 63]) {
     ZP_CUDA(cudaFuncSetAttribute(k_gemv<8, S, BQ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  G::SMEM_BYTES));
@@ -296,7 +299,7 @@ extern "C" int zp_answer_noalloc(zp_db* db, const uint32_t* dQ, uint32_t* dAns, 
                         db->C, ZP_NOALLOC_MAX_C);
   const int dev = db->device;
   if (dev < 0 || dev >= 64) return zp_set_error(ZP_EINVAL, "zp_answer_noalloc: device %d", dev);
-  ZP_CUDA(cudaSetDevice(dev));
+  ZP_ON_DEVICE(dev);
   uint32_t* qp;
   {
     std::lock_guard<std::mutex> lk(g_noalloc_mu);

@@ -476,7 +476,7 @@ extern "C" int zp_lc_create(int device, uint32_t key_bits, const uint32_t* hM, z
     Big m2 = mul(m, m);
     m2.resize(2 * L, 0);
     const Big r1 = pow2_mod(64 * L, m2), r2 = pow2_mod(128 * L, m2);
-    ZP_CUDA(cudaSetDevice(device));
+    ZP_ON_DEVICE(device);
     zp_lc* lc = new zp_lc();
     lc->device = device;
     lc->key_bits = key_bits;
@@ -508,7 +508,7 @@ extern "C" int zp_lc_create(int device, uint32_t key_bits, const uint32_t* hM, z
 
 extern "C" int zp_lc_destroy(zp_lc* lc) {
   if (!lc) return ZP_OK;
-  cudaSetDevice(lc->device);
+  zp_device_scope _zp_scope(lc->device);
   cudaDeviceSynchronize();
   for (uint32_t* p : {lc->d_m, lc->d_m2, lc->d_r1, lc->d_r2, lc->d_eck})
     if (p) cudaFree(p);
@@ -526,7 +526,7 @@ extern "C" int zp_lc_set_key(zp_lc* lc, const uint32_t* dCk, uint32_t n, uint32_
   if (T == 0 || T > lc->key_bits)
     return zp_set_error(ZP_EINVAL, "zp_lc_set_key: T=%u out of [1, %u]", T, lc->key_bits);
   if (!aligned16(dCk)) return zp_set_error(ZP_EINVAL, "zp_lc_set_key: dCk must be 16-byte aligned");
-  ZP_CUDA(cudaSetDevice(lc->device));
+  ZP_ON_DEVICE(lc->device);
   const size_t bytes = (size_t)n * T * 8 * lc->L;
   if (lc->d_eck && (size_t)lc->n * lc->T * 8 * lc->L != bytes) {
     cudaFree(lc->d_eck);
@@ -554,7 +554,7 @@ extern "C" int zp_lc_unpack_key(zp_lc* lc, const uint32_t* dPck, uint32_t n, uin
   if (bits(d) < 2) return zp_set_error(ZP_EINVAL, "zp_lc_unpack_key: delta must be at least 2");
   if (!aligned16(dPck) || !aligned16(dCk))
     return zp_set_error(ZP_EINVAL, "zp_lc_unpack_key: dPck and dCk must be 16-byte aligned");
-  ZP_CUDA(cudaSetDevice(lc->device));
+  ZP_ON_DEVICE(lc->device);
   const uint32_t npk = (n + t - 1) / t;
   const SmallWords sd = small_words(hDelta, deltaWords);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -612,7 +612,7 @@ extern "C" int zp_lc_compress(zp_lc* lc, const uint64_t* dA, const uint64_t* dB,
       return zp_set_error(ZP_EINVAL, "zp_lc_compress: the expanded key has %u powers, q needs %u", lc->T, tq);
     const uint32_t EW = folded ? (ebits + 31) / 32 + 1 : (tq + 31) / 32 + 1;
     if (EW > (uint32_t)LC_EW_MAX) return zp_set_error(ZP_EINVAL, "zp_lc_compress: exponents too wide");
-    ZP_CUDA(cudaSetDevice(lc->device));
+    ZP_ON_DEVICE(lc->device);
     const SmallWords sg = small_words(gam.data(), (uint32_t)gam.size());
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     return lc->L == 64 ? lc_compress<4>(lc, dA, dB, count, q, ell, sg, (uint32_t)gam.size(), folded, EW, dX, st)
@@ -632,7 +632,7 @@ extern "C" int zp_lc_rlwe_extract(zp_lc* lc, const uint64_t* dA, const uint64_t*
   if (count > 65535) return zp_set_error(ZP_EINVAL, "zp_lc_rlwe_extract: count=%u above 65535", count);
   for (uint32_t c = 0; c < count; ++c)
     if (hK[c] >= N) return zp_set_error(ZP_EINVAL, "zp_lc_rlwe_extract: coefficient %u >= N=%u", hK[c], N);
-  ZP_CUDA(cudaSetDevice(lc->device));
+  ZP_ON_DEVICE(lc->device);
   int rc = zp_scratch_reserve(&lc->s_k, (size_t)count * 4);
   if (rc) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(stream);

@@ -404,7 +404,7 @@ extern "C" int zp_client_powm(const zp_client* cl, const uint32_t* dBase, const 
   if ((reinterpret_cast<uintptr_t>(dBase) | reinterpret_cast<uintptr_t>(dOut)) & 15u)
     return zp_set_error(ZP_EINVAL, "zp_client_powm: dBase and dOut must be 16-byte aligned");
   if (count == 0) return ZP_OK;
-  ZP_CUDA(cudaSetDevice(cl->device));
+  ZP_ON_DEVICE(cl->device);
   PowExp e{};
   for (uint32_t i = 0; i < expWords; ++i) e.w[i] = hExp[i];
   zp_clear_pending_error();
@@ -438,7 +438,7 @@ extern "C" int zp_client_expand_ckr(const zp_client* cl, const uint8_t* hKey, co
   const uint64_t last_block = ((uint64_t)count * CKR_W - 1) / 16 + 1;  // lanes may make one more
   if ((uint64_t)counter0 + last_block > 0xFFFFFFFFull)
     return zp_set_error(ZP_EINVAL, "zp_client_expand_ckr: the 32-bit block counter would wrap");
-  ZP_CUDA(cudaSetDevice(cl->device));
+  ZP_ON_DEVICE(cl->device);
   const ChachaKey k = chacha_key_from_bytes(hKey, hNonce);
   zp_clear_pending_error();
   cl->ctx->launches++;

@@ -263,7 +263,7 @@ extern "C" int zp_selftest_wait(zp_ctx* c, uint64_t cycles, void* stream) {
   if (!c) return zp_set_error(ZP_EINVAL, "zp_selftest_wait: null argument");
   if (cycles > (1ull << 32))
     return zp_set_error(ZP_EINVAL, "zp_selftest_wait: cycles=%llu above 2^32", (unsigned long long)cycles);
-  ZP_CUDA(cudaSetDevice(c->device));
+  ZP_ON_DEVICE(c->device);
   zp_clear_pending_error();
   c->launches++;
   k_selftest_wait<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>(cycles, c->d_status);

@@ -61,17 +61,16 @@ typedef CUresult (*PFN_encodeTiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_
                                     CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
 static PFN_encodeTiled get_encode_fn() {
-  static PFN_encodeTiled fn = nullptr;
-  static bool tried = false;
-  if (!tried) {
-    tried = true;
+  // looked up once; the initialisation of a function-local static is thread-safe
+  static const PFN_encodeTiled fn = []() -> PFN_encodeTiled {
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
                                          &q) == cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_encodeTiled>(p);
-  }
+      return reinterpret_cast<PFN_encodeTiled>(p);
+    return nullptr;
+  }();
   return fn;
 }
 
@@ -265,7 +264,7 @@ extern "C" int zp_init(int device, const zp_params* P, zp_ctx** out) {
     if (P->key_bits != 32 * ZP_MAX_L)
       return zp_set_error(ZP_EUNSUPPORTED, "zp_init: key_bits=%u (this build: %d)", P->key_bits,
                           32 * ZP_MAX_L);
-    ZP_CUDA(cudaSetDevice(device));
+    ZP_ON_DEVICE(device);
     zp_ctx* c = new zp_ctx();
     c->device = device;
     c->P = *P;
@@ -367,7 +366,7 @@ extern "C" int zp_init(int device, const zp_params* P, zp_ctx** out) {
 
 extern "C" int zp_ctx_destroy(zp_ctx* c) {
   if (!c) return ZP_OK;
-  cudaSetDevice(c->device);
+  zp_device_scope _zp_scope(c->device);
   if (c->d_status) cudaFree(c->d_status);
   if (c->d_rns) cudaFree(c->d_rns);
   delete c;
@@ -432,7 +431,7 @@ extern "C" int zp_kernel_launches(const zp_ctx* c, uint64_t* count) {
 
 extern "C" int zp_device_status(zp_ctx* c, uint32_t* code) {
   if (!c || !code) return zp_set_error(ZP_EINVAL, "zp_device_status: null argument");
-  ZP_CUDA(cudaSetDevice(c->device));
+  ZP_ON_DEVICE(c->device);
   ZP_CUDA(cudaDeviceSynchronize());
   ZP_CUDA(cudaMemcpy(code, c->d_status, sizeof(uint32_t), cudaMemcpyDeviceToHost));
   ZP_CUDA(cudaMemset(c->d_status, 0, sizeof(uint32_t)));
@@ -452,7 +451,7 @@ extern "C" int zp_setup_db(zp_ctx* c, const uint8_t* dD, uint32_t R, uint32_t C,
                           (unsigned long long)ld);
     if (reinterpret_cast<uintptr_t>(dD) % 16 != 0)
       return zp_set_error(ZP_EINVAL, "zp_setup_db: database pointer not 16-byte aligned");
-    ZP_CUDA(cudaSetDevice(c->device));
+    ZP_ON_DEVICE(c->device);
     zp_db* db = new zp_db();
     db->ctx = c;
     db->device = c->device;
@@ -522,7 +521,7 @@ extern "C" int zp_stale_rows(const zp_db* db, uint32_t* count) {
 
 extern "C" int zp_db_destroy(zp_db* db) {
   if (!db) return ZP_OK;
-  cudaSetDevice(db->device);
+  zp_device_scope _zp_scope(db->device);
   cudaDeviceSynchronize();
   if (db->d_rowsum) cudaFree(db->d_rowsum);
   if (db->d_hneg) cudaFree(db->d_hneg);
@@ -639,7 +638,7 @@ extern "C" int zp_gen_hint(zp_db* db, const uint32_t* dA, uint32_t* dH, const ui
     if (hRows && (nrows == 0 || nrows > db->R))
       return zp_set_error(ZP_EINVAL, "zp_gen_hint: nrows=%u out of [1, R]", nrows);
     zp_ctx* c = db->ctx;
-    ZP_CUDA(cudaSetDevice(c->device));
+    ZP_ON_DEVICE(c->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const uint32_t n = c->P.n;
     int rc = alloc_hint_state(db);
@@ -722,7 +721,7 @@ extern "C" int zp_update_rows(zp_db* db, const uint32_t* hRows, uint32_t k, cons
   try {
     if (!db || !hRows || !dNew) return zp_set_error(ZP_EINVAL, "zp_update_rows: null argument");
     if (k == 0 || k > db->R) return zp_set_error(ZP_EINVAL, "zp_update_rows: k=%u out of [1, R]", k);
-    ZP_CUDA(cudaSetDevice(db->ctx->device));
+    ZP_ON_DEVICE(db->ctx->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     uint32_t* dRows = nullptr;
     int rc = stage_rows(db, hRows, k, 0, &dRows, st);
@@ -750,7 +749,7 @@ extern "C" int zp_update_rows(zp_db* db, const uint32_t* hRows, uint32_t k, cons
 extern "C" int zp_answer(zp_db* db, const uint32_t* dQ, uint32_t B, uint32_t* dAns, void* stream) {
   if (!db || !dQ || !dAns) return zp_set_error(ZP_EINVAL, "zp_answer: null argument");
   if (B < 1 || B > 4096) return zp_set_error(ZP_EINVAL, "zp_answer: B=%u out of [1, 4096]", B);
-  ZP_CUDA(cudaSetDevice(db->ctx->device));
+  ZP_ON_DEVICE(db->ctx->device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   zp_ctx* c = db->ctx;
   // One to four queries: one pass of the dp4a GEMV over D (HBM- or dp4a-bound, ahead of
@@ -875,7 +874,7 @@ extern "C" int zp_register_client(zp_ctx* c, const uint32_t* hM, uint32_t L, zp_
         br = (t >> 63) & 1u;
       }
     }
-    ZP_CUDA(cudaSetDevice(c->device));
+    ZP_ON_DEVICE(c->device);
     zp_client* cl = new zp_client();
     cl->ctx = c;
     cl->device = c->device;
@@ -914,7 +913,7 @@ extern "C" int zp_register_client(zp_ctx* c, const uint32_t* hM, uint32_t L, zp_
 
 extern "C" int zp_client_destroy(zp_client* cl) {
   if (!cl) return ZP_OK;
-  cudaSetDevice(cl->device);
+  zp_device_scope _zp_scope(cl->device);
   cudaDeviceSynchronize();
   for (uint32_t* p : {cl->d_m, cl->d_mu, cl->d_m2, cl->d_r1, cl->d_r2, cl->d_mkm})
     if (p) cudaFree(p);
@@ -940,7 +939,7 @@ extern "C" int zp_compress(zp_db* db, zp_client* const* clients, const uint32_t*
     if (!db || !dAns || !dCKO || !dT) return zp_set_error(ZP_EINVAL, "zp_compress: null argument");
     int rc = check_compress_args(db, clients, B);
     if (rc) return rc;
-    ZP_CUDA(cudaSetDevice(db->ctx->device));
+    ZP_ON_DEVICE(db->ctx->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     rc = zp_launch_compress_products(db, dCKO, B, st, 0);
     if (rc) return rc;
@@ -956,7 +955,7 @@ extern "C" int zp_compress_products(zp_db* db, const uint32_t* dCKO, uint32_t B,
     if (B < 1 || B > 4096) return zp_set_error(ZP_EINVAL, "zp_compress_products: B=%u out of [1, 4096]", B);
     if (!db->hint_ready) return zp_set_error(ZP_ESTATE, "zp_compress_products: no hint (call zp_gen_hint)");
     if (db->stale) return zp_set_error(ZP_ESTATE, "zp_compress_products: %u hint rows stale", db->stale);
-    ZP_CUDA(cudaSetDevice(db->ctx->device));
+    ZP_ON_DEVICE(db->ctx->device);
     // only a single query's products share the GPU with an answer
     return zp_launch_compress_products(db, dCKO, B, static_cast<cudaStream_t>(stream),
                                        B == 1 ? db->ctx->overlap_sms : 0u);
@@ -971,7 +970,7 @@ extern "C" int zp_compress_finish(zp_db* db, zp_client* const* clients, const ui
     if (!db || !dAns || !dT) return zp_set_error(ZP_EINVAL, "zp_compress_finish: null argument");
     int rc = check_compress_args(db, clients, B);
     if (rc) return rc;
-    ZP_CUDA(cudaSetDevice(db->ctx->device));
+    ZP_ON_DEVICE(db->ctx->device);
     return zp_launch_compress_finish(db, clients, dAns, B, dT, static_cast<cudaStream_t>(stream));
   } catch (const std::bad_alloc&) {
     return zp_set_error(ZP_ENOMEM, "zp_compress_finish: host allocation failed");
@@ -994,7 +993,7 @@ extern "C" int zp_respond(zp_db* db, zp_client* const* clients, const uint32_t* 
     int rc = check_compress_args(db, clients, B);
     if (rc) return rc;
     zp_ctx* c = db->ctx;
-    ZP_CUDA(cudaSetDevice(c->device));
+    ZP_ON_DEVICE(c->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const bool overlap = B == 1 && c->overlap_sms > 0 && c->answer_path == ZP_PATH_AUTO &&
                          c->compress_path != ZP_PATH_SIMT && c->P.n <= 1024;
@@ -1030,7 +1029,7 @@ extern "C" int zp_client_hint(zp_db* db, const zp_client* cl, const uint32_t* dC
     if (db->stale) return zp_set_error(ZP_ESTATE, "zp_client_hint: %u hint rows stale after updates", db->stale);
     if ((reinterpret_cast<uintptr_t>(dCkr) | reinterpret_cast<uintptr_t>(dK)) & 15u)
       return zp_set_error(ZP_EINVAL, "zp_client_hint: dCkr and dK must be 16-byte aligned");
-    ZP_CUDA(cudaSetDevice(db->ctx->device));
+    ZP_ON_DEVICE(db->ctx->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const uint32_t* dRows = nullptr;
     uint32_t np = db->d1p;
@@ -1058,7 +1057,7 @@ extern "C" int zp_autotune(zp_db* db, void* stream, int64_t* chosen) {
   try {
     if (!db) return zp_set_error(ZP_EINVAL, "zp_autotune: null argument");
     zp_ctx* c = db->ctx;
-    ZP_CUDA(cudaSetDevice(c->device));
+    ZP_ON_DEVICE(c->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const uint32_t BQ = 16, n = c->P.n, L = c->L;
     const int saved_answer = c->answer_path, saved_compress = c->compress_path;
@@ -1177,7 +1176,7 @@ extern "C" int zp_autotune(zp_db* db, void* stream, int64_t* chosen) {
 extern "C" int zp_db_prepare_fp16(zp_db* db, void* stream) {
   if (!db) return zp_set_error(ZP_EINVAL, "zp_db_prepare_fp16: null argument");
   if (db->d_D16) return ZP_OK;
-  ZP_CUDA(cudaSetDevice(db->ctx->device));
+  ZP_ON_DEVICE(db->ctx->device);
   const uint64_t Kp = (db->C + 127) / 128 * 128;  // two K blocks per stage of the fp16 path
   const size_t bytes = (size_t)db->R * Kp * 2;
   if (cudaMalloc(&db->d_D16, bytes) != cudaSuccess) {
@@ -1201,7 +1200,7 @@ extern "C" int zp_db_prepare_rns(zp_db* db, void* stream) {
   if (!db->hint_ready) return zp_set_error(ZP_ESTATE, "zp_db_prepare_rns: no hint (call zp_gen_hint)");
   if (db->stale) return zp_set_error(ZP_ESTATE, "zp_db_prepare_rns: %u hint rows stale after updates", db->stale);
   if (db->ctx->P.n > 1024) return zp_set_error(ZP_EUNSUPPORTED, "zp_db_prepare_rns: needs n <= 1024");
-  ZP_CUDA(cudaSetDevice(db->ctx->device));
+  ZP_ON_DEVICE(db->ctx->device);
   return zp_ensure_rns(db, static_cast<cudaStream_t>(stream));
 }
 
@@ -1236,7 +1235,7 @@ extern "C" int zp_client_decrypt(const zp_client* cl, const uint32_t* hLam, cons
       x = big_mul(x, t);
       x.resize(L);
     }
-    ZP_CUDA(cudaSetDevice(cl->device));
+    ZP_ON_DEVICE(cl->device);
     return zp_launch_decrypt(cl, e.data(), (uint32_t)e.size(), x.data(), dC, dOut, count,
                              static_cast<cudaStream_t>(stream));
   } catch (const std::bad_alloc&) {
@@ -1255,7 +1254,7 @@ extern "C" int zp_combine(zp_db* db, zp_client* const* clients, const uint32_t* 
     }
     if ((reinterpret_cast<uintptr_t>(dK) | reinterpret_cast<uintptr_t>(dT) | reinterpret_cast<uintptr_t>(dOut)) & 15u)
       return zp_set_error(ZP_EINVAL, "zp_combine: dK, dT and dOut must be 16-byte aligned");
-    ZP_CUDA(cudaSetDevice(db->ctx->device));
+    ZP_ON_DEVICE(db->ctx->device);
     return zp_launch_combine(db, clients, dK, dT, B, dOut, static_cast<cudaStream_t>(stream));
   } catch (const std::bad_alloc&) {
     return zp_set_error(ZP_ENOMEM, "zp_combine: host allocation failed");
@@ -1269,7 +1268,7 @@ extern "C" int zp_respond_host(zp_db* db, zp_client* const* clients, const uint3
   int rc = check_compress_args(db, clients, B);
   if (rc) return rc;
   zp_ctx* c = db->ctx;
-  ZP_CUDA(cudaSetDevice(c->device));
+  ZP_ON_DEVICE(c->device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const size_t qb = (size_t)B * db->C * 4, cb = (size_t)B * c->P.n * c->L * 4;
   const size_t ab = (size_t)B * db->R * 4, tb = (size_t)B * db->d1p * c->L * 4;

@@ -139,6 +139,28 @@ int zp_cuda_check(cudaError_t e, const char* what);
 
 int zp_scratch_reserve(zp_scratch* s, size_t bytes);
 
+// Makes `dev` the current device for the lifetime of the scope and gives the caller its
+// own current device back at the end, so that no entry point changes it as a side effect.
+struct zp_device_scope {
+  int prev = -1;
+  cudaError_t err = cudaSuccess;
+  explicit zp_device_scope(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev == dev)
+      prev = -1;
+    else
+      err = cudaSetDevice(dev);
+  }
+  ~zp_device_scope() {
+    if (prev >= 0) (void)cudaSetDevice(prev);
+  }
+  zp_device_scope(const zp_device_scope&) = delete;
+  zp_device_scope& operator=(const zp_device_scope&) = delete;
+};
+#define ZP_ON_DEVICE(dev)                                                         \
+  zp_device_scope _zp_scope(dev);                                                 \
+  if (_zp_scope.err != cudaSuccess) return zp_cuda_check(_zp_scope.err, "cudaSetDevice")
+
 // Clears a pending runtime error left by an unrelated earlier call, so that the
 // check after a launch reports only that launch.
 static inline void zp_clear_pending_error() { (void)cudaGetLastError(); }

@@ -192,6 +192,80 @@ def test_batched_answer_extremes(zp, ctx, dval, qval, fp16):
     db.close()
 
 
+# K positions of the one small term, inside a 1024-long chunk: its first and last term,
+# inside a K = 16 MMA step (5, 1029), at step boundaries (15, 16, 17), mid-chunk (511) and
+# the start of the second chunk (1024) and the last K position (2047)
+ODD_POS = [0, 5, 15, 16, 17, 511, 1023, 1024, 1029, 2047]
+
+
+@pytest.mark.parametrize("fp16", [False, True])
+def test_batched_answer_accumulator_keeps_24_bits(zp, ctx, fp16):
+    """Every fp32 partial sum of a K chunk keeps all 24 bits: in a row, all centred products
+    are 2^14 (bytes 0 x 0) except a few of -128 and one of +-1 (a database byte 129 or 127
+    times a query plane byte 0x81 or 0x7F) at a varying K position, so the chunk sum lands on
+    an odd value just below 2^24 (1023 2^14 +- 1 - 128 k). An accumulator with fewer bits
+    would drop the odd term; the result must equal the oracle's bits."""
+    R, C, B = 2 * len(ODD_POS) * 8, 2048, 8
+    D = np.zeros((R, C), dtype=np.uint8)
+    for r in range(R):
+        D[r, ODD_POS[r % len(ODD_POS)]] = 129 if (r // len(ODD_POS)) % 2 == 0 else 127
+    Q = np.zeros((B, C), dtype=np.uint32)
+    for b in range(B):
+        Q[b, ODD_POS] = 0x81 if b < B // 2 else 0x7F   # plane 0 only; planes 1-3 stay 0
+    Q[B - 1, ODD_POS[3]] |= 0x81000000                 # one plane-3 byte as well
+    dD, ld = to_dev_db(zp, D)
+    db = zp.Database(ctx, dD, R, C, ld)
+    if fp16:
+        db.prepare_fp16()
+    ctx.set_option("answer_path", "tc")
+    try:
+        got = u32_host(db.answer(u32_dev(Q)))
+        got1 = u32_host(db.answer(u32_dev(Q[:1])))      # a single query on the tensor cores
+    finally:
+        ctx.set_option("answer_path", "auto")
+    want = lwe.matmat_mod_q(D, Q.T).T
+    assert np.array_equal(got, want)
+    assert np.array_equal(got1, want[:1])
+    db.close()
+
+
+def test_compression_products_accumulator_keeps_24_bits(zp):
+    """The same 24-bit check for the compression products V = H.cko (byte planes of the
+    negated hint times the bytes of cko, n = 1024 = one K chunk): H row r is zero but for
+    H[r, j_r] = 129 or 127 (the plane-0 byte), cko[i] = 0x81 for i in the set of positions,
+    so plane 0 x byte 0 of cko sums 2^14 terms with -128s and one +-1 to an odd value below
+    2^24. t must equal the oracle's."""
+    n = 1024
+    P = Params(n=n, key_bits=2048)
+    pos = [p for p in ODD_POS if p < n]
+    R = 4 * len(pos)
+    C = R                                   # D = identity: H+ row r = row r of A
+    c = zp.Context(0, n=n)
+    D = np.eye(R, C, dtype=np.uint8)
+    A = np.zeros((C, n), dtype=np.uint32)
+    for r in range(R):
+        hneg = 129 if (r // len(pos)) % 2 == 0 else 127
+        A[r, pos[r % len(pos)]] = (-hneg) % 2**32    # H+ = D.A; the negated hint is hneg
+    Hn = lwe.hint_neg(D, A)
+    assert Hn[0, pos[0]] == 129 and Hn[len(pos), pos[0]] == 127
+    dD, ld = to_dev_db(zp, D)
+    db = zp.Database(c, dD, R, C, ld)
+    db.gen_hint(u32_dev(A))
+    m = synth.random_odd_modulus(2048, 31)
+    cl = c.register_client(m)
+    cko = [0] * n
+    for p in pos:
+        cko[p] = 0x81
+    ans = synth.uniform_queries(1, R, 32)[0]
+    for path in ("tc", "rns", "simt"):           # byte planes; residues; CUDA cores
+        c.set_option("compress_path", path)
+        T = db.compress([cl], u32_dev(ans[None, :]), u32_dev(synth.ints_to_limbs(cko, 64)[None]))
+        assert synth.limbs_to_ints(u32_host(T)[0]) == zippir.compress_rows(ans, Hn, cko, m, P)
+    assert c.device_status() == 0
+    db.close()
+    c.close()
+
+
 @pytest.mark.parametrize("path", ["simt", "tc"])
 def test_single_query_other_paths(zp, path):
     """The CUDA-core and tensor-core kernels also serve B = 1 and agree with the GEMV."""

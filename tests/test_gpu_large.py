@@ -89,3 +89,36 @@ def test_compress_sampled_packed_rows(big):
         t = zippir.compress_rows(full_ans[:r1 - r0], Hpad[:r1 - r0], cko, m, P, packed_rows=[0])
         assert synth.limbs_to_ints(T_h[rp:rp + 1]) == t
     assert ctx.device_status() == 0
+
+
+def test_fp16_copy_answers_and_hint_randomized_check(big):
+    """Batches of 8 and 128 queries answered from the resident fp16 copy of D (the operand the
+    8 GiB benchmark workloads use) give the byte path's bits; every answer of both batches and
+    every entry of the hint H+ = D.A pass the randomized product check against the oracle
+    (tests/bigcheck.py: 16 projections W^T D of the whole database by the oracle's products,
+    a miss probability of at most 2^-16 per wrong column, 2^-32 unless its errors are all
+    multiples of 2^31); sampled rows are recomputed by the oracle directly."""
+    import bigcheck
+    zp, ctx, db, D, A_h, H = big
+    Qs = {B: synth.device_uniform_u32((B, C), 200 + B, "cuda") for B in (8, 128)}
+    by_bytes = {B: db.answer(Q) for B, Q in Qs.items()}
+    db.prepare_fp16()
+    by_fp16 = {B: db.answer(Q) for B, Q in Qs.items()}
+    torch.cuda.synchronize()
+    for B in Qs:
+        assert torch.equal(by_fp16[B], by_bytes[B])
+    assert ctx.device_status() == 0
+    Dh = D.cpu().numpy()
+    W = synth.uniform_queries(16, R, 210).T.copy()        # R x 16
+    U = bigcheck.left_projection(Dh, C, W)
+    rows = [0, 1, 4097, 33333, R - 1]
+    for B, Q in Qs.items():
+        Qh = Q.cpu().numpy().view(np.uint32)
+        got = by_fp16[B].cpu().numpy().view(np.uint32)
+        bad = bigcheck.freivalds(W, U, np.ascontiguousarray(got.T), np.ascontiguousarray(Qh.T))
+        assert bad.size == 0, "B=%d: queries with wrong answers %s" % (B, bad[:10])
+        want = bigcheck.rows_product(np.ascontiguousarray(Dh[rows, :C]), np.ascontiguousarray(Qh.T))
+        assert np.array_equal(got[:, rows], want.T)
+    Hh = H.cpu().numpy().view(np.uint32)
+    bad = bigcheck.freivalds(W, U, Hh, A_h)
+    assert bad.size == 0, "hint columns with wrong entries: %s" % bad[:10]

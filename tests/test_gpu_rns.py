@@ -66,6 +66,37 @@ def test_rns_compress_parity(zp, R, C, n, B, secret, fp16):
     assert c.device_status() == 0
 
 
+@pytest.mark.parametrize("R,B", [(1080, 8), (2100, 17)])
+@pytest.mark.parametrize("fp16", [False, True])
+def test_rns_several_m_tiles_per_prime(zp, R, B, fp16):
+    """n = 1024 and d1' = 40 / 78 packed rows, i.e. two / three 32-packed-row M tiles per
+    prime (the tile index g > 0 of the grouped product), the last packed row ragged at R =
+    2100: every packed row of every query equals the oracle's t, on the byte planes and on
+    their fp16 copy."""
+    n, C = 1024, 64
+    P = Params(n=n, key_bits=2048)
+    assert P.d1p(R) > 32
+    c = zp.Context(0, n=n)
+    c.set_option("compress_path", "rns")
+    D = synth.database(R, C, R + 7)
+    A = synth.seed_matrix(C, n, R + 8)
+    Hn = lwe.hint_neg(D, A)
+    db, dD = _db(zp, c, D)
+    db.gen_hint(u32_dev(A))
+    if fp16:
+        db.prepare_fp16()
+    ms = [synth.random_odd_modulus(2048, 150 + b) for b in range(B)]
+    cls = [c.register_client(m) for m in ms]
+    ckos = [synth.uniform_below(ms[b], n, 160 + b) for b in range(B)]
+    ans = synth.uniform_queries(B, R, 170)
+    T = db.compress(cls, u32_dev(ans), u32_dev(np.stack([synth.ints_to_limbs(x, 64) for x in ckos])))
+    got = u32_host(T)
+    assert got.shape[1] == P.d1p(R)
+    for b in range(B):
+        assert synth.limbs_to_ints(got[b]) == zippir.compress_rows(ans[b], Hn, ckos[b], ms[b], P)
+    assert c.device_status() == 0
+
+
 @pytest.mark.parametrize("fp16", [False, True])
 def test_rns_edge_values(zp, fp16):
     """cko at 0 and m - 1 and answers at 2^32 - 1 (the largest residue products and CRT sums)."""
