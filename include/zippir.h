@@ -188,7 +188,9 @@ int zp_compress_finish(zp_db* db, zp_client* const* clients, const uint32_t* dAn
  * then zp_compress into dT. Asynchronous on `stream`. For one query with the
  * "overlap_sms" option set, the compression products run on an internal stream
  * (forked from and joined back to `stream` with events) on overlap_sms SMs while the
- * answer streams the database on the remaining SMs. */
+ * answer streams the database on the remaining SMs; for a batch answered on the tensor
+ * cores ("batch_overlap"), they run on that stream beside the answers on whatever SMs are
+ * free. */
 int zp_respond(zp_db* db, zp_client* const* clients, const uint32_t* dQ, const uint32_t* dCKO,
                uint32_t B, uint32_t* dAns, uint32_t* dT, void* stream);
 
@@ -278,6 +280,9 @@ int zp_stale_rows(const zp_db* db, uint32_t* count);
  *                    query run while the answer uses the other SMs (zp_respond,
  *                    zp_compress_products, single-query zp_answer); 0 = no overlap.
  *                    Default: about 3/8 of the SMs (56 of 152) on GPUs with >= 64 SMs.
+ *   "batch_overlap": 1 (default) zp_respond runs the compression products of a batch
+ *                    answered on the tensor cores on an internal stream beside the answers
+ *                    (they do not read the answers), 0 one after the other.
  * Every variant computes the same exact result. Errors: ZP_EINVAL (unknown name or value). */
 int zp_set_option(zp_ctx* ctx, const char* name, int64_t value);
 /* Reads an option set by zp_set_option (or its default). Errors: ZP_EINVAL. */

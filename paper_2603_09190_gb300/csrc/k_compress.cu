@@ -85,7 +85,19 @@ __device__ __forceinline__ void warp_mul_cols(const uint32_t* a, int na, const u
     }
     const int i0 = w - (nb - 1) > 0 ? w - (nb - 1) : 0;
     const int i1 = w < na - 1 ? w : na - 1;
-    for (int i = i0; i <= i1; ++i) mac96(c0, c1, c2, a[i], b[w - i]);
+    // two independent carry chains (even and odd terms) for instruction-level parallelism
+    uint32_t d0 = 0, d1 = 0, d2 = 0;
+    int i = i0;
+    for (; i + 1 <= i1; i += 2) {
+      mac96(c0, c1, c2, a[i], b[w - i]);
+      mac96(d0, d1, d2, a[i + 1], b[w - i - 1]);
+    }
+    if (i <= i1) mac96(c0, c1, c2, a[i], b[w - i]);
+    asm("add.cc.u32 %0, %0, %3;\n\t"
+        "addc.cc.u32 %1, %1, %4;\n\t"
+        "addc.u32 %2, %2, %5;"
+        : "+r"(c0), "+r"(c1), "+r"(c2)
+        : "r"(d0), "r"(d1), "r"(d2));
     col[w][0] = c0;
     col[w][1] = c1;
     col[w][2] = c2;
@@ -137,16 +149,13 @@ __device__ __forceinline__ uint32_t mod_p(uint64_t x, uint32_t p, uint64_t mu) {
 
 // grid (ceil(d1p / PACK_WARPS), B), block PACK_WARPS warps, dynamic shared memory
 // PACK_WARPS x (PackBarrett + ell x VW words). Requires L == ZP_MAX_L.
-// V: [b][Rp][VW] words, the exact products V[row] = H[row,:] . cko[b].
-//
-// RNS (the products are residues X[b][r'][k] = H'[r', :] . cko mod p_k): V is absent, the
-// Horner runs over the answers only (b'), and H'.cko is rebuilt by the Chinese remainder
-// theorem modulo m: with y_k = X_k (M/p_k)^{-1} mod p_k, H'.cko = sum_k y_k M/p_k - alpha M,
-// alpha = floor(sum_k y_k / p_k) exactly (H'.cko < M 2^-26, so the double-precision sum
-// plus 2^-30 floors to alpha), and
-//   b' + H'.cko = b' + sum_k y_k (M/p_k mod m) + alpha (m - (M mod m))   (mod m),
-// whose right side (< 2^2083) is summed into X's lazy registers before the reduction.
-template <bool RNS>
+// PACKED = false: V is [b][Rp][VW] words, the exact products V[row] = H[row,:] . cko[b]
+// of every answer row, packed with the answers (W_j = ans + V).
+// PACKED = true (the residue-number-system path): V is [b][Rp][VW] words holding one
+// integer per PACKED row, already reduced congruent to H'.cko mod m by the Chinese remainder
+// theorem (k_crt_prep and the CRT product); the Horner runs over the answers only (b') and V
+// is added once before the reduction.
+template <bool PACKED>
 __global__ void __launch_bounds__(PACK_WARPS * 32)
     k_pack_reduce(const uint32_t* __restrict__ ans, const uint32_t* __restrict__ V, uint32_t R,
                   uint32_t Rp, uint32_t ell, uint32_t d1p, uint32_t g1, uint32_t g2,
@@ -157,7 +166,7 @@ __global__ void __launch_bounds__(PACK_WARPS * 32)
   const uint32_t b = blockIdx.y;
   const uint32_t rp = blockIdx.x * PACK_WARPS + warp;
   if (rp >= d1p) return;
-  const uint32_t per_warp = (uint32_t)(sizeof(PackBarrett) / 4) + (RNS ? 0u : ell * VW);
+  const uint32_t per_warp = (uint32_t)(sizeof(PackBarrett) / 4) + (PACKED ? 0u : ell * VW);
   PackBarrett& S = *reinterpret_cast<PackBarrett*>(pack_smem + warp * per_warp);
   uint32_t* Vs = pack_smem + warp * per_warp + sizeof(PackBarrett) / 4;  // ell x VW
   constexpr int L = ZP_MAX_L;
@@ -166,8 +175,23 @@ __global__ void __launch_bounds__(PACK_WARPS * 32)
   const uint32_t row0 = rp * ell;
   const uint32_t nrows = R - row0 < ell ? R - row0 : ell;
   const uint32_t* src = V + ((uint64_t)b * Rp + row0) * VW;
-  if (!RNS)
-    for (uint32_t idx = lane; idx < nrows * VW; idx += 32) Vs[idx] = __ldg(src + idx);
+  if (!PACKED) {
+    // eight loads in flight per lane before the stores (the rows come from L2)
+    const uint32_t tot = nrows * VW;
+    for (uint32_t base = 0; base < tot; base += 32 * 8) {
+      uint32_t v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const uint32_t idx = base + 32u * u + lane;
+        v[u] = idx < tot ? __ldg(src + idx) : 0u;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const uint32_t idx = base + 32u * u + lane;
+        if (idx < tot) Vs[idx] = v[u];
+      }
+    }
+  }
   for (int x = lane; x < L + 1; x += 32) {
     S.m[x] = x < L ? cl[b].m[x] : 0u;
     S.mu[x] = cl[b].mu[x];
@@ -191,7 +215,7 @@ __global__ void __launch_bounds__(PACK_WARPS * 32)
     v[1] = (uint64_t)g1 * xv[0] + (uint64_t)g2 * xm1;
     v[2] = (uint64_t)g1 * xv[1] + (uint64_t)g2 * xv[0];
     v[3] = (uint64_t)g1 * xv[2] + (uint64_t)g2 * xv[1];
-    if (!RNS) {
+    if (!PACKED) {
 #pragma unroll
       for (int t = 0; t < 4; ++t) {
         const uint32_t x = lane * 4 + t;
@@ -209,57 +233,13 @@ __global__ void __launch_bounds__(PACK_WARPS * 32)
     const uint64_t cin = __shfl_up_sync(0xffffffffu, c, 1);
     if (lane) xv[0] += cin;
   }
-  if (RNS) {
-    // y_k for k = lane + 32 q, and alpha from the warp sum of y_k / p_k
-    constexpr int QK = (ZP_RNS_K + 31) / 32;
-    uint32_t y[QK];
-    double f = 0.0;
-    const uint32_t* Xr = V + ((uint64_t)b * d1p + rp) * ZP_RNS_K;
+  if (PACKED) {  // + the packed row's V (67 words, < 2^2090)
+    const uint32_t* Vp = V + ((uint64_t)b * Rp + rp) * VW;
 #pragma unroll
-    for (int q = 0; q < QK; ++q) {
-      const uint32_t k = lane + 32u * q;
-      y[q] = 0u;
-      if (k < ZP_RNS_K) {
-        y[q] = mod_p((uint64_t)__ldg(Xr + k) * rns->inv[k], rns->p[k], rns->mu[k]);
-        f += (double)y[q] * rns->dinv[k];
-      }
+    for (int t = 0; t < 4; ++t) {
+      const uint32_t x = lane * 4 + t;
+      if (x < VW) xv[t] += __ldg(Vp + x);
     }
-#pragma unroll
-    for (int o = 16; o; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
-    const uint32_t alpha = (uint32_t)floor(f + 0x1p-30);
-    // sum_k y_k (M_k mod m) + alpha (m - M mod m) into words lane*4 .. lane*4+3 (< 64):
-    // low halves to the word, high halves to the next (the top one to the next lane)
-    // The two half-warps take alternate k (the row after the ZP_RNS_K rows of M_k mod m is
-    // m - (M mod m), weighted by alpha); lane l of a half holds words 4 (l % 16) .. + 3.
-    const uint32_t* mk = cl[b].mkm;
-    const uint32_t hl = lane & 15u, half = lane >> 4;
-    uint64_t cv[4] = {0, 0, 0, 0}, hi3 = 0;
-    for (uint32_t k = half; k <= ZP_RNS_K; k += 2) {
-      const uint32_t q = k >> 5;
-      uint32_t yq = y[0];
-#pragma unroll
-      for (int qq = 1; qq < QK; ++qq)
-        if (q == (uint32_t)qq) yq = y[qq];
-      const uint32_t ys = __shfl_sync(0xffffffffu, yq, k & 31);
-      const uint32_t yk = k < ZP_RNS_K ? ys : alpha;
-      const uint4 mw = __ldg(reinterpret_cast<const uint4*>(mk + (uint64_t)k * ZP_MAX_L + hl * 4));
-      const uint64_t p0 = (uint64_t)yk * mw.x, p1 = (uint64_t)yk * mw.y;
-      const uint64_t p2 = (uint64_t)yk * mw.z, p3 = (uint64_t)yk * mw.w;
-      cv[0] += (uint32_t)p0;
-      cv[1] += (uint32_t)p1 + (p0 >> 32);
-      cv[2] += (uint32_t)p2 + (p1 >> 32);
-      cv[3] += (uint32_t)p3 + (p2 >> 32);
-      hi3 += p3 >> 32;
-    }
-#pragma unroll
-    for (int t = 0; t < 4; ++t) cv[t] += __shfl_down_sync(0xffffffffu, cv[t], 16);
-    hi3 += __shfl_down_sync(0xffffffffu, hi3, 16);
-    if (lane < 16) {
-#pragma unroll
-      for (int t = 0; t < 4; ++t) xv[t] += cv[t];
-    }
-    const uint64_t hin = __shfl_up_sync(0xffffffffu, hi3, 1);  // into the next lane's word 0
-    if (lane >= 1 && lane <= 16) xv[0] += hin;
   }
   // final carry resolution, then X to shared memory
   {
@@ -326,6 +306,56 @@ __global__ void __launch_bounds__(PACK_WARPS * 32)
   for (int t = 0; t < 3; ++t) {
     const int x = (int)lane * 3 + t;
     if (x < L) out[x] = r[t];
+  }
+}
+
+// Residue-number-system path, step 1 of the reduction (Sec. 5.2): from the residues
+// X[b][r'][k] = H'[r', :] . cko[b] mod p_k, y_k = X_k (M/p_k)^{-1} mod p_k and alpha =
+// floor(sum_k y_k / p_k) (exact: H'.cko < M 2^-26, so the double-precision sum plus 2^-30
+// floors to alpha), so that H'.cko = sum_k y_k M/p_k - alpha M. Written as the byte planes of
+// the CRT product's A operand: row b 4 Rq + 128 g + 32 a + t (r' = 32 g + t) holds byte a of
+// y_k in column k < ZP_RNS_K and of alpha in column ZP_RNS_K; packed rows r' in [d1', Rq)
+// are zero. yrs: the byte sums of those rows. One warp per (query, packed row < Rq).
+__global__ void k_crt_prep(const uint32_t* __restrict__ X, uint32_t B, uint32_t d1p, uint32_t Rq,
+                           const zp_rns_dev* __restrict__ rns, uint8_t* __restrict__ Yp,
+                           uint32_t ypitch, uint32_t* __restrict__ yrs) {
+  const uint64_t wid = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t lane = threadIdx.x & 31;
+  if (wid >= (uint64_t)B * Rq) return;
+  const uint32_t b = (uint32_t)(wid / Rq), rp = (uint32_t)(wid % Rq);
+  constexpr int QK = (ZP_RNS_K + 1 + 31) / 32;
+  uint32_t y[QK];
+  double f = 0.0;
+  const uint32_t* Xr = X + ((uint64_t)b * d1p + rp) * ZP_RNS_K;
+#pragma unroll
+  for (int q = 0; q < QK; ++q) {
+    const uint32_t k = lane + 32u * q;
+    y[q] = 0u;
+    if (rp < d1p && k < ZP_RNS_K) {
+      y[q] = mod_p((uint64_t)__ldg(Xr + k) * rns->inv[k], rns->p[k], rns->mu[k]);
+      f += (double)y[q] * rns->dinv[k];
+    }
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
+  constexpr uint32_t KA = ZP_RNS_K;  // column of alpha
+  if (rp < d1p && lane == KA % 32) y[KA / 32] = (uint32_t)floor(f + 0x1p-30);
+  const uint64_t row0 = (uint64_t)b * 4 * Rq + 128ull * (rp >> 5) + (rp & 31u);
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    uint8_t* dst = Yp + (row0 + 32u * a) * ypitch;
+    uint32_t sum = 0;
+#pragma unroll
+    for (int q = 0; q < QK; ++q) {
+      const uint32_t k = lane + 32u * q;
+      if (k <= KA) {
+        const uint32_t byte = (y[q] >> (8 * a)) & 0xFFu;
+        dst[k] = (uint8_t)byte;
+        sum += byte;
+      }
+    }
+    sum = __reduce_add_sync(0xffffffffu, sum);
+    if (lane == 0) yrs[row0 + 32u * a] = sum;
   }
 }
 
@@ -414,10 +444,30 @@ int zp_launch_compress_finish(zp_db* db, zp_client* const* clients, const uint32
   zp_clear_pending_error();
   ctx->launches++;
   if (db->v_rns) {
+    // residues -> y, alpha (byte planes) -> exact CRT sums on the tensor cores -> pack + reduce
+    const uint32_t Rq = db->Rq, ypitch = (ZP_RNS_K + 1 + 15) / 16 * 16;
+    const size_t yp_bytes = (size_t)B * 4 * Rq * ypitch, yrs_bytes = (size_t)B * 4 * Rq * 4;
+    const size_t vc_bytes = (size_t)B * Rq * VW * 4;
+    rc = zp_scratch_reserve(&db->s_crt, yp_bytes + yrs_bytes + vc_bytes + 512);
+    if (rc) return rc;
+    uint8_t* Yp = static_cast<uint8_t*>(db->s_crt.p);
+    uint32_t* yrs = reinterpret_cast<uint32_t*>(Yp + (yp_bytes + 255) / 256 * 256);
+    uint32_t* Vc = yrs + (yrs_bytes / 4 + 63) / 64 * 64;
+    const uint64_t warps = (uint64_t)B * Rq;
+    k_crt_prep<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(V, B, db->d1p, Rq, ctx->d_rns, Yp,
+                                                                    ypitch, yrs);
+    ZP_CUDA(cudaGetLastError());
+    // the mkm pointers are the third member of each uploaded ClientPtrs
+    rc = zp_launch_crt_products(db, reinterpret_cast<const uint32_t* const*>(dcl) + 2,
+                                (uint32_t)(sizeof(ClientPtrs) / sizeof(void*)), B, Yp, ypitch, yrs,
+                                Vc, st);
+    if (rc) return rc;
+    zp_clear_pending_error();
+    ctx->launches++;
     const size_t smem = (size_t)PACK_WARPS * sizeof(PackBarrett);
-    k_pack_reduce<true><<<grid, PACK_WARPS * 32, smem, st>>>(dAns, V, db->R, db->Rp, ctx->ell,
-                                                             db->d1p, ctx->gamma_w[1],
-                                                             ctx->gamma_w[2], dcl, dT, ctx->d_rns);
+    k_pack_reduce<true><<<grid, PACK_WARPS * 32, smem, st>>>(dAns, Vc, db->R, Rq, ctx->ell, db->d1p,
+                                                             ctx->gamma_w[1], ctx->gamma_w[2], dcl,
+                                                             dT, nullptr);
   } else {
     const size_t smem = (size_t)PACK_WARPS * (sizeof(PackBarrett) + (size_t)ctx->ell * VW * 4);
     k_pack_reduce<false><<<grid, PACK_WARPS * 32, smem, st>>>(dAns, V, db->R, db->Rp, ctx->ell,

@@ -21,6 +21,11 @@
 //             sum_a 2^(8a) P_a in the epilogue;
 //   MODE_HINT the global hint H+ = D A mod 2^32 (Algorithm "ZipPIR" caption): as
 //             MODE_ANS with the columns of A as queries, written row-major R x n;
+//   MODE_RES  residues of the compression offsets modulo the RNS primes (Sec. 5.2),
+//             cko[b][i] mod p_k = sum_beta byte_beta(cko[b][i]) (2^(8 beta) mod p_k): A = the
+//             256 bytes of every cko[b][i] (K = 256), B = the four bytes c of 2^(8 beta) mod
+//             p_k for 40 primes per N tile (N = 160); the epilogue folds the four sums S_c
+//             of a prime into the residue and writes its bytes as the B operand of MODE_RNS;
 //   MODE_CMP  the compression products V[r] = sum_i H[r][i] cko[i] (Algorithm
 //             "ZipPIR", Response, second line): A = the 4 byte planes of the negated
 //             hint, rows ordered (32 rows of plane 0, of plane 1, ...), B = the 256
@@ -59,7 +64,7 @@ constexpr int NTHREADS = 384;
 constexpr int STG_PITCH = 67;                // words per staged row (odd: no bank conflicts)
 constexpr int STG_BYTES = 4 * 32 * STG_PITCH * 4;
 
-enum { MODE_ANS = 0, MODE_HINT = 1, MODE_CMP = 2, MODE_RNS = 3 };
+enum { MODE_ANS = 0, MODE_HINT = 1, MODE_CMP = 2, MODE_RNS = 3, MODE_RES = 4 };
 
 // Three rings: B (fp16, from L2: deep, it is the largest operand), A as bytes (from
 // HBM, L2-prefetched) and A as fp16 (written by the converters just before the MMA).
@@ -111,14 +116,15 @@ struct GemmArgs {
   // k * num_n_tiles * N; out[(b d1p + r') ZP_RNS_K + k]
   uint32_t mt_per_prime, d1p;
   const zp_rns_dev* rns;
+  // MODE_CMP: the A rows of N tile nt start at nt * a_rows_per_n (0: one A for every N tile)
+  uint32_t a_rows_per_n;
+  // MODE_RES: A row b res_n + i = the 256 bytes of cko[b][i]; output = the B operand of the
+  // RNS product (res_out, centred fp16, tile width res_bt, res_nnt N tiles, K pitch res_kp)
+  // and its row byte sums (res_colsum, zeroed by the caller)
+  uint32_t res_n, res_bt, res_nnt, res_kp;
+  __half* res_out;
+  uint32_t* res_colsum;
 };
-
-// x mod p for x < 2^64, p < 2^32, mu = floor((2^64 - 1) / p) (Barrett; one correction).
-__device__ __forceinline__ uint32_t mod_p(uint64_t x, uint32_t p, uint64_t mu) {
-  const uint64_t q = __umul64hi(x, mu);
-  const uint64_t r = x - q * p;
-  return (uint32_t)(r >= p ? r - p : r);
-}
 
 __device__ __forceinline__ uint32_t cvt_rn(uint32_t fbits) {
   return (uint32_t)__float2int_rn(__uint_as_float(fbits));
@@ -238,7 +244,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       uint32_t pf_tile = blockIdx.x, pf_kb = 0;
       auto pf_step = [&]() {
         if (pf_tile < num_tiles)
-          tma_prefetch_l2_2d(&tmA, (int32_t)(pf_kb * BK), (int32_t)((pf_tile / args.num_n_tiles) * BM));
+          tma_prefetch_l2_2d(&tmA, (int32_t)(pf_kb * BK),
+                             (int32_t)((pf_tile / args.num_n_tiles) * BM +
+                                       (pf_tile % args.num_n_tiles) * args.a_rows_per_n));
         if (++pf_kb == nkb) {
           pf_kb = 0;
           pf_tile += gridDim.x;
@@ -247,6 +255,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       for (uint32_t f = 0; f < PF; ++f) pf_step();
       for (uint32_t tile = blockIdx.x; ok && tile < num_tiles; tile += gridDim.x) {
         const uint32_t mt = tile / args.num_n_tiles;
+        const uint32_t arow = mt * BM + (tile % args.num_n_tiles) * args.a_rows_per_n;
         for (uint32_t ks = 0; ks < nks; ++ks, ++cnt) {
           const uint32_t sb = cnt % SB, rb = cnt / SB;
           if (rb > 0 && !mbar_wait_abortable(&b_empty[sb], (rb - 1) & 1u, abort_flag,
@@ -258,7 +267,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           for (uint32_t h = 0; h < KPS; ++h) {
             pf_step();
             tma_load_2d(a_ring + sb * C::AST + h * A16_BYTES, &tmA, (int32_t)((ks * KPS + h) * BK),
-                        (int32_t)(mt * BM), &b_full[sb]);
+                        (int32_t)arow, &b_full[sb]);
           }
         }
       }
@@ -285,7 +294,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       uint32_t pf_tile = blockIdx.x, pf_p = 0;
       auto pf_step = [&]() {
         if (pf_tile < num_tiles)
-          tma_prefetch_l2_2d(&tmA, (int32_t)(pf_p * 2 * BK), (int32_t)((pf_tile / args.num_n_tiles) * BM));
+          tma_prefetch_l2_2d(&tmA, (int32_t)(pf_p * 2 * BK),
+                             (int32_t)((pf_tile / args.num_n_tiles) * BM +
+                                       (pf_tile % args.num_n_tiles) * args.a_rows_per_n));
         if (++pf_p == npairs) {
           pf_p = 0;
           pf_tile += gridDim.x;
@@ -295,6 +306,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       uint32_t su = 0, pu = 0;
       for (uint32_t tile = blockIdx.x; ok && tile < num_tiles; tile += gridDim.x) {
         const uint32_t mt = tile / args.num_n_tiles;
+        const uint32_t arow = mt * BM + (tile % args.num_n_tiles) * args.a_rows_per_n;
         for (uint32_t p = 0; p < npairs; ++p, ++cnt) {
           pf_step();
           if (cnt >= (uint32_t)SU && !mbar_wait_abortable(&u8_empty[su], pu ^ 1u, abort_flag,
@@ -303,7 +315,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             break;
           }
           mbar_arrive_expect_tx(&u8_full[su], U8_STAGE);
-          tma_load_2d(u8_ring + su * U8_STAGE, &tmA, (int32_t)(p * 2 * BK), (int32_t)(mt * BM),
+          tma_load_2d(u8_ring + su * U8_STAGE, &tmA, (int32_t)(p * 2 * BK), (int32_t)arow,
                       &u8_full[su]);
           if (++su == SU) {
             su = 0;
@@ -477,10 +489,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     for (uint32_t tile = blockIdx.x; ok && tile < num_tiles; tile += gridDim.x) {
       const uint32_t nt = tile % args.num_n_tiles, mt = tile / args.num_n_tiles;
       if constexpr (MODE == MODE_RNS) {
-        // single chunk (n <= 1024). Row (plane e, packed row 32 g + lane) of prime k: the
-        // exact byte-product sums of the 4 BT columns (c, bl) are folded into residues
-        // sum_c 2^(8c) S_c mod p per query bl, then the four planes e are combined with
-        // 2^(8e) mod p through shared memory.
+        // single chunk (n <= 1024). Row (plane e, packed row 32 g + lane) of prime k: column
+        // (c, bl) holds S_c, the exact byte-product sum of plane e of H' mod p and byte c of
+        // cko[bl] mod p (< 2^26 once the centring is undone). The thread folds the four
+        // columns of a query into x = sum_c S_c (2^(8(e + c)) mod p) < 2^55 with 64-bit
+        // multiply-adds, then reduces x below 2^28 by two pseudo-Mersenne folds (p = 2^27 -
+        // dl, dl < 2^12: x = lo + hi 2^27 == lo + hi dl); the four planes are added through
+        // shared memory and reduced once more to [0, p).
         const uint32_t a = acc_cnt & 1u, ra = acc_cnt >> 1;
         if (!bar_and_128(warp_wait(&acc_full[a], ra & 1u, abort_flag, args.status))) {
           ok = false;
@@ -488,49 +503,141 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
         tc_fence_after();
         const uint32_t k = mt / args.mt_per_prime, g = mt % args.mt_per_prime;
-        const uint32_t p = args.rns->p[k];
-        const uint64_t mu = args.rns->mu[k];
-        uint32_t p8[4];
+        const uint32_t p = args.rns->p[k], dl = (1u << 27) - p;
+        uint32_t w[4];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) p8[c] = args.rns->pow8[k][c];
-        const uint32_t corr_row = 128u * __ldg(args.rowsumA + mt * BM + e * 32 + lane) -
-                                  16384u * args.Kp;
+        for (int c = 0; c < 4; ++c) w[c] = args.rns->pow8[k][e + c];
+        // the centring terms: corr_row (this row) times sum_c w[c], and per query the column
+        // sums' 128 sum_c cs[c BT + bl] w[c] (two queries per lane, fetched by shuffles)
+        const int32_t corr_row =
+            (int32_t)(128u * __ldg(args.rowsumA + mt * BM + e * 32 + lane) - 16384u * args.Kp);
+        const uint64_t rowterm =
+            (uint64_t)((int64_t)corr_row * (int64_t)((uint64_t)w[0] + w[1] + w[2] + w[3]));
         const uint32_t* cs = args.colsum + ((uint64_t)k * args.num_n_tiles + nt) * (4 * BT);
-        uint32_t res[BT];
+        constexpr int NH = (BT + 31) / 32;
+        uint64_t qcs[NH];
 #pragma unroll
-        for (int bl = 0; bl < BT; ++bl) res[bl] = 0u;
+        for (int h = 0; h < NH; ++h) {
+          const uint32_t bl = 32u * h + lane;
+          uint64_t q = 0;
+          if (bl < (uint32_t)BT) {
 #pragma unroll
-        for (int g32 = 0; g32 < (4 * BT) / 32; ++g32) {
-          uint32_t r[32];
-          tmem_ld32(tmem_base + lane_addr + a * 256u + 32u * g32, r);
+            for (int c = 0; c < 4; ++c) q += (uint64_t)(128u * __ldg(cs + c * BT + bl)) * w[c];
+          }
+          qcs[h] = q + rowterm;
+        }
+        constexpr int PITCH = BT + 1;  // odd: conflict-free
+        uint32_t* myst = stg + (e * 32 + lane) * PITCH;
+#pragma unroll
+        for (int b16 = 0; b16 < BT / 16; ++b16) {
+          uint32_t r[4][16];
+#pragma unroll
+          for (int c = 0; c < 4; ++c)
+            tmem_ld16(tmem_base + lane_addr + a * 256u + (uint32_t)(c * BT + 16 * b16), r[c]);
           tmem_wait_ld();
 #pragma unroll
-          for (int q = 0; q < 32; ++q) {
-            const int col = 32 * g32 + q, c = col / BT, bl = col % BT;
-            // the exact sum of byte products (< 2^26) after undoing the centring
-            const uint32_t v = cvt_rn(r[q]) + corr_row + 128u * __ldg(cs + col);
-            res[bl] = mod_p((uint64_t)res[bl] + (uint64_t)v * p8[c], p, mu);
+          for (int j = 0; j < 16; ++j) {
+            const int bl = 16 * b16 + j;
+            uint64_t x = __shfl_sync(0xffffffffu, qcs[bl / 32], bl % 32);
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+              x += (uint64_t)((int64_t)__float2int_rn(__uint_as_float(r[c][j])) * (int64_t)w[c]);
+            const uint64_t t1 = (x & 0x7FFFFFFull) + (x >> 27) * dl;            // < 2^41
+            myst[bl] = (uint32_t)((t1 & 0x7FFFFFFull) + (t1 >> 27) * dl);      // < 2^28
           }
         }
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&acc_empty[a]);
         ++acc_cnt;
-        constexpr int PITCH = BT + 1;  // odd: conflict-free
-#pragma unroll
-        for (int bl = 0; bl < BT; ++bl) stg[(e * 32 + lane) * PITCH + bl] = res[bl];
         asm volatile("bar.sync 1, 128;" ::: "memory");
         const uint32_t tid = e * 32 + lane;
         for (uint32_t idx = tid; idx < 32u * BT; idx += 128) {
           const uint32_t t = idx / BT, bl = idx % BT;
-          uint64_t x = 0;
+          uint32_t y = 0;  // < 2^30
 #pragma unroll
-          for (int pl = 0; pl < 4; ++pl) x += (uint64_t)stg[(pl * 32 + t) * PITCH + bl] * p8[pl];
+          for (int pl = 0; pl < 4; ++pl) y += stg[(pl * 32 + t) * PITCH + bl];
+          y = (y & 0x7FFFFFFu) + (y >> 27) * dl;  // < 2^27 + 7 dl < 2p
+          if (y >= p) y -= p;
           const uint32_t rp = g * 32 + t, b = nt * BT + bl;
           if (rp < args.d1p && b < args.Bvalid)
-            args.out[((uint64_t)b * args.d1p + rp) * ZP_RNS_K + k] = mod_p(x, p, mu);
+            args.out[((uint64_t)b * args.d1p + rp) * ZP_RNS_K + k] = y;
         }
         asm volatile("bar.sync 1, 128;" ::: "memory");
+      } else if constexpr (MODE == MODE_RES) {
+        // single chunk (K = 256). Row b n + i, column (k, c): S_c = sum_beta byte_beta(cko)
+        // byte_c(2^(8 beta) mod p_k) < 2^24 once the centring is undone, so the residue is
+        // x = sum_c S_c 2^(8c) < 2^48 folded below p (p = 2^27 - dl, dl < 2^12). Its four
+        // bytes go to the rows of the RNS product's B operand (fp16, centred) and their sums
+        // over i to that operand's row sums.
+        const uint32_t a = acc_cnt & 1u, ra = acc_cnt >> 1;
+        if (!warp_wait(&acc_full[a], ra & 1u, abort_flag, args.status)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t row = mt * BM + e * 32 + lane;  // b n + i
+        const bool live = row < args.Mvalid;
+        const uint32_t b = live ? row / args.res_n : 0u, i = live ? row - b * args.res_n : 0u;
+        const uint32_t b0 = __shfl_sync(0xffffffffu, b, 0);
+        const bool uni = __all_sync(0xffffffffu, !live || b == b0);  // one query in this warp
+        const uint32_t bt = args.res_bt, ntq = b / bt, bl = b % bt;
+        const uint32_t kper = N / 4;  // primes per N tile
+        // centring terms: corr_row (this row) in every byte column, and per prime j of the tile
+        // 128 sum_c cs[4 j + c] 2^(8c) (lanes hold j = lane and lane + 32; fetched by shuffles)
+        const int64_t corr_row =
+            live ? (int64_t)(int32_t)(128u * __ldg(args.rowsumA + row) - 16384u * args.Kp) : 0;
+        const uint64_t rowterm = (uint64_t)(corr_row * 0x01010101ll);
+        const uint32_t* cs = args.colsum + (uint64_t)nt * N;
+        uint64_t csw[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const uint32_t j = 32u * h + lane;
+          uint64_t q = 0;
+          if (j < kper) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) q += (uint64_t)(128u * __ldg(cs + 4 * j + c)) << (8 * c);
+          }
+          csw[h] = q + rowterm;
+        }
+        for (uint32_t g = 0; g < N / 32; ++g) {
+          uint32_t r[32];
+          tmem_ld32(tmem_base + lane_addr + a * 256u + 32u * g, r);
+          tmem_wait_ld();
+#pragma unroll
+          for (int kk = 0; kk < 8; ++kk) {
+            const uint32_t j = g * 8 + kk, k = nt * kper + j;
+            const uint64_t cj = __shfl_sync(0xffffffffu, csw[j >> 5], j & 31);
+            if (k >= ZP_RNS_K) continue;  // uniform across the warp
+            const uint32_t p = args.rns->p[k], dl = (1u << 27) - p;
+            uint64_t x = cj;
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+              x += (uint64_t)((int64_t)__float2int_rn(__uint_as_float(r[4 * kk + c])) << (8 * c));
+            const uint64_t t1 = (x & 0x7FFFFFFull) + (x >> 27) * dl;  // < 2^34
+            uint32_t v = (uint32_t)((t1 & 0x7FFFFFFull) + (t1 >> 27) * dl);  // < 2^27 + 2^19 < 2p
+            if (v >= p) v -= p;
+            const uint64_t brow = ((uint64_t)k * args.res_nnt + ntq) * (4 * bt) + bl;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+              const uint32_t byte = live ? (v >> (8 * c)) & 0xFFu : 0u;
+              if (live) args.res_out[(brow + c * bt) * args.res_kp + i] = __int2half_rn((int)byte - 128);
+              if (uni) {
+                const uint32_t sum = __reduce_add_sync(0xffffffffu, byte);
+                if (lane == 0 && sum) {
+                  const uint64_t brow0 = ((uint64_t)k * args.res_nnt + b0 / bt) * (4 * bt) + b0 % bt;
+                  atomicAdd(&args.res_colsum[brow0 + c * bt], sum);
+                }
+              } else if (byte) {
+                atomicAdd(&args.res_colsum[brow + c * bt], byte);
+              }
+            }
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&acc_empty[a]);
+        ++acc_cnt;
       } else if constexpr (MODE == MODE_CMP) {
         // single chunk (n <= 1024): byte-column sums -> 67-word integer
         const uint32_t a = acc_cnt & 1u, ra = acc_cnt >> 1;
@@ -540,7 +647,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           break;
         }
         tc_fence_after();
-        const uint32_t m = mt * BM + e * 32 + lane;  // row of A (plane e of answer row 32 mt + lane)
+        // row of A (plane e of answer row 32 mt + lane; batched A: of N tile nt's rows)
+        const uint32_t m = mt * BM + e * 32 + lane + nt * args.a_rows_per_n;
         const uint32_t b = nt;
         const uint32_t corr_row = 128u * __ldg(args.rowsumA + m) - 16384u * args.Kp;
         const uint32_t* cs = args.colsum + (uint64_t)b * 256;
@@ -756,14 +864,19 @@ __global__ void k_prep_q_cols(const uint32_t* __restrict__ A, uint32_t B, uint32
 // Compression operand: row (b*256 + beta) of Bc holds byte beta of cko[b][i] - 128 for
 // i < n (raw 0 for n <= i < Kp). colsum[b][beta] += sum_i byte beta of cko[b][i].
 // CTA: one query, 64 offsets; 256 threads.
+// With `srcs` (device array), query b's n values start at srcs[b * src_stride] instead of
+// cko + b n ZP_MAX_L (the CRT product reads each client's table in place).
 __global__ void k_prep_cko(const uint32_t* __restrict__ cko, uint32_t n, uint32_t Kp,
-                           __half* __restrict__ Bc, uint32_t* __restrict__ colsum) {
+                           __half* __restrict__ Bc, uint32_t* __restrict__ colsum,
+                           const uint32_t* const* __restrict__ srcs = nullptr,
+                           uint32_t src_stride = 0) {
   __shared__ uint32_t tile[64][ZP_MAX_L + 1];
   const uint32_t b = blockIdx.y, i0 = blockIdx.x * 64;
+  const uint32_t* src = srcs ? srcs[(uint64_t)b * src_stride] : cko + (uint64_t)b * n * ZP_MAX_L;
   for (uint32_t idx = threadIdx.x; idx < 64u * ZP_MAX_L; idx += blockDim.x) {
     const uint32_t ii = idx / ZP_MAX_L, w = idx % ZP_MAX_L;
     const uint32_t i = i0 + ii;
-    tile[ii][w] = i < n ? cko[((uint64_t)b * n + i) * ZP_MAX_L + w] : 0u;
+    tile[ii][w] = i < n ? src[(uint64_t)i * ZP_MAX_L + w] : 0u;
   }
   __syncthreads();
   const uint32_t beta = threadIdx.x;  // 0..255
@@ -788,7 +901,7 @@ __global__ void k_prep_cko(const uint32_t* __restrict__ cko, uint32_t n, uint32_
 
 // per device, mode, tile width and A operand type: the kernel attribute is set (atomic flags:
 // two host threads may both set an attribute, which is harmless)
-std::atomic<bool> g_attr[64][4][3][2];
+std::atomic<bool> g_attr[64][5][3][2];
 
 template <int MODE, int BT, bool A16 = false>
 int launch_gemm(zp_ctx* ctx, const CUtensorMap& tmA, const CUtensorMap& tmB, const GemmArgs& ga,
@@ -965,68 +1078,14 @@ int zp_launch_vmul_tc(zp_db* db, const uint32_t* dCKO, uint32_t B, uint32_t* V4,
 // H' mod p_k (A, built by zp_launch_rns_planes) times the byte planes of cko mod p_k (B).
 namespace {
 
-constexpr int RG = 16;  // primes per pass of the residue loop
-
-// B operand: row (k nnt + nt) 4 BT + c BT + bl = byte c of (cko[b][i] mod p_k), b = nt BT + bl,
-// centred fp16, columns i < Kp (zero bytes past n and for b >= B); colsum[row] = byte sum.
-// grid (Kp / 128, nnt BT, ceil(ZP_RNS_K / RG)), one thread per (column, query, RG primes).
-__global__ void __launch_bounds__(128) k_prep_cko_rns(const uint32_t* __restrict__ cko, uint32_t B,
-                                                      uint32_t n, uint32_t Kp, uint32_t BT,
-                                                      uint32_t nnt, const zp_rns_dev* __restrict__ rns,
-                                                      __half* __restrict__ Bc,
-                                                      uint32_t* __restrict__ colsum) {
-  __shared__ uint32_t sw[RG][ZP_MAX_L];
-  __shared__ uint32_t sp[RG];
-  __shared__ uint64_t smu[RG];
-  const uint32_t k0 = blockIdx.z * RG;
-  for (uint32_t x = threadIdx.x; x < RG * ZP_MAX_L; x += blockDim.x) {
-    const uint32_t kk = x / ZP_MAX_L, w = x % ZP_MAX_L;
-    sw[kk][w] = k0 + kk < ZP_RNS_K ? rns->w32[k0 + kk][w] : 0u;
-  }
-  for (uint32_t kk = threadIdx.x; kk < (uint32_t)RG; kk += blockDim.x) {
-    sp[kk] = k0 + kk < ZP_RNS_K ? rns->p[k0 + kk] : 1u;
-    smu[kk] = k0 + kk < ZP_RNS_K ? rns->mu[k0 + kk] : 0ull;
-  }
-  __syncthreads();
-  const uint32_t i = blockIdx.x * 128 + threadIdx.x;  // < Kp (Kp is a multiple of 128)
-  const uint32_t b = blockIdx.y;
-  const uint32_t nt = b / BT, bl = b % BT, N = 4 * BT;
-  const uint32_t lane = threadIdx.x & 31;
-  const bool live = i < n && b < B;
-  const uint32_t* src = cko + ((uint64_t)b * n + i) * ZP_MAX_L;
-  uint64_t acc[RG];
-#pragma unroll
-  for (int kk = 0; kk < RG; ++kk) acc[kk] = 0;
-#pragma unroll
-  for (int x4 = 0; x4 < ZP_MAX_L / 4; ++x4) {
-    const uint4 v = live ? __ldg(reinterpret_cast<const uint4*>(src) + x4) : make_uint4(0, 0, 0, 0);
-    const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int x = 4 * x4 + u;
-#pragma unroll
-      for (int kk = 0; kk < RG; ++kk) acc[kk] += (uint64_t)wv[u] * sw[kk][x];  // < 2^59
-      if ((x & 15) == 15) {
-#pragma unroll
-        for (int kk = 0; kk < RG; ++kk) acc[kk] = mod_p(acc[kk], sp[kk], smu[kk]);
-      }
-    }
-  }
-#pragma unroll
-  for (int kk = 0; kk < RG; ++kk) {
-    const uint32_t k = k0 + kk;
-    if (k >= ZP_RNS_K) break;
-    const uint32_t v = mod_p(acc[kk], sp[kk], smu[kk]);
-    const uint64_t row0 = ((uint64_t)k * nnt + nt) * N + bl;
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      const uint32_t byte = (v >> (8 * c)) & 0xFFu;
-      Bc[(row0 + (uint64_t)c * BT) * Kp + i] = __int2half_rn((int)byte - 128);
-      uint32_t s = byte;
-#pragma unroll
-      for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0 && s) atomicAdd(&colsum[row0 + (uint64_t)c * BT], s);
-    }
+// Columns i in [n, Kp) of the B operand of the RNS product: the centred value of a zero byte
+// (they enter every sum). grid (ceil(rows / 8)), 256 threads.
+__global__ void k_rns_kpad(__half* __restrict__ Bc, uint64_t rows, uint32_t n, uint32_t Kp) {
+  const uint32_t w = Kp - n;
+  const uint64_t idx0 = (uint64_t)blockIdx.x * 8 * w;
+  for (uint32_t t = threadIdx.x; t < 8 * w; t += blockDim.x) {
+    const uint64_t r = (idx0 + t) / w;
+    if (r < rows) Bc[r * Kp + n + (uint32_t)((idx0 + t) % w)] = __int2half_rn(-128);
   }
 }
 
@@ -1040,16 +1099,51 @@ int zp_launch_rns_products(zp_db* db, const uint32_t* dCKO, uint32_t B, uint32_t
   const uint64_t brows = (uint64_t)ZP_RNS_K * nnt * N;
   const size_t bc_bytes = (size_t)brows * Kp * 2;
   const size_t cs_bytes = (size_t)brows * 4;
-  int rc = zp_scratch_reserve(&db->s_cko, bc_bytes + cs_bytes + 256);
+  int rc = zp_scratch_reserve(&db->s_cko, bc_bytes + cs_bytes + (size_t)B * n * 4 + 256);
   if (rc) return rc;
   __half* Bc = static_cast<__half*>(db->s_cko.p);
   uint32_t* colsum = reinterpret_cast<uint32_t*>(static_cast<uint8_t*>(db->s_cko.p) + bc_bytes);
   ZP_CUDA(cudaMemsetAsync(colsum, 0, cs_bytes, st));
-  zp_clear_pending_error();
-  ctx->launches++;
-  k_prep_cko_rns<<<dim3(Kp / 128, nnt * BT, (ZP_RNS_K + RG - 1) / RG), 128, 0, st>>>(
-      dCKO, B, n, Kp, BT, nnt, ctx->d_rns, Bc, colsum);
-  ZP_CUDA(cudaGetLastError());
+  // cko mod p_k for every query, offset and prime on the tensor cores (MODE_RES): A = the
+  // 256 bytes of each cko[b][i] straight from dCKO, B = the context's table of 2^(8 beta) mod
+  // p_k; the epilogue writes the byte planes of the residues into Bc and their sums into colsum
+  rc = zp_ensure_res_table(ctx);
+  if (rc) return rc;
+  uint32_t* ckrs = colsum + brows;  // byte sums of the cko elements
+  rc = zp_launch_rowsum_buf(ctx, reinterpret_cast<const uint8_t*>(dCKO), 256, B * n, 256, ckrs, st);
+  if (rc) return rc;
+  if (Kp > n) {
+    zp_clear_pending_error();
+    ctx->launches++;
+    k_rns_kpad<<<(unsigned)((brows + 7) / 8), 256, 0, st>>>(Bc, brows, n, Kp);
+    ZP_CUDA(cudaGetLastError());
+  }
+  {
+    CUtensorMap tmC;
+    rc = zp_encode_tmap_2d(&tmC, CU_TENSOR_MAP_DATA_TYPE_UINT8, dCKO, 256, (uint64_t)B * n, 256, 128,
+                           128, CU_TENSOR_MAP_SWIZZLE_128B);
+    if (rc) return rc;
+    GemmArgs gr{};
+    gr.num_m_tiles = (B * n + BM - 1) / BM;
+    gr.num_n_tiles = ZP_RES_NT;
+    gr.N = 4 * ZP_RES_KPER;
+    gr.nkb = 256 / BK;
+    gr.Kp = 256;
+    gr.Mvalid = B * n;
+    gr.Bvalid = B;
+    gr.rowsumA = ckrs;
+    gr.colsum = ctx->d_resw_cs;
+    gr.status = ctx->d_status;
+    gr.rns = ctx->d_rns;
+    gr.res_n = n;
+    gr.res_bt = BT;
+    gr.res_nnt = nnt;
+    gr.res_kp = Kp;
+    gr.res_out = Bc;
+    gr.res_colsum = colsum;
+    rc = launch_gemm<MODE_RES, 64>(ctx, tmC, ctx->tmap_resw, gr, st);
+    if (rc) return rc;
+  }
   CUtensorMap tmB;
   rc = zp_encode_tmap_2d(&tmB, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, Bc, Kp, brows, (uint64_t)Kp * 2, 64,
                          N, CU_TENSOR_MAP_SWIZZLE_128B);
@@ -1078,4 +1172,50 @@ int zp_launch_rns_products(zp_db* db, const uint32_t* dCKO, uint32_t B, uint32_t
   if (BT == 16) return launch_gemm<MODE_RNS, 16>(ctx, db->tmap_rns, tmB, ga, st);
   if (BT == 32) return launch_gemm<MODE_RNS, 32>(ctx, db->tmap_rns, tmB, ga, st);
   return launch_gemm<MODE_RNS, 64>(ctx, db->tmap_rns, tmB, ga, st);
+}
+
+// ---------------------------------------------------------------------------------
+// CRT products of the residue-number-system compression (Sec. 5.2: one reduction mod m at
+// the end): V[b][r'] = sum_k y[b][r'][k] (M/p_k mod m_b) + alpha (m_b - (M mod m_b)), the
+// Chinese-remainder sum of the residues of H'[r', :] . cko[b] (y, alpha from k_crt_prep, as
+// byte planes Yp), taken exactly on the tensor cores as a batched MODE_CMP product: for query
+// b, A = the byte planes of its y (4 Rq rows, K = ZP_RNS_K + 1), B = the 256 bytes of each
+// of its client's constants M/p_k mod m_b (read in place through mkm_ptrs[b * ptr_stride]).
+int zp_launch_crt_products(zp_db* db, const uint32_t* const* mkm_ptrs, uint32_t ptr_stride,
+                           uint32_t B, const uint8_t* Yp, uint32_t ypitch, const uint32_t* yrs,
+                           uint32_t* Vc, cudaStream_t st) {
+  zp_ctx* ctx = db->ctx;
+  constexpr uint32_t KC = ZP_RNS_K + 1, Kp = (KC + 63) / 64 * 64;
+  const size_t bm_bytes = (size_t)B * 256 * Kp * 2, cs_bytes = (size_t)B * 256 * 4;
+  int rc = zp_scratch_reserve(&db->s_crtb, bm_bytes + cs_bytes + 256);
+  if (rc) return rc;
+  __half* Bm = static_cast<__half*>(db->s_crtb.p);
+  uint32_t* colsum = reinterpret_cast<uint32_t*>(static_cast<uint8_t*>(db->s_crtb.p) + bm_bytes);
+  ZP_CUDA(cudaMemsetAsync(colsum, 0, cs_bytes, st));
+  zp_clear_pending_error();
+  ctx->launches++;
+  k_prep_cko<<<dim3(Kp / 64, B), 256, 0, st>>>(nullptr, KC, Kp, Bm, colsum, mkm_ptrs, ptr_stride);
+  ZP_CUDA(cudaGetLastError());
+  CUtensorMap tmA, tmB;
+  rc = zp_encode_tmap_2d(&tmA, CU_TENSOR_MAP_DATA_TYPE_UINT8, Yp, KC, (uint64_t)B * 4 * db->Rq, ypitch,
+                         128, 128, CU_TENSOR_MAP_SWIZZLE_128B);
+  if (!rc)
+    rc = zp_encode_tmap_2d(&tmB, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, Bm, Kp, (uint64_t)B * 256,
+                           (uint64_t)Kp * 2, 64, 256, CU_TENSOR_MAP_SWIZZLE_128B);
+  if (rc) return rc;
+  GemmArgs ga{};
+  ga.num_m_tiles = db->Rq / 32;
+  ga.num_n_tiles = B;
+  ga.N = 256;
+  ga.nkb = Kp / BK;
+  ga.Kp = Kp;
+  ga.Mvalid = db->d1p;
+  ga.Bvalid = B;
+  ga.rowsumA = yrs;
+  ga.colsum = colsum;
+  ga.out = Vc;
+  ga.Rp = db->Rq;
+  ga.a_rows_per_n = 4 * db->Rq;
+  ga.status = ctx->d_status;
+  return launch_gemm<MODE_CMP, 64>(ctx, tmA, tmB, ga, st);
 }

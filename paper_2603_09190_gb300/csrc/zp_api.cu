@@ -208,11 +208,14 @@ static bool is_prime_u32(uint32_t x) {  // deterministic Miller-Rabin for 32-bit
 
 // RNS constants of a context: the ZP_RNS_K largest primes below 2^27 and the tables of
 // zp_rns_dev (host copy).
-static void rns_setup(zp_ctx* c, zp_rns_dev& h) {
+static bool rns_setup(zp_ctx* c, zp_rns_dev& h) {
   std::vector<uint32_t>& P = c->rns_p;
   P.clear();
   for (uint32_t x = (1u << 27) - 1; P.size() < ZP_RNS_K; x -= 2)
     if (is_prime_u32(x)) P.push_back(x);
+  // the residue folds of the tensor-core products rely on p = 2^27 - dl with dl < 2^12
+  // (the smallest of these primes is 2^27 - 2797)
+  if ((1u << 27) - P.back() >= (1u << 12)) return false;
   memset(&h, 0, sizeof(h));
   for (int k = 0; k < ZP_RNS_K; ++k) {
     const uint64_t p = P[k];
@@ -235,8 +238,10 @@ static void rns_setup(zp_ctx* c, zp_rns_dev& h) {
       h.gj[k][j] = (uint32_t)gj;
       gj = gj * g % p;
     }
-    for (int a = 0; a < 4; ++a) h.pow8[k][a] = (uint32_t)((1ull << (8 * a)) % p);
+    uint64_t p8 = 1 % p;
+    for (int a = 0; a < 8; ++a, p8 = (p8 << 8) % p) h.pow8[k][a] = (uint32_t)p8;
   }
+  return true;
 }
 
 // ------------------------------------------------------------------ context
@@ -332,9 +337,13 @@ extern "C" int zp_init(int device, const zp_params* P, zp_ctx** out) {
     c->rns_min_batch = 8;
     c->gemv_max_batch = 4;  // one dp4a pass beats the tensor cores up to 4 queries (1 GiB)
     c->answer_fp16 = 1;
+    c->batch_overlap = 1;
     {
       zp_rns_dev h;
-      rns_setup(c, h);
+      if (!rns_setup(c, h)) {
+        delete c;
+        return zp_set_error(ZP_EUNSUPPORTED, "zp_init: RNS primes too far below 2^27");
+      }
       if (cudaMalloc(&c->d_rns, sizeof(zp_rns_dev)) != cudaSuccess) {
         c->d_rns = nullptr;
         delete c;
@@ -369,6 +378,8 @@ extern "C" int zp_ctx_destroy(zp_ctx* c) {
   zp_device_scope _zp_scope(c->device);
   if (c->d_status) cudaFree(c->d_status);
   if (c->d_rns) cudaFree(c->d_rns);
+  if (c->d_resw) cudaFree(c->d_resw);
+  if (c->d_resw_cs) cudaFree(c->d_resw_cs);
   delete c;
   return ZP_OK;
 }
@@ -401,6 +412,12 @@ extern "C" int zp_set_option(zp_ctx* c, const char* name, int64_t value) {
     c->answer_fp16 = (uint32_t)value;
     return ZP_OK;
   }
+  if (k == "batch_overlap") {
+    if (value < 0 || value > 1)
+      return zp_set_error(ZP_EINVAL, "zp_set_option: batch_overlap=%lld out of [0, 1]", (long long)value);
+    c->batch_overlap = (uint32_t)value;
+    return ZP_OK;
+  }
   if (k == "rns_min_batch") {
     if (value < 0 || value > 4096)
       return zp_set_error(ZP_EINVAL, "zp_set_option: rns_min_batch=%lld out of [0, 4096]", (long long)value);
@@ -419,6 +436,7 @@ extern "C" int zp_get_option(const zp_ctx* c, const char* name, int64_t* value) 
   else if (k == "rns_min_batch") *value = c->rns_min_batch;
   else if (k == "gemv_max_batch") *value = c->gemv_max_batch;
   else if (k == "answer_fp16") *value = c->answer_fp16;
+  else if (k == "batch_overlap") *value = c->batch_overlap;
   else return zp_set_error(ZP_EINVAL, "zp_get_option: unknown option '%s'", name);
   return ZP_OK;
 }
@@ -538,7 +556,8 @@ extern "C" int zp_db_destroy(zp_db* db) {
   }
   zp_scratch* all[] = {&db->s_qplanes, &db->s_v,   &db->s_q,   &db->s_cko,  &db->s_ans,
                        &db->s_t,       &db->s_clients, &db->s_misc, &db->s_tcq, &db->s_hq,
-                       &db->s_hcko, &db->s_ptab, &db->s_krows, &db->s_m2consts, &db->s_prows};
+                       &db->s_hcko, &db->s_ptab, &db->s_krows, &db->s_m2consts, &db->s_prows,
+                       &db->s_crt, &db->s_crtb};
   for (zp_scratch* s : all) scratch_free(s);
   delete db;
   return ZP_OK;
@@ -580,6 +599,56 @@ int zp_ensure_rns(zp_db* db, cudaStream_t st) {
   if (rc) return rc;
   rc = zp_launch_rns_planes(db, nullptr, db->d1p, st);
   return rc ? rc : zp_ensure_rns16(db, st);
+}
+
+int zp_ensure_res_table(zp_ctx* c) {
+  if (c->d_resw) return ZP_OK;
+  std::vector<uint16_t> w((size_t)ZP_RES_ROWS * 256);
+  std::vector<uint32_t> cs(ZP_RES_ROWS, 0);
+  for (int k = 0; k < ZP_RES_KPER * ZP_RES_NT; ++k) {
+    uint64_t pw = 1;  // 2^(8 beta) mod p_k
+    const uint64_t p = k < ZP_RNS_K ? c->rns_p[k] : 0;
+    for (int beta = 0; beta < 256; ++beta) {
+      for (int cc = 0; cc < 4; ++cc) {
+        const uint32_t byte = p ? (uint32_t)(pw >> (8 * cc)) & 0xFFu : 0u;
+        // centred byte - 128 as an fp16 bit pattern (exact: |v| <= 128)
+        const int v = (int)byte - 128;
+        const uint32_t mag = (uint32_t)(v < 0 ? -v : v);
+        uint16_t h = 0;
+        if (mag) {
+          int ex = 31 - __builtin_clz(mag);
+          h = (uint16_t)(((ex + 15) << 10) | ((mag << (10 - ex)) & 0x3FFu));
+        }
+        if (v < 0) h |= 0x8000u;
+        w[(size_t)(4 * k + cc) * 256 + beta] = h;
+        cs[4 * k + cc] += byte;
+      }
+      if (p) pw = (pw << 8) % p;
+    }
+  }
+  void* dw = nullptr;
+  uint32_t* dcs = nullptr;
+  if (cudaMalloc(&dw, w.size() * 2) != cudaSuccess || cudaMalloc(&dcs, cs.size() * 4) != cudaSuccess) {
+    if (dw) cudaFree(dw);
+    zp_clear_pending_error();
+    return zp_set_error(ZP_ENOMEM, "cudaMalloc(residue table)");
+  }
+  if (cudaMemcpy(dw, w.data(), w.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(dcs, cs.data(), cs.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaFree(dw);
+    cudaFree(dcs);
+    return zp_set_error(ZP_ECUDA, "copy of the residue table");
+  }
+  int rc = zp_encode_tmap_2d(&c->tmap_resw, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, dw, 256, ZP_RES_ROWS,
+                             256 * 2, 64, 4 * ZP_RES_KPER, CU_TENSOR_MAP_SWIZZLE_128B);
+  if (rc) {
+    cudaFree(dw);
+    cudaFree(dcs);
+    return rc;
+  }
+  c->d_resw = dw;
+  c->d_resw_cs = dcs;
+  return ZP_OK;
 }
 
 int zp_ensure_rns16(zp_db* db, cudaStream_t st) {
@@ -997,6 +1066,23 @@ extern "C" int zp_respond(zp_db* db, zp_client* const* clients, const uint32_t* 
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const bool overlap = B == 1 && c->overlap_sms > 0 && c->answer_path == ZP_PATH_AUTO &&
                          c->compress_path != ZP_PATH_SIMT && c->P.n <= 1024;
+    // a batch answered on the tensor cores: its compression products (which do not read the
+    // answers) run on the internal stream beside it and take the SMs its last wave leaves idle
+    const bool overlap_batch = B > 1 && c->batch_overlap && B > c->gemv_max_batch &&
+                               c->answer_path != ZP_PATH_SIMT;
+    if (overlap_batch) {
+      rc = ensure_side_stream(db);
+      if (rc) return rc;
+      ZP_CUDA(cudaEventRecord(db->ev_fork, st));
+      ZP_CUDA(cudaStreamWaitEvent(db->side, db->ev_fork, 0));
+      rc = zp_launch_compress_products(db, dCKO, B, db->side, 0);
+      if (rc) return rc;
+      rc = zp_answer(db, dQ, B, dAns, stream);
+      if (rc) return rc;
+      ZP_CUDA(cudaEventRecord(db->ev_join, db->side));
+      ZP_CUDA(cudaStreamWaitEvent(st, db->ev_join, 0));
+      return zp_launch_compress_finish(db, clients, dAns, B, dT, st);
+    }
     if (!overlap) {
       rc = zp_answer(db, dQ, B, dAns, stream);
       if (rc) return rc;
@@ -1272,12 +1358,14 @@ extern "C" int zp_respond_host(zp_db* db, zp_client* const* clients, const uint3
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const size_t qb = (size_t)B * db->C * 4, cb = (size_t)B * c->P.n * c->L * 4;
   const size_t ab = (size_t)B * db->R * 4, tb = (size_t)B * db->d1p * c->L * 4;
-  if ((rc = zp_scratch_reserve(&db->s_q, qb)) || (rc = zp_scratch_reserve(&db->s_cko, cb)) ||
+  // the inputs go to buffers of their own: the kernels' operand scratch (s_cko, s_q, ...)
+  // is rewritten by zp_respond while it reads its inputs
+  if ((rc = zp_scratch_reserve(&db->s_hq, qb)) || (rc = zp_scratch_reserve(&db->s_hcko, cb)) ||
       (rc = zp_scratch_reserve(&db->s_ans, ab)) || (rc = zp_scratch_reserve(&db->s_t, tb)))
     return rc;
-  ZP_CUDA(cudaMemcpyAsync(db->s_q.p, hQ, qb, cudaMemcpyHostToDevice, st));
-  ZP_CUDA(cudaMemcpyAsync(db->s_cko.p, hCKO, cb, cudaMemcpyHostToDevice, st));
-  rc = zp_respond(db, clients, static_cast<uint32_t*>(db->s_q.p), static_cast<uint32_t*>(db->s_cko.p),
+  ZP_CUDA(cudaMemcpyAsync(db->s_hq.p, hQ, qb, cudaMemcpyHostToDevice, st));
+  ZP_CUDA(cudaMemcpyAsync(db->s_hcko.p, hCKO, cb, cudaMemcpyHostToDevice, st));
+  rc = zp_respond(db, clients, static_cast<uint32_t*>(db->s_hq.p), static_cast<uint32_t*>(db->s_hcko.p),
                   B, static_cast<uint32_t*>(db->s_ans.p), static_cast<uint32_t*>(db->s_t.p), stream);
   if (rc) return rc;
   ZP_CUDA(cudaMemcpyAsync(hT, db->s_t.p, tb, cudaMemcpyDeviceToHost, st));

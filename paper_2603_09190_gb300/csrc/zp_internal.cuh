@@ -38,8 +38,14 @@ struct zp_rns_dev {             // device copy, one per context
   double dinv[ZP_RNS_K];        // 1 / p
   uint32_t w32[ZP_RNS_K][ZP_MAX_L];  // 2^(32 w) mod p
   uint32_t gj[ZP_RNS_K][64];    // gamma^j mod p, j < ell
-  uint32_t pow8[ZP_RNS_K][4];   // 2^(8 a) mod p
+  uint32_t pow8[ZP_RNS_K][8];   // 2^(8 a) mod p, a < 8
 };
+
+// Residues of the compression offsets on the tensor cores: the table of the bytes of
+// 2^(8 beta) mod p_k (beta < 256), ZP_RES_KPER primes per N tile of the product.
+#define ZP_RES_KPER 40
+#define ZP_RES_NT ((ZP_RNS_K + ZP_RES_KPER - 1) / ZP_RES_KPER)
+#define ZP_RES_ROWS (4 * ZP_RES_KPER * ZP_RES_NT)
 
 struct zp_ctx {
   int device;
@@ -54,7 +60,13 @@ struct zp_ctx {
   uint32_t rns_min_batch;  // batches of at least this many queries compress in RNS (0: never)
   uint32_t gemv_max_batch; // batches of at most this many queries (<= 4) answer by the GEMV
   uint32_t answer_fp16;    // tensor-core answers read a database's fp16 copy when it has one
+  uint32_t batch_overlap;  // zp_respond runs a batch's compression products beside its answers
   zp_rns_dev* d_rns;   // RNS constants (device)
+  // ZP_RES_ROWS x 256 centred fp16: row 4 k + c, column beta = byte c of 2^(8 beta) mod p_k
+  // (zero bytes for k >= ZP_RNS_K), its row byte sums, and its tensor map (built on first use)
+  void* d_resw;
+  uint32_t* d_resw_cs;
+  CUtensorMap tmap_resw;
   std::vector<uint32_t> rns_p;  // the primes (host)
   int num_sms;
   uint32_t* d_status;  // device status word (ZP_DEV_* flags)
@@ -126,6 +138,7 @@ struct zp_db {
   zp_scratch s_qplanes, s_v, s_q, s_cko, s_ans, s_t, s_clients, s_misc, s_tcq, s_hq, s_hcko;
   zp_scratch s_ptab, s_krows, s_m2consts;  // per-client hint and combined response
   zp_scratch s_prows;                      // packed rows whose RNS planes are rebuilt
+  zp_scratch s_crt, s_crtb;                // CRT of the residue-number-system compression
 };
 
 // error reporting (thread-local message)
@@ -201,12 +214,20 @@ int zp_launch_decrypt(const zp_client* cl, const uint32_t* e, uint32_t ew, const
 int zp_launch_rns_planes(zp_db* db, const uint32_t* dRows, uint32_t nprows, cudaStream_t st);
 // allocates and builds the RNS planes of H' on first use (zp_api.cu)
 int zp_ensure_rns(zp_db* db, cudaStream_t st);
+// builds the context's table of 2^(8 beta) mod p_k on first use (zp_api.cu)
+int zp_ensure_res_table(zp_ctx* c);
 // the fp16 copy of the RNS plane rows of the listed packed rows (dRows device; NULL = packed
 // rows 0 .. nprows - 1, the padding rows up to Rq included) (k_rns.cu)
 int zp_launch_rns16_rows(zp_db* db, const uint32_t* dRows, uint32_t nprows, cudaStream_t st);
 // builds the fp16 copy of the RNS planes when the database has both (zp_api.cu)
 int zp_ensure_rns16(zp_db* db, cudaStream_t st);
 int zp_launch_rns_products(zp_db* db, const uint32_t* dCKO, uint32_t B, uint32_t* X, cudaStream_t st);
+// the exact CRT sums V[b][r'] (67 words, Rq rows per query) from the byte planes Yp of y and
+// alpha (B x 4 Rq rows of ypitch bytes, row sums yrs) and the clients' constants M/p_k mod m
+// read through mkm_ptrs[b * ptr_stride] (k_gemm_tc.cu)
+int zp_launch_crt_products(zp_db* db, const uint32_t* const* mkm_ptrs, uint32_t ptr_stride,
+                           uint32_t B, const uint8_t* Yp, uint32_t ypitch, const uint32_t* yrs,
+                           uint32_t* Vc, cudaStream_t st);
 // B in 1..4 queries (dq: B x C, dans: B x R); max_ctas limits the single-query grid.
 int zp_launch_gemv(zp_db* db, const uint32_t* dq, uint32_t B, uint32_t* dans, cudaStream_t st,
                    uint32_t max_ctas);
@@ -398,6 +419,17 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
   asm volatile(
       "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
           smem_u32(bar))
+      : "memory");
+}
+// 16 consecutive 32-bit columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
       : "memory");
 }
 // 32 consecutive 32-bit columns of this thread's TMEM lane.

@@ -438,6 +438,37 @@ def test_respond_host_matches_device(zp):
     c.close()
 
 
+@pytest.mark.parametrize("B", [1, 9])
+def test_respond_host_after_device_calls(zp, B):
+    """zp_respond_host after device-buffer calls have sized the products' scratch (n = 1024,
+    the single-query overlap path and the RNS path of nine queries): its inputs must not share
+    a buffer with the kernels' operands, and t equals the oracle's."""
+    R, C, n = 2100, 512, 1024
+    P = Params(n=n, key_bits=2048)
+    c = zp.Context(0, n=n)
+    D = synth.database(R, C, 21)
+    A = synth.seed_matrix(C, n, 22)
+    Hn = lwe.hint_neg(D, A)
+    dD, ld = to_dev_db(zp, D)
+    db = zp.Database(c, dD, R, C, ld)
+    db.gen_hint(u32_dev(A))
+    ms = [synth.random_odd_modulus(2048, 23 + b) for b in range(B)]
+    cls = [c.register_client(m) for m in ms]
+    q = synth.uniform_queries(B, C, 24)
+    ckos = [synth.uniform_below(ms[b], n, 25 + b) for b in range(B)]
+    cko = np.stack([synth.ints_to_limbs(x, 64) for x in ckos])
+    for _ in range(2):
+        ans_d, T_d = db.respond(cls, u32_dev(q), u32_dev(cko))
+    hans = np.empty((B, R), dtype=np.uint32)
+    for _ in range(2):
+        T_h = db.respond_host(cls, q, cko, hAns=hans)
+        assert np.array_equal(T_h, u32_host(T_d)) and np.array_equal(hans, u32_host(ans_d))
+    for b in (0, B - 1):
+        assert synth.limbs_to_ints(T_h[b]) == zippir.compress_rows(hans[b], Hn, ckos[b], ms[b], P)
+    db.close()
+    c.close()
+
+
 def test_invalid_arguments_fail_loudly(zp, ctx):
     D = synth.database(10, 16, 1)
     dD, ld = to_dev_db(zp, D)

@@ -179,3 +179,33 @@ def test_prepare_rns(zp):
     T = u32_host(db.compress([cl] * B, u32_dev(ans), u32_dev(np.stack([synth.ints_to_limbs(x, 64) for x in ckos]))))
     for b in (0, B - 1):
         assert synth.limbs_to_ints(T[b]) == zippir.compress_rows(ans[b], Hn, ckos[b], m, P)
+
+
+def test_batched_respond_overlap_on_and_off(zp):
+    """zp_respond of a batch on the tensor cores with its compression products beside the
+    answers on the internal stream ("batch_overlap" 1) and one after the other (0): the same
+    bits, and t and the answers equal the oracle's (d1' = 78, n = 1024, ragged n % 128 = 0)."""
+    R, C, n, B = 2100, 256, 1024, 12
+    P = Params(n=n, key_bits=2048)
+    c = zp.Context(0, n=n)
+    D = synth.database(R, C, 321)
+    A = synth.seed_matrix(C, n, 322)
+    Hn = lwe.hint_neg(D, A)
+    db, dD = _db(zp, c, D)
+    db.gen_hint(u32_dev(A))
+    ms = [synth.random_odd_modulus(2048, 330 + b) for b in range(B)]
+    cls = [c.register_client(m) for m in ms]
+    ckos = [synth.uniform_below(ms[b], n, 340 + b) for b in range(B)]
+    Q = synth.uniform_queries(B, C, 350)
+    CKO = u32_dev(np.stack([synth.ints_to_limbs(x, 64) for x in ckos]))
+    outs = []
+    for ov in (1, 0):
+        c.set_option("batch_overlap", ov)
+        ans, T = db.respond(cls, u32_dev(Q), CKO)
+        outs.append((u32_host(ans), u32_host(T)))
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+    ans_h, T_h = outs[0]
+    assert np.array_equal(ans_h, lwe.matmat_mod_q(D, Q.T).T)
+    for b in (0, 5, B - 1):
+        assert synth.limbs_to_ints(T_h[b]) == zippir.compress_rows(ans_h[b], Hn, ckos[b], ms[b], P)
+    assert c.device_status() == 0
