@@ -735,7 +735,7 @@ def run_serve(args, world, rank, local):
     dev = torch.device("cuda", local)
     n = 1024
     ctx = zp.Context(local, n=n, key_bits=KEY_BITS)
-    be = ZipBackend(ctx, max_batch=args.serve_batch)
+    be = ZipBackend(ctx, max_batch=args.serve_batch, slots=args.serve_slots)
     shapes = {"db256m": (16384, 16384), "db1g": (32768, 32768), "db4g": (65536, 65536)}
     if args.serve_small:
         shapes = {"db256m": (4096, 4096), "db1g": (8192, 8192), "db4g": (16384, 16384)}
@@ -759,7 +759,7 @@ def run_serve(args, world, rank, local):
     budget = int(free * 0.9) + sum(be.db_bytes(nm) for nm in shapes)
     results = []
     for rate in args.serve_rates:
-        srv = Server(be, hbm_budget=budget, max_batch=args.serve_batch)
+        srv = Server(be, hbm_budget=budget, max_batch=args.serve_batch, slots=args.serve_slots)
         for name, (R, C) in shapes.items():
             srv.add_database(name, R, C)
         stop = threading.Event()
@@ -813,7 +813,7 @@ def run_serve(args, world, rank, local):
                                        "updated with idle-time hint regeneration, %d s per rate"
                                        % (",".join("%s %dx%d" % (k, *v) for k, v in shapes.items()),
                                           nclients, args.serve_seconds),
-                           "max_batch": args.serve_batch},
+                           "max_batch": args.serve_batch, "slots_per_db": args.serve_slots},
                 "rates": results, "device_status": status}
         print(json.dumps(line))
     return 0
@@ -1035,8 +1035,10 @@ def main():
                     help="keep the library's default thresholds and SM split")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the 64-query measurement of the default workload")
-    ap.add_argument("--serve-rates", type=float, nargs="*", default=[50, 200, 1000, 2000])
-    ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--serve-rates", type=float, nargs="*", default=[50, 100, 200, 500, 1000, 2000])
+    ap.add_argument("--serve-seconds", type=float, default=60.0)
+    ap.add_argument("--serve-slots", type=int, default=2,
+                    help="batches of one database in flight at once (database views)")
     ap.add_argument("--serve-clients", type=int, default=1000)
     ap.add_argument("--serve-batch", type=int, default=64)
     ap.add_argument("--serve-small", action="store_true", help="smaller databases (smoke)")

@@ -103,6 +103,20 @@ int zp_ctx_destroy(zp_ctx* ctx);
 int zp_setup_db(zp_ctx* ctx, const uint8_t* dD, uint32_t R, uint32_t C, uint64_t ld_bytes,
                 zp_db** out);
 
+/* A second handle on the database db (the paper has no counterpart): the view shares
+ * everything db holds (D, its fp16 copy, the hint and its byte planes, the RNS tables) and
+ * owns only its own working buffers, internal stream and events, so that several batches of
+ * one database can be in flight at once, each on its own handle and stream (a serving loop
+ * that overlaps same-database batches). The view reads db's current state at every call.
+ * Calls that change that state (zp_gen_hint, zp_update_rows, zp_db_prepare_fp16,
+ * zp_db_prepare_rns, zp_autotune) are refused on a view (ZP_EINVAL) and must be made on db,
+ * ordered on the GPU after the views' work that reads the old state; a view compresses large
+ * batches in RNS only after zp_db_prepare_rns(db) (ZP_ESTATE otherwise). Calls on db and its
+ * views from different host threads need the caller's own lock. Given a view, the new view
+ * shares the same database. Destroy views (zp_db_destroy) before db; destroying a view frees
+ * only what it owns. Errors: ZP_EINVAL, ZP_ENOMEM. */
+int zp_db_view(zp_db* db, zp_db** out);
+
 /* Reports the packing of this database: slots per Paillier plaintext (ell), packed
  * rows d1' = ceil(R / ell), and 32-bit limbs per element of Z_m (L = key_bits/32). */
 int zp_db_info(const zp_db* db, uint32_t* ell, uint32_t* d1p, uint32_t* L);
@@ -229,14 +243,22 @@ int zp_client_hint(zp_db* db, const zp_client* cl, const uint32_t* dCkr, uint32_
                    const uint32_t* hPackedRows, uint32_t nrows, void* stream);
 
 /* Autotuner: measures on `db` (zero-filled test buffers it allocates and frees; the
- * kernels' time does not depend on the values) the one-pass GEMV against the tensor-core
- * GEMM for 2..4 queries, the byte-plane against the RNS compression for 2..16 queries
- * (when the hint is ready, n <= 1024 and "compress_path" is auto; this builds the RNS
- * tables), and the SM split of the single-query zp_respond (0 and 24%..52% of the SMs),
- * and sets the context options "gemv_max_batch", "rns_min_batch" and "overlap_sms" to the
- * fastest choices. chosen (may be NULL): receives those three values. Synchronous on
- * `stream`; tens of milliseconds at 1 GiB. Errors: ZP_EINVAL, ZP_ENOMEM, ZP_ECUDA (the
- * options are left as they were). */
+ * kernels' time does not depend on the values) and sets the context options to the fastest
+ * choices:
+ *  - "gemv_max_batch": the one-pass GEMV against the tensor-core GEMM for 2..4 queries;
+ *  - "rns_min_batch": the byte-plane against the RNS compression for 2..16 queries (when the
+ *    hint is ready, n <= 1024 and "compress_path" is auto; this builds the RNS tables);
+ *  - "gemv_cfg_alone": the GEMV configuration of a single-query answer on the whole GPU;
+ *  - "overlap_sms" and "gemv_cfg_shared": the SM split of the single-query zp_respond (0 and
+ *    24%..52% of the SMs) and the GEMV configuration beside the compression products;
+ *  - "answer_bt_small/mid/large": the tile width (16, 32 or 64 queries) of the tensor-core
+ *    answers for batches of 16, 32 and 64 queries, and "answer_fp16" (the fp16 copy of D
+ *    against its bytes, when the copy exists);
+ *  - "rns_bt_small/mid/large" and "batch_overlap": the tile width of the RNS products and
+ *    whether a batch's products run beside its answers (when the RNS path was measured).
+ * chosen (may be NULL): receives the first three values ("gemv_max_batch", "rns_min_batch",
+ * "overlap_sms"); zp_get_option reads the others. Synchronous on `stream`; about a second
+ * at 1 GiB. Errors: ZP_EINVAL, ZP_ENOMEM, ZP_ECUDA (the options are left as they were). */
 int zp_autotune(zp_db* db, void* stream, int64_t* chosen);
 
 /* Builds now the residues of H' modulo the RNS primes that the compression of large
@@ -280,6 +302,14 @@ int zp_stale_rows(const zp_db* db, uint32_t* count);
  *                    query run while the answer uses the other SMs (zp_respond,
  *                    zp_compress_products, single-query zp_answer); 0 = no overlap.
  *                    Default: about 3/8 of the SMs (56 of 152) on GPUs with >= 64 SMs.
+ *   "answer_bt_small", "answer_bt_mid", "answer_bt_large": queries per N tile (16, 32, 64;
+ *                    at most 16 / 32 / 64) of the tensor-core answers for batches of <= 16,
+ *                    <= 32 and more queries (defaults 16, 32, 64); "rns_bt_small", ...: the
+ *                    same for the RNS products;
+ *   "gemv_cfg_alone", "gemv_cfg_shared": the GEMV configuration on the whole GPU and beside
+ *                    the compression products: 1 = 8 consumer warps x 12 stages of 64-row
+ *                    tiles (default alone), 2 = 16 warps x 6 stages of 128-row tiles
+ *                    (default shared);
  *   "batch_overlap": 1 (default) zp_respond runs the compression products of a batch
  *                    answered on the tensor cores on an internal stream beside the answers
  *                    (they do not read the answers), 0 one after the other.

@@ -34,7 +34,7 @@ EXPORTS = [
     "zp_db_prepare_rns", "zp_selftest_wait", "zp_autotune", "zp_prg_chacha20", "zp_client_powm",
     "zp_client_expand_ckr", "zp_client_decrypt", "zp_db_prepare_fp16",
     "zp_lc_create", "zp_lc_destroy", "zp_lc_set_key", "zp_lc_unpack_key", "zp_lc_compress",
-    "zp_lc_rlwe_extract", "zp_lc_rescale",
+    "zp_lc_rlwe_extract", "zp_lc_rescale", "zp_db_view",
 ]
 
 
@@ -70,6 +70,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "zp_setup_db": (i32, [vp, vp, u32, u32, u64, pp]),
         "zp_db_info": (i32, [vp, ctypes.POINTER(u32), ctypes.POINTER(u32), ctypes.POINTER(u32)]),
         "zp_db_destroy": (i32, [vp]),
+        "zp_db_view": (i32, [vp, pp]),
         "zp_gen_hint": (i32, [vp, vp, vp, vp, u32, vp]),
         "zp_answer": (i32, [vp, vp, u32, vp, vp]),
         "zp_register_client": (i32, [vp, vp, u32, pp]),
@@ -190,6 +191,12 @@ def zp_db_info(db: int) -> tuple[int, int, int]:
 
 def zp_db_destroy(db: int):
     _check(load_library().zp_db_destroy(db))
+
+
+def zp_db_view(db: int) -> int:
+    out = ctypes.c_void_p()
+    _check(load_library().zp_db_view(db, ctypes.byref(out)))
+    return out.value
 
 
 def zp_gen_hint(db: int, dA: int, dH: int | None, hRows: np.ndarray | None, stream: int | None):
@@ -444,12 +451,21 @@ class Database:
     Database and must be changed only through ``update_rows``.
     """
 
-    def __init__(self, ctx: Context, D, R: int, C: int, ld: int | None = None):
+    def __init__(self, ctx: Context, D, R: int, C: int, ld: int | None = None, _view_of=None):
         ld = db_pitch(C) if ld is None else ld
         _need(D, "u8", R * ld, "D")
         self.ctx, self.D, self.R, self.C, self.ld = ctx, D, R, C, ld
-        self.handle = zp_setup_db(ctx.handle, _ptr(D), R, C, ld)
+        self.base = _view_of
+        self.handle = zp_db_view(_view_of.handle) if _view_of is not None else \
+            zp_setup_db(ctx.handle, _ptr(D), R, C, ld)
         self.ell, self.d1p, self.L = zp_db_info(self.handle)
+
+    def view(self) -> "Database":
+        """A second handle on this database with working buffers of its own (zp_db_view), so
+        that batches of one database can be in flight at once on different streams. Close
+        views before the database."""
+        base = self.base if self.base is not None else self
+        return Database(self.ctx, base.D, base.R, base.C, base.ld, _view_of=base)
 
     def gen_hint(self, A, H=None, rows=None, stream=None):
         import torch
@@ -523,11 +539,16 @@ class Database:
         zp_combine(self.handle, clients, _ptr(K), _ptr(T), B, _ptr(out), _stream(stream))
         return out
 
+    TUNED = ("gemv_max_batch", "rns_min_batch", "overlap_sms", "gemv_cfg_alone", "gemv_cfg_shared",
+             "answer_bt_small", "answer_bt_mid", "answer_bt_large", "answer_fp16",
+             "rns_bt_small", "rns_bt_mid", "rns_bt_large", "batch_overlap")
+
     def autotune(self, stream=None) -> dict:
-        """Measures and sets the context's batch thresholds and SM split (zp_autotune)."""
+        """Measures and sets the context's thresholds, tile widths, GEMV configurations and SM
+        split (zp_autotune); returns every tuned option."""
         out = (ctypes.c_int64 * 3)()
         _check(load_library().zp_autotune(self.handle, _stream(stream), out))
-        return {"gemv_max_batch": out[0], "rns_min_batch": out[1], "overlap_sms": out[2]}
+        return {k: zp_get_option_value(self.ctx, k) for k in self.TUNED}
 
     def prepare_fp16(self, stream=None):
         """Builds the resident fp16 copy of D (twice its bytes) that batched answers read."""

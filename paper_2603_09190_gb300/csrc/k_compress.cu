@@ -140,13 +140,6 @@ struct ClientPtrs {
   const uint32_t* mkm;  // RNS: M_k mod m (ZP_RNS_K x L), then m - (M mod m)
 };
 
-// x mod p for x < 2^64 (Barrett with mu = floor((2^64 - 1) / p); one correction).
-__device__ __forceinline__ uint32_t mod_p(uint64_t x, uint32_t p, uint64_t mu) {
-  const uint64_t q = __umul64hi(x, mu);
-  const uint64_t r = x - q * p;
-  return (uint32_t)(r >= p ? r - p : r);
-}
-
 // grid (ceil(d1p / PACK_WARPS), B), block PACK_WARPS warps, dynamic shared memory
 // PACK_WARPS x (PackBarrett + ell x VW words). Requires L == ZP_MAX_L.
 // PACKED = false: V is [b][Rp][VW] words, the exact products V[row] = H[row,:] . cko[b]
@@ -197,7 +190,8 @@ __global__ void __launch_bounds__(PACK_WARPS * 32)
     S.mu[x] = cl[b].mu[x];
   }
   const uint32_t* ansb = ans + (uint64_t)b * R + row0;
-  for (uint32_t j = lane; j < nrows; j += 32) S.ans[j] = __ldg(ansb + j);
+  if (!PACKED)
+    for (uint32_t j = lane; j < nrows; j += 32) S.ans[j] = __ldg(ansb + j);
   __syncwarp();
 
   // ---- Horner: X <- X gamma + W_j (j = ell-1 .. 0), gamma = g1 2^32 + g2 2^64,
@@ -205,7 +199,7 @@ __global__ void __launch_bounds__(PACK_WARPS * 32)
   // (words 4 lane .. 4 lane + 3), each below 2^33, so one step needs a local carry
   // pass and one shuffle instead of a full carry resolution.
   uint64_t xv[4] = {0, 0, 0, 0};
-  for (int j = (int)nrows - 1; j >= 0; --j) {
+  for (int j = PACKED ? -1 : (int)nrows - 1; j >= 0; --j) {
     const uint64_t pm1 = __shfl_up_sync(0xffffffffu, xv[3], 1);  // word 4 lane - 1
     const uint64_t pm2 = __shfl_up_sync(0xffffffffu, xv[2], 1);  // word 4 lane - 2
     const uint64_t xm1 = lane ? pm1 : 0, xm2 = lane ? pm2 : 0;
@@ -233,7 +227,7 @@ __global__ void __launch_bounds__(PACK_WARPS * 32)
     const uint64_t cin = __shfl_up_sync(0xffffffffu, c, 1);
     if (lane) xv[0] += cin;
   }
-  if (PACKED) {  // + the packed row's V (67 words, < 2^2090)
+  if (PACKED) {  // X = V of the packed row (67 words), congruent to b-prime + H'.cko mod m
     const uint32_t* Vp = V + ((uint64_t)b * Rp + rp) * VW;
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
@@ -311,35 +305,65 @@ __global__ void __launch_bounds__(PACK_WARPS * 32)
 
 // Residue-number-system path, step 1 of the reduction (Sec. 5.2): from the residues
 // X[b][r'][k] = H'[r', :] . cko[b] mod p_k, y_k = X_k (M/p_k)^{-1} mod p_k and alpha =
-// floor(sum_k y_k / p_k) (exact: H'.cko < M 2^-26, so the double-precision sum plus 2^-30
-// floors to alpha), so that H'.cko = sum_k y_k M/p_k - alpha M. Written as the byte planes of
-// the CRT product's A operand: row b 4 Rq + 128 g + 32 a + t (r' = 32 g + t) holds byte a of
-// y_k in column k < ZP_RNS_K and of alpha in column ZP_RNS_K; packed rows r' in [d1', Rq)
-// are zero. yrs: the byte sums of those rows. One warp per (query, packed row < Rq).
+// floor(sum_k y_k / p_k), so that H'.cko = sum_k y_k M/p_k - alpha M. The sum is taken in
+// 64.64 fixed point with integer arithmetic only: S = sum_k y_k floor(2^64 / p_k) (128-bit
+// accumulators) is below 2^64 sum_k y_k / p_k by less than 153 2^27 < 2^34.3 units, and
+// H'.cko < M 2^-26 puts the fractional part of sum_k y_k / p_k in [0, 2^-26), so
+// floor((S + 2^35) / 2^64) = alpha exactly. y_k = X_k inv_k mod p_k by two pseudo-Mersenne
+// folds (p = 2^27 - dl, dl < 2^12). Written as the byte planes of the CRT product's A
+// operand: row b 4 Rq + 128 g + 32 a + t (r' = 32 g + t) holds byte a of y_k in column k <
+// ZP_RNS_K and of alpha in column ZP_RNS_K; packed rows r' in [d1', Rq) are zero. yrs: the
+// byte sums of those rows. Columns ZP_RNS_K + 1 + j (j < ell) hold the answers ans[b][r' ell
+// + j] (zero past R), which the CRT product weighs by gamma^j: the packed answer b'. One warp
+// per (query, packed row < Rq).
 __global__ void k_crt_prep(const uint32_t* __restrict__ X, uint32_t B, uint32_t d1p, uint32_t Rq,
                            const zp_rns_dev* __restrict__ rns, uint8_t* __restrict__ Yp,
-                           uint32_t ypitch, uint32_t* __restrict__ yrs) {
+                           uint32_t ypitch, uint32_t* __restrict__ yrs,
+                           const uint32_t* __restrict__ ans, uint32_t R, uint32_t ell) {
   const uint64_t wid = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint32_t lane = threadIdx.x & 31;
   if (wid >= (uint64_t)B * Rq) return;
   const uint32_t b = (uint32_t)(wid / Rq), rp = (uint32_t)(wid % Rq);
-  constexpr int QK = (ZP_RNS_K + 1 + 31) / 32;
+  constexpr int QK = (ZP_RNS_K + 1 + 64 + 31) / 32;  // residues, alpha, up to 64 answers
   uint32_t y[QK];
-  double f = 0.0;
+  uint64_t s_lo = 0, s_hi = 0;  // 128-bit sum of y_k floor(2^64 / p_k)
   const uint32_t* Xr = X + ((uint64_t)b * d1p + rp) * ZP_RNS_K;
 #pragma unroll
   for (int q = 0; q < QK; ++q) {
     const uint32_t k = lane + 32u * q;
     y[q] = 0u;
     if (rp < d1p && k < ZP_RNS_K) {
-      y[q] = mod_p((uint64_t)__ldg(Xr + k) * rns->inv[k], rns->p[k], rns->mu[k]);
-      f += (double)y[q] * rns->dinv[k];
+      const uint32_t p = rns->p[k], dl = (1u << 27) - p;
+      const uint64_t x = (uint64_t)__ldg(Xr + k) * rns->inv[k];             // < 2^54
+      const uint64_t t1 = (x & 0x7FFFFFFull) + (x >> 27) * dl;             // < 2^40
+      uint32_t v = (uint32_t)((t1 & 0x7FFFFFFull) + (t1 >> 27) * dl);       // < 2^27 + 2^25
+      if (v >= p) v -= p;
+      y[q] = v;
+      const uint64_t r = rns->mu[k];  // floor((2^64 - 1) / p) = floor(2^64 / p) (p odd)
+      const uint64_t lo = (uint64_t)v * r, hi = __umul64hi((uint64_t)v, r);
+      s_lo += lo;
+      s_hi += hi + (s_lo < lo ? 1u : 0u);
     }
   }
 #pragma unroll
-  for (int o = 16; o; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
+  for (int o = 16; o; o >>= 1) {
+    const uint64_t olo = __shfl_xor_sync(0xffffffffu, s_lo, o);
+    const uint64_t ohi = __shfl_xor_sync(0xffffffffu, s_hi, o);
+    s_lo += olo;
+    s_hi += ohi + (s_lo < olo ? 1u : 0u);
+  }
   constexpr uint32_t KA = ZP_RNS_K;  // column of alpha
-  if (rp < d1p && lane == KA % 32) y[KA / 32] = (uint32_t)floor(f + 0x1p-30);
+  if (rp < d1p && lane == KA % 32)
+    y[KA / 32] = (uint32_t)(s_hi + ((s_lo + (1ull << 35)) < s_lo ? 1u : 0u));
+  const uint32_t KE = KA + ell;  // column of answer ell - 1
+#pragma unroll
+  for (int q = 0; q < QK; ++q) {
+    const uint32_t k = lane + 32u * q;
+    if (k > KA && k <= KE) {
+      const uint64_t r = (uint64_t)rp * ell + (k - KA - 1);
+      y[q] = (rp < d1p && r < R) ? __ldg(ans + (uint64_t)b * R + r) : 0u;
+    }
+  }
   const uint64_t row0 = (uint64_t)b * 4 * Rq + 128ull * (rp >> 5) + (rp & 31u);
 #pragma unroll
   for (int a = 0; a < 4; ++a) {
@@ -348,7 +372,7 @@ __global__ void k_crt_prep(const uint32_t* __restrict__ X, uint32_t B, uint32_t 
 #pragma unroll
     for (int q = 0; q < QK; ++q) {
       const uint32_t k = lane + 32u * q;
-      if (k <= KA) {
+      if (k <= KE) {
         const uint32_t byte = (y[q] >> (8 * a)) & 0xFFu;
         dst[k] = (uint8_t)byte;
         sum += byte;
@@ -445,7 +469,7 @@ int zp_launch_compress_finish(zp_db* db, zp_client* const* clients, const uint32
   ctx->launches++;
   if (db->v_rns) {
     // residues -> y, alpha (byte planes) -> exact CRT sums on the tensor cores -> pack + reduce
-    const uint32_t Rq = db->Rq, ypitch = (ZP_RNS_K + 1 + 15) / 16 * 16;
+    const uint32_t Rq = db->Rq, ypitch = (zp_crt_k(ctx) + 15) / 16 * 16;
     const size_t yp_bytes = (size_t)B * 4 * Rq * ypitch, yrs_bytes = (size_t)B * 4 * Rq * 4;
     const size_t vc_bytes = (size_t)B * Rq * VW * 4;
     rc = zp_scratch_reserve(&db->s_crt, yp_bytes + yrs_bytes + vc_bytes + 512);
@@ -455,7 +479,8 @@ int zp_launch_compress_finish(zp_db* db, zp_client* const* clients, const uint32
     uint32_t* Vc = yrs + (yrs_bytes / 4 + 63) / 64 * 64;
     const uint64_t warps = (uint64_t)B * Rq;
     k_crt_prep<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(V, B, db->d1p, Rq, ctx->d_rns, Yp,
-                                                                    ypitch, yrs);
+                                                                    ypitch, yrs, dAns, db->R,
+                                                                    ctx->ell);
     ZP_CUDA(cudaGetLastError());
     // the mkm pointers are the third member of each uploaded ClientPtrs
     rc = zp_launch_crt_products(db, reinterpret_cast<const uint32_t* const*>(dcl) + 2,

@@ -508,7 +508,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
         for (int c = 0; c < 4; ++c) w[c] = args.rns->pow8[k][e + c];
         // the centring terms: corr_row (this row) times sum_c w[c], and per query the column
-        // sums' 128 sum_c cs[c BT + bl] w[c] (two queries per lane, fetched by shuffles)
+        // sums' 128 sum_c cs[c BT + bl] w[c] (one or two queries per lane, fetched by shuffles;
+        // the row term is this thread's own and is added after the shuffle)
         const int32_t corr_row =
             (int32_t)(128u * __ldg(args.rowsumA + mt * BM + e * 32 + lane) - 16384u * args.Kp);
         const uint64_t rowterm =
@@ -524,7 +525,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
             for (int c = 0; c < 4; ++c) q += (uint64_t)(128u * __ldg(cs + c * BT + bl)) * w[c];
           }
-          qcs[h] = q + rowterm;
+          qcs[h] = q;
         }
         constexpr int PITCH = BT + 1;  // odd: conflict-free
         uint32_t* myst = stg + (e * 32 + lane) * PITCH;
@@ -538,7 +539,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
             const int bl = 16 * b16 + j;
-            uint64_t x = __shfl_sync(0xffffffffu, qcs[bl / 32], bl % 32);
+            uint64_t x = __shfl_sync(0xffffffffu, qcs[bl / 32], bl % 32) + rowterm;
 #pragma unroll
             for (int c = 0; c < 4; ++c)
               x += (uint64_t)((int64_t)__float2int_rn(__uint_as_float(r[c][j])) * (int64_t)w[c]);
@@ -570,6 +571,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         // x = sum_c S_c 2^(8c) < 2^48 folded below p (p = 2^27 - dl, dl < 2^12). Its four
         // bytes go to the rows of the RNS product's B operand (fp16, centred) and their sums
         // over i to that operand's row sums.
+        constexpr int NR = 4 * ZP_RES_KPER;  // columns per tile (N)
         const uint32_t a = acc_cnt & 1u, ra = acc_cnt >> 1;
         if (!warp_wait(&acc_full[a], ra & 1u, abort_flag, args.status)) {
           ok = false;
@@ -581,55 +583,64 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const uint32_t b = live ? row / args.res_n : 0u, i = live ? row - b * args.res_n : 0u;
         const uint32_t b0 = __shfl_sync(0xffffffffu, b, 0);
         const bool uni = __all_sync(0xffffffffu, !live || b == b0);  // one query in this warp
-        const uint32_t bt = args.res_bt, ntq = b / bt, bl = b % bt;
-        const uint32_t kper = N / 4;  // primes per N tile
-        // centring terms: corr_row (this row) in every byte column, and per prime j of the tile
-        // 128 sum_c cs[4 j + c] 2^(8c) (lanes hold j = lane and lane + 32; fetched by shuffles)
+        // output addresses: B row (k nnt + b / bt) 4 bt + c bt + b % bt, column i
+        const uint32_t bt = args.res_bt;
+        const uint64_t nq = (uint64_t)args.res_nnt * 4 * bt;  // B rows per prime
+        const uint64_t kp = args.res_kp;
+        __half* outp = args.res_out + ((uint64_t)(b / bt) * 4 * bt + b % bt) * kp + i;
+        uint32_t* csp = args.res_colsum + (uint64_t)(b / bt) * 4 * bt + b % bt;
+        const uint64_t kstep = nq * kp, cstep = (uint64_t)bt * kp;
+        // centring terms: corr_row (this row) in every byte column; per prime j of the tile
+        // 128 sum_c cs[4 j + c] 2^(8c) and p_j (lanes hold j = lane and lane + 32, fetched
+        // by shuffles; the row term is this thread's own)
         const int64_t corr_row =
             live ? (int64_t)(int32_t)(128u * __ldg(args.rowsumA + row) - 16384u * args.Kp) : 0;
         const uint64_t rowterm = (uint64_t)(corr_row * 0x01010101ll);
-        const uint32_t* cs = args.colsum + (uint64_t)nt * N;
+        const uint32_t* cs = args.colsum + (uint64_t)nt * NR;
         uint64_t csw[2];
+        uint32_t pj[2];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-          const uint32_t j = 32u * h + lane;
+          const uint32_t j = 32u * h + lane, k = nt * ZP_RES_KPER + j;
           uint64_t q = 0;
-          if (j < kper) {
+          if (j < (uint32_t)ZP_RES_KPER) {
 #pragma unroll
             for (int c = 0; c < 4; ++c) q += (uint64_t)(128u * __ldg(cs + 4 * j + c)) << (8 * c);
           }
-          csw[h] = q + rowterm;
+          csw[h] = q;
+          pj[h] = (j < (uint32_t)ZP_RES_KPER && k < ZP_RNS_K) ? args.rns->p[k] : 1u;
         }
-        for (uint32_t g = 0; g < N / 32; ++g) {
+#pragma unroll
+        for (int g = 0; g < NR / 32; ++g) {
           uint32_t r[32];
           tmem_ld32(tmem_base + lane_addr + a * 256u + 32u * g, r);
           tmem_wait_ld();
 #pragma unroll
           for (int kk = 0; kk < 8; ++kk) {
-            const uint32_t j = g * 8 + kk, k = nt * kper + j;
+            const int j = g * 8 + kk;
+            const uint32_t k = nt * ZP_RES_KPER + j;
             const uint64_t cj = __shfl_sync(0xffffffffu, csw[j >> 5], j & 31);
+            const uint32_t p = __shfl_sync(0xffffffffu, pj[j >> 5], j & 31);
             if (k >= ZP_RNS_K) continue;  // uniform across the warp
-            const uint32_t p = args.rns->p[k], dl = (1u << 27) - p;
-            uint64_t x = cj;
+            const uint32_t dl = (1u << 27) - p;
+            uint64_t x = cj + rowterm;
 #pragma unroll
             for (int c = 0; c < 4; ++c)
               x += (uint64_t)((int64_t)__float2int_rn(__uint_as_float(r[4 * kk + c])) << (8 * c));
             const uint64_t t1 = (x & 0x7FFFFFFull) + (x >> 27) * dl;  // < 2^34
             uint32_t v = (uint32_t)((t1 & 0x7FFFFFFull) + (t1 >> 27) * dl);  // < 2^27 + 2^19 < 2p
             if (v >= p) v -= p;
-            const uint64_t brow = ((uint64_t)k * args.res_nnt + ntq) * (4 * bt) + bl;
+            __half* o = outp + (uint64_t)k * kstep;
+            uint32_t* csk = csp + (uint64_t)k * nq;
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
               const uint32_t byte = live ? (v >> (8 * c)) & 0xFFu : 0u;
-              if (live) args.res_out[(brow + c * bt) * args.res_kp + i] = __int2half_rn((int)byte - 128);
+              if (live) o[c * cstep] = __int2half_rn((int)byte - 128);
               if (uni) {
                 const uint32_t sum = __reduce_add_sync(0xffffffffu, byte);
-                if (lane == 0 && sum) {
-                  const uint64_t brow0 = ((uint64_t)k * args.res_nnt + b0 / bt) * (4 * bt) + b0 % bt;
-                  atomicAdd(&args.res_colsum[brow0 + c * bt], sum);
-                }
+                if (lane == 0 && sum) atomicAdd(csk + c * bt, sum);  // lane 0 holds the query
               } else if (byte) {
-                atomicAdd(&args.res_colsum[brow + c * bt], byte);
+                atomicAdd(csk + c * bt, byte);
               }
             }
           }
@@ -865,18 +876,21 @@ __global__ void k_prep_q_cols(const uint32_t* __restrict__ A, uint32_t B, uint32
 // i < n (raw 0 for n <= i < Kp). colsum[b][beta] += sum_i byte beta of cko[b][i].
 // CTA: one query, 64 offsets; 256 threads.
 // With `srcs` (device array), query b's n values start at srcs[b * src_stride] instead of
-// cko + b n ZP_MAX_L (the CRT product reads each client's table in place).
+// cko + b n ZP_MAX_L (the CRT product reads each client's table in place), and the ntail
+// values after them come from `tail` (the same for every query).
 __global__ void k_prep_cko(const uint32_t* __restrict__ cko, uint32_t n, uint32_t Kp,
                            __half* __restrict__ Bc, uint32_t* __restrict__ colsum,
                            const uint32_t* const* __restrict__ srcs = nullptr,
-                           uint32_t src_stride = 0) {
+                           uint32_t src_stride = 0, const uint32_t* __restrict__ tail = nullptr,
+                           uint32_t ntail = 0) {
   __shared__ uint32_t tile[64][ZP_MAX_L + 1];
   const uint32_t b = blockIdx.y, i0 = blockIdx.x * 64;
   const uint32_t* src = srcs ? srcs[(uint64_t)b * src_stride] : cko + (uint64_t)b * n * ZP_MAX_L;
   for (uint32_t idx = threadIdx.x; idx < 64u * ZP_MAX_L; idx += blockDim.x) {
     const uint32_t ii = idx / ZP_MAX_L, w = idx % ZP_MAX_L;
     const uint32_t i = i0 + ii;
-    tile[ii][w] = i < n ? src[(uint64_t)i * ZP_MAX_L + w] : 0u;
+    tile[ii][w] = i < n ? src[(uint64_t)i * ZP_MAX_L + w]
+                        : (i < n + ntail ? tail[(uint64_t)(i - n) * ZP_MAX_L + w] : 0u);
   }
   __syncthreads();
   const uint32_t beta = threadIdx.x;  // 0..255
@@ -926,7 +940,6 @@ int launch_gemm(zp_ctx* ctx, const CUtensorMap& tmA, const CUtensorMap& tmB, con
 }  // namespace
 
 // Queries per N tile for a batch of B queries (N = 4 * BT rows of the B operand).
-static uint32_t pick_bt(uint32_t B) { return B <= 16 ? 16u : (B <= 32 ? 32u : 64u); }
 
 // Batched product out = D . Q^T (MODE_ANS: out[b][r]) or D . A (MODE_HINT: out[r][i]).
 // Q(b, k) = dQ[b*C + k] (rows) or dQ[k*B + b] (cols). D given by its tensor map.
@@ -937,7 +950,8 @@ int zp_launch_answer_tc(zp_db* db, const CUtensorMap& tmD, uint32_t Rrows, const
   const uint32_t C = db->C;
   // the fp16 A path takes two K blocks per stage: K padded to 128
   const uint32_t Kp = a16 ? (C + 127) / 128 * 128 : (C + 63) / 64 * 64;
-  const uint32_t BT = pick_bt(B);
+  // the hint (columns of A as queries, n of them) keeps the widest tile
+  const uint32_t BT = hint ? 64u : zp_pick_bt(ctx->ans_bt, B);
   const uint32_t N = 4 * BT;
   const uint32_t nnt = (B + BT - 1) / BT;
   const size_t qc_bytes = (size_t)nnt * N * Kp * 2;
@@ -1095,7 +1109,7 @@ int zp_launch_rns_products(zp_db* db, const uint32_t* dCKO, uint32_t B, uint32_t
   zp_ctx* ctx = db->ctx;
   const uint32_t n = ctx->P.n;
   const uint32_t Kp = (n + 127) / 128 * 128;
-  const uint32_t BT = pick_bt(B), N = 4 * BT, nnt = (B + BT - 1) / BT;
+  const uint32_t BT = zp_pick_bt(ctx->rns_bt, B), N = 4 * BT, nnt = (B + BT - 1) / BT;
   const uint64_t brows = (uint64_t)ZP_RNS_K * nnt * N;
   const size_t bc_bytes = (size_t)brows * Kp * 2;
   const size_t cs_bytes = (size_t)brows * 4;
@@ -1176,16 +1190,18 @@ int zp_launch_rns_products(zp_db* db, const uint32_t* dCKO, uint32_t B, uint32_t
 
 // ---------------------------------------------------------------------------------
 // CRT products of the residue-number-system compression (Sec. 5.2: one reduction mod m at
-// the end): V[b][r'] = sum_k y[b][r'][k] (M/p_k mod m_b) + alpha (m_b - (M mod m_b)), the
-// Chinese-remainder sum of the residues of H'[r', :] . cko[b] (y, alpha from k_crt_prep, as
-// byte planes Yp), taken exactly on the tensor cores as a batched MODE_CMP product: for query
-// b, A = the byte planes of its y (4 Rq rows, K = ZP_RNS_K + 1), B = the 256 bytes of each
-// of its client's constants M/p_k mod m_b (read in place through mkm_ptrs[b * ptr_stride]).
+// the end): V[b][r'] = sum_k y[b][r'][k] (M/p_k mod m_b) + alpha (m_b - (M mod m_b))
+// + sum_{j<ell} gamma^j ans[b][r' ell + j], i.e. the Chinese-remainder sum of the residues of
+// H'[r', :] . cko[b] plus the packed answer b' (congruent to b' + H'.cko mod m_b, below
+// 2^2084), taken exactly on the tensor cores as a batched MODE_CMP product: for query b,
+// A = the byte planes of its y, alpha and answers (k_crt_prep; 4 Rq rows, K = ZP_RNS_K + 1 +
+// ell), B = the 256 bytes of each of its client's constants M/p_k mod m_b (read in place
+// through mkm_ptrs[b * ptr_stride]) followed by those of gamma^j (the context's table).
 int zp_launch_crt_products(zp_db* db, const uint32_t* const* mkm_ptrs, uint32_t ptr_stride,
                            uint32_t B, const uint8_t* Yp, uint32_t ypitch, const uint32_t* yrs,
                            uint32_t* Vc, cudaStream_t st) {
   zp_ctx* ctx = db->ctx;
-  constexpr uint32_t KC = ZP_RNS_K + 1, Kp = (KC + 63) / 64 * 64;
+  const uint32_t KC = zp_crt_k(ctx), Kp = (KC + 63) / 64 * 64;
   const size_t bm_bytes = (size_t)B * 256 * Kp * 2, cs_bytes = (size_t)B * 256 * 4;
   int rc = zp_scratch_reserve(&db->s_crtb, bm_bytes + cs_bytes + 256);
   if (rc) return rc;
@@ -1194,7 +1210,8 @@ int zp_launch_crt_products(zp_db* db, const uint32_t* const* mkm_ptrs, uint32_t 
   ZP_CUDA(cudaMemsetAsync(colsum, 0, cs_bytes, st));
   zp_clear_pending_error();
   ctx->launches++;
-  k_prep_cko<<<dim3(Kp / 64, B), 256, 0, st>>>(nullptr, KC, Kp, Bm, colsum, mkm_ptrs, ptr_stride);
+  k_prep_cko<<<dim3(Kp / 64, B), 256, 0, st>>>(nullptr, ZP_RNS_K + 1, Kp, Bm, colsum, mkm_ptrs,
+                                                ptr_stride, ctx->d_gam, ctx->ell);
   ZP_CUDA(cudaGetLastError());
   CUtensorMap tmA, tmB;
   rc = zp_encode_tmap_2d(&tmA, CU_TENSOR_MAP_DATA_TYPE_UINT8, Yp, KC, (uint64_t)B * 4 * db->Rq, ypitch,

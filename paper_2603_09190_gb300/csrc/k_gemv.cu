@@ -251,6 +251,7 @@ int zp_launch_gemv(zp_db* db, const uint32_t* dq, uint32_t B, uint32_t* dans, cu
   if (B == 3) return launch_gemv_multi<3>(db, qp, dans, nct, st);
   if (B == 4) return launch_gemv_multi<4>(db, qp, dans, nct, st);
   const bool shared_gpu = max_ctas && max_ctas < (uint32_t)ctx->num_sms;
+  const bool wide = ctx->gemv_cfg[shared_gpu ? 1 : 0] == 2;  // 16 warps x 128-row tiles
   if (!g_attr_done[ctx->device & 63]) {
     ZP_CUDA(cudaFuncSetAttribute(k_gemv<8, 12>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  GemvCfg<8, 12>::SMEM_BYTES));
@@ -258,7 +259,7 @@ int zp_launch_gemv(zp_db* db, const uint32_t* dq, uint32_t B, uint32_t* dans, cu
                                  GemvCfg<16, 6>::SMEM_BYTES));
     g_attr_done[ctx->device & 63] = true;
   }
-  const uint32_t tr = shared_gpu ? GemvCfg<16, 6>::TR : GemvCfg<8, 12>::TR;
+  const uint32_t tr = wide ? GemvCfg<16, 6>::TR : GemvCfg<8, 12>::TR;
   const uint32_t nrbs = (db->R + tr - 1) / tr;
   const uint64_t T = (uint64_t)nrbs * nct;
   uint64_t grid = (uint64_t)ctx->num_sms * CTAS_PER_SM;
@@ -266,7 +267,7 @@ int zp_launch_gemv(zp_db* db, const uint32_t* dq, uint32_t B, uint32_t* dans, cu
   if (grid > T) grid = T;
   zp_clear_pending_error();
   ctx->launches++;
-  if (shared_gpu)
+  if (wide)
     k_gemv<16, 6><<<(unsigned)grid, 17 * 32, GemvCfg<16, 6>::SMEM_BYTES, st>>>(
         db->tmap_gemv128, qp, dans, db->R, nrbs, nct, ctx->d_status);
   else
@@ -293,6 +294,7 @@ uint32_t* g_noalloc_planes[64] = {nullptr};
 
 extern "C" int zp_answer_noalloc(zp_db* db, const uint32_t* dQ, uint32_t* dAns, void* stream) {
   if (!db || !dQ || !dAns) return zp_set_error(ZP_EINVAL, "zp_answer_noalloc: null argument");
+  zp_view_sync(db);
   if (db->C > ZP_NOALLOC_MAX_C)
     return zp_set_error(ZP_EINVAL,
                         "zp_answer_noalloc: C=%u exceeds the %u columns its static buffer holds",

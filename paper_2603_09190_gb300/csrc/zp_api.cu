@@ -338,6 +338,9 @@ extern "C" int zp_init(int device, const zp_params* P, zp_ctx** out) {
     c->gemv_max_batch = 4;  // one dp4a pass beats the tensor cores up to 4 queries (1 GiB)
     c->answer_fp16 = 1;
     c->batch_overlap = 1;
+    for (int i = 0; i < 3; ++i) c->ans_bt[i] = c->rns_bt[i] = 16u << i;  // 16, 32, 64
+    c->gemv_cfg[0] = 1;  // whole GPU: 8 warps x 12 stages
+    c->gemv_cfg[1] = 2;  // beside the products: 16 warps x 6 stages
     {
       zp_rns_dev h;
       if (!rns_setup(c, h)) {
@@ -353,6 +356,22 @@ extern "C" int zp_init(int device, const zp_params* P, zp_ctx** out) {
         cudaFree(c->d_rns);
         delete c;
         return zp_set_error(ZP_ECUDA, "copy of the RNS constants");
+      }
+    }
+    // gamma^j (j < ell) as ZP_MAX_L-word integers: the packing weights of the answers in the
+    // CRT product of the residue-number-system compression
+    {
+      std::vector<uint32_t> tab((size_t)c->ell * ZP_MAX_L, 0), pw(1, 1);
+      for (uint32_t j = 0; j < c->ell; ++j) {
+        for (size_t w = 0; w < pw.size() && w < ZP_MAX_L; ++w) tab[(size_t)j * ZP_MAX_L + w] = pw[w];
+        big_mul_small(pw, c->gamma_w, 3);
+      }
+      if (cudaMalloc(&c->d_gam, tab.size() * 4) != cudaSuccess ||
+          cudaMemcpy(c->d_gam, tab.data(), tab.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
+        if (c->d_gam) cudaFree(c->d_gam);
+        cudaFree(c->d_rns);
+        delete c;
+        return zp_set_error(ZP_ENOMEM, "zp_init: powers of gamma");
       }
     }
     // default SM split of zp_respond for one query: about 3/8 of the SMs run the
@@ -379,6 +398,7 @@ extern "C" int zp_ctx_destroy(zp_ctx* c) {
   if (c->d_status) cudaFree(c->d_status);
   if (c->d_rns) cudaFree(c->d_rns);
   if (c->d_resw) cudaFree(c->d_resw);
+  if (c->d_gam) cudaFree(c->d_gam);
   if (c->d_resw_cs) cudaFree(c->d_resw_cs);
   delete c;
   return ZP_OK;
@@ -412,6 +432,24 @@ extern "C" int zp_set_option(zp_ctx* c, const char* name, int64_t value) {
     c->answer_fp16 = (uint32_t)value;
     return ZP_OK;
   }
+  static const char* bt_names[2][3] = {{"answer_bt_small", "answer_bt_mid", "answer_bt_large"},
+                                       {"rns_bt_small", "rns_bt_mid", "rns_bt_large"}};
+  for (int t = 0; t < 2; ++t)
+    for (int cl = 0; cl < 3; ++cl)
+      if (k == bt_names[t][cl]) {
+        // at most the class's largest batch (16, 32, 64 queries)
+        if ((value != 16 && value != 32 && value != 64) || value > (16 << cl))
+          return zp_set_error(ZP_EINVAL, "zp_set_option: %s=%lld (16, 32 or 64, at most %d)", name,
+                              (long long)value, 16 << cl);
+        (t ? c->rns_bt : c->ans_bt)[cl] = (uint32_t)value;
+        return ZP_OK;
+      }
+  if (k == "gemv_cfg_alone" || k == "gemv_cfg_shared") {
+    if (value != 1 && value != 2)
+      return zp_set_error(ZP_EINVAL, "zp_set_option: %s=%lld (1 or 2)", name, (long long)value);
+    c->gemv_cfg[k == "gemv_cfg_shared"] = (uint32_t)value;
+    return ZP_OK;
+  }
   if (k == "batch_overlap") {
     if (value < 0 || value > 1)
       return zp_set_error(ZP_EINVAL, "zp_set_option: batch_overlap=%lld out of [0, 1]", (long long)value);
@@ -437,6 +475,14 @@ extern "C" int zp_get_option(const zp_ctx* c, const char* name, int64_t* value) 
   else if (k == "gemv_max_batch") *value = c->gemv_max_batch;
   else if (k == "answer_fp16") *value = c->answer_fp16;
   else if (k == "batch_overlap") *value = c->batch_overlap;
+  else if (k == "answer_bt_small") *value = c->ans_bt[0];
+  else if (k == "answer_bt_mid") *value = c->ans_bt[1];
+  else if (k == "answer_bt_large") *value = c->ans_bt[2];
+  else if (k == "rns_bt_small") *value = c->rns_bt[0];
+  else if (k == "rns_bt_mid") *value = c->rns_bt[1];
+  else if (k == "rns_bt_large") *value = c->rns_bt[2];
+  else if (k == "gemv_cfg_alone") *value = c->gemv_cfg[0];
+  else if (k == "gemv_cfg_shared") *value = c->gemv_cfg[1];
   else return zp_set_error(ZP_EINVAL, "zp_get_option: unknown option '%s'", name);
   return ZP_OK;
 }
@@ -523,6 +569,52 @@ static std::vector<uint8_t>& stale_flags(zp_db* db) {
   return db->stale_v;
 }
 
+void zp_view_sync(zp_db* v) {
+  const zp_db* b = v->base;
+  if (!b) return;
+  v->d_D16 = b->d_D16;
+  v->tmap_d16 = b->tmap_d16;
+  v->d_hneg = b->d_hneg;
+  v->d_hpl = b->d_hpl;
+  v->d_hpl_rowsum = b->d_hpl_rowsum;
+  v->hpl_ld = b->hpl_ld;
+  v->tmap_hpl = b->tmap_hpl;
+  v->hint_ready = b->hint_ready;
+  v->stale = b->stale;
+  v->d_rns_hpl = b->d_rns_hpl;
+  v->d_rns_rowsum = b->d_rns_rowsum;
+  v->Rq = b->Rq;
+  v->tmap_rns = b->tmap_rns;
+  v->d_rns16 = b->d_rns16;
+  v->tmap_rns16 = b->tmap_rns16;
+}
+
+extern "C" int zp_db_view(zp_db* db, zp_db** out) {
+  try {
+    if (!db || !out) return zp_set_error(ZP_EINVAL, "zp_db_view: null argument");
+    zp_db* base = db->base ? db->base : db;
+    zp_db* v = new zp_db();
+    v->base = base;
+    v->ctx = base->ctx;
+    v->device = base->device;
+    v->dD = base->dD;
+    v->R = base->R;
+    v->C = base->C;
+    v->ld = base->ld;
+    v->d1p = base->d1p;
+    v->Rp = base->Rp;
+    v->d_rowsum = base->d_rowsum;
+    v->tmap_gemv = base->tmap_gemv;
+    v->tmap_gemv128 = base->tmap_gemv128;
+    v->tmap_gemm = base->tmap_gemm;
+    zp_view_sync(v);
+    *out = v;
+    return ZP_OK;
+  } catch (const std::bad_alloc&) {
+    return zp_set_error(ZP_ENOMEM, "zp_db_view: host allocation failed");
+  }
+}
+
 extern "C" int zp_db_info(const zp_db* db, uint32_t* ell, uint32_t* d1p, uint32_t* L) {
   if (!db) return zp_set_error(ZP_EINVAL, "zp_db_info: null db");
   if (ell) *ell = db->ctx->ell;
@@ -533,7 +625,7 @@ extern "C" int zp_db_info(const zp_db* db, uint32_t* ell, uint32_t* d1p, uint32_
 
 extern "C" int zp_stale_rows(const zp_db* db, uint32_t* count) {
   if (!db || !count) return zp_set_error(ZP_EINVAL, "zp_stale_rows: null argument");
-  *count = db->stale;
+  *count = db->base ? db->base->stale : db->stale;
   return ZP_OK;
 }
 
@@ -541,6 +633,11 @@ extern "C" int zp_db_destroy(zp_db* db) {
   if (!db) return ZP_OK;
   zp_device_scope _zp_scope(db->device);
   cudaDeviceSynchronize();
+  if (db->base) {  // a view owns only its scratch, stream and events
+    db->d_rowsum = db->d_hneg = db->d_hpl_rowsum = db->d_rns_rowsum = nullptr;
+    db->d_hpl = db->d_rns_hpl = nullptr;
+    db->d_D16 = db->d_rns16 = nullptr;
+  }
   if (db->d_rowsum) cudaFree(db->d_rowsum);
   if (db->d_hneg) cudaFree(db->d_hneg);
   if (db->d_hpl) cudaFree(db->d_hpl);
@@ -578,6 +675,9 @@ static int stage_rows(zp_db* db, const uint32_t* hRows, uint32_t k, size_t extra
 
 int zp_ensure_rns(zp_db* db, cudaStream_t st) {
   if (db->d_rns_hpl) return ZP_OK;
+  if (db->base)
+    return zp_set_error(ZP_ESTATE, "RNS tables missing: call zp_db_prepare_rns on the database "
+                                   "before its views compress large batches");
   const uint32_t n = db->ctx->P.n;
   db->Rq = (db->d1p + 31) / 32 * 32;
   const uint64_t rows = (uint64_t)ZP_RNS_K * 4 * db->Rq;
@@ -652,7 +752,7 @@ int zp_ensure_res_table(zp_ctx* c) {
 }
 
 int zp_ensure_rns16(zp_db* db, cudaStream_t st) {
-  if (db->d_rns16 || !db->d_rns_hpl || !db->d_D16) return ZP_OK;
+  if (db->d_rns16 || !db->d_rns_hpl || !db->d_D16 || db->base) return ZP_OK;
   const uint64_t Kp = (db->ctx->P.n + 127) / 128 * 128;
   const uint64_t rows = (uint64_t)ZP_RNS_K * 4 * db->Rq;
   const size_t bytes = (size_t)rows * Kp * 2;
@@ -704,6 +804,7 @@ extern "C" int zp_gen_hint(zp_db* db, const uint32_t* dA, uint32_t* dH, const ui
                            uint32_t nrows, void* stream) {
   try {
     if (!db || !dA) return zp_set_error(ZP_EINVAL, "zp_gen_hint: null argument");
+    if (db->base) return zp_set_error(ZP_EINVAL, "zp_gen_hint: called on a view (call it on its database)");
     if (hRows && (nrows == 0 || nrows > db->R))
       return zp_set_error(ZP_EINVAL, "zp_gen_hint: nrows=%u out of [1, R]", nrows);
     zp_ctx* c = db->ctx;
@@ -789,6 +890,7 @@ extern "C" int zp_update_rows(zp_db* db, const uint32_t* hRows, uint32_t k, cons
                               void* stream) {
   try {
     if (!db || !hRows || !dNew) return zp_set_error(ZP_EINVAL, "zp_update_rows: null argument");
+    if (db->base) return zp_set_error(ZP_EINVAL, "zp_update_rows: called on a view (call it on its database)");
     if (k == 0 || k > db->R) return zp_set_error(ZP_EINVAL, "zp_update_rows: k=%u out of [1, R]", k);
     ZP_ON_DEVICE(db->ctx->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -817,6 +919,7 @@ extern "C" int zp_update_rows(zp_db* db, const uint32_t* hRows, uint32_t k, cons
 // ------------------------------------------------------------------ online Response
 extern "C" int zp_answer(zp_db* db, const uint32_t* dQ, uint32_t B, uint32_t* dAns, void* stream) {
   if (!db || !dQ || !dAns) return zp_set_error(ZP_EINVAL, "zp_answer: null argument");
+  zp_view_sync(db);
   if (B < 1 || B > 4096) return zp_set_error(ZP_EINVAL, "zp_answer: B=%u out of [1, 4096]", B);
   ZP_ON_DEVICE(db->ctx->device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -1006,6 +1109,7 @@ extern "C" int zp_compress(zp_db* db, zp_client* const* clients, const uint32_t*
                            const uint32_t* dCKO, uint32_t B, uint32_t* dT, void* stream) {
   try {
     if (!db || !dAns || !dCKO || !dT) return zp_set_error(ZP_EINVAL, "zp_compress: null argument");
+    zp_view_sync(db);
     int rc = check_compress_args(db, clients, B);
     if (rc) return rc;
     ZP_ON_DEVICE(db->ctx->device);
@@ -1021,6 +1125,7 @@ extern "C" int zp_compress(zp_db* db, zp_client* const* clients, const uint32_t*
 extern "C" int zp_compress_products(zp_db* db, const uint32_t* dCKO, uint32_t B, void* stream) {
   try {
     if (!db || !dCKO) return zp_set_error(ZP_EINVAL, "zp_compress_products: null argument");
+    zp_view_sync(db);
     if (B < 1 || B > 4096) return zp_set_error(ZP_EINVAL, "zp_compress_products: B=%u out of [1, 4096]", B);
     if (!db->hint_ready) return zp_set_error(ZP_ESTATE, "zp_compress_products: no hint (call zp_gen_hint)");
     if (db->stale) return zp_set_error(ZP_ESTATE, "zp_compress_products: %u hint rows stale", db->stale);
@@ -1037,6 +1142,7 @@ extern "C" int zp_compress_finish(zp_db* db, zp_client* const* clients, const ui
                                   uint32_t B, uint32_t* dT, void* stream) {
   try {
     if (!db || !dAns || !dT) return zp_set_error(ZP_EINVAL, "zp_compress_finish: null argument");
+    zp_view_sync(db);
     int rc = check_compress_args(db, clients, B);
     if (rc) return rc;
     ZP_ON_DEVICE(db->ctx->device);
@@ -1059,6 +1165,7 @@ extern "C" int zp_respond(zp_db* db, zp_client* const* clients, const uint32_t* 
                           void* stream) {
   try {
     if (!db || !dQ || !dCKO || !dAns || !dT) return zp_set_error(ZP_EINVAL, "zp_respond: null argument");
+    zp_view_sync(db);
     int rc = check_compress_args(db, clients, B);
     if (rc) return rc;
     zp_ctx* c = db->ctx;
@@ -1110,6 +1217,7 @@ extern "C" int zp_client_hint(zp_db* db, const zp_client* cl, const uint32_t* dC
                               const uint32_t* hPackedRows, uint32_t nrows, void* stream) {
   try {
     if (!db || !cl || !dCkr || !dK) return zp_set_error(ZP_EINVAL, "zp_client_hint: null argument");
+    zp_view_sync(db);
     if (cl->ctx != db->ctx) return zp_set_error(ZP_EINVAL, "zp_client_hint: client from another context");
     if (!db->hint_ready) return zp_set_error(ZP_ESTATE, "zp_client_hint: no hint (call zp_gen_hint)");
     if (db->stale) return zp_set_error(ZP_ESTATE, "zp_client_hint: %u hint rows stale after updates", db->stale);
@@ -1142,13 +1250,18 @@ extern "C" int zp_client_hint(zp_db* db, const zp_client* cl, const uint32_t* dC
 extern "C" int zp_autotune(zp_db* db, void* stream, int64_t* chosen) {
   try {
     if (!db) return zp_set_error(ZP_EINVAL, "zp_autotune: null argument");
+    if (db->base) return zp_set_error(ZP_EINVAL, "zp_autotune: called on a view (call it on its database)");
     zp_ctx* c = db->ctx;
     ZP_ON_DEVICE(c->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const uint32_t BQ = 16, n = c->P.n, L = c->L;
+    const uint32_t BQ = 64, n = c->P.n, L = c->L;
     const int saved_answer = c->answer_path, saved_compress = c->compress_path;
     const uint32_t saved_overlap = c->overlap_sms, saved_gemv = c->gemv_max_batch,
-                   saved_rns = c->rns_min_batch;
+                   saved_rns = c->rns_min_batch, saved_fp16 = c->answer_fp16,
+                   saved_bo = c->batch_overlap;
+    uint32_t saved_abt[3], saved_rbt[3], saved_gcfg[2];
+    for (int i = 0; i < 3; ++i) saved_abt[i] = c->ans_bt[i], saved_rbt[i] = c->rns_bt[i];
+    for (int i = 0; i < 2; ++i) saved_gcfg[i] = c->gemv_cfg[i];
     uint32_t *dQ = nullptr, *dAns = nullptr, *dCKO = nullptr, *dT = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     zp_client* cl = nullptr;
@@ -1166,6 +1279,10 @@ extern "C" int zp_autotune(zp_db* db, void* stream, int64_t* chosen) {
       c->overlap_sms = saved_overlap;
       c->gemv_max_batch = saved_gemv;
       c->rns_min_batch = saved_rns;
+      c->answer_fp16 = saved_fp16;
+      c->batch_overlap = saved_bo;
+      for (int i = 0; i < 3; ++i) c->ans_bt[i] = saved_abt[i], c->rns_bt[i] = saved_rbt[i];
+      for (int i = 0; i < 2; ++i) c->gemv_cfg[i] = saved_gcfg[i];
       return rc;
     };
     if (cudaMalloc(&dQ, (size_t)BQ * db->C * 4) != cudaSuccess ||
@@ -1229,23 +1346,94 @@ extern "C" int zp_autotune(zp_db* db, void* stream, int64_t* chosen) {
       c->compress_path = saved_compress;
     }
     c->rns_min_batch = rns_min;
-    // (3) the SM split of the single-query Response
+    // (3) the GEMV configuration of a single-query answer alone on the whole GPU
+    {
+      c->overlap_sms = 0;
+      float best = 1e30f;
+      uint32_t best_cfg = saved_gcfg[0];
+      for (uint32_t cfg = 1; cfg <= 2; ++cfg) {
+        c->gemv_cfg[0] = cfg;
+        const float t = time_ms([&] { return zp_answer(db, dQ, 1, dAns, stream); });
+        if (err) return fail(err);
+        if (t < best) best = t, best_cfg = cfg;
+      }
+      c->gemv_cfg[0] = best_cfg;
+      c->overlap_sms = saved_overlap;
+    }
+    // (4) the SM split of the single-query Response and the GEMV configuration beside the
+    // compression products
     if (cl && c->num_sms >= 64) {
       float best = 1e30f;
-      uint32_t best_ov = 0;
-      for (uint32_t frac = 0; frac <= 8; ++frac) {  // 0 and 24% .. 52% of the SMs
-        const uint32_t ov = frac == 0 ? 0u : (uint32_t)(c->num_sms * (20 + 4 * frac) / 100);
-        c->overlap_sms = ov;
-        const float r = time_ms([&] {
-          return zp_respond(db, &cl, dQ, dCKO, 1, dAns, dT, stream);
-        });
-        if (err) return fail(err);
-        if (r < best) {
-          best = r;
-          best_ov = ov;
+      uint32_t best_ov = 0, best_cfg = saved_gcfg[1];
+      for (uint32_t cfg = 1; cfg <= 2; ++cfg) {
+        c->gemv_cfg[1] = cfg;
+        for (uint32_t frac = 0; frac <= 8; ++frac) {  // 0 and 24% .. 52% of the SMs
+          if (frac == 0 && cfg == 2) continue;        // no split: the whole-GPU configuration
+          const uint32_t ov = frac == 0 ? 0u : (uint32_t)(c->num_sms * (20 + 4 * frac) / 100);
+          c->overlap_sms = ov;
+          const float r = time_ms([&] {
+            return zp_respond(db, &cl, dQ, dCKO, 1, dAns, dT, stream);
+          });
+          if (err) return fail(err);
+          if (r < best) best = r, best_ov = ov, best_cfg = cfg;
         }
       }
       c->overlap_sms = best_ov;
+      c->gemv_cfg[1] = best_cfg;
+    }
+    // (5) tile widths of the tensor-core answers per batch class (16, 32, 64 queries), and
+    // the operand (the fp16 copy of D against its bytes) when the copy exists
+    if (c->answer_path != ZP_PATH_SIMT) {
+      const int saved_path = c->answer_path;
+      c->answer_path = ZP_PATH_TC;
+      for (int cls_i = 0; cls_i < 3; ++cls_i) {
+        const uint32_t B = 16u << cls_i;
+        float best = 1e30f;
+        uint32_t best_bt = c->ans_bt[cls_i];
+        for (uint32_t bt = 16; bt <= B; bt *= 2) {
+          c->ans_bt[cls_i] = bt;
+          const float t = time_ms([&] { return zp_answer(db, dQ, B, dAns, stream); });
+          if (err) return fail(err);
+          if (t < best) best = t, best_bt = bt;
+        }
+        c->ans_bt[cls_i] = best_bt;
+      }
+      if (db->d_D16) {
+        float tf[2];
+        for (uint32_t f16 = 0; f16 <= 1; ++f16) {
+          c->answer_fp16 = f16;
+          tf[f16] = time_ms([&] { return zp_answer(db, dQ, BQ, dAns, stream); });
+          if (err) return fail(err);
+        }
+        c->answer_fp16 = tf[1] <= tf[0] ? 1u : 0u;
+      }
+      c->answer_path = saved_path;
+    }
+    // (6) tile widths of the RNS products per batch class, and whether a batch's products run
+    // beside its answers in zp_respond
+    if (cl && saved_compress == ZP_PATH_AUTO && rns_min && db->d_rns_hpl) {
+      std::vector<zp_client*> cls(BQ, cl);
+      c->compress_path = ZP_PATH_RNS;
+      for (int cls_i = 0; cls_i < 3; ++cls_i) {
+        const uint32_t B = 16u << cls_i;
+        float best = 1e30f;
+        uint32_t best_bt = c->rns_bt[cls_i];
+        for (uint32_t bt = 16; bt <= B; bt *= 2) {
+          c->rns_bt[cls_i] = bt;
+          const float t = time_ms([&] { return zp_compress(db, cls.data(), dAns, dCKO, B, dT, stream); });
+          if (err) return fail(err);
+          if (t < best) best = t, best_bt = bt;
+        }
+        c->rns_bt[cls_i] = best_bt;
+      }
+      c->compress_path = saved_compress;
+      float tb[2];
+      for (uint32_t bo = 0; bo <= 1; ++bo) {
+        c->batch_overlap = bo;
+        tb[bo] = time_ms([&] { return zp_respond(db, cls.data(), dQ, dCKO, BQ, dAns, dT, stream); });
+        if (err) return fail(err);
+      }
+      c->batch_overlap = tb[1] <= tb[0] ? 1u : 0u;
     }
     cleanup();
     if (chosen) {
@@ -1261,6 +1449,7 @@ extern "C" int zp_autotune(zp_db* db, void* stream, int64_t* chosen) {
 
 extern "C" int zp_db_prepare_fp16(zp_db* db, void* stream) {
   if (!db) return zp_set_error(ZP_EINVAL, "zp_db_prepare_fp16: null argument");
+  if (db->base) return zp_set_error(ZP_EINVAL, "zp_db_prepare_fp16: called on a view (call it on its database)");
   if (db->d_D16) return ZP_OK;
   ZP_ON_DEVICE(db->ctx->device);
   const uint64_t Kp = (db->C + 127) / 128 * 128;  // two K blocks per stage of the fp16 path
@@ -1283,6 +1472,7 @@ extern "C" int zp_db_prepare_fp16(zp_db* db, void* stream) {
 
 extern "C" int zp_db_prepare_rns(zp_db* db, void* stream) {
   if (!db) return zp_set_error(ZP_EINVAL, "zp_db_prepare_rns: null argument");
+  if (db->base) return zp_set_error(ZP_EINVAL, "zp_db_prepare_rns: called on a view (call it on its database)");
   if (!db->hint_ready) return zp_set_error(ZP_ESTATE, "zp_db_prepare_rns: no hint (call zp_gen_hint)");
   if (db->stale) return zp_set_error(ZP_ESTATE, "zp_db_prepare_rns: %u hint rows stale after updates", db->stale);
   if (db->ctx->P.n > 1024) return zp_set_error(ZP_EUNSUPPORTED, "zp_db_prepare_rns: needs n <= 1024");
@@ -1333,6 +1523,7 @@ extern "C" int zp_combine(zp_db* db, zp_client* const* clients, const uint32_t* 
                           uint32_t B, uint32_t* dOut, void* stream) {
   try {
     if (!db || !clients || !dK || !dT || !dOut) return zp_set_error(ZP_EINVAL, "zp_combine: null argument");
+    zp_view_sync(db);
     if (B < 1 || B > 4096) return zp_set_error(ZP_EINVAL, "zp_combine: B=%u out of [1, 4096]", B);
     for (uint32_t b = 0; b < B; ++b) {
       if (!clients[b]) return zp_set_error(ZP_EINVAL, "zp_combine: clients[%u] is null", b);
@@ -1351,6 +1542,7 @@ extern "C" int zp_respond_host(zp_db* db, zp_client* const* clients, const uint3
                                const uint32_t* hCKO, uint32_t B, uint32_t* hT, uint32_t* hAns,
                                void* stream) {
   if (!db || !hQ || !hCKO || !hT) return zp_set_error(ZP_EINVAL, "zp_respond_host: null argument");
+  zp_view_sync(db);
   int rc = check_compress_args(db, clients, B);
   if (rc) return rc;
   zp_ctx* c = db->ctx;

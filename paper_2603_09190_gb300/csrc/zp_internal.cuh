@@ -61,12 +61,19 @@ struct zp_ctx {
   uint32_t gemv_max_batch; // batches of at most this many queries (<= 4) answer by the GEMV
   uint32_t answer_fp16;    // tensor-core answers read a database's fp16 copy when it has one
   uint32_t batch_overlap;  // zp_respond runs a batch's compression products beside its answers
+  // tile widths (queries per N tile: 16, 32 or 64) of the tensor-core answers and of the RNS
+  // products for batches of <= 16, <= 32 and > 32 queries (zp_autotune measures them)
+  uint32_t ans_bt[3], rns_bt[3];
+  // GEMV configuration on the whole GPU [0] and beside the compression products [1]:
+  // 1 = 8 consumer warps x 12 stages of 64 rows, 2 = 16 warps x 6 stages of 128 rows
+  uint32_t gemv_cfg[2];
   zp_rns_dev* d_rns;   // RNS constants (device)
   // ZP_RES_ROWS x 256 centred fp16: row 4 k + c, column beta = byte c of 2^(8 beta) mod p_k
   // (zero bytes for k >= ZP_RNS_K), its row byte sums, and its tensor map (built on first use)
   void* d_resw;
   uint32_t* d_resw_cs;
   CUtensorMap tmap_resw;
+  uint32_t* d_gam;     // ell x ZP_MAX_L words: gamma^j, j < ell (each < 2^(key_bits - 1))
   std::vector<uint32_t> rns_p;  // the primes (host)
   int num_sms;
   uint32_t* d_status;  // device status word (ZP_DEV_* flags)
@@ -95,6 +102,7 @@ struct zp_scratch {
 };
 
 struct zp_db {
+  zp_db* base;        // a view (zp_db_view): the database whose state it shares; else null
   zp_ctx* ctx;
   int device;
   const uint8_t* dD;  // caller-owned, R rows of ld bytes
@@ -152,6 +160,10 @@ int zp_cuda_check(cudaError_t e, const char* what);
 
 int zp_scratch_reserve(zp_scratch* s, size_t bytes);
 
+// A view reads its database's shared state (hint, planes, fp16 copies, RNS tables) at every
+// call: copies the pointers and flags of db->base into the view (no-op for a database).
+void zp_view_sync(zp_db* db);
+
 // Makes `dev` the current device for the lifetime of the scope and gives the caller its
 // own current device back at the end, so that no entry point changes it as a side effect.
 struct zp_device_scope {
@@ -185,6 +197,10 @@ int zp_encode_tmap_2d(CUtensorMap* map, CUtensorMapDataType dt, const void* base
 
 // ------------------------------------------------------------------ kernel launchers
 // (defined in the k_*.cu translation units; all asynchronous on `st`)
+// tile width for a batch of B queries from a per-class table (B <= 16, <= 32, > 32)
+static inline uint32_t zp_pick_bt(const uint32_t (&table)[3], uint32_t B) {
+  return table[B <= 16 ? 0 : (B <= 32 ? 1 : 2)];
+}
 int zp_launch_rowsum(const zp_db* db, const uint32_t* rows, uint32_t nrows, cudaStream_t st);
 int zp_launch_rowsum_buf(zp_ctx* ctx, const uint8_t* M, uint64_t ld, uint32_t rows, uint32_t cols,
                          uint32_t* out, cudaStream_t st);
@@ -228,6 +244,8 @@ int zp_launch_rns_products(zp_db* db, const uint32_t* dCKO, uint32_t B, uint32_t
 int zp_launch_crt_products(zp_db* db, const uint32_t* const* mkm_ptrs, uint32_t ptr_stride,
                            uint32_t B, const uint8_t* Yp, uint32_t ypitch, const uint32_t* yrs,
                            uint32_t* Vc, cudaStream_t st);
+// columns of the CRT product's K: ZP_RNS_K residues, alpha, then the ell answers of b'
+static inline uint32_t zp_crt_k(const zp_ctx* c) { return ZP_RNS_K + 1 + c->ell; }
 // B in 1..4 queries (dq: B x C, dans: B x R); max_ctas limits the single-query grid.
 int zp_launch_gemv(zp_db* db, const uint32_t* dq, uint32_t B, uint32_t* dans, cudaStream_t st,
                    uint32_t max_ctas);

@@ -28,9 +28,9 @@ class FakeBackend:
     def batch_bytes(self, name, B):
         return B * self.per_query
 
-    def launch(self, name, reqs):
-        self.launches.append((self.clock(), name, [r.rid for r in reqs]))
-        self.busy[name] = self.clock() + self.dur
+    def launch(self, name, reqs, slot=0):
+        self.launches.append((self.clock(), name, [r.rid for r in reqs], slot))
+        self.busy[name] = max(self.busy.get(name, -1), self.clock() + self.dur)
         return (name, self.clock() + self.dur)
 
     def poll(self, h):
@@ -52,9 +52,11 @@ def _req(rid, db, t):
 
 
 def test_continuous_batching_and_overlap():
+    """One slot per database: requests that arrive while its batch runs form the next one;
+    batches of different databases overlap."""
     clk = FakeClock()
     be = FakeBackend(clk)
-    srv = Server(be, hbm_budget=10_000, max_batch=8, clock=clk)
+    srv = Server(be, hbm_budget=10_000, max_batch=8, clock=clk, slots=1)
     srv.add_database("a", 10, 10)
     srv.add_database("b", 10, 10)
     srv.submit(_req(0, "a", 0.0))
@@ -78,6 +80,38 @@ def test_continuous_batching_and_overlap():
     assert sorted(r.rid for r in srv.done) == sorted([0, 1, 2, 3, 4, 5] + [101, 102, 103, 104, 105])
     for r in srv.done:
         assert r.T[0] == r.rid and r.t_done >= r.t_launch >= r.t_arrival
+
+
+def test_same_database_batches_overlap():
+    """Two slots per database: a second batch of the same database starts while the first
+    runs, a third waits for a free slot, and every result comes back."""
+    clk = FakeClock()
+    be = FakeBackend(clk)
+    srv = Server(be, hbm_budget=10_000, max_batch=8, clock=clk, slots=2)
+    srv.add_database("a", 10, 10)
+    for rid in range(3):
+        srv.submit(_req(rid, "a", 0.0))
+    srv.step()
+    clk.t = 0.2
+    for rid in (3, 4):
+        srv.submit(_req(rid, "a", 0.2))
+    srv.step()
+    assert [(l[0], l[2], l[3]) for l in be.launches] == [(0.0, [0, 1, 2], 0), (0.2, [3, 4], 1)]
+    assert srv.max_same_db == 2
+    clk.t = 0.5
+    srv.submit(_req(5, "a", 0.5))
+    srv.step()
+    assert len(be.launches) == 2                  # both slots busy: 5 waits
+    clk.t = 1.0
+    srv.step()                                    # the first batch ends; 5 takes its slot
+    assert be.launches[-1] == (1.0, "a", [5], 0)
+    while srv.pending():
+        clk.t += 1.0
+        srv.step()
+    assert sorted(r.rid for r in srv.done) == list(range(6))
+    for r in srv.done:
+        assert r.T[0] == r.rid and r.t_done >= r.t_launch >= r.t_arrival
+    assert srv.report(0.0, clk.t)["max_batches_of_one_db_in_flight"] == 2
 
 
 def test_hbm_budget_limits_batches():
@@ -135,7 +169,7 @@ def test_results_identical_alone_and_in_mix():
 
     n = 256
     ctx = zp.Context(0, n=n)
-    be = ZipBackend(ctx, max_batch=16)
+    be = ZipBackend(ctx, max_batch=16, slots=2)
     shapes = {"small": (600, 700), "mid": (1500, 1100), "wide": (300, 4000)}
     host = {}
     for i, (name, (R, C)) in enumerate(shapes.items()):
@@ -163,8 +197,11 @@ def test_results_identical_alone_and_in_mix():
         cko = synth.ints_to_limbs(synth.uniform_below(moduli[cid], n, 1000 + rid), 64)
         reqs.append((rid, name, cid, q, cko))
 
+    max_same_db = [0]
+
     def serve(batch_all):
-        srv = Server(be, hbm_budget=40 << 30, max_batch=16)
+        # batches of at most 8: a database with more requests fills both of its slots
+        srv = Server(be, hbm_budget=40 << 30, max_batch=8, slots=2)
         for name, (R, C) in shapes.items():
             srv.add_database(name, R, C)
         out = {}
@@ -173,6 +210,7 @@ def test_results_identical_alone_and_in_mix():
                 srv.submit(Request(rid, name, cid, q, cko))
             srv.run_until_idle()
             assert srv.batches < len(reqs)       # requests were really batched together
+            max_same_db[0] = srv.max_same_db
         else:
             for rid, name, cid, q, cko in reqs:
                 srv.submit(Request(rid, name, cid, q, cko))
@@ -186,6 +224,7 @@ def test_results_identical_alone_and_in_mix():
     assert alone.keys() == mix.keys() == set(range(40))
     for rid in range(40):
         assert np.array_equal(alone[rid][0], mix[rid][0]) and np.array_equal(alone[rid][1], mix[rid][1])
+    assert max_same_db[0] >= 2                   # batches of one database overlapped
     # and the results are the oracle's
     P = Params(n=n)
     for rid, name, cid, q, cko in reqs[:4]:
