@@ -25,7 +25,8 @@
 //             cko[b][i] mod p_k = sum_beta byte_beta(cko[b][i]) (2^(8 beta) mod p_k): A = the
 //             256 bytes of every cko[b][i] (K = 256), B = the four bytes c of 2^(8 beta) mod
 //             p_k for 40 primes per N tile (N = 160); the epilogue folds the four sums S_c
-//             of a prime into the residue and writes its bytes as the B operand of MODE_RNS;
+//             of a prime into the residue and writes its bytes as the B operand of MODE_RNS
+//             (whose row sums k_fp16_rowsum takes afterwards);
 //   MODE_CMP  the compression products V[r] = sum_i H[r][i] cko[i] (Algorithm
 //             "ZipPIR", Response, second line): A = the 4 byte planes of the negated
 //             hint, rows ordered (32 rows of plane 0, of plane 1, ...), B = the 256
@@ -120,10 +121,8 @@ struct GemmArgs {
   uint32_t a_rows_per_n;
   // MODE_RES: A row b res_n + i = the 256 bytes of cko[b][i]; output = the B operand of the
   // RNS product (res_out, centred fp16, tile width res_bt, res_nnt N tiles, K pitch res_kp)
-  // and its row byte sums (res_colsum, zeroed by the caller)
   uint32_t res_n, res_bt, res_nnt, res_kp;
   __half* res_out;
-  uint32_t* res_colsum;
 };
 
 __device__ __forceinline__ uint32_t cvt_rn(uint32_t fbits) {
@@ -569,8 +568,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         // single chunk (K = 256). Row b n + i, column (k, c): S_c = sum_beta byte_beta(cko)
         // byte_c(2^(8 beta) mod p_k) < 2^24 once the centring is undone, so the residue is
         // x = sum_c S_c 2^(8c) < 2^48 folded below p (p = 2^27 - dl, dl < 2^12). Its four
-        // bytes go to the rows of the RNS product's B operand (fp16, centred) and their sums
-        // over i to that operand's row sums.
+        // bytes go to the rows of the RNS product's B operand (fp16, centred).
         constexpr int NR = 4 * ZP_RES_KPER;  // columns per tile (N)
         const uint32_t a = acc_cnt & 1u, ra = acc_cnt >> 1;
         if (!warp_wait(&acc_full[a], ra & 1u, abort_flag, args.status)) {
@@ -581,14 +579,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const uint32_t row = mt * BM + e * 32 + lane;  // b n + i
         const bool live = row < args.Mvalid;
         const uint32_t b = live ? row / args.res_n : 0u, i = live ? row - b * args.res_n : 0u;
-        const uint32_t b0 = __shfl_sync(0xffffffffu, b, 0);
-        const bool uni = __all_sync(0xffffffffu, !live || b == b0);  // one query in this warp
         // output addresses: B row (k nnt + b / bt) 4 bt + c bt + b % bt, column i
         const uint32_t bt = args.res_bt;
         const uint64_t nq = (uint64_t)args.res_nnt * 4 * bt;  // B rows per prime
         const uint64_t kp = args.res_kp;
         __half* outp = args.res_out + ((uint64_t)(b / bt) * 4 * bt + b % bt) * kp + i;
-        uint32_t* csp = args.res_colsum + (uint64_t)(b / bt) * 4 * bt + b % bt;
         const uint64_t kstep = nq * kp, cstep = (uint64_t)bt * kp;
         // centring terms: corr_row (this row) in every byte column; per prime j of the tile
         // 128 sum_c cs[4 j + c] 2^(8c) and p_j (lanes hold j = lane and lane + 32, fetched
@@ -630,18 +625,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             const uint64_t t1 = (x & 0x7FFFFFFull) + (x >> 27) * dl;  // < 2^34
             uint32_t v = (uint32_t)((t1 & 0x7FFFFFFull) + (t1 >> 27) * dl);  // < 2^27 + 2^19 < 2p
             if (v >= p) v -= p;
-            __half* o = outp + (uint64_t)k * kstep;
-            uint32_t* csk = csp + (uint64_t)k * nq;
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-              const uint32_t byte = live ? (v >> (8 * c)) & 0xFFu : 0u;
-              if (live) o[c * cstep] = __int2half_rn((int)byte - 128);
-              if (uni) {
-                const uint32_t sum = __reduce_add_sync(0xffffffffu, byte);
-                if (lane == 0 && sum) atomicAdd(csk + c * bt, sum);  // lane 0 holds the query
-              } else if (byte) {
-                atomicAdd(csk + c * bt, byte);
-              }
+            if (live) {
+              __half* o = outp + (uint64_t)k * kstep;
+              uint32_t lo, hi;  // the four bytes as centred fp16 (exact)
+              bytes_to_centred_f16(v, lo, hi);
+              o[0] = __ushort_as_half((unsigned short)(lo & 0xFFFFu));
+              o[cstep] = __ushort_as_half((unsigned short)(lo >> 16));
+              o[2 * cstep] = __ushort_as_half((unsigned short)(hi & 0xFFFFu));
+              o[3 * cstep] = __ushort_as_half((unsigned short)(hi >> 16));
             }
           }
         }
@@ -1092,6 +1083,28 @@ int zp_launch_vmul_tc(zp_db* db, const uint32_t* dCKO, uint32_t B, uint32_t* V4,
 // H' mod p_k (A, built by zp_launch_rns_planes) times the byte planes of cko mod p_k (B).
 namespace {
 
+// Byte sums of rows of a centred fp16 matrix (value + 128 summed over the row): the row sums
+// of the RNS product's B operand, after MODE_RES wrote it. One warp per row; cols % 8 == 0.
+__global__ void k_fp16_rowsum(const __half* __restrict__ M, uint64_t rows, uint32_t cols,
+                              uint32_t* __restrict__ out) {
+  const uint64_t wid = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t lane = threadIdx.x & 31;
+  if (wid >= rows) return;
+  const uint4* src = reinterpret_cast<const uint4*>(M + wid * cols);
+  int32_t s = 0;
+  for (uint32_t c = lane; c < cols / 8; c += 32) {
+    const uint4 v = __ldg(src + c);
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const __half2 h = *reinterpret_cast<const __half2*>(&w[t]);
+      s += __half2int_rn(__low2half(h)) + __half2int_rn(__high2half(h));
+    }
+  }
+  s = (int32_t)__reduce_add_sync(0xffffffffu, (uint32_t)s);
+  if (lane == 0) out[wid] = (uint32_t)(s + 128 * (int32_t)cols);
+}
+
 // Columns i in [n, Kp) of the B operand of the RNS product: the centred value of a zero byte
 // (they enter every sum). grid (ceil(rows / 8)), 256 threads.
 __global__ void k_rns_kpad(__half* __restrict__ Bc, uint64_t rows, uint32_t n, uint32_t Kp) {
@@ -1117,10 +1130,11 @@ int zp_launch_rns_products(zp_db* db, const uint32_t* dCKO, uint32_t B, uint32_t
   if (rc) return rc;
   __half* Bc = static_cast<__half*>(db->s_cko.p);
   uint32_t* colsum = reinterpret_cast<uint32_t*>(static_cast<uint8_t*>(db->s_cko.p) + bc_bytes);
-  ZP_CUDA(cudaMemsetAsync(colsum, 0, cs_bytes, st));
   // cko mod p_k for every query, offset and prime on the tensor cores (MODE_RES): A = the
   // 256 bytes of each cko[b][i] straight from dCKO, B = the context's table of 2^(8 beta) mod
-  // p_k; the epilogue writes the byte planes of the residues into Bc and their sums into colsum
+  // p_k; the epilogue writes the byte planes of the residues into Bc, k_fp16_rowsum their
+  // sums into colsum (rows of queries past B hold whatever the buffer held: their columns of
+  // the product are discarded)
   rc = zp_ensure_res_table(ctx);
   if (rc) return rc;
   uint32_t* ckrs = colsum + brows;  // byte sums of the cko elements
@@ -1154,9 +1168,12 @@ int zp_launch_rns_products(zp_db* db, const uint32_t* dCKO, uint32_t B, uint32_t
     gr.res_nnt = nnt;
     gr.res_kp = Kp;
     gr.res_out = Bc;
-    gr.res_colsum = colsum;
     rc = launch_gemm<MODE_RES, 64>(ctx, tmC, ctx->tmap_resw, gr, st);
     if (rc) return rc;
+    zp_clear_pending_error();
+    ctx->launches++;
+    k_fp16_rowsum<<<(unsigned)((brows * 32 + 255) / 256), 256, 0, st>>>(Bc, brows, Kp, colsum);
+    ZP_CUDA(cudaGetLastError());
   }
   CUtensorMap tmB;
   rc = zp_encode_tmap_2d(&tmB, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, Bc, Kp, brows, (uint64_t)Kp * 2, 64,
