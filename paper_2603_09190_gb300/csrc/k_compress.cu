@@ -12,9 +12,11 @@
 //  * k_pack_reduce: one warp per (query, packed row): the ell rows of V are staged
 //    in shared memory, then Horner evaluation
 //    X = (..((W_{ell-1}) gamma + W_{ell-2}) gamma + ..) gamma + W_0 with
-//    W_j = ans + V of row r' ell + j (X < 2^4064) in registers, then Barrett reduction mod m
-//    (Barrett, CRYPTO '86; the quotient-estimate form of the Handbook of Applied
-//    Cryptography, Alg. 14.42) with the per-client constant mu = floor(2^(64 L) / m).
+//    W_j = ans + V of row r' ell + j (X < 2^4064) in registers; the high words of X are
+//    folded with the client's table of 2^(32 w) mod m (Z = X mod 2^(32 L) + sum_w X_w
+//    (2^(32 w) mod m) < 2^2087, Z == X mod m), then Barrett reduction mod m (Barrett,
+//    CRYPTO '86; the quotient-estimate form of the Handbook of Applied Cryptography, Alg.
+//    14.42) with the per-client constant mu = floor(2^(64 L) / m) on 2-3 quotient words.
 //    Big integers live in shared memory; products are summed per output column in
 //    96-bit accumulators and carries are resolved across the warp with a
 //    generate/propagate ballot (one integer addition over the 32 lane flags).
@@ -138,6 +140,7 @@ struct ClientPtrs {
   const uint32_t* m;
   const uint32_t* mu;
   const uint32_t* mkm;  // RNS: M_k mod m (ZP_RNS_K x L), then m - (M mod m)
+  const uint32_t* pw;   // 2^(32 w) mod m, w = L .. 2L - 2
 };
 
 // grid (ceil(d1p / PACK_WARPS), B), block PACK_WARPS warps, dynamic shared memory
@@ -241,6 +244,35 @@ __global__ void __launch_bounds__(PACK_WARPS * 32)
     warp_normalize<4>(xv, w);
 #pragma unroll
     for (int t = 0; t < 4; ++t) S.X[lane * 4 + t] = w[t];
+  }
+  __syncwarp();
+  if (!PACKED) {
+    // X < 2^4064 (127 words): fold its high words with the client's table, Z = (X mod
+    // 2^(32 L)) + sum_{w = L}^{2L - 2} X_w (2^(32 w) mod m) == X (mod m), Z < 2^2087, so the
+    // Barrett reduction below works on 2-3 quotient words. Lane l sums the columns 2l, 2l+1
+    // (96-bit accumulators; the 63 table rows are coalesced loads).
+    const uint32_t* pw = cl[b].pw;
+    uint32_t a0 = S.X[2 * lane], a1 = 0, a2 = 0, b0 = S.X[2 * lane + 1], b1 = 0, b2 = 0;
+#pragma unroll 8
+    for (int w = L; w < 2 * L - 1; ++w) {
+      const uint32_t x = S.X[w];
+      const uint2 t = __ldg(reinterpret_cast<const uint2*>(pw + (size_t)(w - L) * L) + lane);
+      mac96(a0, a1, a2, x, t.x);
+      mac96(b0, b1, b2, x, t.y);
+    }
+    S.col[2 * lane][0] = a0;
+    S.col[2 * lane][1] = a1;
+    S.col[2 * lane][2] = a2;
+    S.col[2 * lane + 1][0] = b0;
+    S.col[2 * lane + 1][1] = b1;
+    S.col[2 * lane + 1][2] = b2;
+    __syncwarp();
+    uint32_t zw[3];  // words 3 lane .. 3 lane + 2 of Z
+    warp_cols_to_words<3>(S.col, 2 * L, zw);
+    __syncwarp();
+#pragma unroll
+    for (int t = 0; t < 3; ++t) S.X[lane * 3 + t] = zw[t];
+    S.X[96 + lane] = 0u;
   }
   __syncwarp();
 
@@ -436,18 +468,19 @@ int zp_launch_compress_finish(zp_db* db, zp_client* const* clients, const uint32
   if (rc) return rc;
   ClientPtrs* dcl = static_cast<ClientPtrs*>(db->s_clients.p);
   // upload the per-query client constants only when the list changed
-  bool same = db->cl_cache.size() == 3 * (size_t)B;
+  bool same = db->cl_cache.size() == 4 * (size_t)B;
   for (uint32_t b = 0; same && b < B; ++b)
-    same = db->cl_cache[3 * b] == clients[b]->d_m && db->cl_cache[3 * b + 1] == clients[b]->d_mu &&
-           db->cl_cache[3 * b + 2] == clients[b]->d_mkm;
+    same = db->cl_cache[4 * b] == clients[b]->d_m && db->cl_cache[4 * b + 1] == clients[b]->d_mu &&
+           db->cl_cache[4 * b + 2] == clients[b]->d_mkm && db->cl_cache[4 * b + 3] == clients[b]->d_pow;
   if (!same) {
     std::vector<ClientPtrs> h(B);
-    db->cl_cache.resize(3 * (size_t)B);
+    db->cl_cache.resize(4 * (size_t)B);
     for (uint32_t b = 0; b < B; ++b) {
-      h[b] = ClientPtrs{clients[b]->d_m, clients[b]->d_mu, clients[b]->d_mkm};
-      db->cl_cache[3 * b] = clients[b]->d_m;
-      db->cl_cache[3 * b + 1] = clients[b]->d_mu;
-      db->cl_cache[3 * b + 2] = clients[b]->d_mkm;
+      h[b] = ClientPtrs{clients[b]->d_m, clients[b]->d_mu, clients[b]->d_mkm, clients[b]->d_pow};
+      db->cl_cache[4 * b] = clients[b]->d_m;
+      db->cl_cache[4 * b + 1] = clients[b]->d_mu;
+      db->cl_cache[4 * b + 2] = clients[b]->d_mkm;
+      db->cl_cache[4 * b + 3] = clients[b]->d_pow;
     }
     // pageable source: the copy is staged before cudaMemcpyAsync returns
     cudaError_t e = cudaMemcpyAsync(dcl, h.data(), B * sizeof(ClientPtrs), cudaMemcpyHostToDevice, st);

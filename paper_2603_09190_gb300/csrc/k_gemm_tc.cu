@@ -90,7 +90,7 @@ struct Cfg {
   static constexpr int BST = A16 ? KPS * 4 * BT * BK * 2
                                  : ((ANS_BYTES && ZP_ANS_FIT) ? 4 * BT * BK * 2 : B_MAX_BYTES);  // B stage stride
   static constexpr int AST = KPS * A16_BYTES;                              // A stage stride
-  static constexpr int SB = A16 ? (MODE == MODE_RNS ? (BT == 32 ? 2 : 3)  // the RNS epilogue stages rows
+  static constexpr int SB = A16 ? (MODE == MODE_RNS ? (BT == 32 ? 3 : 4)  // with the RNS epilogue's staging: 227 KiB
                                                    : (BT == 16 ? 4 : (BT == 32 ? 3 : 4)))
                                 : ((MODE == MODE_CMP || MODE == MODE_RNS) ? 3 : (ANS_BYTES ? ZP_ANS_SB : 4));
   static constexpr int SA = SB;  // the A and B stages of a K block are filled and freed together

@@ -1046,21 +1046,36 @@ extern "C" int zp_register_client(zp_ctx* c, const uint32_t* hM, uint32_t L, zp_
         br = (t >> 63) & 1u;
       }
     }
+    // 2^(32 w) mod m, w = L .. 2L - 2 (each from the previous one times 2^32)
+    std::vector<uint32_t> pw((size_t)(L - 1) * L, 0);
+    {
+      std::vector<uint32_t> x(L + 1, 0);
+      x[L] = 1;  // 2^(32 L)
+      std::vector<uint32_t> t = big_barrett(x, m, mu);
+      for (uint32_t w = 0; w + 1 < L; ++w) {
+        t.resize(L, 0);
+        std::copy(t.begin(), t.end(), pw.begin() + (size_t)w * L);
+        std::vector<uint32_t> sh(L + 1, 0);
+        std::copy(t.begin(), t.end(), sh.begin() + 1);
+        t = big_barrett(sh, m, mu);
+      }
+    }
     ZP_ON_DEVICE(c->device);
     zp_client* cl = new zp_client();
     cl->ctx = c;
     cl->device = c->device;
     cl->L = L;
-    cl->d_m = cl->d_mu = cl->d_m2 = cl->d_r1 = cl->d_r2 = cl->d_mkm = nullptr;
+    cl->d_m = cl->d_mu = cl->d_m2 = cl->d_r1 = cl->d_r2 = cl->d_mkm = cl->d_pow = nullptr;
     cl->m2inv = m2inv;
     cl->h_m = m;
     auto free_all = [cl]() {
-      for (uint32_t* p : {cl->d_m, cl->d_mu, cl->d_m2, cl->d_r1, cl->d_r2, cl->d_mkm})
+      for (uint32_t* p : {cl->d_m, cl->d_mu, cl->d_m2, cl->d_r1, cl->d_r2, cl->d_mkm, cl->d_pow})
         if (p) cudaFree(p);
     };
     if (cudaMalloc(&cl->d_m, L * 4) != cudaSuccess || cudaMalloc(&cl->d_mu, (L + 1) * 4) != cudaSuccess ||
         cudaMalloc(&cl->d_m2, L2 * 4) != cudaSuccess || cudaMalloc(&cl->d_r1, L2 * 4) != cudaSuccess ||
-        cudaMalloc(&cl->d_r2, L2 * 4) != cudaSuccess || cudaMalloc(&cl->d_mkm, mkm.size() * 4) != cudaSuccess) {
+        cudaMalloc(&cl->d_r2, L2 * 4) != cudaSuccess || cudaMalloc(&cl->d_mkm, mkm.size() * 4) != cudaSuccess ||
+        cudaMalloc(&cl->d_pow, pw.size() * 4) != cudaSuccess) {
       free_all();
       delete cl;
       return zp_set_error(ZP_ENOMEM, "zp_register_client: cudaMalloc");
@@ -1071,6 +1086,7 @@ extern "C" int zp_register_client(zp_ctx* c, const uint32_t* hM, uint32_t L, zp_
     if (e == cudaSuccess) e = cudaMemcpy(cl->d_r1, r1.data(), L2 * 4, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(cl->d_r2, r2.data(), L2 * 4, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(cl->d_mkm, mkm.data(), mkm.size() * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(cl->d_pow, pw.data(), pw.size() * 4, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
       free_all();
       delete cl;
@@ -1087,7 +1103,7 @@ extern "C" int zp_client_destroy(zp_client* cl) {
   if (!cl) return ZP_OK;
   zp_device_scope _zp_scope(cl->device);
   cudaDeviceSynchronize();
-  for (uint32_t* p : {cl->d_m, cl->d_mu, cl->d_m2, cl->d_r1, cl->d_r2, cl->d_mkm})
+  for (uint32_t* p : {cl->d_m, cl->d_mu, cl->d_m2, cl->d_r1, cl->d_r2, cl->d_mkm, cl->d_pow})
     if (p) cudaFree(p);
   delete cl;
   return ZP_OK;
