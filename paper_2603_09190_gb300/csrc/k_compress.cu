@@ -268,7 +268,7 @@ __global__ void __launch_bounds__(PACK_WARPS * 32)
     S.col[2 * lane + 1][2] = b2;
     __syncwarp();
     uint32_t zw[3];  // words 3 lane .. 3 lane + 2 of Z
-    warp_cols_to_words<3>(S.col, 2 * L, zw);
+    warp_cols_to_words<3>(S.col, L, zw);  // the L columns above (words up to L + 1)
     __syncwarp();
 #pragma unroll
     for (int t = 0; t < 3; ++t) S.X[lane * 3 + t] = zw[t];
