@@ -12,7 +12,7 @@
 //  * k_pack_reduce: one warp per (query, packed row): the ell rows of V are staged
 //    in shared memory, then Horner evaluation
 //    X = (..((W_{ell-1}) gamma + W_{ell-2}) gamma + ..) gamma + W_0 with
-//    W_j = ans + V of row r' ell + j (X < 2^4064) in registers; the high words of X are
+//    W_j = ans + V of row r' ell + j (X < 2^4096) in registers; the high words of X are
 //    folded with the client's table of 2^(32 w) mod m (Z = X mod 2^(32 L) + sum_w X_w
 //    (2^(32 w) mod m) < 2^2087, Z == X mod m), then Barrett reduction mod m (Barrett,
 //    CRYPTO '86; the quotient-estimate form of the Handbook of Applied Cryptography, Alg.
@@ -125,7 +125,7 @@ __device__ __forceinline__ void warp_cols_to_words(const uint32_t (*col)[3], int
 }
 
 struct PackBarrett {
-  uint32_t X[ZP_XW];        // the packed sum before reduction (< 2^4064)
+  uint32_t X[ZP_XW];        // the packed sum before reduction (< 2^4096)
   uint32_t ans[64];         // the ell (< 64) answers of the packed row
   uint32_t col[160][3];     // product columns
   uint32_t q1[ZP_MAX_L + 1];
@@ -140,7 +140,7 @@ struct ClientPtrs {
   const uint32_t* m;
   const uint32_t* mu;
   const uint32_t* mkm;  // RNS: M_k mod m (ZP_RNS_K x L), then m - (M mod m)
-  const uint32_t* pw;   // 2^(32 w) mod m, w = L .. 2L - 2
+  const uint32_t* pw;   // 2^(32 w) mod m, w = L .. 2L - 1
 };
 
 // grid (ceil(d1p / PACK_WARPS), B), block PACK_WARPS warps, dynamic shared memory
@@ -247,14 +247,15 @@ __global__ void __launch_bounds__(PACK_WARPS * 32)
   }
   __syncwarp();
   if (!PACKED) {
-    // X < 2^4064 (127 words): fold its high words with the client's table, Z = (X mod
-    // 2^(32 L)) + sum_{w = L}^{2L - 2} X_w (2^(32 w) mod m) == X (mod m), Z < 2^2087, so the
-    // Barrett reduction below works on 2-3 quotient words. Lane l sums the columns 2l, 2l+1
-    // (96-bit accumulators; the 63 table rows are coalesced loads).
+    // X < 2^(64 L) (2L words; 4077 bits for the binary secret at n = 48): fold its high words
+    // with the client's table, Z = (X mod 2^(32 L)) + sum_{w = L}^{2L - 1} X_w (2^(32 w) mod m)
+    // == X (mod m), Z < 2^2087, so the Barrett reduction below works on 2-3 quotient words.
+    // Lane l sums the columns 2l, 2l+1 (96-bit accumulators; the L table rows are coalesced
+    // loads).
     const uint32_t* pw = cl[b].pw;
     uint32_t a0 = S.X[2 * lane], a1 = 0, a2 = 0, b0 = S.X[2 * lane + 1], b1 = 0, b2 = 0;
 #pragma unroll 8
-    for (int w = L; w < 2 * L - 1; ++w) {
+    for (int w = L; w < 2 * L; ++w) {
       const uint32_t x = S.X[w];
       const uint2 t = __ldg(reinterpret_cast<const uint2*>(pw + (size_t)(w - L) * L) + lane);
       mac96(a0, a1, a2, x, t.x);

@@ -1046,13 +1046,13 @@ extern "C" int zp_register_client(zp_ctx* c, const uint32_t* hM, uint32_t L, zp_
         br = (t >> 63) & 1u;
       }
     }
-    // 2^(32 w) mod m, w = L .. 2L - 2 (each from the previous one times 2^32)
-    std::vector<uint32_t> pw((size_t)(L - 1) * L, 0);
+    // 2^(32 w) mod m, w = L .. 2L - 1 (each from the previous one times 2^32)
+    std::vector<uint32_t> pw((size_t)L * L, 0);
     {
       std::vector<uint32_t> x(L + 1, 0);
       x[L] = 1;  // 2^(32 L)
       std::vector<uint32_t> t = big_barrett(x, m, mu);
-      for (uint32_t w = 0; w + 1 < L; ++w) {
+      for (uint32_t w = 0; w < L; ++w) {
         t.resize(L, 0);
         std::copy(t.begin(), t.end(), pw.begin() + (size_t)w * L);
         std::vector<uint32_t> sh(L + 1, 0);

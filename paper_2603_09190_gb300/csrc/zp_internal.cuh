@@ -94,8 +94,8 @@ struct zp_client {
   uint32_t m2inv;  // -(m^2)^{-1} mod 2^32
   // CRT of the RNS compression: M_k mod m (ZP_RNS_K x L limbs), then m - (M mod m) (L limbs)
   uint32_t* d_mkm;
-  // 2^(32 w) mod m for w = L .. 2L - 2 ((L - 1) x L limbs): folds the high words of the
-  // packed sum before its reduction mod m
+  // 2^(32 w) mod m for w = L .. 2L - 1 (L x L limbs): folds the high words of the packed
+  // sum before its reduction mod m
   uint32_t* d_pow;
 };
 
