@@ -251,10 +251,10 @@ int zp_client_hint(zp_db* db, const zp_client* cl, const uint32_t* dCkr, uint32_
  *  - "gemv_cfg_alone": the GEMV configuration of a single-query answer on the whole GPU;
  *  - "overlap_sms" and "gemv_cfg_shared": the SM split of the single-query zp_respond (0 and
  *    24%..52% of the SMs) and the GEMV configuration beside the compression products;
- *  - "answer_bt_small/mid/large": the tile width (16, 32 or 64 queries) of the tensor-core
- *    answers for batches of 16, 32 and 64 queries, and "answer_fp16" (the fp16 copy of D
+ *  - "answer_bt_16/32/64/128": the tile width (16, 32 or 64 queries) of the tensor-core
+ *    answers for batches of 16, 32, 64 and 128 queries, and "answer_fp16" (the fp16 copy of D
  *    against its bytes, when the copy exists);
- *  - "rns_bt_small/mid/large" and "batch_overlap": the tile width of the RNS products and
+ *  - "rns_bt_16/32/64/128" and "batch_overlap": the tile width of the RNS products and
  *    whether a batch's products run beside its answers (when the RNS path was measured).
  * chosen (may be NULL): receives the first three values ("gemv_max_batch", "rns_min_batch",
  * "overlap_sms"); zp_get_option reads the others. Synchronous on `stream`; about a second
@@ -302,10 +302,10 @@ int zp_stale_rows(const zp_db* db, uint32_t* count);
  *                    query run while the answer uses the other SMs (zp_respond,
  *                    zp_compress_products, single-query zp_answer); 0 = no overlap.
  *                    Default: about 3/8 of the SMs (56 of 152) on GPUs with >= 64 SMs.
- *   "answer_bt_small", "answer_bt_mid", "answer_bt_large": queries per N tile (16, 32, 64;
- *                    at most 16 / 32 / 64) of the tensor-core answers for batches of <= 16,
- *                    <= 32 and more queries (defaults 16, 32, 64); "rns_bt_small", ...: the
- *                    same for the RNS products;
+ *   "answer_bt_16", "answer_bt_32", "answer_bt_64", "answer_bt_128": queries per N tile
+ *                    (16, 32 or 64; at most 16 / 32 / 64 / 64) of the tensor-core answers for
+ *                    batches of <= 16, <= 32, <= 64 and more queries (defaults 16, 32, 64,
+ *                    64); "rns_bt_16", ...: the same for the RNS products;
  *   "gemv_cfg_alone", "gemv_cfg_shared": the GEMV configuration on the whole GPU and beside
  *                    the compression products: 1 = 8 consumer warps x 12 stages of 64-row
  *                    tiles (default alone), 2 = 16 warps x 6 stages of 128-row tiles

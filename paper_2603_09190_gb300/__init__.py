@@ -540,8 +540,8 @@ class Database:
         return out
 
     TUNED = ("gemv_max_batch", "rns_min_batch", "overlap_sms", "gemv_cfg_alone", "gemv_cfg_shared",
-             "answer_bt_small", "answer_bt_mid", "answer_bt_large", "answer_fp16",
-             "rns_bt_small", "rns_bt_mid", "rns_bt_large", "batch_overlap")
+             "answer_bt_16", "answer_bt_32", "answer_bt_64", "answer_bt_128", "answer_fp16",
+             "rns_bt_16", "rns_bt_32", "rns_bt_64", "rns_bt_128", "batch_overlap")
 
     def autotune(self, stream=None) -> dict:
         """Measures and sets the context's thresholds, tile widths, GEMV configurations and SM

@@ -338,7 +338,7 @@ extern "C" int zp_init(int device, const zp_params* P, zp_ctx** out) {
     c->gemv_max_batch = 4;  // one dp4a pass beats the tensor cores up to 4 queries (1 GiB)
     c->answer_fp16 = 1;
     c->batch_overlap = 1;
-    for (int i = 0; i < 3; ++i) c->ans_bt[i] = c->rns_bt[i] = 16u << i;  // 16, 32, 64
+    for (int i = 0; i < 4; ++i) c->ans_bt[i] = c->rns_bt[i] = 16u << (i < 2 ? i : 2);  // 16, 32, 64, 64
     c->gemv_cfg[0] = 1;  // whole GPU: 8 warps x 12 stages
     c->gemv_cfg[1] = 2;  // beside the products: 16 warps x 6 stages
     {
@@ -432,15 +432,16 @@ extern "C" int zp_set_option(zp_ctx* c, const char* name, int64_t value) {
     c->answer_fp16 = (uint32_t)value;
     return ZP_OK;
   }
-  static const char* bt_names[2][3] = {{"answer_bt_small", "answer_bt_mid", "answer_bt_large"},
-                                       {"rns_bt_small", "rns_bt_mid", "rns_bt_large"}};
+  static const char* bt_names[2][4] = {{"answer_bt_16", "answer_bt_32", "answer_bt_64", "answer_bt_128"},
+                                       {"rns_bt_16", "rns_bt_32", "rns_bt_64", "rns_bt_128"}};
   for (int t = 0; t < 2; ++t)
-    for (int cl = 0; cl < 3; ++cl)
+    for (int cl = 0; cl < 4; ++cl)
       if (k == bt_names[t][cl]) {
-        // at most the class's largest batch (16, 32, 64 queries)
-        if ((value != 16 && value != 32 && value != 64) || value > (16 << cl))
-          return zp_set_error(ZP_EINVAL, "zp_set_option: %s=%lld (16, 32 or 64, at most %d)", name,
-                              (long long)value, 16 << cl);
+        // at most the class's largest batch (16, 32, 64 queries; 64 for the class above 64)
+        const int64_t most = 16 << (cl < 2 ? cl : 2);
+        if ((value != 16 && value != 32 && value != 64) || value > most)
+          return zp_set_error(ZP_EINVAL, "zp_set_option: %s=%lld (16, 32 or 64, at most %lld)", name,
+                              (long long)value, (long long)most);
         (t ? c->rns_bt : c->ans_bt)[cl] = (uint32_t)value;
         return ZP_OK;
       }
@@ -475,12 +476,14 @@ extern "C" int zp_get_option(const zp_ctx* c, const char* name, int64_t* value) 
   else if (k == "gemv_max_batch") *value = c->gemv_max_batch;
   else if (k == "answer_fp16") *value = c->answer_fp16;
   else if (k == "batch_overlap") *value = c->batch_overlap;
-  else if (k == "answer_bt_small") *value = c->ans_bt[0];
-  else if (k == "answer_bt_mid") *value = c->ans_bt[1];
-  else if (k == "answer_bt_large") *value = c->ans_bt[2];
-  else if (k == "rns_bt_small") *value = c->rns_bt[0];
-  else if (k == "rns_bt_mid") *value = c->rns_bt[1];
-  else if (k == "rns_bt_large") *value = c->rns_bt[2];
+  else if (k == "answer_bt_16") *value = c->ans_bt[0];
+  else if (k == "answer_bt_32") *value = c->ans_bt[1];
+  else if (k == "answer_bt_64") *value = c->ans_bt[2];
+  else if (k == "answer_bt_128") *value = c->ans_bt[3];
+  else if (k == "rns_bt_16") *value = c->rns_bt[0];
+  else if (k == "rns_bt_32") *value = c->rns_bt[1];
+  else if (k == "rns_bt_64") *value = c->rns_bt[2];
+  else if (k == "rns_bt_128") *value = c->rns_bt[3];
   else if (k == "gemv_cfg_alone") *value = c->gemv_cfg[0];
   else if (k == "gemv_cfg_shared") *value = c->gemv_cfg[1];
   else return zp_set_error(ZP_EINVAL, "zp_get_option: unknown option '%s'", name);
@@ -1270,13 +1273,13 @@ extern "C" int zp_autotune(zp_db* db, void* stream, int64_t* chosen) {
     zp_ctx* c = db->ctx;
     ZP_ON_DEVICE(c->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const uint32_t BQ = 64, n = c->P.n, L = c->L;
+    const uint32_t BQ = 128, n = c->P.n, L = c->L;
     const int saved_answer = c->answer_path, saved_compress = c->compress_path;
     const uint32_t saved_overlap = c->overlap_sms, saved_gemv = c->gemv_max_batch,
                    saved_rns = c->rns_min_batch, saved_fp16 = c->answer_fp16,
                    saved_bo = c->batch_overlap;
-    uint32_t saved_abt[3], saved_rbt[3], saved_gcfg[2];
-    for (int i = 0; i < 3; ++i) saved_abt[i] = c->ans_bt[i], saved_rbt[i] = c->rns_bt[i];
+    uint32_t saved_abt[4], saved_rbt[4], saved_gcfg[2];
+    for (int i = 0; i < 4; ++i) saved_abt[i] = c->ans_bt[i], saved_rbt[i] = c->rns_bt[i];
     for (int i = 0; i < 2; ++i) saved_gcfg[i] = c->gemv_cfg[i];
     uint32_t *dQ = nullptr, *dAns = nullptr, *dCKO = nullptr, *dT = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -1297,7 +1300,7 @@ extern "C" int zp_autotune(zp_db* db, void* stream, int64_t* chosen) {
       c->rns_min_batch = saved_rns;
       c->answer_fp16 = saved_fp16;
       c->batch_overlap = saved_bo;
-      for (int i = 0; i < 3; ++i) c->ans_bt[i] = saved_abt[i], c->rns_bt[i] = saved_rbt[i];
+      for (int i = 0; i < 4; ++i) c->ans_bt[i] = saved_abt[i], c->rns_bt[i] = saved_rbt[i];
       for (int i = 0; i < 2; ++i) c->gemv_cfg[i] = saved_gcfg[i];
       return rc;
     };
@@ -1402,11 +1405,11 @@ extern "C" int zp_autotune(zp_db* db, void* stream, int64_t* chosen) {
     if (c->answer_path != ZP_PATH_SIMT) {
       const int saved_path = c->answer_path;
       c->answer_path = ZP_PATH_TC;
-      for (int cls_i = 0; cls_i < 3; ++cls_i) {
-        const uint32_t B = 16u << cls_i;
+      for (int cls_i = 0; cls_i < 4; ++cls_i) {
+        const uint32_t B = 16u << cls_i;  // 16, 32, 64, 128 queries
         float best = 1e30f;
         uint32_t best_bt = c->ans_bt[cls_i];
-        for (uint32_t bt = 16; bt <= B; bt *= 2) {
+        for (uint32_t bt = 16; bt <= B && bt <= 64; bt *= 2) {
           c->ans_bt[cls_i] = bt;
           const float t = time_ms([&] { return zp_answer(db, dQ, B, dAns, stream); });
           if (err) return fail(err);
@@ -1430,11 +1433,11 @@ extern "C" int zp_autotune(zp_db* db, void* stream, int64_t* chosen) {
     if (cl && saved_compress == ZP_PATH_AUTO && rns_min && db->d_rns_hpl) {
       std::vector<zp_client*> cls(BQ, cl);
       c->compress_path = ZP_PATH_RNS;
-      for (int cls_i = 0; cls_i < 3; ++cls_i) {
+      for (int cls_i = 0; cls_i < 4; ++cls_i) {
         const uint32_t B = 16u << cls_i;
         float best = 1e30f;
         uint32_t best_bt = c->rns_bt[cls_i];
-        for (uint32_t bt = 16; bt <= B; bt *= 2) {
+        for (uint32_t bt = 16; bt <= B && bt <= 64; bt *= 2) {
           c->rns_bt[cls_i] = bt;
           const float t = time_ms([&] { return zp_compress(db, cls.data(), dAns, dCKO, B, dT, stream); });
           if (err) return fail(err);

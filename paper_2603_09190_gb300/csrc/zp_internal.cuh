@@ -62,8 +62,8 @@ struct zp_ctx {
   uint32_t answer_fp16;    // tensor-core answers read a database's fp16 copy when it has one
   uint32_t batch_overlap;  // zp_respond runs a batch's compression products beside its answers
   // tile widths (queries per N tile: 16, 32 or 64) of the tensor-core answers and of the RNS
-  // products for batches of <= 16, <= 32 and > 32 queries (zp_autotune measures them)
-  uint32_t ans_bt[3], rns_bt[3];
+  // products for batches of <= 16, <= 32, <= 64 and > 64 queries (zp_autotune measures them)
+  uint32_t ans_bt[4], rns_bt[4];
   // GEMV configuration on the whole GPU [0] and beside the compression products [1]:
   // 1 = 8 consumer warps x 12 stages of 64 rows, 2 = 16 warps x 6 stages of 128 rows
   uint32_t gemv_cfg[2];
@@ -200,9 +200,9 @@ int zp_encode_tmap_2d(CUtensorMap* map, CUtensorMapDataType dt, const void* base
 
 // ------------------------------------------------------------------ kernel launchers
 // (defined in the k_*.cu translation units; all asynchronous on `st`)
-// tile width for a batch of B queries from a per-class table (B <= 16, <= 32, > 32)
-static inline uint32_t zp_pick_bt(const uint32_t (&table)[3], uint32_t B) {
-  return table[B <= 16 ? 0 : (B <= 32 ? 1 : 2)];
+// tile width for a batch of B queries from a per-class table (B <= 16, <= 32, <= 64, > 64)
+static inline uint32_t zp_pick_bt(const uint32_t (&table)[4], uint32_t B) {
+  return table[B <= 16 ? 0 : (B <= 32 ? 1 : (B <= 64 ? 2 : 3))];
 }
 int zp_launch_rowsum(const zp_db* db, const uint32_t* rows, uint32_t nrows, cudaStream_t st);
 int zp_launch_rowsum_buf(zp_ctx* ctx, const uint8_t* M, uint64_t ld, uint32_t rows, uint32_t cols,

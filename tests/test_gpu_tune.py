@@ -41,15 +41,16 @@ def test_autotune_then_exact(zp):
     assert got["rns_min_batch"] in (0, 2, 4, 6, 8, 12, 16)
     assert 0 <= got["overlap_sms"] < 200
     assert got["gemv_cfg_alone"] in (1, 2) and got["gemv_cfg_shared"] in (1, 2)
-    assert got["answer_bt_small"] == 16 and got["answer_bt_mid"] in (16, 32)
-    assert got["answer_bt_large"] in (16, 32, 64) and got["answer_fp16"] in (0, 1)
-    assert got["rns_bt_small"] == 16 and got["rns_bt_large"] in (16, 32, 64)
+    assert got["answer_bt_16"] == 16 and got["answer_bt_32"] in (16, 32)
+    assert got["answer_bt_64"] in (16, 32, 64) and got["answer_bt_128"] in (16, 32, 64)
+    assert got["answer_fp16"] in (0, 1)
+    assert got["rns_bt_16"] == 16 and got["rns_bt_128"] in (16, 32, 64)
     assert got["batch_overlap"] in (0, 1)
     for k, v in got.items():
         assert zp.zp_get_option_value(c, k) == v
     assert c.device_status() == 0
     Hn = lwe.hint_neg(D, A)
-    for B in (1, 3, 9, 20, 64):
+    for B in (1, 3, 9, 20, 64, 100):
         Q = synth.uniform_queries(B, C, 20 + B)
         ans = db.answer(u32_dev(Q))
         assert np.array_equal(ans.cpu().numpy().view(np.uint32), lwe.matmat_mod_q(D, Q.T).T)
@@ -63,7 +64,7 @@ def test_autotune_then_exact(zp):
             assert synth.limbs_to_ints(Th[b]) == zippir.compress_rows(a_h[b], Hn, ckos[b], m, P)
 
 
-@pytest.mark.parametrize("B", [16, 32, 64])
+@pytest.mark.parametrize("B", [16, 32, 64, 128])
 def test_every_tile_width_exact(zp, B):
     """Every tile width the tuner can choose for a batch class, for the answers (byte and
     fp16 operands) and for the RNS products, gives the oracle's bits."""
@@ -85,13 +86,13 @@ def test_every_tile_width_exact(zp, B):
     cl = c.register_client(m)
     ckos = [synth.uniform_below(m, n, 74 + b) for b in range(B)]
     CKO = u32_dev(np.stack([synth.ints_to_limbs(x, 64) for x in ckos]))
-    cls_name = {16: "small", 32: "mid", 64: "large"}[B]
+    cls_name = str(B)
     first = None
     for fp16 in (False, True):
         if fp16:
             db.prepare_fp16()
         for bt in (16, 32, 64):
-            if bt > B:
+            if bt > min(B, 64):
                 continue
             c.set_option("answer_bt_" + cls_name, bt)
             c.set_option("rns_bt_" + cls_name, bt)
@@ -105,5 +106,5 @@ def test_every_tile_width_exact(zp, B):
                     assert synth.limbs_to_ints(T[b]) == zippir.compress_rows(a_h[b], Hn, ckos[b], m, P)
             assert np.array_equal(T, first), (fp16, bt)
     with pytest.raises(zp.ZipPIRError):
-        c.set_option("answer_bt_small", 32)
+        c.set_option("answer_bt_16", 32)
     assert c.device_status() == 0
