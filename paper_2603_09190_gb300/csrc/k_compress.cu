@@ -337,15 +337,15 @@ __global__ void __launch_bounds__(PACK_WARPS * 32)
 }
 
 // Residue-number-system path, step 1 of the reduction (Sec. 5.2): from the residues
-// X[b][r'][k] = H'[r', :] . cko[b] mod p_k, y_k = X_k (M/p_k)^{-1} mod p_k and alpha =
-// floor(sum_k y_k / p_k), so that H'.cko = sum_k y_k M/p_k - alpha M. The sum is taken in
+// X[b][k][r'] = H'[r', :] . cko[b] mod p_k (row pitch Rq), y_k = X_k (M/p_k)^{-1} mod p_k
+// and alpha = floor(sum_k y_k / p_k), so that H'.cko = sum_k y_k M/p_k - alpha M. The sum is taken in
 // 64.64 fixed point with integer arithmetic only: S = sum_k y_k floor(2^64 / p_k) (128-bit
 // accumulators) is below 2^64 sum_k y_k / p_k by less than 153 2^27 < 2^34.3 units, and
 // H'.cko < M 2^-26 puts the fractional part of sum_k y_k / p_k in [0, 2^-26), so
 // floor((S + 2^35) / 2^64) = alpha exactly. y_k = X_k inv_k mod p_k by two pseudo-Mersenne
 // folds (p = 2^27 - dl, dl < 2^12). Written as the byte planes of the CRT product's A
-// operand: row b 4 Rq + 128 g + 32 a + t (r' = 32 g + t) holds byte a of y_k in column k <
-// ZP_RNS_K and of alpha in column ZP_RNS_K; packed rows r' in [d1', Rq) are zero. yrs: the
+// operand: row (4 b + a) Rq + r' holds byte a of y_k in column k < ZP_RNS_K and of alpha in
+// column ZP_RNS_K; packed rows r' in [d1', Rq) are zero. yrs: the
 // byte sums of those rows. Columns ZP_RNS_K + 1 + j (j < ell) hold the answers ans[b][r' ell
 // + j] (zero past R), which the CRT product weighs by gamma^j: the packed answer b'. One warp
 // per (query, packed row < Rq).
@@ -360,14 +360,14 @@ __global__ void k_crt_prep(const uint32_t* __restrict__ X, uint32_t B, uint32_t 
   constexpr int QK = (ZP_RNS_K + 1 + 64 + 31) / 32;  // residues, alpha, up to 64 answers
   uint32_t y[QK];
   uint64_t s_lo = 0, s_hi = 0;  // 128-bit sum of y_k floor(2^64 / p_k)
-  const uint32_t* Xr = X + ((uint64_t)b * d1p + rp) * ZP_RNS_K;
+  const uint32_t* Xr = X + (uint64_t)b * ZP_RNS_K * Rq + rp;  // X[b][k][rp], row pitch Rq
 #pragma unroll
   for (int q = 0; q < QK; ++q) {
     const uint32_t k = lane + 32u * q;
     y[q] = 0u;
     if (rp < d1p && k < ZP_RNS_K) {
       const uint32_t p = rns->p[k], dl = (1u << 27) - p;
-      const uint64_t x = (uint64_t)__ldg(Xr + k) * rns->inv[k];             // < 2^54
+      const uint64_t x = (uint64_t)__ldg(Xr + (uint64_t)k * Rq) * rns->inv[k];  // < 2^54
       const uint64_t t1 = (x & 0x7FFFFFFull) + (x >> 27) * dl;             // < 2^40
       uint32_t v = (uint32_t)((t1 & 0x7FFFFFFull) + (t1 >> 27) * dl);       // < 2^27 + 2^25
       if (v >= p) v -= p;
@@ -397,10 +397,10 @@ __global__ void k_crt_prep(const uint32_t* __restrict__ X, uint32_t B, uint32_t 
       y[q] = (rp < d1p && r < R) ? __ldg(ans + (uint64_t)b * R + r) : 0u;
     }
   }
-  const uint64_t row0 = (uint64_t)b * 4 * Rq + 128ull * (rp >> 5) + (rp & 31u);
+  const uint64_t row0 = (uint64_t)b * 4 * Rq + rp;
 #pragma unroll
   for (int a = 0; a < 4; ++a) {
-    uint8_t* dst = Yp + (row0 + 32u * a) * ypitch;
+    uint8_t* dst = Yp + (row0 + (uint64_t)a * Rq) * ypitch;
     uint32_t sum = 0;
 #pragma unroll
     for (int q = 0; q < QK; ++q) {
@@ -412,7 +412,7 @@ __global__ void k_crt_prep(const uint32_t* __restrict__ X, uint32_t B, uint32_t 
       }
     }
     sum = __reduce_add_sync(0xffffffffu, sum);
-    if (lane == 0) yrs[row0 + 32u * a] = sum;
+    if (lane == 0) yrs[row0 + (uint64_t)a * Rq] = sum;
   }
 }
 
@@ -432,7 +432,7 @@ int zp_launch_compress_products(zp_db* db, const uint32_t* dCKO, uint32_t B, cud
                      B >= ctx->rns_min_batch));
   if (rns) {
     int rc = zp_ensure_rns(db, st);
-    if (!rc) rc = zp_scratch_reserve(&db->s_v, (size_t)B * db->d1p * ZP_RNS_K * sizeof(uint32_t));
+    if (!rc) rc = zp_scratch_reserve(&db->s_v, (size_t)B * ZP_RNS_K * db->Rq * sizeof(uint32_t));
     if (!rc) rc = zp_launch_rns_products(db, dCKO, B, static_cast<uint32_t*>(db->s_v.p), st);
     if (rc) return rc;
     db->v_batch = B;

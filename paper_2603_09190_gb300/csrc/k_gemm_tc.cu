@@ -65,7 +65,7 @@ constexpr int NTHREADS = 384;
 constexpr int STG_PITCH = 67;                // words per staged row (odd: no bank conflicts)
 constexpr int STG_BYTES = 4 * 32 * STG_PITCH * 4;
 
-enum { MODE_ANS = 0, MODE_HINT = 1, MODE_CMP = 2, MODE_RNS = 3, MODE_RES = 4 };
+enum { MODE_ANS = 0, MODE_HINT = 1, MODE_CMP = 2, MODE_RNS = 3, MODE_RES = 4, MODE_CRT = 5 };
 
 // Three rings: B (fp16, from L2: deep, it is the largest operand), A as bytes (from
 // HBM, L2-prefetched) and A as fp16 (written by the converters just before the MMA).
@@ -92,12 +92,17 @@ struct Cfg {
   static constexpr int AST = KPS * A16_BYTES;                              // A stage stride
   static constexpr int SB = A16 ? (MODE == MODE_RNS ? (BT == 32 ? 3 : 4)  // with the RNS epilogue's staging: 227 KiB
                                                    : (BT == 16 ? 4 : (BT == 32 ? 3 : 4)))
-                                : ((MODE == MODE_CMP || MODE == MODE_RNS) ? 3 : (ANS_BYTES ? ZP_ANS_SB : 4));
+                                : ((MODE == MODE_CMP || MODE == MODE_RNS || MODE == MODE_CRT) ? 3
+                                                                                   : (ANS_BYTES ? ZP_ANS_SB : 4));
   static constexpr int SA = SB;  // the A and B stages of a K block are filled and freed together
+  // epilogue warps: with an fp16 A operand the converter warps 8-11 have no conversion to do,
+  // so the RNS product (whose epilogue bounds it) drains TMEM with eight warps, two per lane
+  // quarter, each taking half of the tile's queries
+  static constexpr int EPW = (A16 && MODE == MODE_RNS) ? 8 : 4;
   // stages of two K blocks of A bytes: the ring that hides the HBM latency
   static constexpr int SU_FIT = (224 * 1024 - SB * BST - SA * AST) / U8_STAGE;
   static constexpr int SU = A16 ? 0 : (ANS_BYTES ? (ZP_ANS_SU < SU_FIT ? ZP_ANS_SU : SU_FIT) : 2);
-  static constexpr int STG = (MODE == MODE_CMP || MODE == MODE_RNS) ? STG_BYTES : 0;
+  static constexpr int STG = (MODE == MODE_CMP || MODE == MODE_RNS || MODE == MODE_CRT) ? STG_BYTES : 0;
   static constexpr int SMEM = SB * BST + SA * AST + SU * U8_STAGE + STG + 1024 + 512;
   static_assert(SMEM <= 232448, "shared memory above the per-block limit");
   static_assert(A16 || SU >= 1, "at least one byte stage");
@@ -114,7 +119,7 @@ struct GemmArgs {
   uint32_t Rp;                // CMP: plane stride (rows) of the output
   uint32_t* status;
   // MODE_RNS: the M tiles of prime k are k * mt_per_prime ..; its B rows start at
-  // k * num_n_tiles * N; out[(b d1p + r') ZP_RNS_K + k]
+  // k * num_n_tiles * N; out[(b ZP_RNS_K + k) Rp + r'] (Rp = Rq)
   uint32_t mt_per_prime, d1p;
   const zp_rns_dev* rns;
   // MODE_CMP: the A rows of N tile nt start at nt * a_rows_per_n (0: one A for every N tile)
@@ -152,20 +157,39 @@ __device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity,
   return ok != 0;
 }
 
-// AND of `pred` over the 128 threads of the four epilogue warps (named barrier 1).
-__device__ __forceinline__ bool bar_and_128(bool pred) {
+// AND of `pred` over the NT threads of the epilogue warps (named barrier 1).
+template <int NT = 128>
+__device__ __forceinline__ bool bar_and_epi(bool pred) {
   uint32_t r;
   asm volatile(
       "{\n"
       ".reg .pred p, q;\n"
       "setp.ne.u32 p, %1, 0;\n"
-      "bar.red.and.pred q, 1, 128, p;\n"
+      "bar.red.and.pred q, 1, %2, p;\n"
       "selp.u32 %0, 1, 0, q;\n"
       "}\n"
       : "=r"(r)
-      : "r"((uint32_t)pred)
+      : "r"((uint32_t)pred), "n"(NT)
       : "memory");
   return r != 0;
+}
+// Named barrier 1 over the NT threads of the epilogue warps.
+template <int NT = 128>
+__device__ __forceinline__ void bar_epi() {
+  asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory");
+}
+
+// Static persistent schedule: CTA c takes tiles c, c + G, c + 2G, .. (G = gridDim.x). MODE_CRT
+// tiles come in pairs (the two column halves of one M tile) that one CTA takes back to back,
+// so that the epilogue carries the lower half's carry into the upper half in a register:
+// tile 2 q + h, CTA c takes pairs c, c + G, ..
+template <int MODE>
+__device__ __forceinline__ uint32_t first_tile() {
+  return MODE == MODE_CRT ? 2u * blockIdx.x : blockIdx.x;
+}
+template <int MODE>
+__device__ __forceinline__ uint32_t next_tile(uint32_t t) {
+  return MODE == MODE_CRT ? ((t & 1u) ? t + 2u * gridDim.x - 1u : t + 1u) : t + gridDim.x;
 }
 
 template <int MODE, int BT, bool A16 = false>
@@ -197,7 +221,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   volatile uint32_t* abort_flag = tmem_holder + 1;
 
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t num_tiles = args.num_m_tiles * args.num_n_tiles;
+  const uint32_t num_tiles = args.num_m_tiles * args.num_n_tiles * (MODE == MODE_CRT ? 2u : 1u);
   const uint32_t N = args.N, nkb = args.nkb;
   constexpr uint32_t KPS = C::KPS;
   const uint32_t nks = nkb / KPS;  // stages per tile (nkb is a multiple of KPS)
@@ -217,7 +241,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
     for (int s = 0; s < 2; ++s) {
       mbar_init(&acc_full[s], 1);
-      mbar_init(&acc_empty[s], 4);
+      mbar_init(&acc_empty[s], C::EPW);
     }
     mbar_init(mma_done, 1);
     *abort_flag = 0u;
@@ -240,7 +264,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       uint32_t cnt = 0;
       bool ok = true;
       constexpr uint32_t PF = 16;  // K blocks of L2 prefetch ahead of the loads
-      uint32_t pf_tile = blockIdx.x, pf_kb = 0;
+      uint32_t pf_tile = first_tile<MODE>(), pf_kb = 0;
       auto pf_step = [&]() {
         if (pf_tile < num_tiles)
           tma_prefetch_l2_2d(&tmA, (int32_t)(pf_kb * BK),
@@ -248,11 +272,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                                        (pf_tile % args.num_n_tiles) * args.a_rows_per_n));
         if (++pf_kb == nkb) {
           pf_kb = 0;
-          pf_tile += gridDim.x;
+          pf_tile = next_tile<MODE>(pf_tile);
         }
       };
       for (uint32_t f = 0; f < PF; ++f) pf_step();
-      for (uint32_t tile = blockIdx.x; ok && tile < num_tiles; tile += gridDim.x) {
+      for (uint32_t tile = first_tile<MODE>(); ok && tile < num_tiles; tile = next_tile<MODE>(tile)) {
         const uint32_t mt = tile / args.num_n_tiles;
         const uint32_t arow = mt * BM + (tile % args.num_n_tiles) * args.a_rows_per_n;
         for (uint32_t ks = 0; ks < nks; ++ks, ++cnt) {
@@ -290,22 +314,35 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       constexpr uint32_t PF = 16;
       // prefetch cursor: (tile, pair of K blocks) PF pairs ahead of the load cursor
       const uint32_t npairs = (nkb + 1) / 2;
-      uint32_t pf_tile = blockIdx.x, pf_p = 0;
+      uint32_t pf_tile = first_tile<MODE>(), pf_p = 0;
+      // coordinates of the pair p of K blocks of a tile's A. MODE_CRT: K block kb of the
+      // product is K block kb % (Kp / BK) of plane kb / (Kp / BK) (Kp a multiple of 2 BK),
+      // rows (query b, plane a, packed row): b a_rows_per_n + a Rp + mt BM
+      auto a_xy = [&](uint32_t t, uint32_t p, int32_t& x, int32_t& y) {
+        if constexpr (MODE == MODE_CRT) {
+          const uint32_t q = t >> 1, b = q / args.num_m_tiles, mt = q % args.num_m_tiles;
+          const uint32_t k0 = p * 2 * BK, a = k0 / args.Kp;
+          x = (int32_t)(k0 - a * args.Kp);
+          y = (int32_t)(b * args.a_rows_per_n + a * args.Rp + mt * BM);
+        } else {
+          x = (int32_t)(p * 2 * BK);
+          y = (int32_t)((t / args.num_n_tiles) * BM + (t % args.num_n_tiles) * args.a_rows_per_n);
+        }
+      };
       auto pf_step = [&]() {
-        if (pf_tile < num_tiles)
-          tma_prefetch_l2_2d(&tmA, (int32_t)(pf_p * 2 * BK),
-                             (int32_t)((pf_tile / args.num_n_tiles) * BM +
-                                       (pf_tile % args.num_n_tiles) * args.a_rows_per_n));
+        if (pf_tile < num_tiles) {
+          int32_t x, y;
+          a_xy(pf_tile, pf_p, x, y);
+          tma_prefetch_l2_2d(&tmA, x, y);
+        }
         if (++pf_p == npairs) {
           pf_p = 0;
-          pf_tile += gridDim.x;
+          pf_tile = next_tile<MODE>(pf_tile);
         }
       };
       for (uint32_t f = 0; f < PF / 2; ++f) pf_step();
       uint32_t su = 0, pu = 0;
-      for (uint32_t tile = blockIdx.x; ok && tile < num_tiles; tile += gridDim.x) {
-        const uint32_t mt = tile / args.num_n_tiles;
-        const uint32_t arow = mt * BM + (tile % args.num_n_tiles) * args.a_rows_per_n;
+      for (uint32_t tile = first_tile<MODE>(); ok && tile < num_tiles; tile = next_tile<MODE>(tile)) {
         for (uint32_t p = 0; p < npairs; ++p, ++cnt) {
           pf_step();
           if (cnt >= (uint32_t)SU && !mbar_wait_abortable(&u8_empty[su], pu ^ 1u, abort_flag,
@@ -314,8 +351,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             break;
           }
           mbar_arrive_expect_tx(&u8_full[su], U8_STAGE);
-          tma_load_2d(u8_ring + su * U8_STAGE, &tmA, (int32_t)(p * 2 * BK), (int32_t)arow,
-                      &u8_full[su]);
+          int32_t ax, ay;
+          a_xy(tile, p, ax, ay);
+          tma_load_2d(u8_ring + su * U8_STAGE, &tmA, ax, ay, &u8_full[su]);
           if (++su == SU) {
             su = 0;
             pu ^= 1u;
@@ -338,7 +376,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       prefetch_tmap(&tmB);
       uint32_t cnt = 0;
       bool ok = true;
-      for (uint32_t tile = blockIdx.x; ok && tile < num_tiles; tile += gridDim.x) {
+      for (uint32_t tile = first_tile<MODE>(); ok && tile < num_tiles; tile = next_tile<MODE>(tile)) {
         const uint32_t nt = tile % args.num_n_tiles;
         // B rows of this tile (RNS: the block of the tile's prime)
         const uint32_t brow0 = nt * N + (MODE == MODE_RNS ? (tile / args.num_n_tiles) /
@@ -353,9 +391,18 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             break;
           }
           mbar_arrive_expect_tx(&b_full[sb], KPS * N * BK * 2);
-          for (uint32_t h = 0; h < KPS; ++h)
-            tma_load_2d(b_ring + sb * C::BST + h * (N * BK * 2), &tmB, (int32_t)((ks * KPS + h) * BK),
-                        (int32_t)brow0, &b_full[sb]);
+          if constexpr (MODE == MODE_CRT) {
+            // plane a of the A rows pairs with the constants' bytes shifted up by a columns:
+            // B rows N h - a .. of query b (rows outside 0..255 read as zero)
+            const uint32_t q = tile >> 1, h = tile & 1u, b = q / args.num_m_tiles;
+            const uint32_t a = ks * BK / args.Kp;
+            tma_load_3d(b_ring + sb * C::BST, &tmB, (int32_t)(ks * BK - a * args.Kp),
+                        (int32_t)(N * h) - (int32_t)a, (int32_t)b, &b_full[sb]);
+          } else {
+            for (uint32_t h = 0; h < KPS; ++h)
+              tma_load_2d(b_ring + sb * C::BST + h * (N * BK * 2), &tmB, (int32_t)((ks * KPS + h) * BK),
+                          (int32_t)brow0, &b_full[sb]);
+          }
         }
       }
       // Stay until the copies issued last have landed (bounded, ignores the abort flag).
@@ -376,7 +423,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const uint64_t bdesc0 = sdesc_k_sw128(smem_u32(b_ring));
       uint32_t sb = 0, pb = 0, sa = 0, pa = 0, acc_cnt = 0;
       bool ok = true;
-      for (uint32_t tile = blockIdx.x; ok && tile < num_tiles; tile += gridDim.x) {
+      for (uint32_t tile = first_tile<MODE>(); ok && tile < num_tiles; tile = next_tile<MODE>(tile)) {
         uint32_t d = tmem_base, kin = 0;
         for (uint32_t ks = 0; ks < nks; ++ks) {
           if (kin == 0) {
@@ -429,13 +476,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         atomicOr(args.status, ZP_DEV_TIMEOUT_GEMM);
     }
     __syncwarp();
-  } else if (warp >= 8) {
+  } else if (warp >= 8 && C::EPW == 4) {
     // ------------------------------------------------------------ converters
     if constexpr (!A16) {
     const uint32_t ct = threadIdx.x - 256;  // 0..127
     uint32_t cnt = 0, su = 0, pu = 0;
     bool ok = true;
-    for (uint32_t tile = blockIdx.x; ok && tile < num_tiles; tile += gridDim.x) {
+    for (uint32_t tile = first_tile<MODE>(); ok && tile < num_tiles; tile = next_tile<MODE>(tile)) {
       for (uint32_t kb = 0; kb < nkb; ++kb, ++cnt) {
         const uint32_t h = kb & 1u;  // which K block of the 128-byte byte rows
         const uint32_t sa = cnt % SA, rra = cnt / SA;
@@ -480,12 +527,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
   } else if (warp >= 4) {
     // ------------------------------------------------------------ epilogue
-    const uint32_t e = warp - 4;  // TMEM lane quarter
+    const uint32_t e = warp & 3u;          // TMEM lane quarter (a warp reads lanes 32 (warp % 4) ..)
+    const uint32_t eh = (warp - 4u) >> 2;  // which half of the queries (eight epilogue warps)
     const uint32_t lane_addr = (32u * e) << 16;
     uint32_t acc_cnt = 0;
     bool ok = true;
     const uint32_t nchunks = (nkb + KCHUNK - 1) / KCHUNK;
-    for (uint32_t tile = blockIdx.x; ok && tile < num_tiles; tile += gridDim.x) {
+    int64_t crt_carry = 0;  // MODE_CRT: carry out of the lower column half of this thread's row
+    for (uint32_t tile = first_tile<MODE>(); ok && tile < num_tiles; tile = next_tile<MODE>(tile)) {
       const uint32_t nt = tile % args.num_n_tiles, mt = tile / args.num_n_tiles;
       if constexpr (MODE == MODE_RNS) {
         // single chunk (n <= 1024). Row (plane e, packed row 32 g + lane) of prime k: column
@@ -494,9 +543,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         // columns of a query into x = sum_c S_c (2^(8(e + c)) mod p) < 2^55 with 64-bit
         // multiply-adds, then reduces x below 2^28 by two pseudo-Mersenne folds (p = 2^27 -
         // dl, dl < 2^12: x = lo + hi 2^27 == lo + hi dl); the four planes are added through
-        // shared memory and reduced once more to [0, p).
+        // shared memory and reduced once more to [0, p). With eight epilogue warps, warp
+        // half eh takes queries [eh BT / 2, (eh + 1) BT / 2).
+        constexpr int EPW = C::EPW, NTE = 32 * EPW;
+        constexpr int QH = BT / (EPW / 4);     // queries of this warp
+        constexpr int GW = QH < 16 ? QH : 16;  // columns per TMEM load
+        const uint32_t q0 = eh * QH;
         const uint32_t a = acc_cnt & 1u, ra = acc_cnt >> 1;
-        if (!bar_and_128(warp_wait(&acc_full[a], ra & 1u, abort_flag, args.status))) {
+        if (!bar_and_epi<NTE>(warp_wait(&acc_full[a], ra & 1u, abort_flag, args.status))) {
           ok = false;
           break;
         }
@@ -507,63 +561,66 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
         for (int c = 0; c < 4; ++c) w[c] = args.rns->pow8[k][e + c];
         // the centring terms: corr_row (this row) times sum_c w[c], and per query the column
-        // sums' 128 sum_c cs[c BT + bl] w[c] (one or two queries per lane, fetched by shuffles;
-        // the row term is this thread's own and is added after the shuffle)
+        // sums' 128 sum_c cs[c BT + bl] w[c] (lane holds queries q0 + 32 h + lane, fetched by
+        // shuffles; the row term is this thread's own and is added after the shuffle)
         const int32_t corr_row =
             (int32_t)(128u * __ldg(args.rowsumA + mt * BM + e * 32 + lane) - 16384u * args.Kp);
         const uint64_t rowterm =
             (uint64_t)((int64_t)corr_row * (int64_t)((uint64_t)w[0] + w[1] + w[2] + w[3]));
         const uint32_t* cs = args.colsum + ((uint64_t)k * args.num_n_tiles + nt) * (4 * BT);
-        constexpr int NH = (BT + 31) / 32;
+        constexpr int NH = (QH + 31) / 32;
         uint64_t qcs[NH];
 #pragma unroll
         for (int h = 0; h < NH; ++h) {
-          const uint32_t bl = 32u * h + lane;
+          const uint32_t bl = q0 + 32u * h + lane;
           uint64_t q = 0;
-          if (bl < (uint32_t)BT) {
+          if (32u * h + lane < (uint32_t)QH) {
 #pragma unroll
             for (int c = 0; c < 4; ++c) q += (uint64_t)(128u * __ldg(cs + c * BT + bl)) * w[c];
           }
           qcs[h] = q;
         }
         constexpr int PITCH = BT + 1;  // odd: conflict-free
-        uint32_t* myst = stg + (e * 32 + lane) * PITCH;
+        uint32_t* myst = stg + (e * 32 + lane) * PITCH + q0;
 #pragma unroll
-        for (int b16 = 0; b16 < BT / 16; ++b16) {
-          uint32_t r[4][16];
+        for (int gq = 0; gq < QH / GW; ++gq) {
+          uint32_t r[4][GW];
 #pragma unroll
-          for (int c = 0; c < 4; ++c)
-            tmem_ld16(tmem_base + lane_addr + a * 256u + (uint32_t)(c * BT + 16 * b16), r[c]);
+          for (int c = 0; c < 4; ++c) {
+            const uint32_t ta = tmem_base + lane_addr + a * 256u + (uint32_t)(c * BT) + q0 + GW * gq;
+            if constexpr (GW == 8) tmem_ld8(ta, r[c]);
+            else tmem_ld16(ta, r[c]);
+          }
           tmem_wait_ld();
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int bl = 16 * b16 + j;
-            uint64_t x = __shfl_sync(0xffffffffu, qcs[bl / 32], bl % 32) + rowterm;
+          for (int j = 0; j < GW; ++j) {
+            const int bq = GW * gq + j;  // query q0 + bq
+            uint64_t x = __shfl_sync(0xffffffffu, qcs[bq / 32], bq % 32) + rowterm;
 #pragma unroll
             for (int c = 0; c < 4; ++c)
               x += (uint64_t)((int64_t)__float2int_rn(__uint_as_float(r[c][j])) * (int64_t)w[c]);
             const uint64_t t1 = (x & 0x7FFFFFFull) + (x >> 27) * dl;            // < 2^41
-            myst[bl] = (uint32_t)((t1 & 0x7FFFFFFull) + (t1 >> 27) * dl);      // < 2^28
+            myst[bq] = (uint32_t)((t1 & 0x7FFFFFFull) + (t1 >> 27) * dl);      // < 2^28
           }
         }
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&acc_empty[a]);
         ++acc_cnt;
-        asm volatile("bar.sync 1, 128;" ::: "memory");
-        const uint32_t tid = e * 32 + lane;
-        for (uint32_t idx = tid; idx < 32u * BT; idx += 128) {
-          const uint32_t t = idx / BT, bl = idx % BT;
+        bar_epi<NTE>();
+        // out[b][k][rp] (row pitch Rp = Rq): a warp writes the 32 packed rows of one query,
+        // one 128-byte line
+        for (uint32_t bl = warp - 4u; bl < (uint32_t)BT; bl += EPW) {
+          const uint32_t t = lane;
           uint32_t y = 0;  // < 2^30
 #pragma unroll
           for (int pl = 0; pl < 4; ++pl) y += stg[(pl * 32 + t) * PITCH + bl];
           y = (y & 0x7FFFFFFu) + (y >> 27) * dl;  // < 2^27 + 7 dl < 2p
           if (y >= p) y -= p;
-          const uint32_t rp = g * 32 + t, b = nt * BT + bl;
-          if (rp < args.d1p && b < args.Bvalid)
-            args.out[((uint64_t)b * args.d1p + rp) * ZP_RNS_K + k] = y;
+          const uint32_t b = nt * BT + bl;
+          if (b < args.Bvalid) args.out[((uint64_t)b * ZP_RNS_K + k) * args.Rp + g * 32 + t] = y;
         }
-        asm volatile("bar.sync 1, 128;" ::: "memory");
+        bar_epi<NTE>();
       } else if constexpr (MODE == MODE_RES) {
         // single chunk (K = 256). Row b n + i, column (k, c): S_c = sum_beta byte_beta(cko)
         // byte_c(2^(8 beta) mod p_k) < 2^24 once the centring is undone, so the residue is
@@ -640,11 +697,99 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         __syncwarp();
         if (lane == 0) mbar_arrive(&acc_empty[a]);
         ++acc_cnt;
+      } else if constexpr (MODE == MODE_CRT) {
+        // single chunk (K = 4 Kp <= 1024). Tile (query b, packed rows 128 mt .., half h):
+        // thread row = packed row rp; column c of the tile is byte position t = 144 h + c of
+        // V = sum_a 2^(8a) (plane a of the A row) . constants, i.e. c_t = sum_{a, k} A_a[k]
+        // B[k][t - a] over 0 <= t - a < 256 (the B rows shifted by a read zero outside), exact
+        // in fp32. Undoing the centring adds, per valid (a, t), 128 rowsum_a + 128 colsum[t - a]
+        // - 16384 Kp. Words w = 36 h .. of V are c_t gathered four at a time with the carry
+        // chain in 64-bit; the lower half's final carry stays in crt_carry for the upper half.
+        const uint32_t q = tile >> 1, hh = tile & 1u;
+        const uint32_t b = q / args.num_m_tiles, mq = q % args.num_m_tiles;
+        const uint32_t a = acc_cnt & 1u, ra = acc_cnt >> 1;
+        if (!bar_and_epi(warp_wait(&acc_full[a], ra & 1u, abort_flag, args.status))) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t rl = e * 32 + lane, rp = mq * BM + rl;
+        uint32_t rs[4];
+#pragma unroll
+        for (int pl = 0; pl < 4; ++pl)
+          rs[pl] = rp < args.Rp
+                       ? __ldg(args.rowsumA + (uint64_t)b * args.a_rows_per_n + pl * args.Rp + rp)
+                       : 0u;
+        // row terms: 128 sum_{a valid} rowsum_a per byte column, as 64-bit words
+        const int64_t r4 = 128 * (int64_t)(rs[0] + rs[1] + rs[2] + rs[3]);
+        const int64_t rw_mid = r4 * 0x01010101ll;
+        const int64_t rw_lo = 128 * ((int64_t)rs[0] + ((int64_t)(rs[0] + rs[1]) << 8) +
+                                     ((int64_t)(rs[0] + rs[1] + rs[2]) << 16)) + (r4 << 24);
+        const int64_t rw_hi = 128 * ((int64_t)(rs[1] + rs[2] + rs[3]) + ((int64_t)(rs[2] + rs[3]) << 8) +
+                                     ((int64_t)rs[3] << 16));
+        // column terms of words w0 + lane and w0 + 32 + lane (fetched by shuffles)
+        const uint32_t w0 = 36u * hh;
+        const uint32_t* cs = args.colsum + (uint64_t)b * 256;
+        const int64_t kterm = 16384 * (int64_t)args.Kp;
+        int64_t cw[2];
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+          const uint32_t w = w0 + 32u * i + lane;
+          int64_t v = 0;
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int t = 4 * (int)w + j;
+            int64_t ct = 0;
+#pragma unroll
+            for (int pl = 0; pl < 4; ++pl)
+              if (t - pl >= 0 && t - pl < 256) ct += 128 * (int64_t)__ldg(cs + t - pl) - kterm;
+            v += ct << (8 * j);
+          }
+          cw[i] = v;
+        }
+        if (hh == 0) crt_carry = 0;
+        int64_t carry = crt_carry;
+        uint32_t* myst = stg + rl * 37;  // 37 words per staged row (odd pitch)
+        const uint32_t tcol = tmem_base + lane_addr + a * 256u;
+#pragma unroll
+        for (int gq = 0; gq < 5; ++gq) {  // words 8 gq .. 8 gq + 7 of the half (the fifth: 4)
+          if (gq == 4 && hh) break;
+          uint32_t r[32];
+          if (gq < 4) tmem_ld32(tcol + 32u * gq, r);
+          else tmem_ld16(tcol + 128u, *reinterpret_cast<uint32_t(*)[16]>(r));
+          tmem_wait_ld();
+#pragma unroll
+          for (int wl = 0; wl < 8; ++wl) {
+            if (gq == 4 && wl >= 4) break;
+            const int wi = 8 * gq + wl;  // word of the half
+            const uint32_t w = w0 + wi;
+            const int64_t c = (int64_t)(((uint64_t)__shfl_sync(0xffffffffu, (uint32_t)(cw[wi / 32] >> 32), wi % 32) << 32) |
+                                        __shfl_sync(0xffffffffu, (uint32_t)cw[wi / 32], wi % 32));
+            int64_t sv = carry + c + (w == 0 ? rw_lo : (w < 64 ? rw_mid : (w == 64 ? rw_hi : 0)));
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+              sv += (int64_t)__float2int_rn(__uint_as_float(r[4 * wl + j])) * (int64_t)(1u << (8 * j));
+            myst[wi] = (uint32_t)sv;
+            carry = sv >> 32;
+          }
+        }
+        crt_carry = carry;
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&acc_empty[a]);
+        ++acc_cnt;
+        bar_epi();
+        // rows of this tile out, coalesced: words w0 .. w0 + nw - 1 of V[b][rp]
+        const uint32_t nw = hh ? (uint32_t)ZP_VW - 36u : 36u;
+        uint32_t* dst = args.out + ((uint64_t)b * args.Rp + (uint64_t)mq * BM) * ZP_VW + w0;
+        for (uint32_t row = e; row < BM && mq * BM + row < args.Mvalid; row += 4)
+          for (uint32_t wl = lane; wl < nw; wl += 32) dst[(uint64_t)row * ZP_VW + wl] = stg[row * 37 + wl];
+        bar_epi();
       } else if constexpr (MODE == MODE_CMP) {
         // single chunk (n <= 1024): byte-column sums -> 67-word integer
         const uint32_t a = acc_cnt & 1u, ra = acc_cnt >> 1;
         // the four epilogue warps agree on the verdict before their named barriers
-        if (!bar_and_128(warp_wait(&acc_full[a], ra & 1u, abort_flag, args.status))) {
+        if (!bar_and_epi(warp_wait(&acc_full[a], ra & 1u, abort_flag, args.status))) {
           ok = false;
           break;
         }
@@ -906,7 +1051,7 @@ __global__ void k_prep_cko(const uint32_t* __restrict__ cko, uint32_t n, uint32_
 
 // per device, mode, tile width and A operand type: the kernel attribute is set (atomic flags:
 // two host threads may both set an attribute, which is harmless)
-std::atomic<bool> g_attr[64][5][3][2];
+std::atomic<bool> g_attr[64][6][3][2];
 
 template <int MODE, int BT, bool A16 = false>
 int launch_gemm(zp_ctx* ctx, const CUtensorMap& tmA, const CUtensorMap& tmB, const GemmArgs& ga,
@@ -1078,7 +1223,7 @@ int zp_launch_vmul_tc(zp_db* db, const uint32_t* dCKO, uint32_t B, uint32_t* V4,
 }
 
 // ---------------------------------------------------------------------------------
-// RNS compression products (Sec. 5.2): X[b][r'][k] = H'[r', :] . cko[b] mod p_k for the
+// RNS compression products (Sec. 5.2): X[b][k][r'] = H'[r', :] . cko[b] mod p_k for the
 // ZP_RNS_K primes, as one grouped tensor-core product: for prime k, the byte planes of
 // H' mod p_k (A, built by zp_launch_rns_planes) times the byte planes of cko mod p_k (B).
 namespace {
@@ -1194,6 +1339,7 @@ int zp_launch_rns_products(zp_db* db, const uint32_t* dCKO, uint32_t B, uint32_t
   ga.status = ctx->d_status;
   ga.mt_per_prime = db->Rq / 32;
   ga.d1p = db->d1p;
+  ga.Rp = db->Rq;  // out[b][k][r'], r' < Rq
   ga.rns = ctx->d_rns;
   if (db->d_rns16 && ctx->answer_fp16) {  // the resident fp16 copy of the residue planes
     if (BT == 16) return launch_gemm<MODE_RNS, 16, true>(ctx, db->tmap_rns16, tmB, ga, st);
@@ -1210,15 +1356,21 @@ int zp_launch_rns_products(zp_db* db, const uint32_t* dCKO, uint32_t B, uint32_t
 // the end): V[b][r'] = sum_k y[b][r'][k] (M/p_k mod m_b) + alpha (m_b - (M mod m_b))
 // + sum_{j<ell} gamma^j ans[b][r' ell + j], i.e. the Chinese-remainder sum of the residues of
 // H'[r', :] . cko[b] plus the packed answer b' (congruent to b' + H'.cko mod m_b, below
-// 2^2084), taken exactly on the tensor cores as a batched MODE_CMP product: for query b,
-// A = the byte planes of its y, alpha and answers (k_crt_prep; 4 Rq rows, K = ZP_RNS_K + 1 +
-// ell), B = the 256 bytes of each of its client's constants M/p_k mod m_b (read in place
-// through mkm_ptrs[b * ptr_stride]) followed by those of gamma^j (the context's table).
+// 2^2084), taken exactly on the tensor cores (MODE_CRT): for query b, A = the byte planes of
+// its y, alpha and answers (k_crt_prep; plane a of packed row r' is row (4 b + a) Rq + r', K =
+// ZP_RNS_K + 1 + ell), B = the 256 bytes of each of its client's constants M/p_k mod m_b (read
+// in place through mkm_ptrs[b * ptr_stride]) followed by those of gamma^j (the context's
+// table). The four planes run along K against the constants' bytes shifted by a, so one
+// accumulator row is a whole packed row and its 259 byte columns are V's base-256 digits
+// before carries; the columns are taken in two halves of 144.
 int zp_launch_crt_products(zp_db* db, const uint32_t* const* mkm_ptrs, uint32_t ptr_stride,
                            uint32_t B, const uint8_t* Yp, uint32_t ypitch, const uint32_t* yrs,
                            uint32_t* Vc, cudaStream_t st) {
   zp_ctx* ctx = db->ctx;
-  const uint32_t KC = zp_crt_k(ctx), Kp = (KC + 63) / 64 * 64;
+  // K per plane padded to two K blocks (the A producer copies two at a time); 4 Kp <= 1024
+  // keeps every partial sum of the fp32 accumulator below 2^24
+  const uint32_t KC = zp_crt_k(ctx), Kp = (KC + 2 * BK - 1) / (2 * BK) * (2 * BK);
+  if (4 * Kp > (uint32_t)(KCHUNK * BK)) return zp_set_error(ZP_EINVAL, "CRT product: K %u too large", KC);
   const size_t bm_bytes = (size_t)B * 256 * Kp * 2, cs_bytes = (size_t)B * 256 * 4;
   int rc = zp_scratch_reserve(&db->s_crtb, bm_bytes + cs_bytes + 256);
   if (rc) return rc;
@@ -1230,18 +1382,19 @@ int zp_launch_crt_products(zp_db* db, const uint32_t* const* mkm_ptrs, uint32_t 
   k_prep_cko<<<dim3(Kp / 64, B), 256, 0, st>>>(nullptr, ZP_RNS_K + 1, Kp, Bm, colsum, mkm_ptrs,
                                                 ptr_stride, ctx->d_gam, ctx->ell);
   ZP_CUDA(cudaGetLastError());
+  constexpr uint32_t NH = 144;  // columns per half (two halves cover byte positions 0..287)
   CUtensorMap tmA, tmB;
   rc = zp_encode_tmap_2d(&tmA, CU_TENSOR_MAP_DATA_TYPE_UINT8, Yp, KC, (uint64_t)B * 4 * db->Rq, ypitch,
                          128, 128, CU_TENSOR_MAP_SWIZZLE_128B);
   if (!rc)
-    rc = zp_encode_tmap_2d(&tmB, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, Bm, Kp, (uint64_t)B * 256,
-                           (uint64_t)Kp * 2, 64, 256, CU_TENSOR_MAP_SWIZZLE_128B);
+    rc = zp_encode_tmap_3d(&tmB, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, Bm, Kp, 256, B, (uint64_t)Kp * 2,
+                           (uint64_t)256 * Kp * 2, 64, NH, CU_TENSOR_MAP_SWIZZLE_128B);
   if (rc) return rc;
   GemmArgs ga{};
-  ga.num_m_tiles = db->Rq / 32;
+  ga.num_m_tiles = (db->d1p + BM - 1) / BM;
   ga.num_n_tiles = B;
-  ga.N = 256;
-  ga.nkb = Kp / BK;
+  ga.N = NH;
+  ga.nkb = 4 * Kp / BK;
   ga.Kp = Kp;
   ga.Mvalid = db->d1p;
   ga.Bvalid = B;
@@ -1251,5 +1404,5 @@ int zp_launch_crt_products(zp_db* db, const uint32_t* const* mkm_ptrs, uint32_t 
   ga.Rp = db->Rq;
   ga.a_rows_per_n = 4 * db->Rq;
   ga.status = ctx->d_status;
-  return launch_gemm<MODE_CMP, 64>(ctx, tmA, tmB, ga, st);
+  return launch_gemm<MODE_CRT, 64>(ctx, tmA, tmB, ga, st);
 }

@@ -90,6 +90,22 @@ int zp_encode_tmap_2d(CUtensorMap* map, CUtensorMapDataType dt, const void* base
   return ZP_OK;
 }
 
+int zp_encode_tmap_3d(CUtensorMap* map, CUtensorMapDataType dt, const void* base, uint64_t dim0,
+                      uint64_t dim1, uint64_t dim2, uint64_t stride1_bytes, uint64_t stride2_bytes,
+                      uint32_t box0, uint32_t box1, CUtensorMapSwizzle swz) {
+  PFN_encodeTiled fn = get_encode_fn();
+  if (!fn) return zp_set_error(ZP_ECUDA, "cuTensorMapEncodeTiled entry point unavailable");
+  cuuint64_t dims[3] = {dim0, dim1, dim2};
+  cuuint64_t strides[2] = {stride1_bytes, stride2_bytes};
+  cuuint32_t box[3] = {box0, box1, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = fn(map, dt, 3, const_cast<void*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return zp_set_error(ZP_ECUDA, "cuTensorMapEncodeTiled (3-D) failed (%d)", (int)r);
+  return ZP_OK;
+}
+
 // ------------------------------------------------------------------ small host bignum helpers
 // little-endian u32 words
 static void big_mul_small(std::vector<uint32_t>& a, const uint32_t* g, int gw) {

@@ -197,6 +197,10 @@ static inline void zp_clear_pending_error() { (void)cudaGetLastError(); }
 int zp_encode_tmap_2d(CUtensorMap* map, CUtensorMapDataType dt, const void* base, uint64_t dim0,
                       uint64_t dim1, uint64_t stride1_bytes, uint32_t box0, uint32_t box1,
                       CUtensorMapSwizzle swz);
+// 3-D map: dims (dim0, dim1, dim2), byte strides of dims 1 and 2, box (box0, box1, 1).
+int zp_encode_tmap_3d(CUtensorMap* map, CUtensorMapDataType dt, const void* base, uint64_t dim0,
+                      uint64_t dim1, uint64_t dim2, uint64_t stride1_bytes, uint64_t stride2_bytes,
+                      uint32_t box0, uint32_t box1, CUtensorMapSwizzle swz);
 
 // ------------------------------------------------------------------ kernel launchers
 // (defined in the k_*.cu translation units; all asynchronous on `st`)
@@ -229,7 +233,7 @@ int zp_launch_decrypt(const zp_client* cl, const uint32_t* e, uint32_t ew, const
                       const uint32_t* dC, uint32_t* dOut, uint32_t count, cudaStream_t st);
 // RNS compression (k_rns.cu, k_gemm_tc.cu): the residue planes of H' for the listed packed
 // rows (dRows device, NULL = all), the B operand of ck_o residues, and the residue product
-// X[b][r'][k] = H'[r', :] . cko[b] mod p_k
+// X[b][k][r'] = H'[r', :] . cko[b] mod p_k (row pitch Rq)
 int zp_launch_rns_planes(zp_db* db, const uint32_t* dRows, uint32_t nprows, cudaStream_t st);
 // allocates and builds the RNS planes of H' on first use (zp_api.cu)
 int zp_ensure_rns(zp_db* db, cudaStream_t st);
@@ -334,6 +338,17 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
       "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
       " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// 3-D tiled TMA load (tile mode) completing on `bar`; coordinates outside the tensor read
+// as zero (x must stay a multiple of 16 bytes).
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int32_t x,
+                                            int32_t y, int32_t z, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
       : "memory");
 }
 
@@ -442,7 +457,14 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
           smem_u32(bar))
       : "memory");
 }
-// 16 consecutive 32-bit columns of this thread's TMEM lane.
+// 8 / 16 consecutive 32-bit columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                 "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr)
+               : "memory");
+}
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x16.b32 "

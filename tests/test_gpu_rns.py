@@ -66,13 +66,14 @@ def test_rns_compress_parity(zp, R, C, n, B, secret, fp16):
     assert c.device_status() == 0
 
 
-@pytest.mark.parametrize("R,B", [(1080, 8), (2100, 17)])
+@pytest.mark.parametrize("R,B", [(1080, 8), (2100, 17), (3600, 6)])
 @pytest.mark.parametrize("fp16", [False, True])
 def test_rns_several_m_tiles_per_prime(zp, R, B, fp16):
-    """n = 1024 and d1' = 40 / 78 packed rows, i.e. two / three 32-packed-row M tiles per
-    prime (the tile index g > 0 of the grouped product), the last packed row ragged at R =
-    2100: every packed row of every query equals the oracle's t, on the byte planes and on
-    their fp16 copy."""
+    """n = 1024 and d1' = 40 / 78 / 134 packed rows, i.e. two / three / five 32-packed-row M
+    tiles per prime (the tile index g > 0 of the grouped product) and, at d1' = 134, two
+    128-row M tiles of the CRT product (the second ragged); the last packed row ragged at R =
+    2100 and 3600: every packed row of every query equals the oracle's t, on the byte planes
+    and on their fp16 copy."""
     n, C = 1024, 64
     P = Params(n=n, key_bits=2048)
     assert P.d1p(R) > 32
