@@ -349,25 +349,39 @@ __global__ void __launch_bounds__(PACK_WARPS * 32)
 // byte sums of those rows. Columns ZP_RNS_K + 1 + j (j < ell) hold the answers ans[b][r' ell
 // + j] (zero past R), which the CRT product weighs by gamma^j: the packed answer b'. One warp
 // per (query, packed row < Rq).
+constexpr uint32_t CRT_PREP_ROWS = 8;  // warps (packed rows) per block of k_crt_prep
 __global__ void k_crt_prep(const uint32_t* __restrict__ X, uint32_t B, uint32_t d1p, uint32_t Rq,
                            const zp_rns_dev* __restrict__ rns, uint8_t* __restrict__ Yp,
                            uint32_t ypitch, uint32_t* __restrict__ yrs,
                            const uint32_t* __restrict__ ans, uint32_t R, uint32_t ell) {
+  // A block is CRT_PREP_ROWS warps on consecutive packed rows of one query (Rq is a multiple
+  // of 32): their residues X[b][k][rp0 ..] come in as one 32-byte sector per prime, through
+  // shared memory (pitch 9: the warps' column reads are conflict-free).
+  __shared__ uint32_t xs[ZP_RNS_K * (CRT_PREP_ROWS + 1)];
   const uint64_t wid = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const uint32_t lane = threadIdx.x & 31;
-  if (wid >= (uint64_t)B * Rq) return;
+  const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const uint64_t wid0 = (uint64_t)blockIdx.x * CRT_PREP_ROWS;
+  if (wid0 >= (uint64_t)B * Rq) return;  // whole blocks only
   const uint32_t b = (uint32_t)(wid / Rq), rp = (uint32_t)(wid % Rq);
+  {
+    const uint32_t b0 = (uint32_t)(wid0 / Rq), rp0 = (uint32_t)(wid0 % Rq);
+    const uint32_t* X0 = X + (uint64_t)b0 * ZP_RNS_K * Rq + rp0;  // X[b][k][rp], row pitch Rq
+    for (uint32_t i = threadIdx.x; i < ZP_RNS_K * CRT_PREP_ROWS; i += blockDim.x) {
+      const uint32_t k = i / CRT_PREP_ROWS, j = i % CRT_PREP_ROWS;
+      xs[k * (CRT_PREP_ROWS + 1) + j] = rp0 + j < d1p ? __ldg(X0 + (uint64_t)k * Rq + j) : 0u;
+    }
+    __syncthreads();
+  }
   constexpr int QK = (ZP_RNS_K + 1 + 64 + 31) / 32;  // residues, alpha, up to 64 answers
   uint32_t y[QK];
   uint64_t s_lo = 0, s_hi = 0;  // 128-bit sum of y_k floor(2^64 / p_k)
-  const uint32_t* Xr = X + (uint64_t)b * ZP_RNS_K * Rq + rp;  // X[b][k][rp], row pitch Rq
 #pragma unroll
   for (int q = 0; q < QK; ++q) {
     const uint32_t k = lane + 32u * q;
     y[q] = 0u;
     if (rp < d1p && k < ZP_RNS_K) {
       const uint32_t p = rns->p[k], dl = (1u << 27) - p;
-      const uint64_t x = (uint64_t)__ldg(Xr + (uint64_t)k * Rq) * rns->inv[k];  // < 2^54
+      const uint64_t x = (uint64_t)xs[k * (CRT_PREP_ROWS + 1) + w] * rns->inv[k];  // < 2^54
       const uint64_t t1 = (x & 0x7FFFFFFull) + (x >> 27) * dl;             // < 2^40
       uint32_t v = (uint32_t)((t1 & 0x7FFFFFFull) + (t1 >> 27) * dl);       // < 2^27 + 2^25
       if (v >= p) v -= p;
@@ -512,9 +526,8 @@ int zp_launch_compress_finish(zp_db* db, zp_client* const* clients, const uint32
     uint32_t* yrs = reinterpret_cast<uint32_t*>(Yp + (yp_bytes + 255) / 256 * 256);
     uint32_t* Vc = yrs + (yrs_bytes / 4 + 63) / 64 * 64;
     const uint64_t warps = (uint64_t)B * Rq;
-    k_crt_prep<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(V, B, db->d1p, Rq, ctx->d_rns, Yp,
-                                                                    ypitch, yrs, dAns, db->R,
-                                                                    ctx->ell);
+    k_crt_prep<<<(unsigned)(warps / CRT_PREP_ROWS), 32 * CRT_PREP_ROWS, 0, st>>>(
+        V, B, db->d1p, Rq, ctx->d_rns, Yp, ypitch, yrs, dAns, db->R, ctx->ell);
     ZP_CUDA(cudaGetLastError());
     // the mkm pointers are the third member of each uploaded ClientPtrs
     rc = zp_launch_crt_products(db, reinterpret_cast<const uint32_t* const*>(dcl) + 2,

@@ -96,9 +96,9 @@ struct Cfg {
                                                                                    : (ANS_BYTES ? ZP_ANS_SB : 4));
   static constexpr int SA = SB;  // the A and B stages of a K block are filled and freed together
   // epilogue warps: with an fp16 A operand the converter warps 8-11 have no conversion to do,
-  // so the RNS product (whose epilogue bounds it) drains TMEM with eight warps, two per lane
-  // quarter, each taking half of the tile's queries
-  static constexpr int EPW = (A16 && MODE == MODE_RNS) ? 8 : 4;
+  // so the RNS and residue products (whose epilogues bound them) drain TMEM with eight warps,
+  // two per lane quarter, each taking half of the tile's columns
+  static constexpr int EPW = (A16 && (MODE == MODE_RNS || MODE == MODE_RES)) ? 8 : 4;
   // stages of two K blocks of A bytes: the ring that hides the HBM latency
   static constexpr int SU_FIT = (224 * 1024 - SB * BST - SA * AST) / U8_STAGE;
   static constexpr int SU = A16 ? 0 : (ANS_BYTES ? (ZP_ANS_SU < SU_FIT ? ZP_ANS_SU : SU_FIT) : 2);
@@ -197,8 +197,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
               const GemmArgs args) {
   using C = Cfg<MODE, BT, A16>;
-  static_assert(!A16 || MODE == MODE_ANS || MODE == MODE_RNS,
-                "fp16 A operand: batched answers and RNS compression products only");
+  static_assert(!A16 || MODE == MODE_ANS || MODE == MODE_RNS || MODE == MODE_RES,
+                "fp16 A operand: batched answers, RNS and residue products only");
   constexpr int SB = C::SB, SA = C::SA, SU = C::SU;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
@@ -263,19 +263,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       prefetch_tmap(&tmA);
       uint32_t cnt = 0;
       bool ok = true;
-      constexpr uint32_t PF = 16;  // K blocks of L2 prefetch ahead of the loads
-      uint32_t pf_tile = first_tile<MODE>(), pf_kb = 0;
-      auto pf_step = [&]() {
-        if (pf_tile < num_tiles)
-          tma_prefetch_l2_2d(&tmA, (int32_t)(pf_kb * BK),
-                             (int32_t)((pf_tile / args.num_n_tiles) * BM +
-                                       (pf_tile % args.num_n_tiles) * args.a_rows_per_n));
-        if (++pf_kb == nkb) {
-          pf_kb = 0;
-          pf_tile = next_tile<MODE>(pf_tile);
-        }
-      };
-      for (uint32_t f = 0; f < PF; ++f) pf_step();
+      // no L2 prefetch ahead of these loads: measured slower (prefetch 4 to 64 K blocks
+      // ahead: 3 to 43 % on 1 GiB x 64 queries), the TMA loads alone keep HBM busier
       for (uint32_t tile = first_tile<MODE>(); ok && tile < num_tiles; tile = next_tile<MODE>(tile)) {
         const uint32_t mt = tile / args.num_n_tiles;
         const uint32_t arow = mt * BM + (tile % args.num_n_tiles) * args.a_rows_per_n;
@@ -288,7 +277,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           }
           mbar_arrive_expect_tx(&b_full[sb], KPS * A16_BYTES);
           for (uint32_t h = 0; h < KPS; ++h) {
-            pf_step();
             tma_load_2d(a_ring + sb * C::AST + h * A16_BYTES, &tmA, (int32_t)((ks * KPS + h) * BK),
                         (int32_t)arow, &b_full[sb]);
           }
@@ -662,17 +650,21 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           csw[h] = q;
           pj[h] = (j < (uint32_t)ZP_RES_KPER && k < ZP_RNS_K) ? args.rns->p[k] : 1u;
         }
+        // primes j0 .. j0 + PH - 1 of the tile: all of them, or a half with eight warps
+        constexpr int PH = ZP_RES_KPER / (C::EPW / 4);
+        static_assert(PH % 4 == 0, "four primes per 16-column TMEM load");
+        const uint32_t j0 = eh * PH;
 #pragma unroll
-        for (int g = 0; g < NR / 32; ++g) {
-          uint32_t r[32];
-          tmem_ld32(tmem_base + lane_addr + a * 256u + 32u * g, r);
+        for (int g = 0; g < PH / 4; ++g) {
+          uint32_t r[16];
+          tmem_ld16(tmem_base + lane_addr + a * 256u + 4u * j0 + 16u * g, r);
           tmem_wait_ld();
 #pragma unroll
-          for (int kk = 0; kk < 8; ++kk) {
-            const int j = g * 8 + kk;
+          for (int kk = 0; kk < 4; ++kk) {
+            const uint32_t j = j0 + 4 * g + kk;
             const uint32_t k = nt * ZP_RES_KPER + j;
-            const uint64_t cj = __shfl_sync(0xffffffffu, csw[j >> 5], j & 31);
-            const uint32_t p = __shfl_sync(0xffffffffu, pj[j >> 5], j & 31);
+            const uint64_t cj = __shfl_sync(0xffffffffu, (j >> 5) ? csw[1] : csw[0], j & 31);
+            const uint32_t p = __shfl_sync(0xffffffffu, (j >> 5) ? pj[1] : pj[0], j & 31);
             if (k >= ZP_RNS_K) continue;  // uniform across the warp
             const uint32_t dl = (1u << 27) - p;
             uint64_t x = cj + rowterm;
@@ -1228,6 +1220,23 @@ int zp_launch_vmul_tc(zp_db* db, const uint32_t* dCKO, uint32_t B, uint32_t* V4,
 // H' mod p_k (A, built by zp_launch_rns_planes) times the byte planes of cko mod p_k (B).
 namespace {
 
+// The 256 bytes of each cko element as centred fp16 (byte - 128, exact), the A operand of
+// MODE_RES, and their byte sums. One warp per element; lane l takes bytes 8 l .. 8 l + 7.
+__global__ void k_cko_f16(const uint32_t* __restrict__ cko, uint32_t rows, __half* __restrict__ out,
+                          uint32_t* __restrict__ rowsum) {
+  const uint64_t row = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t lane = threadIdx.x & 31;
+  if (row >= rows) return;
+  const uint2 w = __ldg(reinterpret_cast<const uint2*>(cko + row * 64) + lane);
+  uint4 o;
+  bytes_to_centred_f16(w.x, o.x, o.y);
+  bytes_to_centred_f16(w.y, o.z, o.w);
+  reinterpret_cast<uint4*>(out + row * 256)[lane] = o;
+  uint32_t sum = __dp4a(w.x, 0x01010101u, 0u) + __dp4a(w.y, 0x01010101u, 0u);
+  sum = __reduce_add_sync(0xffffffffu, sum);
+  if (lane == 0) rowsum[row] = sum;
+}
+
 // Byte sums of rows of a centred fp16 matrix (value + 128 summed over the row): the row sums
 // of the RNS product's B operand, after MODE_RES wrote it. One warp per row; cols % 8 == 0.
 __global__ void k_fp16_rowsum(const __half* __restrict__ M, uint64_t rows, uint32_t cols,
@@ -1271,20 +1280,24 @@ int zp_launch_rns_products(zp_db* db, const uint32_t* dCKO, uint32_t B, uint32_t
   const uint64_t brows = (uint64_t)ZP_RNS_K * nnt * N;
   const size_t bc_bytes = (size_t)brows * Kp * 2;
   const size_t cs_bytes = (size_t)brows * 4;
-  int rc = zp_scratch_reserve(&db->s_cko, bc_bytes + cs_bytes + (size_t)B * n * 4 + 256);
+  const size_t ac_off = (bc_bytes + cs_bytes + (size_t)B * n * 4 + 255) / 256 * 256;
+  int rc = zp_scratch_reserve(&db->s_cko, ac_off + (size_t)B * n * 512);
   if (rc) return rc;
   __half* Bc = static_cast<__half*>(db->s_cko.p);
   uint32_t* colsum = reinterpret_cast<uint32_t*>(static_cast<uint8_t*>(db->s_cko.p) + bc_bytes);
+  __half* Ac = reinterpret_cast<__half*>(static_cast<uint8_t*>(db->s_cko.p) + ac_off);
   // cko mod p_k for every query, offset and prime on the tensor cores (MODE_RES): A = the
-  // 256 bytes of each cko[b][i] straight from dCKO, B = the context's table of 2^(8 beta) mod
-  // p_k; the epilogue writes the byte planes of the residues into Bc, k_fp16_rowsum their
-  // sums into colsum (rows of queries past B hold whatever the buffer held: their columns of
-  // the product are discarded)
+  // 256 bytes of each cko[b][i] as centred fp16 (k_cko_f16, with their byte sums), B = the
+  // context's table of 2^(8 beta) mod p_k; the epilogue writes the byte planes of the residues
+  // into Bc, k_fp16_rowsum their sums into colsum (rows of queries past B hold whatever the
+  // buffer held: their columns of the product are discarded)
   rc = zp_ensure_res_table(ctx);
   if (rc) return rc;
   uint32_t* ckrs = colsum + brows;  // byte sums of the cko elements
-  rc = zp_launch_rowsum_buf(ctx, reinterpret_cast<const uint8_t*>(dCKO), 256, B * n, 256, ckrs, st);
-  if (rc) return rc;
+  zp_clear_pending_error();
+  ctx->launches++;
+  k_cko_f16<<<(unsigned)(((uint64_t)B * n * 32 + 255) / 256), 256, 0, st>>>(dCKO, B * n, Ac, ckrs);
+  ZP_CUDA(cudaGetLastError());
   if (Kp > n) {
     zp_clear_pending_error();
     ctx->launches++;
@@ -1293,7 +1306,7 @@ int zp_launch_rns_products(zp_db* db, const uint32_t* dCKO, uint32_t B, uint32_t
   }
   {
     CUtensorMap tmC;
-    rc = zp_encode_tmap_2d(&tmC, CU_TENSOR_MAP_DATA_TYPE_UINT8, dCKO, 256, (uint64_t)B * n, 256, 128,
+    rc = zp_encode_tmap_2d(&tmC, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, Ac, 256, (uint64_t)B * n, 512, 64,
                            128, CU_TENSOR_MAP_SWIZZLE_128B);
     if (rc) return rc;
     GemmArgs gr{};
@@ -1313,7 +1326,7 @@ int zp_launch_rns_products(zp_db* db, const uint32_t* dCKO, uint32_t B, uint32_t
     gr.res_nnt = nnt;
     gr.res_kp = Kp;
     gr.res_out = Bc;
-    rc = launch_gemm<MODE_RES, 64>(ctx, tmC, ctx->tmap_resw, gr, st);
+    rc = launch_gemm<MODE_RES, 64, true>(ctx, tmC, ctx->tmap_resw, gr, st);
     if (rc) return rc;
     zp_clear_pending_error();
     ctx->launches++;
