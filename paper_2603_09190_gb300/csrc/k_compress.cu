@@ -6,7 +6,7 @@
 // (b'[r'] + sum_i H'[r', i] cko[i]) mod m without ever forming the ~2000-bit packed
 // hint: the wide products are taken per answer row and packed afterwards.
 //
-// Two kernels:
+// Three kernels:
 //  * k_vmul_simt: V on CUDA cores, one thread per (row, limb of cko), 96-bit
 //    column accumulators, then one carry-propagation pass per row;
 //  * k_pack_reduce: one warp per (query, packed row): the ell rows of V are staged
@@ -19,7 +19,10 @@
 //    14.42) with the per-client constant mu = floor(2^(64 L) / m) on 2-3 quotient words.
 //    Big integers live in shared memory; products are summed per output column in
 //    96-bit accumulators and carries are resolved across the warp with a
-//    generate/propagate ballot (one integer addition over the 32 lane flags).
+//    generate/propagate ballot (one integer addition over the 32 lane flags);
+//  * k_mod_packed (the residue-number-system path of large batches): the packed rows'
+//    CRT sums V < 2^2087 mod m, the quotient (< 2^40) estimated from the top words of V and
+//    of mu, one product q m and at most two subtractions.
 #include <atomic>
 
 #include "zp_internal.cuh"
@@ -145,24 +148,18 @@ struct ClientPtrs {
 
 // grid (ceil(d1p / PACK_WARPS), B), block PACK_WARPS warps, dynamic shared memory
 // PACK_WARPS x (PackBarrett + ell x VW words). Requires L == ZP_MAX_L.
-// PACKED = false: V is [b][Rp][VW] words, the exact products V[row] = H[row,:] . cko[b]
-// of every answer row, packed with the answers (W_j = ans + V).
-// PACKED = true (the residue-number-system path): V is [b][Rp][VW] words holding one
-// integer per PACKED row, already reduced congruent to H'.cko mod m by the Chinese remainder
-// theorem (k_crt_prep and the CRT product); the Horner runs over the answers only (b') and V
-// is added once before the reduction.
-template <bool PACKED>
+// V is [b][Rp][VW] words, the exact products V[row] = H[row,:] . cko[b] of every answer
+// row, packed with the answers (W_j = ans + V).
 __global__ void __launch_bounds__(PACK_WARPS * 32)
     k_pack_reduce(const uint32_t* __restrict__ ans, const uint32_t* __restrict__ V, uint32_t R,
                   uint32_t Rp, uint32_t ell, uint32_t d1p, uint32_t g1, uint32_t g2,
-                  const ClientPtrs* __restrict__ cl, uint32_t* __restrict__ T,
-                  const zp_rns_dev* __restrict__ rns) {
+                  const ClientPtrs* __restrict__ cl, uint32_t* __restrict__ T) {
   extern __shared__ __align__(16) uint32_t pack_smem[];
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t b = blockIdx.y;
   const uint32_t rp = blockIdx.x * PACK_WARPS + warp;
   if (rp >= d1p) return;
-  const uint32_t per_warp = (uint32_t)(sizeof(PackBarrett) / 4) + (PACKED ? 0u : ell * VW);
+  const uint32_t per_warp = (uint32_t)(sizeof(PackBarrett) / 4) + ell * VW;
   PackBarrett& S = *reinterpret_cast<PackBarrett*>(pack_smem + warp * per_warp);
   uint32_t* Vs = pack_smem + warp * per_warp + sizeof(PackBarrett) / 4;  // ell x VW
   constexpr int L = ZP_MAX_L;
@@ -171,7 +168,7 @@ __global__ void __launch_bounds__(PACK_WARPS * 32)
   const uint32_t row0 = rp * ell;
   const uint32_t nrows = R - row0 < ell ? R - row0 : ell;
   const uint32_t* src = V + ((uint64_t)b * Rp + row0) * VW;
-  if (!PACKED) {
+  {
     // eight loads in flight per lane before the stores (the rows come from L2)
     const uint32_t tot = nrows * VW;
     for (uint32_t base = 0; base < tot; base += 32 * 8) {
@@ -193,8 +190,7 @@ __global__ void __launch_bounds__(PACK_WARPS * 32)
     S.mu[x] = cl[b].mu[x];
   }
   const uint32_t* ansb = ans + (uint64_t)b * R + row0;
-  if (!PACKED)
-    for (uint32_t j = lane; j < nrows; j += 32) S.ans[j] = __ldg(ansb + j);
+  for (uint32_t j = lane; j < nrows; j += 32) S.ans[j] = __ldg(ansb + j);
   __syncwarp();
 
   // ---- Horner: X <- X gamma + W_j (j = ell-1 .. 0), gamma = g1 2^32 + g2 2^64,
@@ -202,7 +198,7 @@ __global__ void __launch_bounds__(PACK_WARPS * 32)
   // (words 4 lane .. 4 lane + 3), each below 2^33, so one step needs a local carry
   // pass and one shuffle instead of a full carry resolution.
   uint64_t xv[4] = {0, 0, 0, 0};
-  for (int j = PACKED ? -1 : (int)nrows - 1; j >= 0; --j) {
+  for (int j = (int)nrows - 1; j >= 0; --j) {
     const uint64_t pm1 = __shfl_up_sync(0xffffffffu, xv[3], 1);  // word 4 lane - 1
     const uint64_t pm2 = __shfl_up_sync(0xffffffffu, xv[2], 1);  // word 4 lane - 2
     const uint64_t xm1 = lane ? pm1 : 0, xm2 = lane ? pm2 : 0;
@@ -212,7 +208,7 @@ __global__ void __launch_bounds__(PACK_WARPS * 32)
     v[1] = (uint64_t)g1 * xv[0] + (uint64_t)g2 * xm1;
     v[2] = (uint64_t)g1 * xv[1] + (uint64_t)g2 * xv[0];
     v[3] = (uint64_t)g1 * xv[2] + (uint64_t)g2 * xv[1];
-    if (!PACKED) {
+    {
 #pragma unroll
       for (int t = 0; t < 4; ++t) {
         const uint32_t x = lane * 4 + t;
@@ -230,14 +226,6 @@ __global__ void __launch_bounds__(PACK_WARPS * 32)
     const uint64_t cin = __shfl_up_sync(0xffffffffu, c, 1);
     if (lane) xv[0] += cin;
   }
-  if (PACKED) {  // X = V of the packed row (67 words), congruent to b-prime + H'.cko mod m
-    const uint32_t* Vp = V + ((uint64_t)b * Rp + rp) * VW;
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      const uint32_t x = lane * 4 + t;
-      if (x < VW) xv[t] += __ldg(Vp + x);
-    }
-  }
   // final carry resolution, then X to shared memory
   {
     uint32_t w[4];
@@ -246,7 +234,7 @@ __global__ void __launch_bounds__(PACK_WARPS * 32)
     for (int t = 0; t < 4; ++t) S.X[lane * 4 + t] = w[t];
   }
   __syncwarp();
-  if (!PACKED) {
+  {
     // X < 2^(64 L) (2L words; 4077 bits for the binary secret at n = 48): fold its high words
     // with the client's table, Z = (X mod 2^(32 L)) + sum_{w = L}^{2L - 1} X_w (2^(32 w) mod m)
     // == X (mod m), Z < 2^2087, so the Barrett reduction below works on 2-3 quotient words.
@@ -333,6 +321,69 @@ __global__ void __launch_bounds__(PACK_WARPS * 32)
   for (int t = 0; t < 3; ++t) {
     const int x = (int)lane * 3 + t;
     if (x < L) out[x] = r[t];
+  }
+}
+
+// Residue-number-system path, last step (Sec. 5.2: one reduction mod m at the end): T = V mod
+// m for the CRT sums V < 2^2087 (ZP_VW words, [b][Rq][ZP_VW]) of the packed rows. The
+// quotient q = floor(V / m) is below 2^40 and comes from the top words alone: with the
+// client's Barrett constant mu = floor(2^4096 / m), mu_t = floor(mu / 2^1985) (64 bits) and
+// V_t = floor(V / 2^1984) (< 2^103), q_e = floor(V_t mu_t / 2^127) is at most q (every factor
+// is rounded down) and at least q - 2 (the dropped parts are below V / 2^2111 + mu / 2^2112
+// < 2^-23 of a unit, plus the floors), so r = V - q_e m is below 3m and two conditional
+// subtractions of m end below m. One warp per (query, packed row); lane l holds words 3 l ..
+// 3 l + 2. Requires L == ZP_MAX_L == 64.
+constexpr uint32_t MODP_WARPS = 8;
+__global__ void __launch_bounds__(MODP_WARPS * 32)
+    k_mod_packed(const uint32_t* __restrict__ V, uint32_t Rq, uint32_t d1p,
+                 const ClientPtrs* __restrict__ cl, uint32_t* __restrict__ T) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t rp = blockIdx.x * MODP_WARPS + (threadIdx.x >> 5), b = blockIdx.y;
+  if (rp >= d1p) return;
+  constexpr int L = ZP_MAX_L;
+  static_assert(L == 64 && ZP_VW <= 96, "2048-bit moduli, V within the warp's 96 words");
+  const uint32_t* Vr = V + ((uint64_t)b * Rq + rp) * ZP_VW;
+  const uint32_t* m = cl[b].m;
+  const uint32_t* mu = cl[b].mu;
+  uint32_t v[3], mm[3];
+#pragma unroll
+  for (int t = 0; t < 3; ++t) {
+    const uint32_t x = 3 * lane + t;
+    v[t] = x < (uint32_t)ZP_VW ? __ldg(Vr + x) : 0u;
+    mm[t] = x < (uint32_t)L ? __ldg(m + x) : 0u;
+  }
+  // V_t = words 62..65 of V (lanes 20 and 21), mu_t from words 62..64 of mu
+  const uint32_t w62 = __shfl_sync(0xffffffffu, v[2], 20), w63 = __shfl_sync(0xffffffffu, v[0], 21);
+  const uint32_t w64 = __shfl_sync(0xffffffffu, v[1], 21), w65 = __shfl_sync(0xffffffffu, v[2], 21);
+  const uint64_t mut = ((uint64_t)__ldg(mu + 64) << 63) | ((uint64_t)__ldg(mu + 63) << 31) |
+                       (uint64_t)(__ldg(mu + 62) >> 1);
+  const uint64_t vh = ((uint64_t)w65 << 32) | w64, vl = ((uint64_t)w63 << 32) | w62;
+  // bits 127.. of (vh 2^64 + vl) mu_t
+  const uint64_t a1 = __umul64hi(vl, mut), b0 = vh * mut, b1 = __umul64hi(vh, mut);
+  const uint64_t s1 = a1 + b0, s2 = b1 + (s1 < a1 ? 1u : 0u);
+  const uint64_t q = (s2 << 1) | (s1 >> 63);  // < 2^40
+  const uint32_t ql = (uint32_t)q, qh = (uint32_t)(q >> 32);
+  // q m as 64-bit columns (each < 2^41): word j gets lo(ql m_j) + hi(ql m_{j-1}) + qh m_{j-1}
+  const uint32_t mprev = __shfl_up_sync(0xffffffffu, mm[2], 1);
+  uint64_t col[3];
+#pragma unroll
+  for (int t = 0; t < 3; ++t) {
+    const uint32_t mj1 = t ? mm[t - 1] : (lane ? mprev : 0u);
+    col[t] = (((uint64_t)ql * mm[t]) & 0xFFFFFFFFull) + (((uint64_t)ql * mj1) >> 32) +
+             (uint64_t)qh * mj1;
+  }
+  uint32_t qm[3];
+  warp_normalize<3>(col, qm);
+  warp_sub<3>(v, qm);
+  for (int it = 0; it < 2; ++it) {
+    if (!warp_geq<3>(v, mm)) break;
+    warp_sub<3>(v, mm);
+  }
+  uint32_t* out = T + ((uint64_t)b * d1p + rp) * L;
+#pragma unroll
+  for (int t = 0; t < 3; ++t) {
+    const uint32_t x = 3 * lane + t;
+    if (x < (uint32_t)L) out[x] = v[t];
   }
 }
 
@@ -508,7 +559,7 @@ int zp_launch_compress_finish(zp_db* db, zp_client* const* clients, const uint32
   static std::atomic<bool> attr_dev[64];
   std::atomic<bool>& attr = attr_dev[ctx->device & 63];
   if (!attr) {
-    ZP_CUDA(cudaFuncSetAttribute(k_pack_reduce<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    ZP_CUDA(cudaFuncSetAttribute(k_pack_reduce, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)(PACK_WARPS * (sizeof(PackBarrett) + 64 * VW * 4))));
     attr = true;
   }
@@ -536,15 +587,12 @@ int zp_launch_compress_finish(zp_db* db, zp_client* const* clients, const uint32
     if (rc) return rc;
     zp_clear_pending_error();
     ctx->launches++;
-    const size_t smem = (size_t)PACK_WARPS * sizeof(PackBarrett);
-    k_pack_reduce<true><<<grid, PACK_WARPS * 32, smem, st>>>(dAns, Vc, db->R, Rq, ctx->ell, db->d1p,
-                                                             ctx->gamma_w[1], ctx->gamma_w[2], dcl,
-                                                             dT, nullptr);
+    k_mod_packed<<<dim3((db->d1p + MODP_WARPS - 1) / MODP_WARPS, B), MODP_WARPS * 32, 0, st>>>(
+        Vc, Rq, db->d1p, dcl, dT);
   } else {
     const size_t smem = (size_t)PACK_WARPS * (sizeof(PackBarrett) + (size_t)ctx->ell * VW * 4);
-    k_pack_reduce<false><<<grid, PACK_WARPS * 32, smem, st>>>(dAns, V, db->R, db->Rp, ctx->ell,
-                                                              db->d1p, ctx->gamma_w[1],
-                                                              ctx->gamma_w[2], dcl, dT, nullptr);
+    k_pack_reduce<<<grid, PACK_WARPS * 32, smem, st>>>(dAns, V, db->R, db->Rp, ctx->ell, db->d1p,
+                                                       ctx->gamma_w[1], ctx->gamma_w[2], dcl, dT);
   }
   ZP_CUDA(cudaGetLastError());
   return ZP_OK;
