@@ -395,11 +395,11 @@ __global__ void __launch_bounds__(MODP_WARPS * 32)
 // H'.cko < M 2^-26 puts the fractional part of sum_k y_k / p_k in [0, 2^-26), so
 // floor((S + 2^35) / 2^64) = alpha exactly. y_k = X_k inv_k mod p_k by two pseudo-Mersenne
 // folds (p = 2^27 - dl, dl < 2^12). Written as the byte planes of the CRT product's A
-// operand: row (4 b + a) Rq + r' holds byte a of y_k in column k < ZP_RNS_K and of alpha in
-// column ZP_RNS_K; packed rows r' in [d1', Rq) are zero. yrs: the
-// byte sums of those rows. Columns ZP_RNS_K + 1 + j (j < ell) hold the answers ans[b][r' ell
-// + j] (zero past R), which the CRT product weighs by gamma^j: the packed answer b'. One warp
-// per (query, packed row < Rq).
+// operand: row b Rq + r' holds, at byte a kpl + k (kpl = ypitch / 4, a multiple of 64), byte
+// a of y_k in column k < ZP_RNS_K and of alpha in column ZP_RNS_K; columns ZP_RNS_K + 1 + j
+// (j < ell) hold the answers ans[b][r' ell + j] (zero past R), which the CRT product weighs by
+// gamma^j: the packed answer b'; columns past that and packed rows r' in [d1', Rq) are zero.
+// yrs[(4 b + a) Rq + r']: the byte sums of plane a. One warp per (query, packed row < Rq).
 constexpr uint32_t CRT_PREP_ROWS = 8;  // warps (packed rows) per block of k_crt_prep
 __global__ void k_crt_prep(const uint32_t* __restrict__ X, uint32_t B, uint32_t d1p, uint32_t Rq,
                            const zp_rns_dev* __restrict__ rns, uint8_t* __restrict__ Yp,
@@ -462,23 +462,28 @@ __global__ void k_crt_prep(const uint32_t* __restrict__ X, uint32_t B, uint32_t 
       y[q] = (rp < d1p && r < R) ? __ldg(ans + (uint64_t)b * R + r) : 0u;
     }
   }
-  const uint64_t row0 = (uint64_t)b * 4 * Rq + rp;
+  // Byte plane a of column k goes to byte a kpl + k of row b Rq + rp (planes of kpl = ypitch
+  // / 4 bytes, the tail of each plane zero). Four lanes (k = 4 g .. 4 g + 3 of a block of 32)
+  // trade bytes in two shuffle rounds so that lane 4 g + a holds the four plane-a bytes and
+  // stores them as one word; the byte sums per plane are summed over the lanes of the plane.
+  const uint32_t kpl = ypitch / 4, pa = lane & 3u;
+  uint8_t* dst = Yp + ((uint64_t)b * Rq + rp) * ypitch + (uint64_t)pa * kpl;
+  uint32_t sum = 0;
 #pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    uint8_t* dst = Yp + (row0 + (uint64_t)a * Rq) * ypitch;
-    uint32_t sum = 0;
-#pragma unroll
-    for (int q = 0; q < QK; ++q) {
-      const uint32_t k = lane + 32u * q;
-      if (k <= KE) {
-        const uint32_t byte = (y[q] >> (8 * a)) & 0xFFu;
-        dst[k] = (uint8_t)byte;
-        sum += byte;
-      }
-    }
-    sum = __reduce_add_sync(0xffffffffu, sum);
-    if (lane == 0) yrs[row0 + (uint64_t)a * Rq] = sum;
+  for (int q = 0; q < 8; ++q) {
+    if (32u * q >= kpl) break;
+    const uint32_t x = q < QK ? y[q] : 0u;
+    const uint32_t p1 = __shfl_xor_sync(0xffffffffu, x, 1);
+    const uint32_t w1 = (lane & 1u) ? __byte_perm(x, p1, 0x3715) : __byte_perm(x, p1, 0x6240);
+    const uint32_t p2 = __shfl_xor_sync(0xffffffffu, w1, 2);
+    const uint32_t w2 = (lane & 2u) ? __byte_perm(p2, w1, 0x7632) : __byte_perm(w1, p2, 0x5410);
+    *reinterpret_cast<uint32_t*>(dst + 32u * q + 4u * (lane >> 2)) = w2;
+    sum += __dp4a(w2, 0x01010101u, 0u);
   }
+  sum += __shfl_xor_sync(0xffffffffu, sum, 4);
+  sum += __shfl_xor_sync(0xffffffffu, sum, 8);
+  sum += __shfl_xor_sync(0xffffffffu, sum, 16);
+  if (lane < 4) yrs[((uint64_t)b * 4 + lane) * Rq + rp] = sum;
 }
 
 }  // namespace
@@ -568,8 +573,9 @@ int zp_launch_compress_finish(zp_db* db, zp_client* const* clients, const uint32
   ctx->launches++;
   if (db->v_rns) {
     // residues -> y, alpha (byte planes) -> exact CRT sums on the tensor cores -> pack + reduce
-    const uint32_t Rq = db->Rq, ypitch = (zp_crt_k(ctx) + 15) / 16 * 16;
-    const size_t yp_bytes = (size_t)B * 4 * Rq * ypitch, yrs_bytes = (size_t)B * 4 * Rq * 4;
+    // four planes of K rounded up to 64 bytes (the CRT product takes a plane per K block)
+    const uint32_t Rq = db->Rq, ypitch = 4 * ((zp_crt_k(ctx) + 63) / 64 * 64);
+    const size_t yp_bytes = (size_t)B * Rq * ypitch, yrs_bytes = (size_t)B * 4 * Rq * 4;
     const size_t vc_bytes = (size_t)B * Rq * VW * 4;
     rc = zp_scratch_reserve(&db->s_crt, yp_bytes + yrs_bytes + vc_bytes + 512);
     if (rc) return rc;

@@ -303,15 +303,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       // prefetch cursor: (tile, pair of K blocks) PF pairs ahead of the load cursor
       const uint32_t npairs = (nkb + 1) / 2;
       uint32_t pf_tile = first_tile<MODE>(), pf_p = 0;
-      // coordinates of the pair p of K blocks of a tile's A. MODE_CRT: K block kb of the
-      // product is K block kb % (Kp / BK) of plane kb / (Kp / BK) (Kp a multiple of 2 BK),
-      // rows (query b, plane a, packed row): b a_rows_per_n + a Rp + mt BM
+      // coordinates of the pair p of K blocks of a tile's A. MODE_CRT: row (query b, packed
+      // row) = b Rp + mt BM + .., the four planes of Kp bytes one after the other
       auto a_xy = [&](uint32_t t, uint32_t p, int32_t& x, int32_t& y) {
         if constexpr (MODE == MODE_CRT) {
           const uint32_t q = t >> 1, b = q / args.num_m_tiles, mt = q % args.num_m_tiles;
-          const uint32_t k0 = p * 2 * BK, a = k0 / args.Kp;
-          x = (int32_t)(k0 - a * args.Kp);
-          y = (int32_t)(b * args.a_rows_per_n + a * args.Rp + mt * BM);
+          x = (int32_t)(p * 2 * BK);
+          y = (int32_t)(b * args.Rp + mt * BM);
         } else {
           x = (int32_t)(p * 2 * BK);
           y = (int32_t)((t / args.num_n_tiles) * BM + (t % args.num_n_tiles) * args.a_rows_per_n);
@@ -1370,8 +1368,8 @@ int zp_launch_rns_products(zp_db* db, const uint32_t* dCKO, uint32_t B, uint32_t
 // + sum_{j<ell} gamma^j ans[b][r' ell + j], i.e. the Chinese-remainder sum of the residues of
 // H'[r', :] . cko[b] plus the packed answer b' (congruent to b' + H'.cko mod m_b, below
 // 2^2084), taken exactly on the tensor cores (MODE_CRT): for query b, A = the byte planes of
-// its y, alpha and answers (k_crt_prep; plane a of packed row r' is row (4 b + a) Rq + r', K =
-// ZP_RNS_K + 1 + ell), B = the 256 bytes of each of its client's constants M/p_k mod m_b (read
+// its y, alpha and answers (k_crt_prep; packed row r' is row b Rq + r', its plane a at bytes
+// a Kp .., K = ZP_RNS_K + 1 + ell per plane), B = the 256 bytes of each of its client's constants M/p_k mod m_b (read
 // in place through mkm_ptrs[b * ptr_stride]) followed by those of gamma^j (the context's
 // table). The four planes run along K against the constants' bytes shifted by a, so one
 // accumulator row is a whole packed row and its 259 byte columns are V's base-256 digits
@@ -1380,9 +1378,10 @@ int zp_launch_crt_products(zp_db* db, const uint32_t* const* mkm_ptrs, uint32_t 
                            uint32_t B, const uint8_t* Yp, uint32_t ypitch, const uint32_t* yrs,
                            uint32_t* Vc, cudaStream_t st) {
   zp_ctx* ctx = db->ctx;
-  // K per plane padded to two K blocks (the A producer copies two at a time); 4 Kp <= 1024
-  // keeps every partial sum of the fp32 accumulator below 2^24
-  const uint32_t KC = zp_crt_k(ctx), Kp = (KC + 2 * BK - 1) / (2 * BK) * (2 * BK);
+  // K per plane padded to a K block (the planes lie one after the other in each row of Yp,
+  // ypitch = 4 Kp); 4 Kp <= 1024 keeps every partial sum of the fp32 accumulator below 2^24
+  const uint32_t KC = zp_crt_k(ctx), Kp = (KC + BK - 1) / BK * BK;
+  if (ypitch != 4 * Kp) return zp_set_error(ZP_EINVAL, "CRT product: row pitch %u", ypitch);
   if (4 * Kp > (uint32_t)(KCHUNK * BK)) return zp_set_error(ZP_EINVAL, "CRT product: K %u too large", KC);
   const size_t bm_bytes = (size_t)B * 256 * Kp * 2, cs_bytes = (size_t)B * 256 * 4;
   int rc = zp_scratch_reserve(&db->s_crtb, bm_bytes + cs_bytes + 256);
@@ -1397,7 +1396,7 @@ int zp_launch_crt_products(zp_db* db, const uint32_t* const* mkm_ptrs, uint32_t 
   ZP_CUDA(cudaGetLastError());
   constexpr uint32_t NH = 144;  // columns per half (two halves cover byte positions 0..287)
   CUtensorMap tmA, tmB;
-  rc = zp_encode_tmap_2d(&tmA, CU_TENSOR_MAP_DATA_TYPE_UINT8, Yp, KC, (uint64_t)B * 4 * db->Rq, ypitch,
+  rc = zp_encode_tmap_2d(&tmA, CU_TENSOR_MAP_DATA_TYPE_UINT8, Yp, 4 * Kp, (uint64_t)B * db->Rq, ypitch,
                          128, 128, CU_TENSOR_MAP_SWIZZLE_128B);
   if (!rc)
     rc = zp_encode_tmap_3d(&tmB, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, Bm, Kp, 256, B, (uint64_t)Kp * 2,
