@@ -169,17 +169,17 @@ __global__ void __launch_bounds__(PACK_WARPS * 32)
   const uint32_t nrows = R - row0 < ell ? R - row0 : ell;
   const uint32_t* src = V + ((uint64_t)b * Rp + row0) * VW;
   {
-    // eight loads in flight per lane before the stores (the rows come from L2)
+    // sixteen loads in flight per lane before the stores (the rows come from L2)
     const uint32_t tot = nrows * VW;
-    for (uint32_t base = 0; base < tot; base += 32 * 8) {
-      uint32_t v[8];
+    for (uint32_t base = 0; base < tot; base += 32 * 16) {
+      uint32_t v[16];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
+      for (int u = 0; u < 16; ++u) {
         const uint32_t idx = base + 32u * u + lane;
         v[u] = idx < tot ? __ldg(src + idx) : 0u;
       }
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
+      for (int u = 0; u < 16; ++u) {
         const uint32_t idx = base + 32u * u + lane;
         if (idx < tot) Vs[idx] = v[u];
       }
