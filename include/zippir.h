@@ -255,7 +255,8 @@ int zp_client_hint(zp_db* db, const zp_client* cl, const uint32_t* dCkr, uint32_
  *    answers for batches of 16, 32, 64 and 128 queries, and "answer_fp16" (the fp16 copy of D
  *    against its bytes, when the copy exists);
  *  - "rns_bt_16/32/64/128" and "batch_overlap": the tile width of the RNS products and
- *    whether a batch's products run beside its answers (when the RNS path was measured).
+ *    whether a batch's products run beside its answers (when the RNS path was measured);
+ *  - "pack_split": measured with the single-query SM split.
  * chosen (may be NULL): receives the first three values ("gemv_max_batch", "rns_min_batch",
  * "overlap_sms"); zp_get_option reads the others. Synchronous on `stream`; about a second
  * at 1 GiB. Errors: ZP_EINVAL, ZP_ENOMEM, ZP_ECUDA (the options are left as they were). */
@@ -312,7 +313,12 @@ int zp_stale_rows(const zp_db* db, uint32_t* count);
  *                    (default shared);
  *   "batch_overlap": 1 (default) zp_respond runs the compression products of a batch
  *                    answered on the tensor cores on an internal stream beside the answers
- *                    (they do not read the answers), 0 one after the other.
+ *                    (they do not read the answers), 0 one after the other;
+ *   "pack_split":    1 (default) for one query zp_respond also packs and reduces the
+ *                    products' part Y = (sum_j gamma^j V_j) mod m on the internal stream,
+ *                    beside the answer, and after the join computes only (b' + Y) mod m
+ *                    (one conditional subtraction: b' < m by the choice of ell); 0 packs
+ *                    and reduces everything after the join.
  * Every variant computes the same exact result. Errors: ZP_EINVAL (unknown name or value). */
 int zp_set_option(zp_ctx* ctx, const char* name, int64_t value);
 /* Reads an option set by zp_set_option (or its default). Errors: ZP_EINVAL. */

@@ -541,7 +541,7 @@ class Database:
 
     TUNED = ("gemv_max_batch", "rns_min_batch", "overlap_sms", "gemv_cfg_alone", "gemv_cfg_shared",
              "answer_bt_16", "answer_bt_32", "answer_bt_64", "answer_bt_128", "answer_fp16",
-             "rns_bt_16", "rns_bt_32", "rns_bt_64", "rns_bt_128", "batch_overlap")
+             "rns_bt_16", "rns_bt_32", "rns_bt_64", "rns_bt_128", "batch_overlap", "pack_split")
 
     def autotune(self, stream=None) -> dict:
         """Measures and sets the context's thresholds, tile widths, GEMV configurations and SM

@@ -149,7 +149,8 @@ struct ClientPtrs {
 // grid (ceil(d1p / PACK_WARPS), B), block PACK_WARPS warps, dynamic shared memory
 // PACK_WARPS x (PackBarrett + ell x VW words). Requires L == ZP_MAX_L.
 // V is [b][Rp][VW] words, the exact products V[row] = H[row,:] . cko[b] of every answer
-// row, packed with the answers (W_j = ans + V).
+// row, packed with the answers (W_j = ans + V). ans = NULL packs V alone: T then holds Y =
+// (sum_j gamma^j V_j) mod m, which k_pack_ans completes once the answers exist.
 __global__ void __launch_bounds__(PACK_WARPS * 32)
     k_pack_reduce(const uint32_t* __restrict__ ans, const uint32_t* __restrict__ V, uint32_t R,
                   uint32_t Rp, uint32_t ell, uint32_t d1p, uint32_t g1, uint32_t g2,
@@ -189,8 +190,8 @@ __global__ void __launch_bounds__(PACK_WARPS * 32)
     S.m[x] = x < L ? cl[b].m[x] : 0u;
     S.mu[x] = cl[b].mu[x];
   }
-  const uint32_t* ansb = ans + (uint64_t)b * R + row0;
-  for (uint32_t j = lane; j < nrows; j += 32) S.ans[j] = __ldg(ansb + j);
+  const uint32_t* ansb = ans ? ans + (uint64_t)b * R + row0 : nullptr;
+  for (uint32_t j = lane; j < nrows; j += 32) S.ans[j] = ans ? __ldg(ansb + j) : 0u;
   __syncwarp();
 
   // ---- Horner: X <- X gamma + W_j (j = ell-1 .. 0), gamma = g1 2^32 + g2 2^64,
@@ -321,6 +322,73 @@ __global__ void __launch_bounds__(PACK_WARPS * 32)
   for (int t = 0; t < 3; ++t) {
     const int x = (int)lane * 3 + t;
     if (x < L) out[x] = r[t];
+  }
+}
+
+// The second half of a split packing (one query answered by the GEMV while its products run
+// beside it): t = (b' + Y) mod m with b' = sum_{j<ell} gamma^j ans[r' ell + j] and Y = (sum_j
+// gamma^j V_j) mod m from k_pack_reduce (ans = NULL) on the products' stream. The context
+// picks ell with (bound - 1) sum_{j<ell} gamma^j < 2^(key_bits - 1) (the batching bound), and
+// every answer is below 2^32 <= bound - 1, so b' < 2^(key_bits - 1) <= m: b' + Y < 2m and one
+// conditional subtraction of m ends the reduction. One warp per (query, packed row); Horner
+// on lazy words as in k_pack_reduce, lane l holds words 4 l .. 4 l + 3.
+constexpr uint32_t PACKA_WARPS = 8;
+__global__ void __launch_bounds__(PACKA_WARPS * 32)
+    k_pack_ans(const uint32_t* __restrict__ ans, uint32_t R, uint32_t ell, uint32_t d1p,
+               uint32_t g1, uint32_t g2, const uint32_t* __restrict__ Y,
+               const ClientPtrs* __restrict__ cl, uint32_t* __restrict__ T) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t rp = blockIdx.x * PACKA_WARPS + (threadIdx.x >> 5), b = blockIdx.y;
+  if (rp >= d1p) return;
+  constexpr int L = ZP_MAX_L;
+  const uint32_t row0 = rp * ell;
+  const uint32_t nrows = R - row0 < ell ? R - row0 : ell;
+  const uint32_t* ansb = ans + (uint64_t)b * R + row0;
+  const uint32_t a0 = lane < nrows ? __ldg(ansb + lane) : 0u;            // ell <= 64
+  const uint32_t a1 = lane + 32 < nrows ? __ldg(ansb + lane + 32) : 0u;
+  const uint32_t* Yr = Y + ((uint64_t)b * d1p + rp) * L;
+  const uint32_t* m = cl[b].m;
+  uint64_t xv[4] = {0, 0, 0, 0};
+  for (int j = (int)nrows - 1; j >= 0; --j) {
+    const uint64_t pm1 = __shfl_up_sync(0xffffffffu, xv[3], 1);  // word 4 lane - 1
+    const uint64_t pm2 = __shfl_up_sync(0xffffffffu, xv[2], 1);  // word 4 lane - 2
+    const uint64_t xm1 = lane ? pm1 : 0, xm2 = lane ? pm2 : 0;
+    uint64_t v[4];
+    v[0] = (uint64_t)g1 * xm1 + (uint64_t)g2 * xm2;
+    v[1] = (uint64_t)g1 * xv[0] + (uint64_t)g2 * xm1;
+    v[2] = (uint64_t)g1 * xv[1] + (uint64_t)g2 * xv[0];
+    v[3] = (uint64_t)g1 * xv[2] + (uint64_t)g2 * xv[1];
+    const uint32_t aj = __shfl_sync(0xffffffffu, j < 32 ? a0 : a1, j & 31);
+    if (lane == 0) v[0] += aj;
+    uint64_t c = 0;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const uint64_t sum = v[t] + c;
+      xv[t] = sum & 0xFFFFFFFFull;
+      c = sum >> 32;
+    }
+    const uint64_t cin = __shfl_up_sync(0xffffffffu, c, 1);
+    if (lane) xv[0] += cin;
+  }
+  uint32_t mm[4];
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    const uint32_t x = 4 * lane + t;
+    if (x < (uint32_t)L) {
+      xv[t] += __ldg(Yr + x);
+      mm[t] = __ldg(m + x);
+    } else {
+      mm[t] = 0u;
+    }
+  }
+  uint32_t w[4];
+  warp_normalize<4>(xv, w);
+  if (warp_geq<4>(w, mm)) warp_sub<4>(w, mm);
+  uint32_t* out = T + ((uint64_t)b * d1p + rp) * L;
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    const uint32_t x = 4 * lane + t;
+    if (x < (uint32_t)L) out[x] = w[t];
   }
 }
 
@@ -528,13 +596,11 @@ int zp_launch_compress_products(zp_db* db, const uint32_t* dCKO, uint32_t B, cud
   return ZP_OK;
 }
 
-int zp_launch_compress_finish(zp_db* db, zp_client* const* clients, const uint32_t* dAns,
-                              uint32_t B, uint32_t* dT, cudaStream_t st) {
+// The per-query client constants as a device array (db->s_clients), uploaded on `st` only
+// when the list changed, and the pack kernel's shared-memory attribute.
+static int upload_clients(zp_db* db, zp_client* const* clients, uint32_t B, cudaStream_t st,
+                          ClientPtrs** out) {
   zp_ctx* ctx = db->ctx;
-  if (db->v_batch != B)
-    return zp_set_error(ZP_ESTATE, "compression finish for %u queries, products hold %u", B,
-                        db->v_batch);
-  uint32_t* V = static_cast<uint32_t*>(db->s_v.p);
   int rc = zp_scratch_reserve(&db->s_clients, (size_t)B * sizeof(ClientPtrs));
   if (rc) return rc;
   ClientPtrs* dcl = static_cast<ClientPtrs*>(db->s_clients.p);
@@ -568,6 +634,20 @@ int zp_launch_compress_finish(zp_db* db, zp_client* const* clients, const uint32
                                  (int)(PACK_WARPS * (sizeof(PackBarrett) + 64 * VW * 4))));
     attr = true;
   }
+  *out = dcl;
+  return ZP_OK;
+}
+
+int zp_launch_compress_finish(zp_db* db, zp_client* const* clients, const uint32_t* dAns,
+                              uint32_t B, uint32_t* dT, cudaStream_t st) {
+  zp_ctx* ctx = db->ctx;
+  if (db->v_batch != B)
+    return zp_set_error(ZP_ESTATE, "compression finish for %u queries, products hold %u", B,
+                        db->v_batch);
+  uint32_t* V = static_cast<uint32_t*>(db->s_v.p);
+  ClientPtrs* dcl = nullptr;
+  int rc = upload_clients(db, clients, B, st, &dcl);
+  if (rc) return rc;
   dim3 grid((db->d1p + PACK_WARPS - 1) / PACK_WARPS, B);
   zp_clear_pending_error();
   ctx->launches++;
@@ -600,6 +680,41 @@ int zp_launch_compress_finish(zp_db* db, zp_client* const* clients, const uint32
     k_pack_reduce<<<grid, PACK_WARPS * 32, smem, st>>>(dAns, V, db->R, db->Rp, ctx->ell, db->d1p,
                                                        ctx->gamma_w[1], ctx->gamma_w[2], dcl, dT);
   }
+  ZP_CUDA(cudaGetLastError());
+  return ZP_OK;
+}
+
+// Split packing for one query answered beside its products (zp_respond): Y = (sum_j gamma^j
+// V_j) mod m on the products' stream, before the answers exist ...
+int zp_launch_pack_products(zp_db* db, zp_client* const* clients, uint32_t B, cudaStream_t st) {
+  zp_ctx* ctx = db->ctx;
+  if (db->v_batch != B || db->v_rns)
+    return zp_set_error(ZP_ESTATE, "split packing: the products hold another batch");
+  ClientPtrs* dcl = nullptr;
+  int rc = upload_clients(db, clients, B, st, &dcl);
+  if (!rc) rc = zp_scratch_reserve(&db->s_ypack, (size_t)B * db->d1p * ZP_MAX_L * 4);
+  if (rc) return rc;
+  const size_t smem = (size_t)PACK_WARPS * (sizeof(PackBarrett) + (size_t)ctx->ell * VW * 4);
+  zp_clear_pending_error();
+  ctx->launches++;
+  k_pack_reduce<<<dim3((db->d1p + PACK_WARPS - 1) / PACK_WARPS, B), PACK_WARPS * 32, smem, st>>>(
+      nullptr, static_cast<const uint32_t*>(db->s_v.p), db->R, db->Rp, ctx->ell, db->d1p,
+      ctx->gamma_w[1], ctx->gamma_w[2], dcl, static_cast<uint32_t*>(db->s_ypack.p));
+  ZP_CUDA(cudaGetLastError());
+  return ZP_OK;
+}
+
+// ... and after the join t = (b' + Y) mod m with the answers (the client array uploaded by
+// zp_launch_pack_products, ordered before this launch by the join).
+int zp_launch_pack_answers(zp_db* db, const uint32_t* dAns, uint32_t B, uint32_t* dT,
+                           cudaStream_t st) {
+  zp_ctx* ctx = db->ctx;
+  zp_clear_pending_error();
+  ctx->launches++;
+  k_pack_ans<<<dim3((db->d1p + PACKA_WARPS - 1) / PACKA_WARPS, B), PACKA_WARPS * 32, 0, st>>>(
+      dAns, db->R, ctx->ell, db->d1p, ctx->gamma_w[1], ctx->gamma_w[2],
+      static_cast<const uint32_t*>(db->s_ypack.p), static_cast<const ClientPtrs*>(db->s_clients.p),
+      dT);
   ZP_CUDA(cudaGetLastError());
   return ZP_OK;
 }

@@ -354,6 +354,7 @@ extern "C" int zp_init(int device, const zp_params* P, zp_ctx** out) {
     c->gemv_max_batch = 4;  // one dp4a pass beats the tensor cores up to 4 queries (1 GiB)
     c->answer_fp16 = 1;
     c->batch_overlap = 1;
+    c->pack_split = 1;
     for (int i = 0; i < 4; ++i) c->ans_bt[i] = c->rns_bt[i] = 16u << (i < 2 ? i : 2);  // 16, 32, 64, 64
     c->gemv_cfg[0] = 1;  // whole GPU: 8 warps x 12 stages
     c->gemv_cfg[1] = 2;  // beside the products: 16 warps x 6 stages
@@ -467,6 +468,12 @@ extern "C" int zp_set_option(zp_ctx* c, const char* name, int64_t value) {
     c->gemv_cfg[k == "gemv_cfg_shared"] = (uint32_t)value;
     return ZP_OK;
   }
+  if (k == "pack_split") {
+    if (value < 0 || value > 1)
+      return zp_set_error(ZP_EINVAL, "zp_set_option: pack_split=%lld out of [0, 1]", (long long)value);
+    c->pack_split = (uint32_t)value;
+    return ZP_OK;
+  }
   if (k == "batch_overlap") {
     if (value < 0 || value > 1)
       return zp_set_error(ZP_EINVAL, "zp_set_option: batch_overlap=%lld out of [0, 1]", (long long)value);
@@ -492,6 +499,7 @@ extern "C" int zp_get_option(const zp_ctx* c, const char* name, int64_t* value) 
   else if (k == "gemv_max_batch") *value = c->gemv_max_batch;
   else if (k == "answer_fp16") *value = c->answer_fp16;
   else if (k == "batch_overlap") *value = c->batch_overlap;
+  else if (k == "pack_split") *value = c->pack_split;
   else if (k == "answer_bt_16") *value = c->ans_bt[0];
   else if (k == "answer_bt_32") *value = c->ans_bt[1];
   else if (k == "answer_bt_64") *value = c->ans_bt[2];
@@ -673,7 +681,7 @@ extern "C" int zp_db_destroy(zp_db* db) {
   zp_scratch* all[] = {&db->s_qplanes, &db->s_v,   &db->s_q,   &db->s_cko,  &db->s_ans,
                        &db->s_t,       &db->s_clients, &db->s_misc, &db->s_tcq, &db->s_hq,
                        &db->s_hcko, &db->s_ptab, &db->s_krows, &db->s_m2consts, &db->s_prows,
-                       &db->s_crt, &db->s_crtb};
+                       &db->s_crt, &db->s_crtb, &db->s_ypack};
   for (zp_scratch* s : all) scratch_free(s);
   delete db;
   return ZP_OK;
@@ -1238,10 +1246,18 @@ extern "C" int zp_respond(zp_db* db, zp_client* const* clients, const uint32_t* 
     ZP_CUDA(cudaStreamWaitEvent(db->side, db->ev_fork, 0));
     rc = zp_launch_compress_products(db, dCKO, B, db->side, c->overlap_sms);
     if (rc) return rc;
+    // "pack_split": the Horner over V, its fold and reduction need no answer either, so they
+    // follow the products on the internal stream; after the join only b' + Y remains
+    const bool split = c->pack_split && !db->v_rns;
+    if (split) {
+      rc = zp_launch_pack_products(db, clients, B, db->side);
+      if (rc) return rc;
+    }
     rc = zp_launch_gemv(db, dQ, 1u, dAns, st, (uint32_t)c->num_sms - c->overlap_sms);
     if (rc) return rc;
     ZP_CUDA(cudaEventRecord(db->ev_join, db->side));
     ZP_CUDA(cudaStreamWaitEvent(st, db->ev_join, 0));
+    if (split) return zp_launch_pack_answers(db, dAns, B, dT, st);
     return zp_launch_compress_finish(db, clients, dAns, B, dT, st);
   } catch (const std::bad_alloc&) {
     return zp_set_error(ZP_ENOMEM, "zp_respond: host allocation failed");
@@ -1293,7 +1309,7 @@ extern "C" int zp_autotune(zp_db* db, void* stream, int64_t* chosen) {
     const int saved_answer = c->answer_path, saved_compress = c->compress_path;
     const uint32_t saved_overlap = c->overlap_sms, saved_gemv = c->gemv_max_batch,
                    saved_rns = c->rns_min_batch, saved_fp16 = c->answer_fp16,
-                   saved_bo = c->batch_overlap;
+                   saved_bo = c->batch_overlap, saved_split = c->pack_split;
     uint32_t saved_abt[4], saved_rbt[4], saved_gcfg[2];
     for (int i = 0; i < 4; ++i) saved_abt[i] = c->ans_bt[i], saved_rbt[i] = c->rns_bt[i];
     for (int i = 0; i < 2; ++i) saved_gcfg[i] = c->gemv_cfg[i];
@@ -1316,6 +1332,7 @@ extern "C" int zp_autotune(zp_db* db, void* stream, int64_t* chosen) {
       c->rns_min_batch = saved_rns;
       c->answer_fp16 = saved_fp16;
       c->batch_overlap = saved_bo;
+      c->pack_split = saved_split;
       for (int i = 0; i < 4; ++i) c->ans_bt[i] = saved_abt[i], c->rns_bt[i] = saved_rbt[i];
       for (int i = 0; i < 2; ++i) c->gemv_cfg[i] = saved_gcfg[i];
       return rc;
@@ -1395,26 +1412,30 @@ extern "C" int zp_autotune(zp_db* db, void* stream, int64_t* chosen) {
       c->gemv_cfg[0] = best_cfg;
       c->overlap_sms = saved_overlap;
     }
-    // (4) the SM split of the single-query Response and the GEMV configuration beside the
-    // compression products
+    // (4) the SM split of the single-query Response, the GEMV configuration beside the
+    // compression products and whether the packing of V runs beside the answer too
     if (cl && c->num_sms >= 64) {
       float best = 1e30f;
-      uint32_t best_ov = 0, best_cfg = saved_gcfg[1];
-      for (uint32_t cfg = 1; cfg <= 2; ++cfg) {
-        c->gemv_cfg[1] = cfg;
-        for (uint32_t frac = 0; frac <= 8; ++frac) {  // 0 and 24% .. 52% of the SMs
-          if (frac == 0 && cfg == 2) continue;        // no split: the whole-GPU configuration
-          const uint32_t ov = frac == 0 ? 0u : (uint32_t)(c->num_sms * (20 + 4 * frac) / 100);
-          c->overlap_sms = ov;
-          const float r = time_ms([&] {
-            return zp_respond(db, &cl, dQ, dCKO, 1, dAns, dT, stream);
-          });
-          if (err) return fail(err);
-          if (r < best) best = r, best_ov = ov, best_cfg = cfg;
+      uint32_t best_ov = 0, best_cfg = saved_gcfg[1], best_split = saved_split;
+      for (uint32_t split = 0; split <= 1; ++split) {
+        c->pack_split = split;
+        for (uint32_t cfg = 1; cfg <= 2; ++cfg) {
+          c->gemv_cfg[1] = cfg;
+          for (uint32_t frac = 0; frac <= 8; ++frac) {  // 0 and 24% .. 52% of the SMs
+            if (frac == 0 && (cfg == 2 || split)) continue;  // no split: whole-GPU configuration
+            const uint32_t ov = frac == 0 ? 0u : (uint32_t)(c->num_sms * (20 + 4 * frac) / 100);
+            c->overlap_sms = ov;
+            const float r = time_ms([&] {
+              return zp_respond(db, &cl, dQ, dCKO, 1, dAns, dT, stream);
+            });
+            if (err) return fail(err);
+            if (r < best) best = r, best_ov = ov, best_cfg = cfg, best_split = split;
+          }
         }
       }
       c->overlap_sms = best_ov;
       c->gemv_cfg[1] = best_cfg;
+      c->pack_split = best_split;
     }
     // (5) tile widths of the tensor-core answers per batch class (16, 32, 64 queries), and
     // the operand (the fp16 copy of D against its bytes) when the copy exists

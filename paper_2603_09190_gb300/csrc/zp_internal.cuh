@@ -61,6 +61,7 @@ struct zp_ctx {
   uint32_t gemv_max_batch; // batches of at most this many queries (<= 4) answer by the GEMV
   uint32_t answer_fp16;    // tensor-core answers read a database's fp16 copy when it has one
   uint32_t batch_overlap;  // zp_respond runs a batch's compression products beside its answers
+  uint32_t pack_split;     // one query: the V part of the packing runs beside the answer
   // tile widths (queries per N tile: 16, 32 or 64) of the tensor-core answers and of the RNS
   // products for batches of <= 16, <= 32, <= 64 and > 64 queries (zp_autotune measures them)
   uint32_t ans_bt[4], rns_bt[4];
@@ -150,6 +151,7 @@ struct zp_db {
   zp_scratch s_ptab, s_krows, s_m2consts;  // per-client hint and combined response
   zp_scratch s_prows;                      // packed rows whose RNS planes are rebuilt
   zp_scratch s_crt, s_crtb;                // CRT of the residue-number-system compression
+  zp_scratch s_ypack;                      // split packing: (sum_j gamma^j V_j) mod m per packed row
 };
 
 // error reporting (thread-local message)
@@ -263,6 +265,11 @@ int zp_launch_hint_post(zp_db* db, const uint32_t* dHplus_compact, const uint32_
                         uint32_t nrows, uint32_t* dH, cudaStream_t st);
 int zp_launch_compress_products(zp_db* db, const uint32_t* dCKO, uint32_t B, cudaStream_t st,
                                 uint32_t max_ctas);
+// split packing of one query (zp_respond): Y = (sum_j gamma^j V_j) mod m beside the answer,
+// then t = (b' + Y) mod m after the join (k_compress.cu)
+int zp_launch_pack_products(zp_db* db, zp_client* const* clients, uint32_t B, cudaStream_t st);
+int zp_launch_pack_answers(zp_db* db, const uint32_t* dAns, uint32_t B, uint32_t* dT,
+                           cudaStream_t st);
 int zp_launch_compress_finish(zp_db* db, zp_client* const* clients, const uint32_t* dAns,
                               uint32_t B, uint32_t* dT, cudaStream_t st);
 int zp_launch_update_rows(zp_db* db, const uint32_t* rows, uint32_t k, const uint8_t* dNew,

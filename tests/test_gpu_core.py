@@ -564,6 +564,40 @@ def test_respond_overlap_identical(zp, overlap):
     c.close()
 
 
+@pytest.mark.parametrize("secret,n", [("uniform", 1024), ("binary", 48)])
+def test_respond_pack_split(zp, secret, n):
+    """One query with its products beside the answer: the V part of the packing reduced on
+    the internal stream and (b' + Y) mod m after the join ("pack_split" 1) gives the same bits
+    as packing everything after the join (0) and the oracle's t; ragged last packed row, two
+    calls in a row, for both secrets (binary: ell = 54, X up to 4077 bits before the fold)."""
+    R, C = 2000, 1000
+    P = Params(n=n, key_bits=2048, secret=secret)
+    c = zp.Context(0, n=n, secret=secret)
+    c.set_option("overlap_sms", 40)
+    D = synth.database(R, C, 31)
+    A = synth.seed_matrix(C, n, 32)
+    Hn = lwe.hint_neg(D, A)
+    dD, ld = to_dev_db(zp, D)
+    db = zp.Database(c, dD, R, C, ld)
+    db.gen_hint(u32_dev(A))
+    m = synth.random_odd_modulus(2048, 33)
+    cl = c.register_client(m)
+    outs = []
+    for split in (1, 0, 1):
+        c.set_option("pack_split", split)
+        q = synth.uniform_queries(1, C, 34 + len(outs))
+        cko = synth.uniform_below(m, n, 35)
+        ans, T = db.respond([cl], u32_dev(q), u32_dev(synth.ints_to_limbs(cko, 64)[None]))
+        want = lwe.matvec_mod_q(D, q[0])
+        assert np.array_equal(u32_host(ans)[0], want)
+        t = synth.limbs_to_ints(u32_host(T)[0])
+        assert t == zippir.compress_rows(want, Hn, cko, m, P)
+        outs.append(t)
+    assert c.device_status() == 0
+    db.close()
+    c.close()
+
+
 def test_split_compress_api(zp):
     """zp_compress_products + zp_compress_finish equal zp_compress; a finish whose batch
     does not match the products is refused."""
