@@ -1433,6 +1433,22 @@ extern "C" int zp_autotune(zp_db* db, void* stream, int64_t* chosen) {
           }
         }
       }
+      // refine the split around the best in steps of 2 SMs
+      if (best_ov) {
+        c->gemv_cfg[1] = best_cfg;
+        c->pack_split = best_split;
+        const uint32_t center = best_ov;
+        for (int d : {-4, -2, 2, 4}) {
+          const int ov = (int)center + d;
+          if (ov < 8 || ov > (int)c->num_sms - 8) continue;
+          c->overlap_sms = (uint32_t)ov;
+          const float r = time_ms([&] {
+            return zp_respond(db, &cl, dQ, dCKO, 1, dAns, dT, stream);
+          });
+          if (err) return fail(err);
+          if (r < best) best = r, best_ov = (uint32_t)ov;
+        }
+      }
       c->overlap_sms = best_ov;
       c->gemv_cfg[1] = best_cfg;
       c->pack_split = best_split;
