@@ -506,9 +506,9 @@ __global__ void k_crt_prep(const uint32_t* __restrict__ X, uint32_t B, uint32_t 
       if (v >= p) v -= p;
       y[q] = v;
       const uint64_t r = rns->mu[k];  // floor((2^64 - 1) / p) = floor(2^64 / p) (p odd)
-      const uint64_t lo = (uint64_t)v * r, hi = __umul64hi((uint64_t)v, r);
-      s_lo += lo;
-      s_hi += hi + (s_lo < lo ? 1u : 0u);
+      const uint64_t prod = (uint64_t)v * r;  // v < p: v floor(2^64 / p) < 2^64, no high word
+      s_lo += prod;
+      s_hi += s_lo < prod ? 1u : 0u;
     }
   }
 #pragma unroll
