@@ -1000,19 +1000,20 @@ __global__ void k_prep_q_cols(const uint32_t* __restrict__ A, uint32_t B, uint32
 
 // Compression operand: row (b*256 + beta) of Bc holds byte beta of cko[b][i] - 128 for
 // i < n (raw 0 for n <= i < Kp). colsum[b][beta] += sum_i byte beta of cko[b][i].
-// CTA: one query, 64 offsets; 256 threads.
+// CTA: one query, PREP_IB = 16 offsets (enough CTAs for one query); 256 threads.
 // With `srcs` (device array), query b's n values start at srcs[b * src_stride] instead of
 // cko + b n ZP_MAX_L (the CRT product reads each client's table in place), and the ntail
 // values after them come from `tail` (the same for every query).
+constexpr uint32_t PREP_IB = 16;
 __global__ void k_prep_cko(const uint32_t* __restrict__ cko, uint32_t n, uint32_t Kp,
                            __half* __restrict__ Bc, uint32_t* __restrict__ colsum,
                            const uint32_t* const* __restrict__ srcs = nullptr,
                            uint32_t src_stride = 0, const uint32_t* __restrict__ tail = nullptr,
                            uint32_t ntail = 0) {
-  __shared__ uint32_t tile[64][ZP_MAX_L + 1];
-  const uint32_t b = blockIdx.y, i0 = blockIdx.x * 64;
+  __shared__ uint32_t tile[PREP_IB][ZP_MAX_L + 1];
+  const uint32_t b = blockIdx.y, i0 = blockIdx.x * PREP_IB;
   const uint32_t* src = srcs ? srcs[(uint64_t)b * src_stride] : cko + (uint64_t)b * n * ZP_MAX_L;
-  for (uint32_t idx = threadIdx.x; idx < 64u * ZP_MAX_L; idx += blockDim.x) {
+  for (uint32_t idx = threadIdx.x; idx < PREP_IB * ZP_MAX_L; idx += blockDim.x) {
     const uint32_t ii = idx / ZP_MAX_L, w = idx % ZP_MAX_L;
     const uint32_t i = i0 + ii;
     tile[ii][w] = i < n ? src[(uint64_t)i * ZP_MAX_L + w]
@@ -1024,7 +1025,7 @@ __global__ void k_prep_cko(const uint32_t* __restrict__ cko, uint32_t n, uint32_
   uint32_t s = 0;
   __half* dst = Bc + ((uint64_t)b * 256 + beta) * Kp + i0;
 #pragma unroll
-  for (int g = 0; g < 8; ++g) {
+  for (int g = 0; g < (int)PREP_IB / 8; ++g) {
     uint32_t h[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -1189,7 +1190,7 @@ int zp_launch_vmul_tc(zp_db* db, const uint32_t* dCKO, uint32_t B, uint32_t* V4,
   ZP_CUDA(cudaMemsetAsync(colsum, 0, cs_bytes, st));
   zp_clear_pending_error();
   ctx->launches++;
-  k_prep_cko<<<dim3(Kp / 64, B), 256, 0, st>>>(dCKO, n, Kp, Bc, colsum);
+  k_prep_cko<<<dim3(Kp / PREP_IB, B), 256, 0, st>>>(dCKO, n, Kp, Bc, colsum);
   ZP_CUDA(cudaGetLastError());
   CUtensorMap tmB;
   rc = zp_encode_tmap_2d(&tmB, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, Bc, Kp, (uint64_t)B * 256,
@@ -1391,7 +1392,7 @@ int zp_launch_crt_products(zp_db* db, const uint32_t* const* mkm_ptrs, uint32_t 
   ZP_CUDA(cudaMemsetAsync(colsum, 0, cs_bytes, st));
   zp_clear_pending_error();
   ctx->launches++;
-  k_prep_cko<<<dim3(Kp / 64, B), 256, 0, st>>>(nullptr, ZP_RNS_K + 1, Kp, Bm, colsum, mkm_ptrs,
+  k_prep_cko<<<dim3(Kp / PREP_IB, B), 256, 0, st>>>(nullptr, ZP_RNS_K + 1, Kp, Bm, colsum, mkm_ptrs,
                                                 ptr_stride, ctx->d_gam, ctx->ell);
   ZP_CUDA(cudaGetLastError());
   constexpr uint32_t NH = 144;  // columns per half (two halves cover byte positions 0..287)
