@@ -47,7 +47,7 @@ enum zp_status {
   ZP_ECUDA = -3,       /* a CUDA runtime/driver call failed */
   ZP_ETIMEOUT = -4,    /* a bounded device-side wait gave up (kernel returned early) */
   ZP_ESTATE = -5,      /* call out of order, e.g. zp_compress before zp_gen_hint */
-  ZP_EUNSUPPORTED = -6 /* parameters this build does not implement */
+  ZP_EUNSUPPORTED = -6 /* parameters the compiled library does not implement */
 };
 
 enum zp_secret {
@@ -64,7 +64,7 @@ enum zp_scale {
 
 typedef struct zp_params {
   uint32_t n;        /* LWE dimension (1 <= n <= 4096) */
-  uint32_t key_bits; /* bits of every client's Paillier modulus m; 2048 in this build */
+  uint32_t key_bits; /* bits of every client's Paillier modulus m; 2048 (compile-time limit) */
   uint32_t secret;   /* enum zp_secret */
   uint32_t p_bits;   /* log2 of the plaintext modulus p; must be 8 (one byte per entry) */
   uint32_t scale;    /* enum zp_scale. Slots per packed row: ell = the largest count with

@@ -283,7 +283,7 @@ extern "C" int zp_init(int device, const zp_params* P, zp_ctx** out) {
     if (P->scale != ZP_SCALE_PROVEN && P->scale != ZP_SCALE_OVERLAP)
       return zp_set_error(ZP_EINVAL, "zp_init: bad scale %u", P->scale);
     if (P->key_bits != 32 * ZP_MAX_L)
-      return zp_set_error(ZP_EUNSUPPORTED, "zp_init: key_bits=%u (this build: %d)", P->key_bits,
+      return zp_set_error(ZP_EUNSUPPORTED, "zp_init: key_bits=%u (compiled for %d)", P->key_bits,
                           32 * ZP_MAX_L);
     ZP_ON_DEVICE(device);
     zp_ctx* c = new zp_ctx();

@@ -13,7 +13,7 @@
 #include "../../include/zippir.h"
 
 // ------------------------------------------------------------------ host-side state
-#define ZP_MAX_L 64        // limbs of m (key_bits / 32); this build: 2048-bit keys
+#define ZP_MAX_L 64        // limbs of m (key_bits / 32); the library is compiled for 2048-bit keys
 #define ZP_VW (ZP_MAX_L + 3)  // words of one exact row product V = H[row,:] . cko (< 2^(32L+42))
 #define ZP_XW 128          // words of the packed sum before reduction (< 2^4096)
 
