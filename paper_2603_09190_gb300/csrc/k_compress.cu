@@ -330,67 +330,57 @@ __global__ void __launch_bounds__(PACK_WARPS * 32)
 // gamma^j V_j) mod m from k_pack_reduce (ans = NULL) on the products' stream. The context
 // picks ell with (bound - 1) sum_{j<ell} gamma^j < 2^(key_bits - 1) (the batching bound), and
 // every answer is below 2^32 <= bound - 1, so b' < 2^(key_bits - 1) <= m: b' + Y < 2m and one
-// conditional subtraction of m ends the reduction. One warp per (query, packed row); Horner
-// on lazy words as in k_pack_reduce, lane l holds words 4 l .. 4 l + 3.
+// conditional subtraction of m ends the reduction (a carry out of word L - 1 counts as >= m).
+// b' is summed column by column from the context's table of gamma^j (ell rows of L words):
+// lane l keeps the 96-bit sums of words 2l and 2l + 1, with the table rows fetched nine at a
+// time ahead of their multiply-adds; the columns are then gathered into 32-bit words with one
+// carry resolution (every term is nonnegative and b' < 2^(32 L - 1), so the parts of lane 31
+// above word L - 1 are zero). One warp per (query, packed row).
 constexpr uint32_t PACKA_WARPS = 8;
 __global__ void __launch_bounds__(PACKA_WARPS * 32)
     k_pack_ans(const uint32_t* __restrict__ ans, uint32_t R, uint32_t ell, uint32_t d1p,
-               uint32_t g1, uint32_t g2, const uint32_t* __restrict__ Y,
+               const uint32_t* __restrict__ gam, const uint32_t* __restrict__ Y,
                const ClientPtrs* __restrict__ cl, uint32_t* __restrict__ T) {
   const uint32_t lane = threadIdx.x & 31;
   const uint32_t rp = blockIdx.x * PACKA_WARPS + (threadIdx.x >> 5), b = blockIdx.y;
   if (rp >= d1p) return;
   constexpr int L = ZP_MAX_L;
+  static_assert(L == 64, "two words per lane");
   const uint32_t row0 = rp * ell;
   const uint32_t nrows = R - row0 < ell ? R - row0 : ell;
   const uint32_t* ansb = ans + (uint64_t)b * R + row0;
-  const uint32_t a0 = lane < nrows ? __ldg(ansb + lane) : 0u;            // ell <= 64
-  const uint32_t a1 = lane + 32 < nrows ? __ldg(ansb + lane + 32) : 0u;
-  const uint32_t* Yr = Y + ((uint64_t)b * d1p + rp) * L;
-  const uint32_t* m = cl[b].m;
-  uint64_t xv[4] = {0, 0, 0, 0};
-  for (int j = (int)nrows - 1; j >= 0; --j) {
-    const uint64_t pm1 = __shfl_up_sync(0xffffffffu, xv[3], 1);  // word 4 lane - 1
-    const uint64_t pm2 = __shfl_up_sync(0xffffffffu, xv[2], 1);  // word 4 lane - 2
-    const uint64_t xm1 = lane ? pm1 : 0, xm2 = lane ? pm2 : 0;
-    uint64_t v[4];
-    v[0] = (uint64_t)g1 * xm1 + (uint64_t)g2 * xm2;
-    v[1] = (uint64_t)g1 * xv[0] + (uint64_t)g2 * xm1;
-    v[2] = (uint64_t)g1 * xv[1] + (uint64_t)g2 * xv[0];
-    v[3] = (uint64_t)g1 * xv[2] + (uint64_t)g2 * xv[1];
-    const uint32_t aj = __shfl_sync(0xffffffffu, j < 32 ? a0 : a1, j & 31);
-    if (lane == 0) v[0] += aj;
-    uint64_t c = 0;
+  const uint32_t an0 = lane < nrows ? __ldg(ansb + lane) : 0u;  // ell <= 64
+  const uint32_t an1 = lane + 32 < nrows ? __ldg(ansb + lane + 32) : 0u;
+  const uint2 y = __ldg(reinterpret_cast<const uint2*>(Y + ((uint64_t)b * d1p + rp) * L) + lane);
+  const uint2 mv = __ldg(reinterpret_cast<const uint2*>(cl[b].m) + lane);
+  uint32_t c0 = 0, c1 = 0, c2 = 0, d0 = 0, d1 = 0, d2 = 0;
+  const uint2* g2 = reinterpret_cast<const uint2*>(gam) + lane;
+  constexpr uint32_t U = 9;
+  for (uint32_t j0 = 0; j0 < nrows; j0 += U) {
+    uint2 t[U];
 #pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      const uint64_t sum = v[t] + c;
-      xv[t] = sum & 0xFFFFFFFFull;
-      c = sum >> 32;
-    }
-    const uint64_t cin = __shfl_up_sync(0xffffffffu, c, 1);
-    if (lane) xv[0] += cin;
-  }
-  uint32_t mm[4];
+    for (uint32_t u = 0; u < U; ++u)
+      t[u] = j0 + u < nrows ? __ldg(g2 + (size_t)(j0 + u) * (L / 2)) : make_uint2(0u, 0u);
 #pragma unroll
-  for (int t = 0; t < 4; ++t) {
-    const uint32_t x = 4 * lane + t;
-    if (x < (uint32_t)L) {
-      xv[t] += __ldg(Yr + x);
-      mm[t] = __ldg(m + x);
-    } else {
-      mm[t] = 0u;
+    for (uint32_t u = 0; u < U; ++u) {
+      const uint32_t j = j0 + u;
+      const uint32_t aj = __shfl_sync(0xffffffffu, j < 32 ? an0 : an1, j & 31);
+      mac96(c0, c1, c2, aj, t[u].x);
+      mac96(d0, d1, d2, aj, t[u].y);
     }
   }
-  uint32_t w[4];
-  warp_normalize<4>(xv, w);
-  if (warp_geq<4>(w, mm)) warp_sub<4>(w, mm);
-  uint32_t* out = T + ((uint64_t)b * d1p + rp) * L;
-#pragma unroll
-  for (int t = 0; t < 4; ++t) {
-    const uint32_t x = 4 * lane + t;
-    if (x < (uint32_t)L) out[x] = w[t];
-  }
+  const uint32_t pm = __shfl_up_sync(0xffffffffu, d1, 1), ph = __shfl_up_sync(0xffffffffu, c2, 1),
+                 ph1 = __shfl_up_sync(0xffffffffu, d2, 1);
+  uint64_t v[2];
+  v[0] = (uint64_t)c0 + (lane ? (uint64_t)pm + ph : 0u) + y.x;
+  v[1] = (uint64_t)d0 + c1 + (lane ? (uint64_t)ph1 : 0u) + y.y;
+  uint32_t w[2];
+  const uint32_t top = warp_normalize_top<2>(v, w);
+  const uint32_t mm[2] = {mv.x, mv.y};
+  if (top || warp_geq<2>(w, mm)) warp_sub<2>(w, mm);
+  reinterpret_cast<uint2*>(T + ((uint64_t)b * d1p + rp) * L)[lane] = make_uint2(w[0], w[1]);
 }
+
 
 // Residue-number-system path, last step (Sec. 5.2: one reduction mod m at the end): T = V mod
 // m for the CRT sums V < 2^2087 (ZP_VW words, [b][Rq][ZP_VW]) of the packed rows. The
@@ -712,9 +702,8 @@ int zp_launch_pack_answers(zp_db* db, const uint32_t* dAns, uint32_t B, uint32_t
   zp_clear_pending_error();
   ctx->launches++;
   k_pack_ans<<<dim3((db->d1p + PACKA_WARPS - 1) / PACKA_WARPS, B), PACKA_WARPS * 32, 0, st>>>(
-      dAns, db->R, ctx->ell, db->d1p, ctx->gamma_w[1], ctx->gamma_w[2],
-      static_cast<const uint32_t*>(db->s_ypack.p), static_cast<const ClientPtrs*>(db->s_clients.p),
-      dT);
+      dAns, db->R, ctx->ell, db->d1p, ctx->d_gam, static_cast<const uint32_t*>(db->s_ypack.p),
+      static_cast<const ClientPtrs*>(db->s_clients.p), dT);
   ZP_CUDA(cudaGetLastError());
   return ZP_OK;
 }
