@@ -90,10 +90,12 @@ struct Cfg {
   static constexpr int BST = A16 ? KPS * 4 * BT * BK * 2
                                  : ((ANS_BYTES && ZP_ANS_FIT) ? 4 * BT * BK * 2 : B_MAX_BYTES);  // B stage stride
   static constexpr int AST = KPS * A16_BYTES;                              // A stage stride
-  static constexpr int SB = A16 ? (MODE == MODE_RNS ? (BT == 32 ? 3 : 4)  // with the RNS epilogue's staging: 227 KiB
+  // stages (with the RNS epilogue's staging the fp16 RNS ring fills 227 KiB)
+  static constexpr int SB = A16 ? (MODE == MODE_RNS ? (BT == 32 ? 3 : 4)
                                                    : (BT == 16 ? 4 : (BT == 32 ? 3 : 4)))
-                                : ((MODE == MODE_CMP || MODE == MODE_RNS || MODE == MODE_CRT) ? 3
-                                                                                   : (ANS_BYTES ? ZP_ANS_SB : 4));
+                                : ((MODE == MODE_CMP || MODE == MODE_RNS || MODE == MODE_CRT)
+                                       ? 3
+                                       : (ANS_BYTES ? ZP_ANS_SB : 4));
   static constexpr int SA = SB;  // the A and B stages of a K block are filled and freed together
   // epilogue warps: with an fp16 A operand the converter warps 8-11 have no conversion to do,
   // so the RNS and residue products (whose epilogues bound them) drain TMEM with eight warps,
@@ -753,8 +755,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             if (gq == 4 && wl >= 4) break;
             const int wi = 8 * gq + wl;  // word of the half
             const uint32_t w = w0 + wi;
-            const int64_t c = (int64_t)(((uint64_t)__shfl_sync(0xffffffffu, (uint32_t)(cw[wi / 32] >> 32), wi % 32) << 32) |
-                                        __shfl_sync(0xffffffffu, (uint32_t)cw[wi / 32], wi % 32));
+            const uint32_t chi = __shfl_sync(0xffffffffu, (uint32_t)(cw[wi / 32] >> 32), wi % 32);
+            const uint32_t clo = __shfl_sync(0xffffffffu, (uint32_t)cw[wi / 32], wi % 32);
+            const int64_t c = (int64_t)(((uint64_t)chi << 32) | clo);
             int64_t sv = carry + c + (w == 0 ? rw_lo : (w < 64 ? rw_mid : (w == 64 ? rw_hi : 0)));
 #pragma unroll
             for (int j = 0; j < 4; ++j)
@@ -1368,13 +1371,13 @@ int zp_launch_rns_products(zp_db* db, const uint32_t* dCKO, uint32_t B, uint32_t
 // the end): V[b][r'] = sum_k y[b][r'][k] (M/p_k mod m_b) + alpha (m_b - (M mod m_b))
 // + sum_{j<ell} gamma^j ans[b][r' ell + j], i.e. the Chinese-remainder sum of the residues of
 // H'[r', :] . cko[b] plus the packed answer b' (congruent to b' + H'.cko mod m_b, below
-// 2^2084), taken exactly on the tensor cores (MODE_CRT): for query b, A = the byte planes of
+// 2^2087), taken exactly on the tensor cores (MODE_CRT): for query b, A = the byte planes of
 // its y, alpha and answers (k_crt_prep; packed row r' is row b Rq + r', its plane a at bytes
-// a Kp .., K = ZP_RNS_K + 1 + ell per plane), B = the 256 bytes of each of its client's constants M/p_k mod m_b (read
-// in place through mkm_ptrs[b * ptr_stride]) followed by those of gamma^j (the context's
-// table). The four planes run along K against the constants' bytes shifted by a, so one
-// accumulator row is a whole packed row and its 259 byte columns are V's base-256 digits
-// before carries; the columns are taken in two halves of 144.
+// a Kp .., K = ZP_RNS_K + 1 + ell per plane), B = the 256 bytes of each of its client's
+// constants M/p_k mod m_b (read in place through mkm_ptrs[b * ptr_stride]) followed by those
+// of gamma^j (the context's table). The four planes run along K against the constants' bytes
+// shifted by a, so one accumulator row is a whole packed row and its 259 byte columns are V's
+// base-256 digits before carries; the columns are taken in two halves of 144.
 int zp_launch_crt_products(zp_db* db, const uint32_t* const* mkm_ptrs, uint32_t ptr_stride,
                            uint32_t B, const uint8_t* Yp, uint32_t ypitch, const uint32_t* yrs,
                            uint32_t* Vc, cudaStream_t st) {
